@@ -1,0 +1,542 @@
+/*
+ * oracle.c -- FP64 CPU oracle of the SDFDDGI per-frame probe update.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing on the product path loads this file: the
+ * tests, the smoke check and the bench's CPU-baseline leg do. It is the plain
+ * definition of what the CUDA library must compute, written from the paper
+ * (Hu et al., "Signed Distance Fields Dynamic Diffuse Global Illumination",
+ * arXiv 2007.14394) in double precision, probe by probe, ray by ray, texel by
+ * texel, in the order of Sec. 3.3: trace the probe's rays, shade the hits,
+ * then let every octahedral texel gather its cosine-weighted irradiance from
+ * all of the probe's samples (Eq. 3) and mix it temporally with the last frame.
+ *
+ * Where the paper is silent the readings are the numbered choices O1..O13 of
+ * the design notes; each function names the one it follows. Parity pins:
+ * every function here is checked in tests/test_oracle_pins.py against closed
+ * forms, invariants or brute force (no pin retypes a formula from this file).
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define IRR_N 6   /* interior texels per side of an irradiance map (8x8 with border) */
+#define DEP_N 14  /* interior texels per side of a depth-moment map (16x16 with border) */
+#define IRR_T (IRR_N + 2)
+#define DEP_T (DEP_N + 2)
+#define HUGE_MARGIN 1e300
+
+static const double kPi = 3.14159265358979323846;
+
+/* ---------------------------------------------------------------- helpers */
+
+static double half_to_double(uint16_t b) {
+    int s = (b >> 15) & 1, e = (b >> 10) & 31, m = b & 1023;
+    double v;
+    if (e == 0)
+        v = ldexp((double)m, -24);
+    else if (e == 31)
+        v = m ? NAN : INFINITY;
+    else
+        v = ldexp((double)(1024 + m), e - 25);
+    return s ? -v : v;
+}
+
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static double sign_nz(double x) { return x >= 0.0 ? 1.0 : -1.0; }
+
+static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+/* ------------------------------------------- ray directions (Sec. 3.3, O2) */
+
+/* Spherical Fibonacci point i of n: z = 1 - (2i+1)/n, azimuth = 2 pi frac(i * phi^-1)
+ * with the golden fraction taken in 32-bit fixed point, (i * 2654435769) mod 2^32 / 2^32,
+ * so that both implementations start from the same exact phase. */
+void oracle_sf_dir(int32_t i, int32_t n, double out[3]) {
+    double z = 1.0 - (2.0 * i + 1.0) / n;
+    uint32_t phase = (uint32_t)((uint64_t)(uint32_t)i * 2654435769ull);
+    double phi = 2.0 * kPi * ((double)phase / 4294967296.0);
+    double r = sqrt(fmax(0.0, 1.0 - z * z));
+    out[0] = r * cos(phi);
+    out[1] = r * sin(phi);
+    out[2] = z;
+}
+
+/* ------------------------------------------------ octahedral map (O7, Sec. 3.3) */
+
+void oracle_oct_encode(const double v[3], double uv[2]) {
+    double l1 = fabs(v[0]) + fabs(v[1]) + fabs(v[2]);
+    double qx = v[0] / l1, qy = v[1] / l1;
+    if (v[2] < 0.0) {
+        double ox = (1.0 - fabs(qy)) * sign_nz(qx);
+        double oy = (1.0 - fabs(qx)) * sign_nz(qy);
+        qx = ox;
+        qy = oy;
+    }
+    uv[0] = 0.5 * (qx + 1.0);
+    uv[1] = 0.5 * (qy + 1.0);
+}
+
+void oracle_oct_decode(const double uv[2], double v[3]) {
+    double qx = 2.0 * uv[0] - 1.0, qy = 2.0 * uv[1] - 1.0;
+    double z = 1.0 - fabs(qx) - fabs(qy);
+    double x = qx, y = qy;
+    if (z < 0.0) {
+        x = (1.0 - fabs(qy)) * sign_nz(qx);
+        y = (1.0 - fabs(qx)) * sign_nz(qy);
+    }
+    double len = sqrt(x * x + y * y + z * z);
+    v[0] = x / len;
+    v[1] = y / len;
+    v[2] = z / len;
+}
+
+/* ------------------------------------------------ volume sampling (O1, O4) */
+
+static double voxel_sdf(const or_volume* vol, int x, int y, int z) {
+    size_t i = ((size_t)z * vol->ny + y) * vol->nx + x;
+    if (vol->sdf_dtype == 1) return half_to_double(((const uint16_t*)vol->sdf)[i]);
+    return (double)((const float*)vol->sdf)[i];
+}
+
+/* Trilinear cell and weights of world point p: voxel centres sit at integer
+ * coordinates g = (p - origin)/h - 1/2; the cell is clamped to the volume
+ * (clamp-to-edge) and the fractions to [0, 1]. */
+static void trilinear_cell(const or_volume* vol, const double p[3], int i0[3], double f[3]) {
+    const int n[3] = {vol->nx, vol->ny, vol->nz};
+    for (int a = 0; a < 3; ++a) {
+        double g = (p[a] - vol->origin[a]) / vol->h - 0.5;
+        int i = (int)floor(g);
+        if (i < 0) i = 0;
+        if (i > n[a] - 2) i = n[a] - 2;
+        i0[a] = i;
+        f[a] = clampd(g - i, 0.0, 1.0);
+    }
+}
+
+double oracle_sample_sdf(const or_volume* vol, const double p[3]) {
+    int i0[3];
+    double f[3];
+    trilinear_cell(vol, p, i0, f);
+    double acc = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+        double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+        acc += w * voxel_sdf(vol, i0[0] + dx, i0[1] + dy, i0[2] + dz);
+    }
+    return acc;
+}
+
+/* Albedo and emission at p: the material volume sampled with the same trilinear rule. */
+static void sample_material(const or_volume* vol, const double p[3], double albedo[3], double emission[3]) {
+    for (int k = 0; k < 3; ++k) albedo[k] = emission[k] = 0.0;
+    if (!vol->material) return;
+    int i0[3];
+    double f[3];
+    trilinear_cell(vol, p, i0, f);
+    for (int c = 0; c < 8; ++c) {
+        int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+        double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+        size_t v = ((size_t)(i0[2] + dz) * vol->ny + (i0[1] + dy)) * vol->nx + (i0[0] + dx);
+        const uint16_t* m = vol->material + 8 * v;
+        for (int k = 0; k < 3; ++k) {
+            albedo[k] += w * half_to_double(m[k]);
+            emission[k] += w * half_to_double(m[4 + k]);
+        }
+    }
+}
+
+/* ------------------------------------------------ sphere trace (Sec. 3.3, O6) */
+
+static double g_delta_vox = 2e-4; /* rounding band of distance decisions, voxels */
+static double g_delta_cos = 1e-4; /* rounding band of light-gating decisions */
+
+void oracle_set_delta(double delta_vox, double delta_cos) {
+    g_delta_vox = delta_vox;
+    g_delta_cos = delta_cos;
+}
+
+/* Sphere tracing (Hart 1996) as the probe update uses it: step by the sampled
+ * distance until it falls below eps (HIT), the point leaves the volume box
+ * (LEFT_VOLUME) or t passes the limit (PAST_LIMIT), or the step budget runs out
+ * (EXHAUSTED). `margin` is the closest any of these tests came to the other
+ * outcome. With fe >= 0 the path follows the given event (fe) and step count (fs)
+ * instead of its own tests; every test so overridden increments *forced, and
+ * *hard as well when its margin was at least delta. */
+static int32_t trace_path(const or_volume* vol, const double o[3], const double d[3], double eps_vox,
+                          double tlimit, int32_t max_steps, int32_t fe, int32_t fs, double* t_out,
+                          int32_t* steps_out, double* margin_vox, int32_t* forced, int32_t* hard) {
+    const double h = vol->h, eps = eps_vox * h, band = g_delta_vox * h;
+    const double lo[3] = {vol->origin[0], vol->origin[1], vol->origin[2]};
+    const double hi[3] = {vol->origin[0] + vol->nx * h, vol->origin[1] + vol->ny * h,
+                          vol->origin[2] + vol->nz * h};
+    double t = 0.0, margin = HUGE_MARGIN;
+#define DECIDE(natural, wanted_if_forced, m)                      \
+    ((fe < 0) ? (natural) : ((wanted_if_forced) != (natural)      \
+                                 ? (++*forced, *hard += (m) >= band, (wanted_if_forced)) \
+                                 : (natural)))
+    for (int32_t s = 0; s < max_steps; ++s) {
+        double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+        int outside = 0;
+        double m_out = HUGE_MARGIN;
+        for (int a = 0; a < 3; ++a) {
+            if (p[a] < lo[a] || p[a] > hi[a]) outside = 1;
+            m_out = fmin(m_out, fmin(fabs(p[a] - lo[a]), fabs(p[a] - hi[a])));
+        }
+        margin = fmin(margin, m_out);
+        if (DECIDE(outside, fe == OR_LEFT_VOLUME && s == fs, m_out)) {
+            *t_out = tlimit;
+            *steps_out = s;
+            *margin_vox = margin / h;
+            return OR_LEFT_VOLUME;
+        }
+        double sd = oracle_sample_sdf(vol, p);
+        double m_hit = fabs(sd - eps);
+        margin = fmin(margin, m_hit);
+        if (DECIDE(sd < eps, fe == OR_HIT && s == fs - 1, m_hit)) {
+            *t_out = t;
+            *steps_out = s + 1;
+            *margin_vox = margin / h;
+            return OR_HIT;
+        }
+        t += sd;
+        double m_lim = fabs(t - tlimit);
+        margin = fmin(margin, m_lim);
+        if (DECIDE(t > tlimit, fe == OR_PAST_LIMIT && s == fs - 1, m_lim)) {
+            *t_out = tlimit;
+            *steps_out = s + 1;
+            *margin_vox = margin / h;
+            return OR_PAST_LIMIT;
+        }
+    }
+#undef DECIDE
+    if (fe >= 0 && fe != OR_EXHAUSTED) { /* the followed path ends on an event this path never reached */
+        ++*forced;
+        ++*hard;
+    }
+    *t_out = t;
+    *steps_out = max_steps;
+    *margin_vox = margin / h;
+    return OR_EXHAUSTED;
+}
+
+int32_t oracle_trace(const or_volume* vol, const double o[3], const double d[3],
+                     double eps_vox, double tlimit, int32_t max_steps,
+                     double* t_out, int32_t* steps_out, double* margin_vox) {
+    int32_t forced = 0, hard = 0;
+    return trace_path(vol, o, d, eps_vox, tlimit, max_steps, -1, 0, t_out, steps_out, margin_vox, &forced,
+                      &hard);
+}
+
+static int is_miss(int32_t event) { return event == OR_LEFT_VOLUME || event == OR_PAST_LIMIT; }
+
+/* ------------------------------------------------ border fixup (O8) */
+
+/* Copies into the one-texel border of an (n+2)^2 octahedral map the interior texel
+ * that is its neighbour across the octahedron's fold: each edge is its own mirror
+ * image about its midpoint, and each corner takes the diagonally opposite interior
+ * corner. Map index (row y, column x), channels innermost. */
+void oracle_border(double* map, int32_t n, int32_t C) {
+    const int T = n + 2;
+#define AT(y, x) (map + ((size_t)(y) * T + (x)) * C)
+    for (int x = 1; x <= n; ++x) {
+        memcpy(AT(0, x), AT(1, n + 1 - x), sizeof(double) * C);
+        memcpy(AT(n + 1, x), AT(n, n + 1 - x), sizeof(double) * C);
+    }
+    for (int y = 1; y <= n; ++y) {
+        memcpy(AT(y, 0), AT(n + 1 - y, 1), sizeof(double) * C);
+        memcpy(AT(y, n + 1), AT(n + 1 - y, n), sizeof(double) * C);
+    }
+    memcpy(AT(0, 0), AT(n, n), sizeof(double) * C);
+    memcpy(AT(0, n + 1), AT(n, 1), sizeof(double) * C);
+    memcpy(AT(n + 1, 0), AT(1, n), sizeof(double) * C);
+    memcpy(AT(n + 1, n + 1), AT(1, 1), sizeof(double) * C);
+#undef AT
+}
+
+/* ------------------------------------------------ interpolation rule (O13) */
+
+/* Bilinear fetch of the RGB of an irradiance map at direction v: texel centre of
+ * interior texel a is uv = (a + 1/2)/n and sits at index a + 1 of the bordered map. */
+static void fetch_oct_bilinear(const double* map, const double v[3], double out[3]) {
+    double uv[2];
+    oracle_oct_encode(v, uv);
+    double cx = 1.0 + uv[0] * IRR_N - 0.5, cy = 1.0 + uv[1] * IRR_N - 0.5;
+    int x0 = (int)floor(cx), y0 = (int)floor(cy);
+    if (x0 > IRR_N) x0 = IRR_N;
+    if (y0 > IRR_N) y0 = IRR_N;
+    double fx = cx - x0, fy = cy - y0;
+    for (int k = 0; k < 3; ++k) out[k] = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        int dx = c & 1, dy = c >> 1;
+        double w = (dx ? fx : 1.0 - fx) * (dy ? fy : 1.0 - fy);
+        const double* texel = map + ((size_t)(y0 + dy) * IRR_T + (x0 + dx)) * 4;
+        for (int k = 0; k < 3; ++k) out[k] += w * texel[k];
+    }
+}
+
+/* Normalised irradiance at x for normal nrm: trilinear over the 8 probes of the grid
+ * cell containing x (clamped to the grid), each probe weighted by its trilinear weight
+ * times its history-valid flag, each contributing its map's bilinear value at nrm;
+ * weights are renormalised, and an all-zero weight gives 0. */
+void oracle_sample_irradiance(const or_grid* g, const double* irr, const uint8_t* valid,
+                              const double x[3], const double nrm[3], double out[3]) {
+    int base[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        double c = clampd((x[a] - g->origin[a]) / g->spacing[a], 0.0, (double)(g->dims[a] - 1));
+        int b = (int)floor(c);
+        if (b > g->dims[a] - 2) b = g->dims[a] - 2;
+        if (b < 0) b = 0;
+        base[a] = b;
+        f[a] = g->dims[a] > 1 ? c - b : 0.0;
+    }
+    double sw = 0.0, acc[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < 8; ++c) {
+        int d[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+        double w = 1.0;
+        int idx[3];
+        for (int a = 0; a < 3; ++a) {
+            w *= d[a] ? f[a] : 1.0 - f[a];
+            idx[a] = base[a] + d[a];
+            if (idx[a] > g->dims[a] - 1) idx[a] = g->dims[a] - 1;
+        }
+        size_t p = ((size_t)idx[2] * g->dims[1] + idx[1]) * g->dims[0] + idx[0];
+        w *= valid[p] ? 1.0 : 0.0;
+        if (w <= 0.0) continue;
+        double v[3];
+        fetch_oct_bilinear(irr + p * IRR_T * IRR_T * 4, nrm, v);
+        for (int k = 0; k < 3; ++k) acc[k] += w * v[k];
+        sw += w;
+    }
+    for (int k = 0; k < 3; ++k) out[k] = sw > 0.0 ? acc[k] / sw : 0.0;
+}
+
+/* ------------------------------------------------ shading (Sec. 3.3, O12) */
+
+/* Radiance leaving hit point x back along the ray: emission stored with the scene,
+ * plus Lambertian direct light (each light gated by a binary SDF shadow ray, the
+ * stand-in for the paper's reflective-shadow-map flux), plus the multi-bounce term
+ * albedo * k * (last frame's normalised irradiance at x for normal n). With a force
+ * record, a light's visibility follows the record where this side's own decision
+ * (gating or shadow trace) lay within the rounding band. */
+void oracle_shade(const or_volume* vol, const or_grid* g, const or_light* lights, int32_t n_lights,
+                  const double* prev_irr, const uint8_t* prev_valid,
+                  const double x[3], const double d[3], const or_force* force, or_ray* rec) {
+    const double h = vol->h;
+    double grad[3];
+    for (int a = 0; a < 3; ++a) {
+        double pp[3] = {x[0], x[1], x[2]}, pm[3] = {x[0], x[1], x[2]};
+        pp[a] += 0.5 * h;
+        pm[a] -= 0.5 * h;
+        grad[a] = oracle_sample_sdf(vol, pp) - oracle_sample_sdf(vol, pm);
+    }
+    double glen = sqrt(dot3(grad, grad));
+    double n[3];
+    for (int a = 0; a < 3; ++a) n[a] = glen > 0.0 ? grad[a] / glen : -d[a];
+
+    double albedo[3], emission[3];
+    sample_material(vol, x, albedo, emission);
+
+    double xs[3];
+    for (int a = 0; a < 3; ++a) xs[a] = x[a] + g->bias_vox * h * n[a];
+    const double tmax = g->tmax_vox * h;
+
+    double direct[3] = {0.0, 0.0, 0.0};
+    for (int l = 0; l < n_lights; ++l) {
+        const or_light* li = &lights[l];
+        double ldir[3], scale = 0.0, tlimit = tmax, m_gate;
+        int gate;
+        if (li->type == 0) {
+            for (int a = 0; a < 3; ++a) ldir[a] = li->v[a];
+            double cosv = dot3(n, ldir);
+            m_gate = fabs(cosv);
+            gate = cosv > 0.0;
+            scale = fmax(cosv, 0.0);
+        } else {
+            double Lv[3] = {li->v[0] - x[0], li->v[1] - x[1], li->v[2] - x[2]};
+            double dist = sqrt(dot3(Lv, Lv));
+            if (!(dist > 0.0)) continue;
+            double cosv = (n[0] * Lv[0] + n[1] * Lv[1] + n[2] * Lv[2]) / dist;
+            double q = dist / li->range;
+            double q4 = (q * q) * (q * q);
+            double win = clampd(1.0 - q4, 0.0, 1.0);
+            win = win * win;
+            m_gate = fmin(fabs(cosv), fabs(1.0 - q4));
+            gate = cosv > 0.0 && win > 0.0;
+            scale = fmax(cosv, 0.0) * win / (dist * dist);
+            double Ls[3] = {li->v[0] - xs[0], li->v[1] - xs[1], li->v[2] - xs[2]};
+            double ds = sqrt(dot3(Ls, Ls));
+            for (int a = 0; a < 3; ++a) ldir[a] = Ls[a] / ds;
+            tlimit = ds;
+        }
+        rec->margin_decision = fmin(rec->margin_decision, m_gate);
+        int lit = 0;
+        double m_sh = HUGE_MARGIN;
+        if (gate) {
+            double ts;
+            int32_t st, f0 = 0, h0 = 0;
+            int32_t ev = trace_path(vol, xs, ldir, g->eps_vox, tlimit, g->max_steps, -1, 0, &ts, &st, &m_sh,
+                                    &f0, &h0);
+            rec->traced_mask |= 1u << l;
+            rec->shadow_steps += st;
+            rec->margin_shadow = fmin(rec->margin_shadow, m_sh);
+            lit = is_miss(ev); /* occluded by a hit or by a budget-exhausted graze */
+        }
+        if (lit) rec->natural_lit_mask |= 1u << l;
+        if (force) {
+            int want = (force->lit_mask >> l) & 1u;
+            if (want != lit) {
+                rec->forced++;
+                if (!(m_gate < g_delta_cos || m_sh < g_delta_vox)) rec->hard++;
+                lit = want;
+            }
+        }
+        if (!lit) continue;
+        rec->lit_mask |= 1u << l;
+        for (int k = 0; k < 3; ++k) direct[k] += li->rgb[k] * scale;
+    }
+
+    double indirect[3] = {0.0, 0.0, 0.0};
+    if (g->k_bounce != 0.0) oracle_sample_irradiance(g, prev_irr, prev_valid, x, n, indirect);
+    for (int k = 0; k < 3; ++k)
+        rec->L[k] = emission[k] + albedo[k] / kPi * direct[k] + g->k_bounce * albedo[k] * indirect[k];
+}
+
+/* ------------------------------------------------ probe update (Sec. 3.3, Eq. 3) */
+
+/* Cosine-lobe gather of Eq. 3 into one octahedral map, then temporal mixing:
+ * for interior texel j with direction u_j, new_j = sum_i w_ij v_i / sum_i w_ij with
+ * w_ij = max(0, u_j . d_i)^e (e = 1 for irradiance, e = p for depth moments);
+ * out_j = h old_j + (1 - h) new_j; a texel that no ray reaches keeps its old value. */
+static void gather_map(double* map, const double* old, int n, int C, int exponent,
+                       const double* dirs, const double* vals, int nv, int R, double hyst) {
+    const int T = n + 2;
+    for (int b = 0; b < n; ++b) {
+        for (int a = 0; a < n; ++a) {
+            double uv[2] = {(a + 0.5) / n, (b + 0.5) / n}, u[3];
+            oracle_oct_decode(uv, u);
+            double sw = 0.0, acc[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int i = 0; i < R; ++i) {
+                double c = dot3(u, dirs + 3 * i);
+                if (!(c > 0.0)) continue;
+                double w = exponent == 1 ? c : pow(c, (double)exponent);
+                sw += w;
+                for (int k = 0; k < nv; ++k) acc[k] += w * vals[(size_t)i * nv + k];
+            }
+            double* out = map + ((size_t)(b + 1) * T + (a + 1)) * C;
+            const double* prev = old + ((size_t)(b + 1) * T + (a + 1)) * C;
+            for (int k = 0; k < C; ++k) out[k] = prev[k];
+            if (sw > 0.0) {
+                for (int k = 0; k < nv; ++k) out[k] = hyst * prev[k] + (1.0 - hyst) * (acc[k] / sw);
+                if (C > nv) out[nv] = 1.0; /* irradiance alpha: texel has received rays */
+            }
+        }
+    }
+    oracle_border(map, n, C);
+}
+
+static void update_one_probe(const or_volume* vol, const or_grid* g, const or_light* lights, int32_t n_lights,
+                             const float rot[9], const or_probe* pr, size_t p,
+                             const double* prev_irr, const double* prev_depth, const uint8_t* prev_valid,
+                             double* cur_irr, double* cur_depth, uint8_t* cur_valid, const or_force* force,
+                             or_ray* rays) {
+    const size_t irr_sz = IRR_T * IRR_T * 4, dep_sz = DEP_T * DEP_T * 2;
+    const int R = g->rays;
+    if (!(pr->flags & 1u)) { /* inactive: keeps its maps and history, casts no ray */
+        if (rays) {
+            memset(rays, 0, sizeof(or_ray) * (size_t)R);
+            for (int i = 0; i < R; ++i) rays[i].event = rays[i].natural_event = -1;
+        }
+        memcpy(cur_irr + p * irr_sz, prev_irr + p * irr_sz, sizeof(double) * irr_sz);
+        memcpy(cur_depth + p * dep_sz, prev_depth + p * dep_sz, sizeof(double) * dep_sz);
+        cur_valid[p] = prev_valid[p];
+        return;
+    }
+    double hyst = (prev_valid[p] && !(pr->flags & 2u)) ? g->hysteresis : 0.0;
+    const double h = vol->h, tmax = g->tmax_vox * h;
+    const double o[3] = {pr->pos[0], pr->pos[1], pr->pos[2]};
+
+    double* dirs = (double*)malloc(sizeof(double) * 3 * R);
+    double* rad = (double*)malloc(sizeof(double) * 3 * R);
+    double* mom = (double*)malloc(sizeof(double) * 2 * R);
+
+    for (int i = 0; i < R; ++i) {
+        double s[3], d[3];
+        oracle_sf_dir(i, R, s);
+        for (int r = 0; r < 3; ++r)
+            d[r] = (double)rot[3 * r] * s[0] + (double)rot[3 * r + 1] * s[1] + (double)rot[3 * r + 2] * s[2];
+        memcpy(dirs + 3 * i, d, sizeof d);
+
+        or_ray rec;
+        memset(&rec, 0, sizeof rec);
+        rec.margin_shadow = HUGE_MARGIN;
+        rec.margin_decision = HUGE_MARGIN;
+        const or_force* fi = force ? &force[i] : NULL;
+        double t;
+        rec.natural_event = trace_path(vol, o, d, g->eps_vox, tmax, g->max_steps, -1, 0, &t,
+                                       &rec.natural_steps, &rec.margin_primary, &rec.forced, &rec.hard);
+        rec.event = rec.natural_event;
+        rec.steps = rec.natural_steps;
+        if (fi && (fi->event != rec.natural_event || fi->steps != rec.natural_steps)) {
+            double m_unused;
+            rec.event = trace_path(vol, o, d, g->eps_vox, tmax, g->max_steps, fi->event, fi->steps, &t,
+                                   &rec.steps, &m_unused, &rec.forced, &rec.hard);
+        }
+        rec.t = t;
+        if (is_miss(rec.event)) {
+            for (int k = 0; k < 3; ++k) rec.L[k] = g->sky[k];
+            if (fi && fi->lit_mask) { /* the other side shaded a ray this path misses */
+                rec.forced++;
+                rec.hard++;
+            }
+        } else {
+            double x[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+            oracle_shade(vol, g, lights, n_lights, prev_irr, prev_valid, x, d, fi, &rec);
+        }
+        double td = is_miss(rec.event) ? tmax : fmin(t, tmax);
+        for (int k = 0; k < 3; ++k) rad[3 * i + k] = rec.L[k];
+        mom[2 * i] = td;
+        mom[2 * i + 1] = td * td;
+        if (rays) rays[i] = rec;
+    }
+
+    gather_map(cur_irr + p * irr_sz, prev_irr + p * irr_sz, IRR_N, 4, 1, dirs, rad, 3, R, hyst);
+    gather_map(cur_depth + p * dep_sz, prev_depth + p * dep_sz, DEP_N, 2, g->depth_exponent, dirs, mom, 2, R, hyst);
+    cur_valid[p] = 1;
+    free(dirs);
+    free(rad);
+    free(mom);
+}
+
+int32_t oracle_update(const or_volume* vol, const or_grid* g, const or_light* lights, int32_t n_lights,
+                      const float rot[9], const or_probe* probes,
+                      const double* prev_irr, const double* prev_depth, const uint8_t* prev_valid,
+                      double* cur_irr, double* cur_depth, uint8_t* cur_valid,
+                      const int32_t* subset, int32_t n_subset, const or_force* force, or_ray* rays,
+                      int32_t n_threads) {
+    if (!vol || !g || !rot || !probes || !prev_irr || !prev_depth || !prev_valid || !cur_irr || !cur_depth ||
+        !cur_valid || g->rays < 1 || g->max_steps < 1 || n_lights < 0 || n_lights > 32 || vol->nx < 2 ||
+        vol->ny < 2 || vol->nz < 2 || (subset && n_subset < 0))
+        return -1;
+    const size_t P = (size_t)g->dims[0] * g->dims[1] * g->dims[2];
+    const int32_t n = subset ? n_subset : (int32_t)P;
+    const int R = g->rays;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int32_t j = 0; j < n; ++j) {
+        size_t p = subset ? (size_t)subset[j] : (size_t)j;
+        update_one_probe(vol, g, lights, n_lights, rot, &probes[p], p, prev_irr, prev_depth, prev_valid,
+                         cur_irr, cur_depth, cur_valid, force ? force + (size_t)j * R : NULL,
+                         rays ? rays + (size_t)j * R : NULL);
+    }
+    (void)n_threads;
+    return 0;
+}

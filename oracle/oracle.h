@@ -1,0 +1,146 @@
+/*
+ * oracle.h -- FP64 CPU oracle of the SDFDDGI per-frame probe update.
+ *
+ * TEST INFRASTRUCTURE. Only the tests, the smoke check and the bench's CPU
+ * baseline leg may load this library. It is a plain, slow, obviously correct
+ * restatement of the probe update of "Signed Distance Fields Dynamic Diffuse
+ * Global Illumination" (Hu et al., arXiv 2007.14394), Sec. 3.3 "Probe update"
+ * with Eq. 3, computed in double precision, probe by probe and ray by ray.
+ * It shares no code, header, table or constant with the CUDA library.
+ *
+ * Units: every position and distance is in world units; parameters given
+ * "in voxels" are multiplied by the voxel size h before use.
+ */
+#ifndef SDFDDGI_ORACLE_H
+#define SDFDDGI_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Voxel signed-distance volume plus material volume.
+ * Voxel (x, y, z) holds the field at world point origin + (x+1/2, y+1/2, z+1/2) h,
+ * stored [z][y][x]. sdf_dtype 0 = float32, 1 = IEEE binary16 (raw bits).
+ * material: [z][y][x][8] binary16 raw bits = albedo r,g,b, unused, emission r,g,b, unused;
+ * NULL means albedo 0 and emission 0 everywhere. */
+typedef struct {
+    int32_t nx, ny, nz, sdf_dtype;
+    double h;
+    double origin[3];
+    const void* sdf;
+    const uint16_t* material;
+} or_volume;
+
+/* Light: type 0 = directional (v = unit direction TOWARD the light, rgb = irradiance E),
+ *        type 1 = point (v = position, rgb = intensity I, range r > 0). */
+typedef struct {
+    int32_t type, pad;
+    double v[3];
+    double rgb[3];
+    double range;
+} or_light;
+
+/* Probe volume parameters (the same meaning as the library's volume description). */
+typedef struct {
+    int32_t dims[3];
+    int32_t rays;              /* R, rays per probe */
+    double origin[3];          /* world position of probe (0,0,0) */
+    double spacing[3];         /* world spacing of the probe grid */
+    int32_t max_steps;         /* S_max of every sphere trace */
+    int32_t depth_exponent;    /* p: depth weight max(0, cos)^p */
+    double eps_vox;            /* hit threshold, voxels */
+    double tmax_vox;           /* trace length limit, voxels */
+    double hysteresis;         /* h in out = h old + (1-h) new */
+    double k_bounce;           /* gain of the previous-frame (multi-bounce) term */
+    double bias_vox;           /* shadow-ray origin offset along the normal, voxels */
+    double sky[3];             /* radiance of rays that miss */
+} or_grid;
+
+/* Probe state: world position and flags (bit 0 active, bit 1 reject history). */
+typedef struct {
+    float pos[3];
+    uint32_t flags;
+} or_probe;
+
+/* Exit events of a sphere trace. A ray is a MISS when it ends by LEFT_VOLUME or
+ * PAST_LIMIT; HIT and EXHAUSTED (budget spent, taken as a hit at the final t) shade. */
+#define OR_LEFT_VOLUME 0
+#define OR_HIT 1
+#define OR_PAST_LIMIT 2
+#define OR_EXHAUSTED 3
+
+/* Discrete outcome of one ray as another implementation took it: the event and
+ * step count of the primary trace and the visibility bit of every light. When
+ * given, the oracle follows these decisions wherever its own double-precision
+ * decision lies within delta of the threshold (a rounding-sensitive decision),
+ * counts every such override, and counts as "hard" any override whose margin
+ * was wider than delta. Everything continuous stays double precision. */
+typedef struct {
+    int32_t event;
+    int32_t steps;
+    uint32_t lit_mask;
+    int32_t pad;
+} or_force;
+
+/* Per-ray record of one update (one per (probe, ray)). */
+typedef struct {
+    double t;                /* hit distance (world) along the path taken; MISS records the trace limit */
+    double L[3];             /* radiance carried back to the probe */
+    double margin_primary;   /* voxels: closest approach of a natural termination test to flipping */
+    double margin_shadow;    /* voxels: the same over all natural shadow traces (1e300 if none) */
+    double margin_decision;  /* min over lights of |n.l| and, for point lights, |1-(d/r)^4| */
+    int32_t event;           /* path taken */
+    int32_t steps;           /* SDF samples of the primary trace, path taken */
+    int32_t natural_event;   /* the oracle's own decisions */
+    int32_t natural_steps;
+    uint32_t lit_mask;       /* bit l: light l contributed with visibility 1 (path taken) */
+    uint32_t natural_lit_mask;
+    uint32_t traced_mask;    /* bit l: a natural shadow ray toward light l was traced */
+    int32_t shadow_steps;    /* SDF samples over all natural shadow traces */
+    int32_t forced;          /* decisions taken from the force record */
+    int32_t hard;            /* of those, decisions whose margin exceeded delta */
+} or_ray;
+
+/* Spherical-Fibonacci direction i of n (unrotated). */
+void oracle_sf_dir(int32_t i, int32_t n, double out[3]);
+/* Octahedral map (pole +z). */
+void oracle_oct_encode(const double v[3], double uv[2]);
+void oracle_oct_decode(const double uv[2], double v[3]);
+/* Trilinear sample of the signed-distance volume at world point p. */
+double oracle_sample_sdf(const or_volume* vol, const double p[3]);
+/* One sphere trace; returns the exit event, writes t (world), steps and margin (voxels). */
+int32_t oracle_trace(const or_volume* vol, const double o[3], const double d[3],
+                     double eps_vox, double tlimit, int32_t max_steps,
+                     double* t, int32_t* steps, double* margin_vox);
+/* Border fixup of one (n+2)x(n+2)xC map in place. */
+void oracle_border(double* map, int32_t n, int32_t channels);
+/* Interpolated normalised irradiance at world point x with unit normal nrm. */
+void oracle_sample_irradiance(const or_grid* g, const double* irr, const uint8_t* valid,
+                              const double x[3], const double nrm[3], double out[3]);
+/* Radiance leaving hit point x toward a ray of direction d (shading step). */
+void oracle_shade(const or_volume* vol, const or_grid* g, const or_light* lights, int32_t n_lights,
+                  const double* prev_irr, const uint8_t* prev_valid,
+                  const double x[3], const double d[3], const or_force* force, or_ray* rec);
+
+/* Widths of the rounding-sensitive band: distances in voxels, cosines unitless. */
+void oracle_set_delta(double delta_vox, double delta_cos);
+
+/* One probe update over the probes listed in `subset` (all probes if subset is NULL).
+ * prev_irr [P][8][8][4], prev_depth [P][16][16][2], prev_valid [P]: the previous maps.
+ * cur_*: written for the listed probes only. rays: NULL or [n_subset][R] records.
+ * force: NULL or [n_subset][R] outcomes to follow within the rounding band.
+ * rot: row-major 3x3 frame rotation (float32 values, promoted exactly).
+ * Returns 0, or -1 on invalid arguments. */
+int32_t oracle_update(const or_volume* vol, const or_grid* g, const or_light* lights, int32_t n_lights,
+                      const float rot[9], const or_probe* probes,
+                      const double* prev_irr, const double* prev_depth, const uint8_t* prev_valid,
+                      double* cur_irr, double* cur_depth, uint8_t* cur_valid,
+                      const int32_t* subset, int32_t n_subset, const or_force* force, or_ray* rays,
+                      int32_t n_threads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
