@@ -1,0 +1,219 @@
+/*
+ * sdfddgi.h -- C ABI of the SDFDDGI probe-update library (CUDA, sm_103a).
+ *
+ * The library implements the per-frame probe update of "Signed Distance Fields
+ * Dynamic Diffuse Global Illumination" (Hu et al., arXiv 2007.14394):
+ *   Sec. 3.2 / Eq. 2  -- irradiance E(P, D) is sampled at probes P on a grid;
+ *   Sec. 3.3 / Eq. 3  -- each probe traces low-discrepancy random rays through
+ *                        the scene's signed-distance field, shades the hits
+ *                        (direct light + emission + last frame's probes for
+ *                        multi-bounce), and every octahedral texel gathers
+ *                        E = integral of max(0, cos) L over the probe's samples,
+ *                        mixed temporally with the previous frame;
+ *   Sec. 3.4          -- shading points interpolate the probes.
+ * The scene is a voxel signed-distance volume (the paper's primitives baked at
+ * voxel centres); light visibility is an SDF shadow ray (in place of the
+ * paper's reflective shadow map); depth/depth^2 moments are blended as well.
+ *
+ * Conventions
+ *  - Every call returns SDFDDGI_OK (0) or a negative sdfddgi_status; the text
+ *    of the last failure on the calling thread is sdfddgi_last_error().
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All device work is enqueued on it and is asynchronous to the host unless
+ *    the entry point says otherwise. Argument errors are reported before any
+ *    work is enqueued; launch failures are reported by the call that launched.
+ *  - World units throughout; parameters documented "in voxels" are multiples
+ *    of the scene's voxel size.
+ *  - The library owns the scene and volume storage (device memory obtained
+ *    with cudaMalloc) and copies every input at call time; callers own every
+ *    pointer they pass and may reuse it once the call's work on `stream` has
+ *    completed.
+ *  - Handles are not thread-safe: one host thread at a time per handle.
+ */
+#ifndef SDFDDGI_H
+#define SDFDDGI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SDFDDGI_API __attribute__((visibility("default")))
+#else
+#define SDFDDGI_API
+#endif
+
+typedef enum {
+    SDFDDGI_OK = 0,
+    SDFDDGI_ERR_INVALID_ARG = -1, /* a pointer, size, enum or range is invalid   */
+    SDFDDGI_ERR_OOM = -2,         /* a device or host allocation failed          */
+    SDFDDGI_ERR_CUDA = -3,        /* a CUDA runtime call or launch failed        */
+    SDFDDGI_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up          */
+    SDFDDGI_ERR_STATE = -5        /* the handle is not ready for this call       */
+} sdfddgi_status;
+
+typedef struct sdfddgi_scene sdfddgi_scene;   /* SDF + material volume + lights */
+typedef struct sdfddgi_volume sdfddgi_volume; /* probe grid + ping-pong probe maps */
+
+enum { SDFDDGI_F32 = 0, SDFDDGI_F16 = 1 };                          /* SDF storage type  */
+enum { SDFDDGI_LIGHT_DIRECTIONAL = 0, SDFDDGI_LIGHT_POINT = 1 };    /* light type        */
+enum { SDFDDGI_PROBE_ACTIVE = 1u, SDFDDGI_PROBE_REJECT_HISTORY = 2u }; /* probe flags   */
+enum { SDFDDGI_MAX_LIGHTS = 32, SDFDDGI_MAX_RAYS = 1024, SDFDDGI_MAX_STEPS = 65535 };
+
+/* Octahedral map sizes (Sec. 3.3: octahedral mapping into the probe atlas):
+ * irradiance 6x6 interior texels + 1-texel border = 8x8, RGBA float32 per texel
+ * (A = 1 once the texel has received a ray); depth moments 14x14 + border = 16x16,
+ * (mean distance, mean squared distance) float32 per texel. Probe-major layout:
+ * irradiance [P][8][8][4], depth [P][16][16][2], row = octahedral v, column = u. */
+enum { SDFDDGI_IRR_INTERIOR = 6, SDFDDGI_IRR_SIDE = 8, SDFDDGI_DEPTH_INTERIOR = 14, SDFDDGI_DEPTH_SIDE = 16 };
+
+/* A light (Sec. 3.3 shading). DIRECTIONAL: v = unit direction toward the light,
+ * rgb = irradiance on a surface facing it. POINT: v = position, rgb = radiant
+ * intensity, range = distance at which its smooth window (1-(d/range)^4)^2 reaches 0. */
+typedef struct {
+    int32_t type;
+    float v[3];
+    float rgb[3];
+    float range;
+} sdfddgi_light;
+
+/* Per-probe state (Sec. 3.2, probe choosing): world position and flags. A probe
+ * without SDFDDGI_PROBE_ACTIVE casts no ray and keeps its maps; one with
+ * SDFDDGI_PROBE_REJECT_HISTORY discards its history (no temporal mixing). */
+typedef struct {
+    float pos[3];
+    uint32_t flags;
+} sdfddgi_probe_state;
+
+/* Probe volume description (Sec. 3.2 grid; Sec. 3.3 update parameters). */
+typedef struct {
+    int32_t dims[3];          /* probes along x, y, z (each >= 1); probe index = (z*dy + y)*dx + x */
+    int32_t rays_per_probe;   /* R, 1..SDFDDGI_MAX_RAYS, spherical-Fibonacci set rotated per frame */
+    float origin[3];          /* world position of probe (0,0,0) */
+    float spacing[3];         /* world distance between neighbouring probes (each > 0) */
+    int32_t max_steps;        /* sphere-trace step budget, 1..SDFDDGI_MAX_STEPS */
+    int32_t depth_exponent;   /* p >= 1: depth texels weight rays by max(0, cos)^p */
+    float eps;                /* hit threshold, voxels (> 0) */
+    float t_max;              /* trace length limit, voxels; <= 0 selects the volume diagonal */
+    float hysteresis;         /* temporal mixing weight of the old value, in [0, 1] */
+    float multibounce_k;      /* gain of the last-frame probe term, in [0, 1] */
+    float normal_bias;        /* shadow-ray origin offset along the normal, voxels (>= 0) */
+    uint32_t seed;            /* seed of the per-frame ray rotation */
+    uint32_t volume_id;       /* distinguishes rotations of volumes sharing a seed */
+    uint32_t flags;           /* reserved, must be 0 */
+} sdfddgi_volume_desc;
+
+/* Per-ray record of one update (32 bytes), written only when requested:
+ * the primary trace's exit event (0 left the volume, 1 hit, 2 passed t_max,
+ * 3 step budget spent; 255 for rays of inactive probes), its step count, the
+ * hit distance (t_max for misses), the radiance carried back, which lights were
+ * visible, and the total steps of the shadow rays. */
+typedef struct {
+    float t;
+    float L[3];
+    uint32_t lit_mask;
+    uint32_t shadow_steps;
+    uint16_t steps;
+    uint8_t event;
+    uint8_t reserved0;
+    uint32_t reserved1;
+} sdfddgi_ray_record;
+
+/* Text of the last failure on this thread ("" if none). Never NULL. */
+SDFDDGI_API const char* sdfddgi_last_error(void);
+
+/* ---- scene (Sec. 3.1: the scene's SDF representation) ------------------- */
+
+/* Creates an empty scene on the current CUDA device. *out receives the handle. */
+SDFDDGI_API int sdfddgi_create_scene(sdfddgi_scene** out);
+SDFDDGI_API void sdfddgi_destroy_scene(sdfddgi_scene* s);
+
+/* Copies a signed-distance volume (and optionally its material volume) into the
+ * scene, replacing any previous one. Voxel (x,y,z) holds the signed distance
+ * (world units; negative inside geometry) at world point
+ * origin + (x+1/2, y+1/2, z+1/2) * voxel_size; layout [z][y][x], x fastest.
+ * dtype SDFDDGI_F32 (float) or SDFDDGI_F16 (IEEE binary16). dims each >= 2.
+ * material: NULL (albedo 0, emission 0) or [z][y][x][8] binary16 values
+ * (albedo r,g,b, unused, emission r,g,b, unused), sampled trilinearly.
+ * is_device_ptr: 1 if sdf/material are device pointers, 0 for host memory.
+ * Synchronous with respect to the host for host inputs. */
+SDFDDGI_API int sdfddgi_upload_sdf(sdfddgi_scene* s, const void* sdf, const int32_t dims[3], float voxel_size,
+                                   const float origin[3], int32_t dtype, const void* material,
+                                   int32_t is_device_ptr, void* stream);
+
+/* Replaces the scene's lights (host array of n, 0..SDFDDGI_MAX_LIGHTS) and the
+ * radiance of rays that leave the scene (sky_rgb, host, may be NULL for black). */
+SDFDDGI_API int sdfddgi_set_lights(sdfddgi_scene* s, const sdfddgi_light* lights, int32_t n,
+                                   const float sky_rgb[3]);
+
+/* ---- probe volume (Sec. 3.2 probe grid) -------------------------------- */
+
+/* Creates a probe volume over scene s (which must outlive it) with zeroed maps
+ * and no history. The scene's SDF may be replaced later; the volume uses
+ * whatever the scene holds at each update. */
+SDFDDGI_API int sdfddgi_create_volume(const sdfddgi_volume_desc* desc, sdfddgi_scene* s, sdfddgi_volume** out);
+SDFDDGI_API void sdfddgi_destroy_volume(sdfddgi_volume* v);
+
+/* Number of probes of the volume. */
+SDFDDGI_API int sdfddgi_volume_probe_count(const sdfddgi_volume* v, int64_t* n_probes);
+
+/* The frame's ray rotation (row-major float 3x3) as update_probes derives it
+ * when given no rotation: three uniforms from splitmix64 (Steele, Lea, Flood
+ * 2014) started at seed*0x9E3779B97F4A7C15 + frame*0xBF58476D1CE4E5B9 +
+ * volume_id*0x94D049BB133111EB, each (z >> 11) * 2^-53, mapped to a unit
+ * quaternion by Shoemake's uniform random rotation (Graphics Gems III). */
+SDFDDGI_API int sdfddgi_frame_rotation(uint32_t seed, uint32_t frame, uint32_t volume_id, float out[9]);
+
+/* One probe update (Sec. 3.3, Eq. 3) on `stream`: for every active probe, R
+ * rays d_i = Rot * sf(i, R) (spherical Fibonacci: z = 1-(2i+1)/R, azimuth
+ * 2*pi*((i*2654435769) mod 2^32)/2^32) are sphere-traced through the SDF
+ * from the probe; hits are shaded (emission + albedo/pi * sum of visible
+ * lights' irradiance * cos + k * albedo * last frame's interpolated
+ * irradiance); each interior octahedral texel of direction u takes
+ * sum_i w_i v_i / sum_i w_i with w_i = max(0, u.d_i) (irradiance) or
+ * max(0, u.d_i)^p (distance, distance^2; misses count as t_max), mixed as
+ * h*old + (1-h)*new (h = 0 without history); then the borders are filled.
+ *  frame     -- selects the rotation when `rotation` is NULL.
+ *  rotation  -- NULL or host float[9] (row-major) rotation to use instead.
+ *  states    -- NULL (every probe active at its grid position) or P states,
+ *               host (states_on_device = 0) or device (1) memory.
+ *  records   -- NULL or a device array of P*R records ([probe][ray]).
+ * The maps of the previous update become the "previous" input (ping-pong). */
+SDFDDGI_API int sdfddgi_update_probes(sdfddgi_volume* v, uint32_t frame, const float* rotation,
+                                      const sdfddgi_probe_state* states, int32_t states_on_device,
+                                      sdfddgi_ray_record* records, void* stream);
+
+/* Interpolated normalised irradiance (Sec. 3.4 probe interpolation, without the
+ * per-pixel SDF visibility test) at n world points with unit normals: trilinear
+ * over the 8 probes of the grid cell containing the point (clamped to the grid),
+ * each weighted by its trilinear weight times "has history", each contributing
+ * the bilinear value of its irradiance map at the normal's octahedral
+ * coordinates; weights renormalised, 0 where all are 0.
+ * points, normals: device float[n][3]; out_rgb: device float[n][3]; n >= 0. */
+SDFDDGI_API int sdfddgi_sample_irradiance(const sdfddgi_volume* v, const float* points, const float* normals,
+                                          int64_t n, float* out_rgb, void* stream);
+
+/* Device pointers to the current (latest) maps: irradiance [P][8][8][4] float,
+ * depth [P][16][16][2] float, valid [P] uint8 (1 = probe has history). They stay
+ * valid until the next update_probes / write_state / destroy. Any may be NULL. */
+SDFDDGI_API int sdfddgi_get_maps(const sdfddgi_volume* v, const float** irr, const float** depth,
+                                 const uint8_t** valid);
+
+/* Checkpoint: copy the current maps out (read) or in (write). Arrays as in
+ * get_maps; host (on_device = 0) or device (1) memory. write_state makes the
+ * written maps the history of the next update. Host copies are synchronous. */
+SDFDDGI_API int sdfddgi_read_state(const sdfddgi_volume* v, float* irr, float* depth, uint8_t* valid,
+                                   int32_t on_device, void* stream);
+SDFDDGI_API int sdfddgi_write_state(sdfddgi_volume* v, const float* irr, const float* depth,
+                                    const uint8_t* valid, int32_t on_device, void* stream);
+
+/* Clears every map and the history (as at creation). */
+SDFDDGI_API int sdfddgi_reset(sdfddgi_volume* v, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDFDDGI_H */

@@ -1,0 +1,253 @@
+"""Python binding of the SDFDDGI probe-update library (libsdfddgi.so, CUDA sm_103a).
+
+Argument marshalling only: every step of the probe update runs in the library's
+CUDA kernels; PyTorch supplies device memory and streams. The functions keep the
+C names without the ``sdfddgi_`` prefix (see include/sdfddgi.h for the contract
+of each). There is no CPU fallback: importing this package fails loudly when the
+compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsdfddgi.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5
+F32, F16 = 0, 1
+LIGHT_DIRECTIONAL, LIGHT_POINT = 0, 1
+PROBE_ACTIVE, PROBE_REJECT_HISTORY = 1, 2
+MAX_LIGHTS, MAX_RAYS, MAX_STEPS = 32, 1024, 65535
+IRR_SIDE, DEPTH_SIDE = 8, 16
+EVENT_LEFT_VOLUME, EVENT_HIT, EVENT_PAST_LIMIT, EVENT_EXHAUSTED, EVENT_NO_RAY = 0, 1, 2, 3, 255
+
+
+class SdfddgiError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sdfddgi error {code}: {msg}")
+        self.code = code
+
+
+class Light(C.Structure):
+    _fields_ = [("type", C.c_int32), ("v", C.c_float * 3), ("rgb", C.c_float * 3), ("range", C.c_float)]
+
+
+class ProbeState(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("flags", C.c_uint32)]
+
+
+class VolumeDesc(C.Structure):
+    _fields_ = [("dims", C.c_int32 * 3), ("rays_per_probe", C.c_int32), ("origin", C.c_float * 3),
+                ("spacing", C.c_float * 3), ("max_steps", C.c_int32), ("depth_exponent", C.c_int32),
+                ("eps", C.c_float), ("t_max", C.c_float), ("hysteresis", C.c_float), ("multibounce_k", C.c_float),
+                ("normal_bias", C.c_float), ("seed", C.c_uint32), ("volume_id", C.c_uint32), ("flags", C.c_uint32)]
+
+
+PROBE_STATE_DTYPE = np.dtype([("pos", "f4", (3,)), ("flags", "u4")])
+RAY_RECORD_DTYPE = np.dtype([("t", "f4"), ("L", "f4", (3,)), ("lit_mask", "u4"), ("shadow_steps", "u4"),
+                             ("steps", "u2"), ("event", "u1"), ("reserved0", "u1"), ("reserved1", "u4")])
+assert RAY_RECORD_DTYPE.itemsize == 32 and PROBE_STATE_DTYPE.itemsize == 16
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2007_14394_b300.build` "
+                          "(the CUDA library is required; there is no fallback)")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, u32, i64 = C.c_void_p, C.c_int32, C.c_uint32, C.c_int64
+    sig = {
+        "sdfddgi_last_error": ([], C.c_char_p),
+        "sdfddgi_create_scene": ([C.POINTER(vp)], C.c_int),
+        "sdfddgi_destroy_scene": ([vp], None),
+        "sdfddgi_upload_sdf": ([vp, vp, C.POINTER(i32), C.c_float, C.POINTER(C.c_float), i32, vp, i32, vp], C.c_int),
+        "sdfddgi_set_lights": ([vp, C.POINTER(Light), i32, C.POINTER(C.c_float)], C.c_int),
+        "sdfddgi_create_volume": ([C.POINTER(VolumeDesc), vp, C.POINTER(vp)], C.c_int),
+        "sdfddgi_destroy_volume": ([vp], None),
+        "sdfddgi_volume_probe_count": ([vp, C.POINTER(i64)], C.c_int),
+        "sdfddgi_frame_rotation": ([u32, u32, u32, C.POINTER(C.c_float)], C.c_int),
+        "sdfddgi_update_probes": ([vp, u32, vp, vp, i32, vp, vp], C.c_int),
+        "sdfddgi_sample_irradiance": ([vp, vp, vp, i64, vp, vp], C.c_int),
+        "sdfddgi_get_maps": ([vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)], C.c_int),
+        "sdfddgi_read_state": ([vp, vp, vp, vp, i32, vp], C.c_int),
+        "sdfddgi_write_state": ([vp, vp, vp, vp, i32, vp], C.c_int),
+        "sdfddgi_reset": ([vp, vp], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+lib = _load()
+EXPORTED = ("last_error", "create_scene", "destroy_scene", "upload_sdf", "set_lights", "create_volume",
+            "destroy_volume", "volume_probe_count", "frame_rotation", "update_probes", "sample_irradiance",
+            "get_maps", "read_state", "write_state", "reset")
+
+
+def last_error() -> str:
+    return lib.sdfddgi_last_error().decode()
+
+
+def _check(rc: int) -> None:
+    if rc != OK:
+        raise SdfddgiError(rc, last_error())
+
+
+# ------------------------------------------------------------------ marshalling helpers
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(address, on_device) of a torch tensor or numpy array (contiguous)."""
+    if x is None:
+        return None, 0
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), int(x.is_cuda)
+    a = np.asarray(x)
+    if not a.flags.c_contiguous:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data, 0
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _floats(v, n):
+    return (C.c_float * n)(*[float(x) for x in v])
+
+
+# ------------------------------------------------------------------ C entry points
+def create_scene() -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib.sdfddgi_create_scene(C.byref(h)))
+    return h
+
+
+def destroy_scene(scene) -> None:
+    lib.sdfddgi_destroy_scene(scene)
+
+
+def upload_sdf(scene, sdf, voxel_size: float, origin, material=None, stream=None) -> None:
+    """sdf: [nz,ny,nx] float32/float16 (torch or numpy); material: [nz,ny,nx,8] float16 or None."""
+    shape = tuple(sdf.shape)
+    if len(shape) != 3:
+        raise ValueError("sdf must be 3-D [nz, ny, nx]")
+    name = str(sdf.dtype)
+    dtype = F32 if name.endswith("float32") else F16 if name.endswith("float16") else None
+    if dtype is None:
+        raise ValueError(f"sdf dtype {sdf.dtype} is neither float32 nor float16")
+    p, dev = _ptr(sdf)
+    m, mdev = _ptr(material)
+    if material is not None:
+        if tuple(material.shape) != shape + (8,) or not str(material.dtype).endswith("float16"):
+            raise ValueError("material must be float16 [nz, ny, nx, 8]")
+        if mdev != dev:
+            raise ValueError("sdf and material must both be host or both be device arrays")
+    dims = (C.c_int32 * 3)(shape[2], shape[1], shape[0])
+    _check(lib.sdfddgi_upload_sdf(scene, p, dims, float(voxel_size), _floats(origin, 3), dtype, m, dev,
+                                  _stream(stream)))
+
+
+def set_lights(scene, lights, sky=(0.0, 0.0, 0.0)) -> None:
+    """lights: sequence of dicts {type: 'dir'|'point', v, rgb, range}."""
+    n = len(lights)
+    arr = (Light * max(n, 1))()
+    for i, l in enumerate(lights):
+        arr[i].type = LIGHT_DIRECTIONAL if l["type"] in ("dir", LIGHT_DIRECTIONAL) else LIGHT_POINT
+        arr[i].v = _floats(l["v"], 3)
+        arr[i].rgb = _floats(l["rgb"], 3)
+        arr[i].range = float(l.get("range", 0.0))
+    _check(lib.sdfddgi_set_lights(scene, arr, n, _floats(sky, 3)))
+
+
+def make_desc(dims, rays_per_probe, origin, spacing, max_steps, depth_exponent=50, eps=0.01, t_max=0.0,
+              hysteresis=0.97, multibounce_k=0.9, normal_bias=1.0, seed=0, volume_id=0, flags=0) -> VolumeDesc:
+    return VolumeDesc((C.c_int32 * 3)(*[int(x) for x in dims]), int(rays_per_probe), _floats(origin, 3),
+                      _floats(spacing, 3), int(max_steps), int(depth_exponent), float(eps), float(t_max),
+                      float(hysteresis), float(multibounce_k), float(normal_bias), int(seed), int(volume_id),
+                      int(flags))
+
+
+def create_volume(desc: VolumeDesc, scene) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib.sdfddgi_create_volume(C.byref(desc), scene, C.byref(h)))
+    return h
+
+
+def destroy_volume(volume) -> None:
+    lib.sdfddgi_destroy_volume(volume)
+
+
+def volume_probe_count(volume) -> int:
+    n = C.c_int64()
+    _check(lib.sdfddgi_volume_probe_count(volume, C.byref(n)))
+    return n.value
+
+
+def frame_rotation(seed: int, frame: int, volume_id: int = 0) -> np.ndarray:
+    out = (C.c_float * 9)()
+    _check(lib.sdfddgi_frame_rotation(int(seed), int(frame), int(volume_id), out))
+    return np.array(out[:], dtype=np.float32).reshape(3, 3)
+
+
+def update_probes(volume, frame: int, rotation=None, states=None, records=None, stream=None) -> None:
+    """rotation: None or (3,3) float32 host array; states: None, numpy PROBE_STATE_DTYPE [P] (host) or a
+    device tensor of P*16 bytes; records: None or a device tensor of P*R*32 bytes."""
+    rot = None
+    if rotation is not None:
+        rot = np.ascontiguousarray(np.asarray(rotation, dtype=np.float32).reshape(9))
+    sp, sdev = _ptr(states)
+    rp, rdev = _ptr(records)
+    if records is not None and not rdev:
+        raise ValueError("records must be a device tensor")
+    _check(lib.sdfddgi_update_probes(volume, int(frame), rot.ctypes.data if rot is not None else None, sp, sdev,
+                                     rp, _stream(stream)))
+
+
+def sample_irradiance(volume, points, normals, out, stream=None) -> None:
+    """points, normals, out: device float32 tensors [n, 3]."""
+    n = int(points.shape[0]) if points is not None else 0
+    for t in (points, normals, out):
+        if t is not None and (not _is_torch(t) or not t.is_cuda or str(t.dtype) != "torch.float32"):
+            raise ValueError("points/normals/out must be CUDA float32 tensors")
+    _check(lib.sdfddgi_sample_irradiance(volume, _ptr(points)[0], _ptr(normals)[0], n, _ptr(out)[0],
+                                         _stream(stream)))
+
+
+def get_maps(volume):
+    """Raw device addresses (irr, depth, valid) of the current maps."""
+    a, b, c = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    _check(lib.sdfddgi_get_maps(volume, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def read_state(volume, irr, depth, valid, stream=None) -> None:
+    """Copies the current maps into irr [P,8,8,4] f32, depth [P,16,16,2] f32, valid [P] u8 (host or device)."""
+    (ip, idev), (dp, ddev), (vp_, vdev) = _ptr(irr), _ptr(depth), _ptr(valid)
+    if not (idev == ddev == vdev):
+        raise ValueError("read_state: all three arrays must be host or all device")
+    _check(lib.sdfddgi_read_state(volume, ip, dp, vp_, idev, _stream(stream)))
+
+
+def write_state(volume, irr, depth, valid, stream=None) -> None:
+    (ip, idev), (dp, ddev), (vp_, vdev) = _ptr(irr), _ptr(depth), _ptr(valid)
+    if not (idev == ddev == vdev):
+        raise ValueError("write_state: all three arrays must be host or all device")
+    _check(lib.sdfddgi_write_state(volume, ip, dp, vp_, idev, _stream(stream)))
+
+
+def reset(volume, stream=None) -> None:
+    _check(lib.sdfddgi_reset(volume, _stream(stream)))

@@ -1,0 +1,236 @@
+// device.cuh -- device building blocks of the probe update (FP32 arithmetic).
+//
+// Sampling rule of the signed-distance and material volumes: voxel centres sit at
+// integer coordinates g = (p - lo)/h - 1/2; the trilinear cell is clamped to the
+// volume and the fractions to [0, 1]. Sphere tracing, shading and the octahedral
+// map follow Sec. 3.3 of Hu et al. (arXiv 2007.14394); see the host header for
+// the full statement of each step.
+#pragma once
+
+#include "internal.h"
+
+namespace sdfddgi {
+
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ float3 fma3(float s, float3 d, float3 o) {
+    return f3(fmaf(s, d.x, o.x), fmaf(s, d.y, o.y), fmaf(s, d.z, o.z));
+}
+
+// ------------------------------------------------------------------ volume sampling
+struct Cell {
+    size_t base;  // linear index of corner (0,0,0)
+    float fx, fy, fz;
+};
+
+__device__ __forceinline__ int clamp_index(float g, int n, float* frac) {
+    int i = (int)floorf(g);
+    i = max(0, min(i, n - 2));
+    *frac = fminf(fmaxf(g - (float)i, 0.0f), 1.0f);
+    return i;
+}
+
+__device__ __forceinline__ Cell cell_of(const VolumeView& v, float3 p) {
+    Cell c;
+    int ix = clamp_index(fmaf(p.x - v.lo[0], v.inv_h, -0.5f), v.nx, &c.fx);
+    int iy = clamp_index(fmaf(p.y - v.lo[1], v.inv_h, -0.5f), v.ny, &c.fy);
+    int iz = clamp_index(fmaf(p.z - v.lo[2], v.inv_h, -0.5f), v.nz, &c.fz);
+    c.base = ((size_t)iz * v.ny + iy) * v.nx + ix;
+    return c;
+}
+
+template <typename T>
+__device__ __forceinline__ float ld_sdf(const T* s, size_t i);
+template <>
+__device__ __forceinline__ float ld_sdf<float>(const float* s, size_t i) { return __ldg(s + i); }
+template <>
+__device__ __forceinline__ float ld_sdf<__half>(const __half* s, size_t i) { return __half2float(__ldg(s + i)); }
+
+__device__ __forceinline__ float lerp(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+template <typename T>
+__device__ __forceinline__ float sample_sdf(const VolumeView& v, float3 p) {
+    const Cell c = cell_of(v, p);
+    const T* s = static_cast<const T*>(v.sdf);
+    const size_t sy = (size_t)v.nx, sz = (size_t)v.nx * v.ny, b = c.base;
+    const float c000 = ld_sdf(s, b), c100 = ld_sdf(s, b + 1);
+    const float c010 = ld_sdf(s, b + sy), c110 = ld_sdf(s, b + sy + 1);
+    const float c001 = ld_sdf(s, b + sz), c101 = ld_sdf(s, b + sz + 1);
+    const float c011 = ld_sdf(s, b + sz + sy), c111 = ld_sdf(s, b + sz + sy + 1);
+    const float x00 = lerp(c000, c100, c.fx), x10 = lerp(c010, c110, c.fx);
+    const float x01 = lerp(c001, c101, c.fx), x11 = lerp(c011, c111, c.fx);
+    return lerp(lerp(x00, x10, c.fy), lerp(x01, x11, c.fy), c.fz);
+}
+
+// Albedo and emission: the material volume under the same trilinear rule.
+__device__ __forceinline__ void sample_material(const VolumeView& v, float3 p, float3* albedo, float3* emission) {
+    *albedo = f3(0.f, 0.f, 0.f);
+    *emission = f3(0.f, 0.f, 0.f);
+    if (!v.material) return;
+    const Cell c = cell_of(v, p);
+    const size_t sy = (size_t)v.nx, sz = (size_t)v.nx * v.ny;
+    float a[3] = {0.f, 0.f, 0.f}, e[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+        const float w = (dx ? c.fx : 1.f - c.fx) * (dy ? c.fy : 1.f - c.fy) * (dz ? c.fz : 1.f - c.fz);
+        const uint4 raw = __ldg(v.material + c.base + dz * sz + dy * sy + dx);
+        const __half2 h01 = *reinterpret_cast<const __half2*>(&raw.x);
+        const __half2 h23 = *reinterpret_cast<const __half2*>(&raw.y);
+        const __half2 h45 = *reinterpret_cast<const __half2*>(&raw.z);
+        const __half2 h67 = *reinterpret_cast<const __half2*>(&raw.w);
+        const float2 m01 = __half22float2(h01), m23 = __half22float2(h23);
+        const float2 m45 = __half22float2(h45), m67 = __half22float2(h67);
+        a[0] = fmaf(w, m01.x, a[0]);
+        a[1] = fmaf(w, m01.y, a[1]);
+        a[2] = fmaf(w, m23.x, a[2]);
+        e[0] = fmaf(w, m45.x, e[0]);
+        e[1] = fmaf(w, m45.y, e[1]);
+        e[2] = fmaf(w, m67.x, e[2]);
+    }
+    *albedo = f3(a[0], a[1], a[2]);
+    *emission = f3(e[0], e[1], e[2]);
+}
+
+// ------------------------------------------------------------------ sphere tracing
+struct Trace {
+    float t;
+    int steps;
+    int event;
+};
+
+__device__ __forceinline__ bool is_miss(int event) { return event == kLeftVolume || event == kPastLimit; }
+
+// Sphere tracing (Sec. 3.3, accelerated sphere tracing of the scene SDF): step by the
+// sampled distance until it drops below eps (hit), the point leaves the volume box,
+// t passes `tlimit`, or the budget is spent (taken as a hit at the final t).
+template <typename T>
+__device__ __forceinline__ Trace sphere_trace(const VolumeView& v, float3 o, float3 d, float eps, float tlimit,
+                                              int max_steps) {
+    float t = 0.0f;
+    for (int s = 0; s < max_steps; ++s) {
+        const float3 p = fma3(t, d, o);
+        if (p.x < v.lo[0] || p.x > v.hi[0] || p.y < v.lo[1] || p.y > v.hi[1] || p.z < v.lo[2] || p.z > v.hi[2])
+            return {tlimit, s, kLeftVolume};
+        const float sd = sample_sdf<T>(v, p);
+        if (sd < eps) return {t, s + 1, kHit};
+        t += sd;
+        if (t > tlimit) return {tlimit, s + 1, kPastLimit};
+    }
+    return {t, max_steps, kExhausted};
+}
+
+// ------------------------------------------------------------------ octahedral map
+__device__ __forceinline__ float sign_nz(float x) { return x >= 0.f ? 1.f : -1.f; }
+
+// Octahedral parameterisation of the sphere (pole +z), uv in [0,1]^2.
+__device__ __forceinline__ float2 oct_encode(float3 v) {
+    const float inv_l1 = 1.0f / (fabsf(v.x) + fabsf(v.y) + fabsf(v.z));
+    float qx = v.x * inv_l1, qy = v.y * inv_l1;
+    if (v.z < 0.f) {
+        const float ox = (1.f - fabsf(qy)) * sign_nz(qx);
+        const float oy = (1.f - fabsf(qx)) * sign_nz(qy);
+        qx = ox;
+        qy = oy;
+    }
+    return make_float2(fmaf(0.5f, qx, 0.5f), fmaf(0.5f, qy, 0.5f));
+}
+
+__device__ __forceinline__ float3 oct_decode(float u, float w) {
+    const float qx = fmaf(2.f, u, -1.f), qy = fmaf(2.f, w, -1.f);
+    const float z = 1.f - fabsf(qx) - fabsf(qy);
+    float x = qx, y = qy;
+    if (z < 0.f) {
+        x = (1.f - fabsf(qy)) * sign_nz(qx);
+        y = (1.f - fabsf(qx)) * sign_nz(qy);
+    }
+    const float inv = rsqrtf(x * x + y * y + z * z);
+    return f3(x * inv, y * inv, z * inv);
+}
+
+// Direction of interior texel (a, b) of an n x n octahedral map.
+__device__ __forceinline__ float3 texel_dir(int a, int b, int n) {
+    const float inv_n = 1.0f / (float)n;
+    return oct_decode(((float)a + 0.5f) * inv_n, ((float)b + 0.5f) * inv_n);
+}
+
+// Source texel of bordered-map texel (y, x) for an (n+2)^2 map: interior texels map to
+// themselves; each edge row/column mirrors the adjacent interior row/column about its
+// midpoint, and each corner takes the diagonally opposite interior corner (the
+// octahedron's fold puts those texels next to each other on the sphere).
+__device__ __forceinline__ int2 border_source(int y, int x, int n) {
+    const int last = n + 1;
+    const bool top = y == 0, bottom = y == last, left = x == 0, right = x == last;
+    if ((top || bottom) && (left || right)) return make_int2(top ? n : 1, left ? n : 1);  // corners
+    if (top) return make_int2(1, last - x);
+    if (bottom) return make_int2(n, last - x);
+    if (left) return make_int2(last - y, 1);
+    if (right) return make_int2(last - y, n);
+    return make_int2(y, x);
+}
+
+// ------------------------------------------------------------------ probe interpolation
+// Normalised irradiance at world point x for unit normal nrm from an irradiance atlas:
+// trilinear over the 8 probes of the grid cell (clamped), weighted by trilinear weight
+// times the probe's history flag, each probe contributing its map's bilinear value at
+// oct(nrm); weights renormalised, 0 when they all vanish.
+__device__ __forceinline__ float3 interpolate_irradiance(const int gd[3], const float go[3], const float gs[3],
+                                                         const float4* irr, const uint8_t* valid, float3 x,
+                                                         float3 nrm) {
+    const float xs[3] = {x.x, x.y, x.z};
+    int base[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float c = fminf(fmaxf((xs[a] - go[a]) / gs[a], 0.f), (float)(gd[a] - 1));
+        int b = (int)floorf(c);
+        b = max(0, min(b, gd[a] - 2));
+        base[a] = b;
+        f[a] = gd[a] > 1 ? c - (float)b : 0.f;
+    }
+    const float2 uv = oct_encode(nrm);
+    const float cx = fmaf(uv.x, (float)kIrrN, 0.5f), cy = fmaf(uv.y, (float)kIrrN, 0.5f);  // 1 + uv*n - 1/2
+    const int x0 = min((int)floorf(cx), kIrrN), y0 = min((int)floorf(cy), kIrrN);
+    const float fx = cx - (float)x0, fy = cy - (float)y0;
+    float sw = 0.f, r = 0.f, g = 0.f, bl = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+        const int ix = min(base[0] + dx, gd[0] - 1), iy = min(base[1] + dy, gd[1] - 1), iz = min(base[2] + dz, gd[2] - 1);
+        const size_t p = ((size_t)iz * gd[1] + iy) * gd[0] + ix;
+        float w = (dx ? f[0] : 1.f - f[0]) * (dy ? f[1] : 1.f - f[1]) * (dz ? f[2] : 1.f - f[2]);
+        if (!__ldg(valid + p)) w = 0.f;
+        if (!(w > 0.f)) continue;
+        const float4* m = irr + p * (kIrrT * kIrrT);
+        const float4 t00 = __ldg(m + y0 * kIrrT + x0), t01 = __ldg(m + y0 * kIrrT + x0 + 1);
+        const float4 t10 = __ldg(m + (y0 + 1) * kIrrT + x0), t11 = __ldg(m + (y0 + 1) * kIrrT + x0 + 1);
+        const float w00 = (1.f - fx) * (1.f - fy), w01 = fx * (1.f - fy), w10 = (1.f - fx) * fy, w11 = fx * fy;
+        r = fmaf(w, w00 * t00.x + w01 * t01.x + w10 * t10.x + w11 * t11.x, r);
+        g = fmaf(w, w00 * t00.y + w01 * t01.y + w10 * t10.y + w11 * t11.y, g);
+        bl = fmaf(w, w00 * t00.z + w01 * t01.z + w10 * t10.z + w11 * t11.z, bl);
+        sw += w;
+    }
+    if (!(sw > 0.f)) return f3(0.f, 0.f, 0.f);
+    const float inv = 1.0f / sw;
+    return f3(r * inv, g * inv, bl * inv);
+}
+
+// ------------------------------------------------------------------ ray set
+// Ray i of R: spherical Fibonacci (z = 1 - (2i+1)/R, azimuth = 2 pi frac(i phi^-1) with the
+// golden fraction in 32-bit fixed point) rotated by the frame rotation.
+__device__ __forceinline__ float3 ray_direction(int i, int R, const float rot[9]) {
+    const uint32_t phase = (uint32_t)i * 2654435769u;
+    float s, c;
+    sincospif((float)phase * 0x1p-31f, &s, &c);  // angle 2 pi phase / 2^32
+    const float a = (float)(2 * i + 1) / (float)R;
+    const float z = 1.f - a;
+    const float r = sqrtf(fmaxf(0.f, a * (2.f - a)));  // sqrt(1 - z^2) without cancellation
+    const float3 d = f3(r * c, r * s, z);
+    return f3(fmaf(rot[0], d.x, fmaf(rot[1], d.y, rot[2] * d.z)), fmaf(rot[3], d.x, fmaf(rot[4], d.y, rot[5] * d.z)),
+              fmaf(rot[6], d.x, fmaf(rot[7], d.y, rot[8] * d.z)));
+}
+
+}  // namespace sdfddgi

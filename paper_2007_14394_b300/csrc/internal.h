@@ -1,0 +1,82 @@
+// internal.h -- structures shared by the library's host code and its kernels.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sdfddgi.h"
+
+namespace sdfddgi {
+
+constexpr int kIrrN = SDFDDGI_IRR_INTERIOR;      // 6
+constexpr int kIrrT = SDFDDGI_IRR_SIDE;          // 8
+constexpr int kDepN = SDFDDGI_DEPTH_INTERIOR;    // 14
+constexpr int kDepT = SDFDDGI_DEPTH_SIDE;        // 16
+constexpr int kIrrTexels = kIrrN * kIrrN;        // 36 interior irradiance texels
+constexpr int kDepTexels = kDepN * kDepN;        // 196 interior depth texels
+
+enum Event : uint8_t { kLeftVolume = 0, kHit = 1, kPastLimit = 2, kExhausted = 3, kNoRay = 255 };
+
+// The signed-distance volume and its material volume as the kernels read them.
+struct VolumeView {
+    const void* sdf;          // float or __half, [nz][ny][nx]
+    const uint4* material;    // 8 x binary16 per voxel (albedo rgb, -, emission rgb, -), or null
+    int nx, ny, nz;
+    int dtype;                // SDFDDGI_F32 / SDFDDGI_F16
+    float h, inv_h;
+    float lo[3];              // world box of the volume
+    float hi[3];
+};
+
+struct LightDev {
+    int type;
+    float v[3];
+    float rgb[3];
+    float range;
+};
+
+struct UpdateParams {
+    VolumeView vol;
+    LightDev lights[SDFDDGI_MAX_LIGHTS];
+    int n_lights;
+    float sky[3];
+    int gdims[3];
+    float gorigin[3];
+    float gspacing[3];
+    int P;                    // probe count
+    int R;                    // rays per probe
+    int max_steps;
+    int depth_exp;
+    float eps_w;              // hit threshold, world units
+    float tmax_w;             // trace limit, world units
+    float hyst;
+    float k_bounce;
+    float bias_w;             // shadow-ray offset, world units
+    float rot[9];             // row-major frame rotation
+    const sdfddgi_probe_state* states;  // device; null = grid positions, all active
+    const float4* prev_irr;   // [P][8][8]
+    const float2* prev_depth; // [P][16][16]
+    const uint8_t* prev_valid;
+    float4* cur_irr;
+    float2* cur_depth;
+    uint8_t* cur_valid;
+    sdfddgi_ray_record* records;  // null or [P][R]
+};
+
+struct SampleParams {
+    int gdims[3];
+    float gorigin[3];
+    float gspacing[3];
+    const float4* irr;
+    const uint8_t* valid;
+    const float* points;
+    const float* normals;
+    float* out;
+    int64_t n;
+};
+
+cudaError_t launch_update(const UpdateParams& p, cudaStream_t stream);
+cudaError_t launch_sample(const SampleParams& p, cudaStream_t stream);
+
+}  // namespace sdfddgi
