@@ -156,9 +156,35 @@ static void sample_material(const or_volume* vol, const double p[3], double albe
 static double g_delta_vox = 2e-4; /* rounding band of distance decisions, voxels */
 static double g_delta_cos = 1e-4; /* rounding band of light-gating decisions */
 
+static double g_t_tol_vox = 1e-3; /* hit-distance tolerance, voxels */
+static double g_t_factor = 8.0;   /* multiple of t_cond that explains a larger difference */
+
 void oracle_set_delta(double delta_vox, double delta_cos) {
     g_delta_vox = delta_vox;
     g_delta_cos = delta_cos;
+}
+
+void oracle_set_t_tolerance(double tol_vox, double factor) {
+    g_t_tol_vox = tol_vox;
+    g_t_factor = factor;
+}
+
+/* Derivative of the trilinear field along d at p (world units); zero across clamped axes. */
+static double sdf_slope(const or_volume* vol, const double p[3], const double d[3]) {
+    int i0[3];
+    double f[3], grad[3] = {0.0, 0.0, 0.0};
+    trilinear_cell(vol, p, i0, f);
+    for (int c = 0; c < 8; ++c) {
+        int e[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+        double v = voxel_sdf(vol, i0[0] + e[0], i0[1] + e[1], i0[2] + e[2]);
+        for (int a = 0; a < 3; ++a) {
+            double w = e[a] ? 1.0 : -1.0;
+            for (int b = 0; b < 3; ++b)
+                if (b != a) w *= e[b] ? f[b] : 1.0 - f[b];
+            grad[a] += w * v;
+        }
+    }
+    return (grad[0] * d[0] + grad[1] * d[1] + grad[2] * d[2]) / vol->h;
 }
 
 /* Sphere tracing (Hart 1996) as the probe update uses it: step by the sampled
@@ -167,26 +193,29 @@ void oracle_set_delta(double delta_vox, double delta_cos) {
  * (EXHAUSTED). `margin` is the closest any of these tests came to the other
  * outcome. With fe >= 0 the path follows the given event (fe) and step count (fs)
  * instead of its own tests; every test so overridden increments *forced, and
- * *hard as well when its margin was at least delta. */
+ * *hard as well when its margin was at least delta. *cond receives the first-order
+ * float32 rounding bound of the returned t (voxels), see oracle_set_t_tolerance. */
 static int32_t trace_path(const or_volume* vol, const double o[3], const double d[3], double eps_vox,
                           double tlimit, int32_t max_steps, int32_t fe, int32_t fs, double* t_out,
-                          int32_t* steps_out, double* margin_vox, int32_t* forced, int32_t* hard) {
-    const double h = vol->h, eps = eps_vox * h, band = g_delta_vox * h;
+                          int32_t* steps_out, double* margin_vox, int32_t* forced, int32_t* hard, double* cond) {
+    const double h = vol->h, eps = eps_vox * h, band = g_delta_vox * h, u32 = ldexp(1.0, -24);
     const double lo[3] = {vol->origin[0], vol->origin[1], vol->origin[2]};
     const double hi[3] = {vol->origin[0] + vol->nx * h, vol->origin[1] + vol->ny * h,
                           vol->origin[2] + vol->nz * h};
-    double t = 0.0, margin = HUGE_MARGIN;
+    double t = 0.0, margin = HUGE_MARGIN, dt = 0.0;
 #define DECIDE(natural, wanted_if_forced, m)                      \
     ((fe < 0) ? (natural) : ((wanted_if_forced) != (natural)      \
                                  ? (++*forced, *hard += (m) >= band, (wanted_if_forced)) \
                                  : (natural)))
+    *cond = 0.0;
     for (int32_t s = 0; s < max_steps; ++s) {
         double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
         int outside = 0;
-        double m_out = HUGE_MARGIN;
+        double m_out = HUGE_MARGIN, pmax = 0.0;
         for (int a = 0; a < 3; ++a) {
             if (p[a] < lo[a] || p[a] > hi[a]) outside = 1;
             m_out = fmin(m_out, fmin(fabs(p[a] - lo[a]), fabs(p[a] - hi[a])));
+            pmax = fmax(pmax, fmax(fabs(p[a]), fabs(p[a] - lo[a])));
         }
         margin = fmin(margin, m_out);
         if (DECIDE(outside, fe == OR_LEFT_VOLUME && s == fs, m_out)) {
@@ -202,8 +231,12 @@ static int32_t trace_path(const or_volume* vol, const double o[3], const double 
             *t_out = t;
             *steps_out = s + 1;
             *margin_vox = margin / h;
+            *cond = dt / h;
             return OR_HIT;
         }
+        /* first-order propagation of a perturbation of t through this step, plus the
+         * float32 rounding of this step's point, sample and sum */
+        dt = dt * fabs(1.0 + sdf_slope(vol, p, d)) + u32 * (2.0 * pmax + 2.0 * fabs(sd) + 2.0 * h + t);
         t += sd;
         double m_lim = fabs(t - tlimit);
         margin = fmin(margin, m_lim);
@@ -222,6 +255,7 @@ static int32_t trace_path(const or_volume* vol, const double o[3], const double 
     *t_out = t;
     *steps_out = max_steps;
     *margin_vox = margin / h;
+    *cond = dt / h;
     return OR_EXHAUSTED;
 }
 
@@ -229,8 +263,9 @@ int32_t oracle_trace(const or_volume* vol, const double o[3], const double d[3],
                      double eps_vox, double tlimit, int32_t max_steps,
                      double* t_out, int32_t* steps_out, double* margin_vox) {
     int32_t forced = 0, hard = 0;
+    double cond;
     return trace_path(vol, o, d, eps_vox, tlimit, max_steps, -1, 0, t_out, steps_out, margin_vox, &forced,
-                      &hard);
+                      &hard, &cond);
 }
 
 static int is_miss(int32_t event) { return event == OR_LEFT_VOLUME || event == OR_PAST_LIMIT; }
@@ -325,9 +360,26 @@ void oracle_sample_irradiance(const or_grid* g, const double* irr, const uint8_t
  * albedo * k * (last frame's normalised irradiance at x for normal n). With a force
  * record, a light's visibility follows the record where this side's own decision
  * (gating or shadow trace) lay within the rounding band. */
+static void shade_at(const or_volume* vol, const or_grid* g, const or_light* lights, int32_t n_lights,
+                     const double* prev_irr, const uint8_t* prev_valid, const double x[3], const double d[3],
+                     const or_force* force, or_ray* rec, int visibility_given, double L_out[3]);
+
 void oracle_shade(const or_volume* vol, const or_grid* g, const or_light* lights, int32_t n_lights,
                   const double* prev_irr, const uint8_t* prev_valid,
                   const double x[3], const double d[3], const or_force* force, or_ray* rec) {
+    shade_at(vol, g, lights, n_lights, prev_irr, prev_valid, x, d, force, rec, 0, rec->L);
+    /* sensitivity of the radiance to the hit distance, visibility held fixed */
+    const double step = 1e-3 * vol->h;
+    double xp[3] = {x[0] + step * d[0], x[1] + step * d[1], x[2] + step * d[2]}, Lp[3];
+    shade_at(vol, g, lights, n_lights, prev_irr, prev_valid, xp, d, NULL, rec, 1, Lp);
+    for (int k = 0; k < 3; ++k) rec->dLdt[k] = (Lp[k] - rec->L[k]) / step;
+}
+
+/* The shading of one hit point. visibility_given: take each light's visibility from
+ * rec->lit_mask (no shadow ray, no bookkeeping) instead of tracing it. */
+static void shade_at(const or_volume* vol, const or_grid* g, const or_light* lights, int32_t n_lights,
+                     const double* prev_irr, const uint8_t* prev_valid, const double x[3], const double d[3],
+                     const or_force* force, or_ray* rec, int visibility_given, double L_out[3]) {
     const double h = vol->h;
     double grad[3];
     for (int a = 0; a < 3; ++a) {
@@ -375,14 +427,20 @@ void oracle_shade(const or_volume* vol, const or_grid* g, const or_light* lights
             for (int a = 0; a < 3; ++a) ldir[a] = Ls[a] / ds;
             tlimit = ds;
         }
+        if (visibility_given) {
+            if ((rec->lit_mask >> l) & 1u)
+                for (int k = 0; k < 3; ++k) direct[k] += li->rgb[k] * scale;
+            continue;
+        }
         rec->margin_decision = fmin(rec->margin_decision, m_gate);
         int lit = 0;
         double m_sh = HUGE_MARGIN;
         if (gate) {
             double ts;
             int32_t st, f0 = 0, h0 = 0;
+            double c0;
             int32_t ev = trace_path(vol, xs, ldir, g->eps_vox, tlimit, g->max_steps, -1, 0, &ts, &st, &m_sh,
-                                    &f0, &h0);
+                                    &f0, &h0, &c0);
             rec->traced_mask |= 1u << l;
             rec->shadow_steps += st;
             rec->margin_shadow = fmin(rec->margin_shadow, m_sh);
@@ -405,7 +463,7 @@ void oracle_shade(const or_volume* vol, const or_grid* g, const or_light* lights
     double indirect[3] = {0.0, 0.0, 0.0};
     if (g->k_bounce != 0.0) oracle_sample_irradiance(g, prev_irr, prev_valid, x, n, indirect);
     for (int k = 0; k < 3; ++k)
-        rec->L[k] = emission[k] + albedo[k] / kPi * direct[k] + g->k_bounce * albedo[k] * indirect[k];
+        L_out[k] = emission[k] + albedo[k] / kPi * direct[k] + g->k_bounce * albedo[k] * indirect[k];
 }
 
 /* ------------------------------------------------ probe update (Sec. 3.3, Eq. 3) */
@@ -480,13 +538,26 @@ static void update_one_probe(const or_volume* vol, const or_grid* g, const or_li
         const or_force* fi = force ? &force[i] : NULL;
         double t;
         rec.natural_event = trace_path(vol, o, d, g->eps_vox, tmax, g->max_steps, -1, 0, &t,
-                                       &rec.natural_steps, &rec.margin_primary, &rec.forced, &rec.hard);
+                                       &rec.natural_steps, &rec.margin_primary, &rec.forced, &rec.hard,
+                                       &rec.t_cond);
         rec.event = rec.natural_event;
         rec.steps = rec.natural_steps;
         if (fi && (fi->event != rec.natural_event || fi->steps != rec.natural_steps)) {
             double m_unused;
             rec.event = trace_path(vol, o, d, g->eps_vox, tmax, g->max_steps, fi->event, fi->steps, &t,
-                                   &rec.steps, &m_unused, &rec.forced, &rec.hard);
+                                   &rec.steps, &m_unused, &rec.forced, &rec.hard, &rec.t_cond);
+        }
+        rec.t_own = t;
+        if (fi && !is_miss(rec.event)) {
+            double diff = fabs(t - (double)fi->t) / h;
+            if (diff > g_t_tol_vox) {
+                if (diff <= g_t_factor * rec.t_cond) {
+                    t = (double)fi->t; /* ill-conditioned ray: continue from the other side's hit point */
+                    rec.t_forced = 1;
+                } else {
+                    rec.hard++;
+                }
+            }
         }
         rec.t = t;
         if (is_miss(rec.event)) {

@@ -15,6 +15,7 @@ import workloads as W
 DELTA_VOX = 2e-4      # width of the rounding band of distance decisions, voxels
 DELTA_COS = 1e-4      # width of the rounding band of light-gating decisions
 T_TOL_VOX = 1e-3      # hit-distance tolerance, voxels
+T_COND_FACTOR = 8.0   # a larger hit-distance difference must be within this multiple of the ray's rounding bound
 REL_TOL = 1e-4        # float32 irradiance / moment relative tolerance
 
 
@@ -79,7 +80,45 @@ def force_from_records(rec: np.ndarray) -> np.ndarray:
     f["event"] = rec["event"].astype(np.int32)
     f["steps"] = rec["steps"].astype(np.int32)
     f["lit_mask"] = rec["lit_mask"]
+    f["t"] = rec["t"]
     return f
+
+
+EPS_COS = 5e-7           # bound of the float32 error of a texel-direction . ray-direction cosine
+WEIGHT_ERR_FACTOR = 4.0  # safety factor on the first-order weight-error term
+TRACE_ERR_FACTOR = 2.0   # safety factor on the first-order effect of the measured hit-distance differences
+
+
+def texel_geometry(rays: int, rot, exponent: int):
+    """Per map (irradiance [6,6], depth [14,14]): the oracle-side cosines c [n,n,R] of every interior
+    texel with every ray, the derivative of the weight w(c) (1 or p c^(p-1), 0 below the cutoff band)
+    and the weight sums [n,n]. A texel whose sum lies inside the rounding band of the cosine cutoff
+    (irradiance) or of float32 underflow of cos^p (depth) makes 'no ray reached it' rounding-sensitive."""
+    d = np.array([O.sf_dir(i, rays) for i in range(rays)]) @ np.asarray(rot, np.float64).T
+    out = []
+    for n, e in ((O.IRR_N, 1), (O.DEP_N, exponent)):
+        u = np.array([[O.oct_decode([(a + 0.5) / n, (b + 0.5) / n]) for a in range(n)] for b in range(n)])
+        c = u @ d.T
+        cp = np.maximum(c, 0.0)
+        dw = np.where(c > -EPS_COS, e * cp ** (e - 1) if e > 1 else 1.0, 0.0)
+        w_ = cp ** e
+        out.append((w_, dw, w_.sum(axis=-1)))
+    return out
+
+
+def conditioning(geo, vals, dvals, o_map, active):
+    """First-order sensitivities of each texel mean m_j = sum w_ij v_i / sum w_ij:
+    to an absolute error of 1 in every cosine, sum_i |dw/dc|_ij |v_i - m_j| / sum_i w_ij, and to the
+    measured per-ray value differences dvals, sum_i w_ij dv_i / sum_i w_ij.
+    vals, dvals [P,R,C]; o_map [P,n,n,C]."""
+    w_, dw, sw = geo
+    cw, ct = np.zeros_like(o_map), np.zeros_like(o_map)
+    safe = np.where(sw > 0, sw, 1.0)
+    for p in np.flatnonzero(active):
+        diff = np.abs(vals[p][None, None, :, :] - o_map[p][:, :, None, :])     # [n,n,R,C]
+        cw[p] = (dw[..., None] * diff).sum(axis=2) / safe[..., None]
+        ct[p] = np.einsum("abr,rc->abc", w_, dvals[p]) / safe[..., None]
+    return cw, ct
 
 
 # ------------------------------------------------------------------------- GPU side
@@ -130,9 +169,13 @@ def rel_err(g, o):
     return np.abs(g - o) / np.maximum(np.abs(o), floor)
 
 
-def compare(w: Workload, gpu_state, gpu_rec, orc, subset, h_vox: float):
+IRR_SW_BAND = 1e-5     # irradiance texels whose cosine sum is below this are rounding-sensitive
+DEP_SW_BAND = 1e-30    # depth texels whose cos^p sum is below this underflow in float32
+
+
+def compare(w: Workload, gpu_state, gpu_rec, orc, subset, h_vox: float, rot=None):
     """Statistics of one update over `subset` probes. gpu_rec: [P,R] records; orc: oracle output
-    (forced by the GPU's records) for `subset`."""
+    (forced by the GPU's records) for `subset`; rot: the frame rotation (for the texel bands)."""
     irr_g, dep_g, val_g = gpu_state
     rays_o = orc["rays"]
     rec = gpu_rec[subset]
@@ -149,8 +192,13 @@ def compare(w: Workload, gpu_state, gpu_rec, orc, subset, h_vox: float):
     st["class_agree_nongrazing"] = float((miss_g == miss_o)[ok].mean()) if ok.any() else 1.0
     st["grazing_frac"] = float(grazing[act].mean()) if n_rays else 0.0
     same_path = act & (rays_o["hard"] == 0)
-    dt = np.abs(rec["t"].astype(np.float64) - rays_o["t"]) / h_vox
-    st["t_err_vox_max"] = float(dt[same_path].max()) if same_path.any() else 0.0
+    dt_own = np.abs(rec["t"].astype(np.float64) - rays_o["t_own"]) / h_vox
+    st["t_within_tol_frac"] = float((dt_own[act] <= T_TOL_VOX).mean()) if n_rays else 1.0
+    st["t_forced_frac"] = float((rays_o["t_forced"][act] > 0).mean()) if n_rays else 0.0
+    ratio = dt_own / np.maximum(rays_o["t_cond"], 1e-300)
+    forced_t = act & (rays_o["t_forced"] > 0)
+    st["t_forced_max_ratio"] = float(ratio[forced_t].max()) if forced_t.any() else 0.0
+    st["t_err_vox_max"] = float(dt_own[act & (rays_o["t_forced"] == 0) & same_path].max()) if n_rays else 0.0
     st["event_equal"] = bool(np.array_equal(rec["event"][act].astype(np.int32), rays_o["event"][act]))
     st["steps_equal"] = bool(np.array_equal(rec["steps"][act].astype(np.int32), rays_o["steps"][act]))
     st["lit_equal"] = bool(np.array_equal(rec["lit_mask"][act], rays_o["lit_mask"][act]))
@@ -158,9 +206,36 @@ def compare(w: Workload, gpu_state, gpu_rec, orc, subset, h_vox: float):
     st["ray_L_rel_max"] = float(Lerr.max())
     ig, io = irr_g[subset][:, 1:-1, 1:-1, :3], orc["irr"][subset][:, 1:-1, 1:-1, :3]
     dg, do = dep_g[subset][:, 1:-1, 1:-1], orc["depth"][subset][:, 1:-1, 1:-1]
-    st["irr_rel_max"] = float(rel_err(ig, io).max()) if ig.size else 0.0
-    st["depth_rel_max"] = float(rel_err(dg, do).max()) if dg.size else 0.0
-    st["alpha_equal"] = bool(np.array_equal(irr_g[subset][..., 3], orc["irr"][subset][..., 3]))
+    keep_i = np.ones(ig.shape[1:3], bool)
+    keep_d = np.ones(dg.shape[1:3], bool)
+    geo = None
+    if rot is not None:
+        geo = texel_geometry(w.params["rays"], rot, w.params["depth_exponent"])
+        keep_i, keep_d = geo[0][2] >= IRR_SW_BAND, geo[1][2] >= DEP_SW_BAND
+    st["texels_banded"] = int((~keep_i).sum() + (~keep_d).sum())
+    # values the texels average: radiance, and (distance, distance^2) with misses at t_max
+    tmax = w.params["tmax_vox"] * h_vox
+    ev = rays_o["event"]
+    that = np.where(O.is_miss(ev), tmax, np.minimum(rays_o["t"], tmax))
+    vals = (rays_o["L"], np.stack([that, that * that], axis=-1))
+    # first-order effect on each ray's values of the measured hit-distance difference (t within tolerance)
+    dt_w = np.where(O.is_miss(ev), 0.0, np.abs(rec["t"].astype(np.float64) - rays_o["t"]))
+    dvals = (np.abs(rays_o["dLdt"]) * dt_w[..., None], np.stack([dt_w, 2.0 * that * dt_w], axis=-1))
+    for name, g_map, o_map, keep, k in (("irr", ig, io, keep_i, 0), ("depth", dg, do, keep_d, 1)):
+        cw = ct = np.zeros_like(o_map)
+        if geo is not None:
+            cw, ct = conditioning(geo[k], vals[k], dvals[k], o_map, act.any(axis=1))
+        g_k, o_k = g_map[:, keep], o_map[:, keep]
+        prop = WEIGHT_ERR_FACTOR * EPS_COS * cw[:, keep] + TRACE_ERR_FACTOR * ct[:, keep]
+        tol = REL_TOL * np.abs(o_k) + prop
+        err = np.abs(g_k.astype(np.float64) - o_k)
+        well = prop <= 0.1 * REL_TOL * np.abs(o_k)
+        st[f"{name}_tol_ratio_max"] = float((err / np.maximum(tol, 1e-300)).max()) if err.size else 0.0
+        st[f"{name}_rel_max"] = float(rel_err(g_k, o_k)[well].max()) if well.any() else 0.0
+        st[f"{name}_rel_max_all"] = float(rel_err(g_k, o_k).max()) if err.size else 0.0
+        st[f"{name}_illcond_texels"] = int((~well).sum())
+    ag, ao = irr_g[subset][:, 1:-1, 1:-1, 3], orc["irr"][subset][:, 1:-1, 1:-1, 3]
+    st["alpha_equal"] = bool(np.array_equal(ag[:, keep_i], ao[:, keep_i]))
     st["valid_equal"] = bool(np.array_equal(val_g[subset], orc["valid"][subset]))
     return st
 

@@ -15,7 +15,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from harness import (REL_TOL, T_TOL_VOX, DELTA_VOX, DELTA_COS, GpuVolume, border_is_mirror, compare,
+from harness import (REL_TOL, T_TOL_VOX, T_COND_FACTOR, DELTA_VOX, DELTA_COS, GpuVolume, border_is_mirror, compare,
                      force_from_records, make_workload, oracle_grid, oracle_scene)
 
 pytestmark = pytest.mark.gpu
@@ -24,6 +24,7 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(autouse=True)
 def _band(cuda_device):
     O.set_delta(DELTA_VOX, DELTA_COS)
+    O.set_t_tolerance(T_TOL_VOX, T_COND_FACTOR)
 
 
 def run_and_compare(w, frames=1, subset=None, seed_rot=7, prev_gpu=None, record_check=False):
@@ -44,7 +45,7 @@ def run_and_compare(w, frames=1, subset=None, seed_rot=7, prev_gpu=None, record_
             orc = O.update(sc, g, w.lights, rot, w.states,
                            prev=(prev[0].astype(np.float64), prev[1].astype(np.float64), prev[2]),
                            subset=sub, force=force_from_records(rec[sub]))
-            s = compare(w, cur, rec, orc, sub, h)
+            s = compare(w, cur, rec, orc, sub, h, rot=rot)
             s["border_irr"] = border_is_mirror(cur[0][sub])
             s["border_depth"] = border_is_mirror(cur[1][sub])
             stats.append(s)
@@ -63,8 +64,11 @@ def assert_bar(s, label=""):
     assert s["hard"] == 0, (label, s)
     assert s["class_agree_nongrazing"] >= 0.999, (label, s)
     assert s["t_err_vox_max"] <= T_TOL_VOX, (label, s)
-    assert s["irr_rel_max"] <= REL_TOL, (label, s)
-    assert s["depth_rel_max"] <= REL_TOL, (label, s)
+    assert s["t_within_tol_frac"] >= 0.99, (label, s)      # ill-conditioned rays are the exception
+    # relative 1e-4 on every well-conditioned texel; on all texels, 1e-4 relative plus the
+    # first-order error of the float32 cosine weights
+    assert s["irr_rel_max"] <= REL_TOL and s["irr_tol_ratio_max"] <= 1.0, (label, s)
+    assert s["depth_rel_max"] <= REL_TOL and s["depth_tol_ratio_max"] <= 1.0, (label, s)
     assert s["alpha_equal"] and s["valid_equal"], (label, s)
     assert s["border_irr"] and s["border_depth"], (label, s)
 
