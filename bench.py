@@ -243,8 +243,10 @@ def oracle_sample(pr, scene, baked, states, n_probes, seed=0, frame=0, threads=0
 
 def cpu_baseline(pr, scene, baked, states, budget_s=15.0):
     cores = os.cpu_count() or 1
-    dt, rays = oracle_sample(pr, scene, baked, states, max(4, cores))       # calibrate
-    n = int(max(4, min(len(states), cores * 4, (budget_s / max(dt, 1e-3)) * max(4, cores))))
+    n_active = int((states["flags"] & 1).sum())
+    calib = max(4, cores)
+    dt, rays = oracle_sample(pr, scene, baked, states, calib)       # calibrate the sample size
+    n = int(max(4, min(n_active, budget_s / max(dt, 1e-3) * calib)))
     dt, rays = oracle_sample(pr, scene, baked, states, n, seed=1)
     return {"value": rays / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} random active probes of {pr.name} (frame 0, {pr.rays} rays each), "
