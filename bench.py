@@ -33,6 +33,7 @@ METRIC = "probe-rays/s & ms per probe-volume update; learned vs plain rays at eq
 UNIT = "probe-rays/s"
 WORKLOAD = "open256"
 L2_FLUSH_BYTES = 512 << 20
+KERNELS_PER_UPDATE = 4  # primary trace, hit preparation, shadow trace, gather
 
 
 def peaks():
@@ -208,7 +209,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded scene, baked on the host)", "config": workload_config(pr, rays_per_step),
-        "gpu_launches": args.steps,
+        "gpu_launches": KERNELS_PER_UPDATE * args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": P * 16,
                 "d2h_bytes_per_step": P * (8 * 8 * 4 * 4 + 16 * 16 * 2 * 4 + 1), "ms_per_step": e2e_ms / args.steps},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -17,6 +17,8 @@ struct sdfddgi_scene {
     int device = 0;
     void* sdf = nullptr;
     size_t sdf_bytes = 0;
+    void* quads = nullptr;  // xy-quad copy of the SDF read by the trace kernels
+    size_t quads_bytes = 0;
     void* material = nullptr;
     size_t material_bytes = 0;
     int dims[3] = {0, 0, 0};
@@ -39,6 +41,18 @@ struct sdfddgi_volume {
     uint8_t* valid[2] = {nullptr, nullptr};
     sdfddgi_probe_state* states = nullptr;  // staging for host-side probe states
     int cur = 0;
+    // per-ray scratch of the staged update (P * R entries each) and the shadow-task list
+    float* ray_t = nullptr;
+    uint32_t* ray_es = nullptr;
+    float4* ray_n = nullptr;
+    float4* ray_alb = nullptr;
+    float4* ray_base = nullptr;
+    uint32_t* ray_lit = nullptr;
+    uint32_t* ray_ssteps = nullptr;
+    uint32_t* counters = nullptr;
+    uint32_t* tasks = nullptr;
+    size_t task_capacity = 0;
+    float* weights = nullptr;  // texel weights of the frame's ray set and their column sums
 };
 
 namespace {
@@ -87,6 +101,41 @@ void free_volume_buffers(sdfddgi_volume* v) {
     }
     cudaFree(v->states);
     v->states = nullptr;
+    void* scratch[] = {v->ray_t, v->ray_es, v->ray_n, v->ray_alb, v->ray_base, v->ray_lit, v->ray_ssteps,
+                       v->counters, v->tasks, v->weights};
+    for (void* q : scratch) cudaFree(q);
+    v->weights = nullptr;
+    v->ray_t = nullptr;
+    v->ray_es = nullptr;
+    v->ray_n = v->ray_alb = v->ray_base = nullptr;
+    v->ray_lit = v->ray_ssteps = v->counters = v->tasks = nullptr;
+    v->task_capacity = 0;
+}
+
+int alloc_scratch(sdfddgi_volume* v) {
+    const size_t n = (size_t)v->P * v->desc.rays_per_probe;
+    int rc = alloc((void**)&v->ray_t, n * sizeof(float));
+    if (!rc) rc = alloc((void**)&v->ray_es, n * sizeof(uint32_t));
+    if (!rc) rc = alloc((void**)&v->ray_n, n * sizeof(float4));
+    if (!rc) rc = alloc((void**)&v->ray_alb, n * sizeof(float4));
+    if (!rc) rc = alloc((void**)&v->ray_base, n * sizeof(float4));
+    if (!rc) rc = alloc((void**)&v->ray_lit, n * sizeof(uint32_t));
+    if (!rc) rc = alloc((void**)&v->ray_ssteps, n * sizeof(uint32_t));
+    if (!rc) rc = alloc((void**)&v->counters, 4 * sizeof(uint32_t));
+    if (!rc) rc = alloc((void**)&v->weights, (size_t)(v->desc.rays_per_probe + 1) * kTexels * sizeof(float));
+    return rc;
+}
+
+// The shadow-task list holds at most one task per (ray, light) pair.
+int ensure_task_capacity(sdfddgi_volume* v, int n_lights) {
+    const size_t need = (size_t)v->P * v->desc.rays_per_probe * (size_t)(n_lights > 0 ? n_lights : 1);
+    if (need <= v->task_capacity) return SDFDDGI_OK;
+    cudaFree(v->tasks);
+    v->tasks = nullptr;
+    v->task_capacity = 0;
+    int rc = alloc((void**)&v->tasks, need * sizeof(uint32_t));
+    if (!rc) v->task_capacity = need;
+    return rc;
 }
 
 uint64_t splitmix64_next(uint64_t* state) {
@@ -121,6 +170,7 @@ SDFDDGI_API int sdfddgi_create_scene(sdfddgi_scene** out) {
 SDFDDGI_API void sdfddgi_destroy_scene(sdfddgi_scene* s) {
     if (!s) return;
     cudaFree(s->sdf);
+    cudaFree(s->quads);
     cudaFree(s->material);
     delete s;
 }
@@ -155,6 +205,17 @@ SDFDDGI_API int sdfddgi_upload_sdf(sdfddgi_scene* s, const void* sdf, const int3
         s->sdf_bytes = sdf_bytes;
     }
     CUDA_TRY(cudaMemcpyAsync(s->sdf, sdf, sdf_bytes, cudaMemcpyDefault, st));
+    const size_t qb = quad_bytes(dtype, n);
+    if (s->quads_bytes != qb) {
+        cudaFree(s->quads);
+        s->quads = nullptr;
+        s->quads_bytes = 0;
+        s->has_sdf = false;
+        int rc = alloc(&s->quads, qb);
+        if (rc) return rc;
+        s->quads_bytes = qb;
+    }
+    CUDA_TRY(build_quads(s->sdf, s->quads, dtype, dims, st));
     if (material) {
         if (s->material_bytes != mat_bytes) {
             cudaFree(s->material);
@@ -230,6 +291,8 @@ SDFDDGI_API int sdfddgi_create_volume(const sdfddgi_volume_desc* d, sdfddgi_scen
         P *= d->dims[a];
     }
     if (P > INT32_MAX) return fail(SDFDDGI_ERR_INVALID_ARG, "create_volume: %lld probes exceed 2^31-1", (long long)P);
+    if (P * (int64_t)(d->rays_per_probe > 0 ? d->rays_per_probe : 1) > ((int64_t)1 << 27))
+        return fail(SDFDDGI_ERR_INVALID_ARG, "create_volume: probes x rays_per_probe exceeds 2^27");
     if (d->rays_per_probe < 1 || d->rays_per_probe > SDFDDGI_MAX_RAYS)
         return fail(SDFDDGI_ERR_INVALID_ARG, "create_volume: rays_per_probe %d outside [1, %d]", d->rays_per_probe,
                     SDFDDGI_MAX_RAYS);
@@ -260,6 +323,7 @@ SDFDDGI_API int sdfddgi_create_volume(const sdfddgi_volume_desc* d, sdfddgi_scen
         if (!rc) rc = alloc((void**)&v->valid[k], (size_t)P);
     }
     if (!rc) rc = alloc((void**)&v->states, sizeof(sdfddgi_probe_state) * P);
+    if (!rc) rc = alloc_scratch(v);
     if (rc) {
         free_volume_buffers(v);
         delete v;
@@ -339,6 +403,7 @@ SDFDDGI_API int sdfddgi_update_probes(sdfddgi_volume* v, uint32_t frame, const f
     }
     VolumeView& vol = p.vol;
     vol.sdf = s->sdf;
+    vol.quads = s->quads;
     vol.material = s->has_material ? static_cast<const uint4*>(s->material) : nullptr;
     vol.nx = s->dims[0];
     vol.ny = s->dims[1];
@@ -377,6 +442,19 @@ SDFDDGI_API int sdfddgi_update_probes(sdfddgi_volume* v, uint32_t frame, const f
     p.cur_depth = v->depth[next];
     p.cur_valid = v->valid[next];
     p.records = records;
+    int rc = ensure_task_capacity(v, s->n_lights);
+    if (rc) return rc;
+    p.ray_t = v->ray_t;
+    p.ray_es = v->ray_es;
+    p.ray_n = v->ray_n;
+    p.ray_alb = v->ray_alb;
+    p.ray_base = v->ray_base;
+    p.ray_lit = v->ray_lit;
+    p.ray_ssteps = v->ray_ssteps;
+    p.tasks = v->tasks;
+    p.task_capacity = (uint32_t)(v->task_capacity < 0xffffffffu ? v->task_capacity : 0xffffffffu);
+    p.counters = v->counters;
+    p.weights = v->weights;
     cudaError_t e = launch_update(p, st);
     if (e != cudaSuccess) return fail(SDFDDGI_ERR_CUDA, "update_probes: launch failed: %s", cudaGetErrorString(e));
     v->cur = next;

@@ -42,26 +42,31 @@ __device__ __forceinline__ Cell cell_of(const VolumeView& v, float3 p) {
     return c;
 }
 
-template <typename T>
-__device__ __forceinline__ float ld_sdf(const T* s, size_t i);
-template <>
-__device__ __forceinline__ float ld_sdf<float>(const float* s, size_t i) { return __ldg(s + i); }
-template <>
-__device__ __forceinline__ float ld_sdf<__half>(const __half* s, size_t i) { return __half2float(__ldg(s + i)); }
-
 __device__ __forceinline__ float lerp(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+// The four corners (x,y) (x+1,y) (x,y+1) (x+1,y+1) of one z slice of a cell, from the
+// xy-quad store (one vector load).
+template <typename T>
+__device__ __forceinline__ float4 ld_quad(const void* quads, size_t i);
+template <>
+__device__ __forceinline__ float4 ld_quad<float>(const void* quads, size_t i) {
+    return __ldg(static_cast<const float4*>(quads) + i);
+}
+template <>
+__device__ __forceinline__ float4 ld_quad<__half>(const void* quads, size_t i) {
+    const uint2 r = __ldg(static_cast<const uint2*>(quads) + i);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
 
 template <typename T>
 __device__ __forceinline__ float sample_sdf(const VolumeView& v, float3 p) {
     const Cell c = cell_of(v, p);
-    const T* s = static_cast<const T*>(v.sdf);
-    const size_t sy = (size_t)v.nx, sz = (size_t)v.nx * v.ny, b = c.base;
-    const float c000 = ld_sdf(s, b), c100 = ld_sdf(s, b + 1);
-    const float c010 = ld_sdf(s, b + sy), c110 = ld_sdf(s, b + sy + 1);
-    const float c001 = ld_sdf(s, b + sz), c101 = ld_sdf(s, b + sz + 1);
-    const float c011 = ld_sdf(s, b + sz + sy), c111 = ld_sdf(s, b + sz + sy + 1);
-    const float x00 = lerp(c000, c100, c.fx), x10 = lerp(c010, c110, c.fx);
-    const float x01 = lerp(c001, c101, c.fx), x11 = lerp(c011, c111, c.fx);
+    const float4 q0 = ld_quad<T>(v.quads, c.base);                              // slice z
+    const float4 q1 = ld_quad<T>(v.quads, c.base + (size_t)v.nx * v.ny);        // slice z + 1
+    const float x00 = lerp(q0.x, q0.y, c.fx), x10 = lerp(q0.z, q0.w, c.fx);
+    const float x01 = lerp(q1.x, q1.y, c.fx), x11 = lerp(q1.z, q1.w, c.fx);
     return lerp(lerp(x00, x10, c.fy), lerp(x01, x11, c.fy), c.fz);
 }
 

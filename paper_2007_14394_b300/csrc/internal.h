@@ -21,6 +21,7 @@ enum Event : uint8_t { kLeftVolume = 0, kHit = 1, kPastLimit = 2, kExhausted = 3
 // The signed-distance volume and its material volume as the kernels read them.
 struct VolumeView {
     const void* sdf;          // float or __half, [nz][ny][nx]
+    const void* quads;        // xy-quads of the same values: float4 or 4 x __half per voxel
     const uint4* material;    // 8 x binary16 per voxel (albedo rgb, -, emission rgb, -), or null
     int nx, ny, nz;
     int dtype;                // SDFDDGI_F32 / SDFDDGI_F16
@@ -62,7 +63,21 @@ struct UpdateParams {
     float2* cur_depth;
     uint8_t* cur_valid;
     sdfddgi_ray_record* records;  // null or [P][R]
+    // per-ray scratch of the staged update, index k = probe * R + ray
+    float* ray_t;             // hit distance (t_max for misses)
+    uint32_t* ray_es;         // event | steps << 8
+    float4* ray_n;            // normal at the hit
+    float4* ray_alb;          // albedo
+    float4* ray_base;         // emission + k * albedo * last-frame irradiance
+    uint32_t* ray_lit;        // visible-light mask
+    uint32_t* ray_ssteps;     // shadow steps
+    uint32_t* tasks;          // shadow tasks (k << 5 | light)
+    uint32_t task_capacity;
+    uint32_t* counters;       // [0] primary pool, [1] task count, [2] shadow pool, [3] task overflow
+    float* weights;           // [R][kTexels] texel weights of the frame's ray set, then [kTexels] column sums
 };
+
+constexpr int kTexels = kIrrTexels + kDepTexels;  // 232 gather rows: irradiance texels first
 
 struct SampleParams {
     int gdims[3];
@@ -78,5 +93,7 @@ struct SampleParams {
 
 cudaError_t launch_update(const UpdateParams& p, cudaStream_t stream);
 cudaError_t launch_sample(const SampleParams& p, cudaStream_t stream);
+size_t quad_bytes(int dtype, size_t n_voxels);
+cudaError_t build_quads(const void* sdf, void* quads, int dtype, const int dims[3], cudaStream_t stream);
 
 }  // namespace sdfddgi

@@ -1,32 +1,33 @@
-// update.cu -- the fused per-probe update kernel (Sec. 3.3 of Hu et al., arXiv 2007.14394).
+// update.cu -- the per-frame probe update (Sec. 3.3 of Hu et al., arXiv 2007.14394) as
+// four stages over device-wide work pools:
 //
-// One CTA per probe; the probe's rays are processed in chunks of blockDim rays.
-//  1. primary traces   -- a lane-persistent pool: every lane takes the next ray from a
-//                         shared counter as soon as its current trace ends, so a warp keeps
-//                         all its lanes stepping while trace lengths differ wildly;
-//  2. hit preparation  -- one lane per ray: normal, material, last-frame irradiance
-//                         (multi-bounce term) and the set of lights that can reach the hit;
-//                         the (ray, light) pairs are compacted into a shadow-task list;
-//  3. shadow traces    -- the same lane-persistent pool over the task list; a visible light
-//                         sets its bit in the ray's mask (atomicOr: order-independent);
-//  4. finalize         -- one lane per ray sums its visible lights in light order
-//                         (deterministic) and leaves radiance + clamped distance in shared
-//                         memory, where the paper also keeps its samples;
-//  5. gather (Eq. 3)   -- one thread per octahedral texel averages all samples of the probe
-//                         with cosine (irradiance) or cosine^p (depth moments) weights and
-//                         mixes the result with last frame's texel;
-//  6. borders + store  -- the 1-texel borders are filled in shared memory and each map
-//                         leaves as contiguous 16-byte stores.
+//  1. primary traces   -- a persistent grid; every lane takes the next ray (of any probe)
+//                         as soon as its current sphere trace ends, so all lanes keep
+//                         stepping however much trace lengths differ; tasks come from a
+//                         global counter in batches of 32 per warp;
+//  2. hit preparation  -- one thread per ray: normal, material, last frame's interpolated
+//                         irradiance (the multi-bounce term) and the lights that can reach
+//                         the hit; the (ray, light) pairs are appended to a shadow-task list;
+//  3. shadow traces    -- the same persistent pool over the task list; a visible light sets
+//                         its bit in the ray's mask (atomicOr, order-independent);
+//  4. gather           -- one CTA per probe: each ray's radiance (visible lights summed in
+//                         light order, deterministic) and clamped distance go to shared
+//                         memory, where the paper also keeps its samples; one thread per
+//                         octahedral texel averages them with cosine (irradiance) or
+//                         cosine^p (depth moments) weights (Eq. 3), mixes with last frame's
+//                         texel, fills the 1-texel borders, and each map leaves as
+//                         contiguous 16-byte stores.
+// Device-wide pools pay the latency of the longest ray once per launch instead of once
+// per probe.
 #include "device.cuh"
 
 namespace sdfddgi {
 
-constexpr int kMaxThreads = 256;
+constexpr int kThreads = 256;
+constexpr int kBatch = 32;  // tasks a warp takes from a global pool at once
 
 // c^p for the depth weights; p = 50 (the usual sharpness) as a fixed product chain.
-template <int P>
-__device__ __forceinline__ float pow_fixed(float c) {
-    static_assert(P == 50, "only the fixed exponent 50 has a chain");
+__device__ __forceinline__ float pow50(float c) {
     const float c2 = c * c, c4 = c2 * c2, c8 = c4 * c4, c16 = c8 * c8, c32 = c16 * c16;
     return c32 * c16 * c2;
 }
@@ -45,11 +46,13 @@ struct TraceState {
     float3 o, d;
     float t, tlimit;
     int s;
+    uint32_t aux;  // task payload kept for the completion handler
 };
 
-// Advances a sphere trace by one step (the test sequence of sphere_trace in device.cuh:
-// leave-box, hit, past-limit, budget). Returns the event, or -1 while it continues;
-// on an event, *steps and *t_end receive the step count and the recorded distance.
+// Advances a sphere trace by one step, with the tests of sphere_trace() in device.cuh
+// in the same order (leave the box, hit, pass the limit, spend the budget). Returns the
+// event, or -1 while the trace continues; on an event *steps and *t_end receive the step
+// count and the recorded distance.
 template <typename T>
 __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, float eps, int max_steps,
                                           int* steps, float* t_end) {
@@ -79,111 +82,74 @@ __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, f
     return -1;
 }
 
-// Lane-persistent pool of sphere traces: tasks 0..n-1 are handed out through *counter
-// (one shared atomic per warp and round, for the lanes that need work); init(k, st)
-// sets up trace k, done(k, event, steps, t) consumes its result. Every lane of every
-// warp of the CTA must call this (it uses full-warp votes).
+// Device-wide pool of sphere traces. Tasks 0..n-1 are claimed from *counter by whole
+// warps in batches of kBatch and handed to lanes as they finish their current trace;
+// init(k, st) returns false for a task that needs no trace (it is then complete),
+// done(st, event, steps, t) consumes a finished trace. Every lane of the warp must
+// take part (full-warp votes).
 template <typename T, typename Init, typename Done>
-__device__ __forceinline__ void trace_pool(const VolumeView& v, int n, int* counter, float eps, int max_steps,
-                                           Init init, Done done) {
+__device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint32_t* counter, float eps,
+                                           int max_steps, Init init, Done done) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    int task = -1;
-    bool need = true;
+    uint32_t batch_next = 0, batch_end = 0;  // warp-uniform
+    bool need = true, busy = false, dry = false;
     TraceState st;
     for (;;) {
-        const unsigned want = __ballot_sync(full, need);
+        const unsigned want = __ballot_sync(full, need && !dry);
         if (want) {
-            const int leader = __ffs(want) - 1;
-            int base = 0;
-            if (lane == leader) base = atomicAdd(counter, __popc(want));
-            base = __shfl_sync(full, base, leader);
-            if (need) {
-                const int k = base + __popc(want & ((1u << lane) - 1u));
+            if (batch_next >= batch_end) {
+                uint32_t b = 0;
+                if (lane == 0) b = atomicAdd(counter, (uint32_t)kBatch);
+                b = __shfl_sync(full, b, 0);
+                batch_next = b;
+                batch_end = b + kBatch;
+            }
+            const uint32_t avail = batch_end - batch_next;
+            const uint32_t rank = __popc(want & ((1u << lane) - 1u));
+            if (need && !dry && rank < avail) {
+                const uint32_t k = batch_next + rank;
                 need = false;
-                task = k < n ? k : -1;  // a lane that finds the pool dry stays idle
-                if (task >= 0) {
-                    init(task, st);
+                if (k >= n) {
+                    dry = true;  // the pool is exhausted for this lane
+                } else if (init(k, st)) {
                     st.t = 0.f;
                     st.s = 0;
+                    busy = true;
+                } else {
+                    need = true;  // nothing to trace for this task: take another
                 }
             }
+            batch_next += min((uint32_t)__popc(want), avail);
         }
-        if (!__any_sync(full, task >= 0)) break;
-        if (task >= 0) {
+        if (!__any_sync(full, busy || (need && !dry))) break;
+        if (busy) {
             int steps;
             float t_end;
             const int ev = trace_step<T>(v, st, eps, max_steps, &steps, &t_end);
             if (ev >= 0) {
-                done(task, ev, steps, t_end);
-                task = -1;
+                done(st, ev, steps, t_end);
+                busy = false;
                 need = true;
             }
         }
     }
 }
 
-// Inclusive prefix sum over the CTA (blockDim a multiple of 32, <= 1024).
-__device__ __forceinline__ int block_inclusive_scan(int x, int* s_warp) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+__device__ __forceinline__ float3 probe_origin(const UpdateParams& P, int p, uint32_t* flags) {
+    if (P.states) {
+        const sdfddgi_probe_state st = P.states[p];
+        *flags = st.flags;
+        return f3(st.pos[0], st.pos[1], st.pos[2]);
     }
-    if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        int w = lane < nw ? s_warp[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < nw) s_warp[lane] = w;
-    }
-    __syncthreads();
-    return x + (warp > 0 ? s_warp[warp - 1] : 0);
-}
-
-// Shared-memory layout of one CTA (dynamic part): all R samples, then the per-chunk
-// scratch of chunk = blockDim rays.
-struct Smem {
-    float4* dir;         // [R] ray direction
-    float4* val;         // [R] radiance rgb, clamped distance
-    float* t;            // [chunk] primary hit distance
-    uint32_t* evsteps;   // [chunk] event | steps << 8
-    float4* nrm;         // [chunk] normal
-    float4* alb;         // [chunk] albedo
-    float4* base;        // [chunk] emission + k * albedo * last-frame irradiance
-    float4* xs;          // [chunk] shadow-ray origin
-    uint32_t* lit;       // [chunk] visible-light mask
-    uint32_t* ssteps;    // [chunk] shadow steps
-    uint16_t* tasks;     // [chunk * n_lights] (ray << 5 | light)
-};
-
-__host__ __device__ inline size_t smem_bytes(int R, int chunk, int n_lights) {
-    return (size_t)R * 32 + (size_t)chunk * (4 + 4 + 16 * 4 + 4 + 4) + (size_t)chunk * n_lights * 2 + 16;
-}
-
-__device__ __forceinline__ Smem carve(unsigned char* raw, int R, int chunk) {
-    Smem s;
-    s.dir = reinterpret_cast<float4*>(raw);
-    s.val = s.dir + R;
-    s.nrm = s.val + R;
-    s.alb = s.nrm + chunk;
-    s.base = s.alb + chunk;
-    s.xs = s.base + chunk;
-    s.t = reinterpret_cast<float*>(s.xs + chunk);
-    s.evsteps = reinterpret_cast<uint32_t*>(s.t + chunk);
-    s.lit = s.evsteps + chunk;
-    s.ssteps = s.lit + chunk;
-    s.tasks = reinterpret_cast<uint16_t*>(s.ssteps + chunk);
-    return s;
+    const int ix = p % P.gdims[0], iy = (p / P.gdims[0]) % P.gdims[1], iz = p / (P.gdims[0] * P.gdims[1]);
+    *flags = SDFDDGI_PROBE_ACTIVE;
+    return f3(fmaf((float)ix, P.gspacing[0], P.gorigin[0]), fmaf((float)iy, P.gspacing[1], P.gorigin[1]),
+              fmaf((float)iz, P.gspacing[2], P.gorigin[2]));
 }
 
 // Light l's contribution factor at x with normal n: cos for a directional light,
-// cos * window / d^2 for a point light (0 where the light cannot reach x).
+// cos * window / d^2 for a point light; *gate tells whether the light can reach x.
 __device__ __forceinline__ float light_scale(const LightDev& li, float3 x, float3 n, bool* gate) {
     if (li.type == SDFDDGI_LIGHT_DIRECTIONAL) {
         const float c = dot(n, f3(li.v[0], li.v[1], li.v[2]));
@@ -205,290 +171,379 @@ __device__ __forceinline__ float light_scale(const LightDev& li, float3 x, float
     return c * win / (dist * dist);
 }
 
-template <typename T, int PEXP>
-__global__ void __launch_bounds__(kMaxThreads, 3) probe_update_kernel(const __grid_constant__ UpdateParams P) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ float4 s_irr[kIrrT * kIrrT];
-    __shared__ __align__(16) float2 s_dep[kDepT * kDepT];  // stored out as float4 pairs
-    __shared__ int s_counter[2];
-    __shared__ int s_warp[32];
-    __shared__ int s_ntasks;
-
-    const int chunk = blockDim.x;
-    const Smem S = carve(smem_raw, P.R, chunk);
-    const int p = blockIdx.x;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const VolumeView& V = P.vol;
-    float3 o;
-    uint32_t flags;
-    if (P.states) {
-        const sdfddgi_probe_state st = P.states[p];
-        o = f3(st.pos[0], st.pos[1], st.pos[2]);
-        flags = st.flags;
-    } else {
-        const int ix = p % P.gdims[0], iy = (p / P.gdims[0]) % P.gdims[1], iz = p / (P.gdims[0] * P.gdims[1]);
-        o = f3(fmaf((float)ix, P.gspacing[0], P.gorigin[0]), fmaf((float)iy, P.gspacing[1], P.gorigin[1]),
-               fmaf((float)iz, P.gspacing[2], P.gorigin[2]));
-        flags = SDFDDGI_PROBE_ACTIVE;
-    }
-    const float4* prev_i = P.prev_irr + (size_t)p * (kIrrT * kIrrT);
-    const float2* prev_d = P.prev_depth + (size_t)p * (kDepT * kDepT);
-    float4* cur_i = P.cur_irr + (size_t)p * (kIrrT * kIrrT);
-    float4* cur_d4 = reinterpret_cast<float4*>(P.cur_depth + (size_t)p * (kDepT * kDepT));
-
-    if (!(flags & SDFDDGI_PROBE_ACTIVE)) {  // inactive: keep maps and history, cast nothing
-        for (int k = tid; k < kIrrT * kIrrT; k += nt) cur_i[k] = __ldg(prev_i + k);
-        const float4* pd4 = reinterpret_cast<const float4*>(prev_d);
-        for (int k = tid; k < kDepT * kDepT / 2; k += nt) cur_d4[k] = __ldg(pd4 + k);
-        if (tid == 0) P.cur_valid[p] = P.prev_valid[p];
-        if (P.records)
-            for (int i = tid; i < P.R; i += nt) {
-                sdfddgi_ray_record rec = {};
-                rec.event = kNoRay;
-                P.records[(size_t)p * P.R + i] = rec;
+// ------------------------------------------------------------------ 1. primary traces
+template <typename T>
+__global__ void __launch_bounds__(kThreads) primary_kernel(const __grid_constant__ UpdateParams P) {
+    const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
+    trace_pool<T>(
+        P.vol, n, &P.counters[0], P.eps_w, P.max_steps,
+        [&](uint32_t k, TraceState& st) {
+            const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
+            uint32_t flags;
+            st.o = probe_origin(P, p, &flags);
+            if (!(flags & SDFDDGI_PROBE_ACTIVE)) {
+                P.ray_es[k] = kNoRay;
+                return false;
             }
-        return;
-    }
-    const float hyst = (P.prev_valid[p] && !(flags & SDFDDGI_PROBE_REJECT_HISTORY)) ? P.hyst : 0.f;
-
-    for (int c0 = 0; c0 < P.R; c0 += chunk) {
-        const int nc = min(chunk, P.R - c0);
-        if (tid == 0) {
-            s_counter[0] = 0;
-            s_counter[1] = 0;
-        }
-        __syncthreads();
-
-        // ---- 1. primary traces
-        trace_pool<T>(
-            V, nc, &s_counter[0], P.eps_w, P.max_steps,
-            [&](int k, TraceState& st) {
-                st.o = o;
-                st.d = ray_direction(c0 + k, P.R, P.rot);
-                st.tlimit = P.tmax_w;
-            },
-            [&](int k, int ev, int steps, float t_end) {
-                S.t[k] = t_end;
-                S.evsteps[k] = (uint32_t)ev | ((uint32_t)steps << 8);
-            });
-        __syncthreads();
-
-        // ---- 2. hit preparation and shadow-task compaction (one lane per ray)
-        uint32_t gate = 0;
-        if (tid < nc) {
-            const int i = c0 + tid;
-            const float3 d = ray_direction(i, P.R, P.rot);
-            S.dir[i] = make_float4(d.x, d.y, d.z, 0.f);
-            S.lit[tid] = 0;
-            S.ssteps[tid] = 0;
-            const int ev = (int)(S.evsteps[tid] & 0xffu);
-            if (!is_miss(ev)) {
-                const float3 x = fma3(S.t[tid], d, o);
-                const float hh = 0.5f * V.h;
-                const float gx = sample_sdf<T>(V, f3(x.x + hh, x.y, x.z)) - sample_sdf<T>(V, f3(x.x - hh, x.y, x.z));
-                const float gy = sample_sdf<T>(V, f3(x.x, x.y + hh, x.z)) - sample_sdf<T>(V, f3(x.x, x.y - hh, x.z));
-                const float gz = sample_sdf<T>(V, f3(x.x, x.y, x.z + hh)) - sample_sdf<T>(V, f3(x.x, x.y, x.z - hh));
-                const float glen = sqrtf(gx * gx + gy * gy + gz * gz);
-                const float3 n = glen > 0.f ? f3(gx / glen, gy / glen, gz / glen) : f3(-d.x, -d.y, -d.z);
-                float3 albedo, emission;
-                sample_material(V, x, &albedo, &emission);
-                float3 ind = f3(0.f, 0.f, 0.f);
-                if (P.k_bounce != 0.f)
-                    ind = interpolate_irradiance(P.gdims, P.gorigin, P.gspacing, P.prev_irr, P.prev_valid, x, n);
-                const float3 xs = fma3(P.bias_w, n, x);
-                for (int l = 0; l < P.n_lights; ++l) {
-                    bool g;
-                    light_scale(P.lights[l], x, n, &g);
-                    if (g) gate |= 1u << l;
-                }
-                S.nrm[tid] = make_float4(n.x, n.y, n.z, 0.f);
-                S.alb[tid] = make_float4(albedo.x, albedo.y, albedo.z, 0.f);
-                S.base[tid] = make_float4(emission.x + albedo.x * P.k_bounce * ind.x,
-                                          emission.y + albedo.y * P.k_bounce * ind.y,
-                                          emission.z + albedo.z * P.k_bounce * ind.z, 0.f);
-                S.xs[tid] = make_float4(xs.x, xs.y, xs.z, 0.f);
-            }
-        }
-        const int cnt = __popc(gate);
-        const int incl = block_inclusive_scan(cnt, s_warp);
-        if (tid == nt - 1) s_ntasks = incl;
-        {
-            int pos = incl - cnt;
-            uint32_t g = gate;
-            while (g) {
-                const int l = __ffs(g) - 1;
-                g &= g - 1;
-                S.tasks[pos++] = (uint16_t)((tid << 5) | l);
-            }
-        }
-        __syncthreads();
-
-        // ---- 3. shadow traces toward every light that can reach a hit
-        trace_pool<T>(
-            V, s_ntasks, &s_counter[1], P.eps_w, P.max_steps,
-            [&](int k, TraceState& st) {
-                const uint32_t tk = S.tasks[k];
-                const int r = (int)(tk >> 5), l = (int)(tk & 31u);
-                const LightDev& li = P.lights[l];
-                const float4 xs = S.xs[r];
-                st.o = f3(xs.x, xs.y, xs.z);
-                if (li.type == SDFDDGI_LIGHT_DIRECTIONAL) {
-                    st.d = f3(li.v[0], li.v[1], li.v[2]);
-                    st.tlimit = P.tmax_w;
-                } else {
-                    const float3 Ls = f3(li.v[0], li.v[1], li.v[2]) - st.o;
-                    const float ds = sqrtf(dot(Ls, Ls));
-                    st.d = (1.f / ds) * Ls;
-                    st.tlimit = ds;
-                }
-            },
-            [&](int k, int ev, int steps, float) {
-                const uint32_t tk = S.tasks[k];
-                const int r = (int)(tk >> 5), l = (int)(tk & 31u);
-                atomicAdd(&S.ssteps[r], (uint32_t)steps);
-                if (is_miss(ev)) atomicOr(&S.lit[r], 1u << l);  // occluded by a hit or an exhausted graze
-            });
-        __syncthreads();
-
-        // ---- 4. finalize radiance (one lane per ray, lights in order)
-        if (tid < nc) {
-            const int i = c0 + tid;
-            const float4 d4 = S.dir[i];
-            const uint32_t es = S.evsteps[tid];
-            const int ev = (int)(es & 0xffu);
-            const float t = S.t[tid];
-            float3 L;
-            uint32_t lit = 0;
-            if (is_miss(ev)) {
-                L = f3(P.sky[0], P.sky[1], P.sky[2]);
-            } else {
-                const float3 d = f3(d4.x, d4.y, d4.z);
-                const float3 x = fma3(t, d, o);
-                const float4 n4 = S.nrm[tid];
-                const float3 n = f3(n4.x, n4.y, n4.z);
-                lit = S.lit[tid];
-                float3 direct = f3(0.f, 0.f, 0.f);
-                for (int l = 0; l < P.n_lights; ++l) {
-                    if (!((lit >> l) & 1u)) continue;
-                    bool g;
-                    const float sc = light_scale(P.lights[l], x, n, &g);
-                    direct = fma3(sc, f3(P.lights[l].rgb[0], P.lights[l].rgb[1], P.lights[l].rgb[2]), direct);
-                }
-                const float inv_pi = 0.318309886183790671538f;
-                const float4 a = S.alb[tid], b = S.base[tid];
-                L = f3(fmaf(a.x * inv_pi, direct.x, b.x), fmaf(a.y * inv_pi, direct.y, b.y),
-                       fmaf(a.z * inv_pi, direct.z, b.z));
-            }
-            const float td = is_miss(ev) ? P.tmax_w : fminf(t, P.tmax_w);
-            S.val[i] = make_float4(L.x, L.y, L.z, td);
-            if (P.records) {
-                sdfddgi_ray_record rec;
-                rec.t = t;
-                rec.L[0] = L.x;
-                rec.L[1] = L.y;
-                rec.L[2] = L.z;
-                rec.lit_mask = lit;
-                rec.shadow_steps = S.ssteps[tid];
-                rec.steps = (uint16_t)(es >> 8);
-                rec.event = (uint8_t)ev;
-                rec.reserved0 = 0;
-                rec.reserved1 = 0;
-                P.records[(size_t)p * P.R + i] = rec;
-            }
-        }
-        __syncthreads();
-    }
-
-    // ---- 5. one texel per thread, cosine-lobe gather over all samples (Eq. 3)
-    for (int task = tid; task < kIrrTexels + kDepTexels; task += nt) {
-        if (task < kIrrTexels) {
-            const int a = task % kIrrN, b = task / kIrrN;
-            const float3 u = texel_dir(a, b, kIrrN);
-            float sw = 0.f, r = 0.f, g = 0.f, bl = 0.f;
-            for (int i = 0; i < P.R; ++i) {
-                const float4 di = S.dir[i];
-                const float c = fmaf(u.x, di.x, fmaf(u.y, di.y, u.z * di.z));
-                if (c > 0.f) {
-                    const float4 vi = S.val[i];
-                    sw += c;
-                    r = fmaf(c, vi.x, r);
-                    g = fmaf(c, vi.y, g);
-                    bl = fmaf(c, vi.z, bl);
-                }
-            }
-            const int k = (b + 1) * kIrrT + (a + 1);
-            float4 out = __ldg(prev_i + k);
-            if (sw > 0.f) {
-                const float inv = 1.f / sw, keep = 1.f - hyst;
-                out.x = fmaf(hyst, out.x, keep * (r * inv));
-                out.y = fmaf(hyst, out.y, keep * (g * inv));
-                out.z = fmaf(hyst, out.z, keep * (bl * inv));
-                out.w = 1.f;
-            }
-            s_irr[k] = out;
-        } else {
-            const int j = task - kIrrTexels;
-            const int a = j % kDepN, b = j / kDepN;
-            const float3 u = texel_dir(a, b, kDepN);
-            float sw = 0.f, m1 = 0.f, m2 = 0.f;
-            for (int i = 0; i < P.R; ++i) {
-                const float4 di = S.dir[i];
-                const float c = fmaf(u.x, di.x, fmaf(u.y, di.y, u.z * di.z));
-                if (c > 0.f) {
-                    const float w = PEXP > 0 ? pow_fixed<(PEXP > 0 ? PEXP : 50)>(c) : pow_runtime(c, P.depth_exp);
-                    const float t = S.val[i].w;
-                    sw += w;
-                    m1 = fmaf(w, t, m1);
-                    m2 = fmaf(w, t * t, m2);
-                }
-            }
-            const int k = (b + 1) * kDepT + (a + 1);
-            float2 out = __ldg(prev_d + k);
-            if (sw > 0.f) {
-                const float inv = 1.f / sw, keep = 1.f - hyst;
-                out.x = fmaf(hyst, out.x, keep * (m1 * inv));
-                out.y = fmaf(hyst, out.y, keep * (m2 * inv));
-            }
-            s_dep[k] = out;
-        }
-    }
-    __syncthreads();
-
-    // ---- 6. borders from the interior, then contiguous vector stores
-    for (int k = tid; k < kIrrT * kIrrT; k += nt) {
-        const int y = k / kIrrT, x = k % kIrrT;
-        const int2 s = border_source(y, x, kIrrN);
-        if (s.x != y || s.y != x) s_irr[k] = s_irr[s.x * kIrrT + s.y];
-    }
-    for (int k = tid; k < kDepT * kDepT; k += nt) {
-        const int y = k / kDepT, x = k % kDepT;
-        const int2 s = border_source(y, x, kDepN);
-        if (s.x != y || s.y != x) s_dep[k] = s_dep[s.x * kDepT + s.y];
-    }
-    __syncthreads();
-    for (int k = tid; k < kIrrT * kIrrT; k += nt) cur_i[k] = s_irr[k];
-    const float4* sd4 = reinterpret_cast<const float4*>(s_dep);
-    for (int k = tid; k < kDepT * kDepT / 2; k += nt) cur_d4[k] = sd4[k];
-    if (tid == 0) P.cur_valid[p] = 1;
+            st.d = ray_direction(i, P.R, P.rot);
+            st.tlimit = P.tmax_w;
+            st.aux = k;
+            return true;
+        },
+        [&](const TraceState& st, int ev, int steps, float t_end) {
+            P.ray_t[st.aux] = t_end;
+            P.ray_es[st.aux] = (uint32_t)ev | ((uint32_t)steps << 8);
+        });
 }
 
-template <typename T, int PEXP>
-static cudaError_t launch_typed(const UpdateParams& p, int threads, size_t smem, cudaStream_t stream) {
-    auto* k = probe_update_kernel<T, PEXP>;
+// ------------------------------------------------------------------ 2. hit preparation
+template <typename T>
+__global__ void __launch_bounds__(kThreads) prep_kernel(const __grid_constant__ UpdateParams P) {
+    const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    uint32_t gate = 0;
+    if (k < n) {
+        const uint32_t es = P.ray_es[k];
+        const int ev = (int)(es & 0xffu);
+        P.ray_lit[k] = 0;
+        P.ray_ssteps[k] = 0;
+        if (ev != kNoRay && !is_miss(ev)) {
+            const VolumeView& V = P.vol;
+            const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
+            uint32_t flags;
+            const float3 o = probe_origin(P, p, &flags);
+            const float3 d = ray_direction(i, P.R, P.rot);
+            const float3 x = fma3(P.ray_t[k], d, o);
+            const float hh = 0.5f * V.h;
+            const float gx = sample_sdf<T>(V, f3(x.x + hh, x.y, x.z)) - sample_sdf<T>(V, f3(x.x - hh, x.y, x.z));
+            const float gy = sample_sdf<T>(V, f3(x.x, x.y + hh, x.z)) - sample_sdf<T>(V, f3(x.x, x.y - hh, x.z));
+            const float gz = sample_sdf<T>(V, f3(x.x, x.y, x.z + hh)) - sample_sdf<T>(V, f3(x.x, x.y, x.z - hh));
+            const float glen = sqrtf(gx * gx + gy * gy + gz * gz);
+            const float3 nr = glen > 0.f ? f3(gx / glen, gy / glen, gz / glen) : f3(-d.x, -d.y, -d.z);
+            float3 albedo, emission;
+            sample_material(V, x, &albedo, &emission);
+            float3 ind = f3(0.f, 0.f, 0.f);
+            if (P.k_bounce != 0.f)
+                ind = interpolate_irradiance(P.gdims, P.gorigin, P.gspacing, P.prev_irr, P.prev_valid, x, nr);
+            for (int l = 0; l < P.n_lights; ++l) {
+                bool g;
+                light_scale(P.lights[l], x, nr, &g);
+                if (g) gate |= 1u << l;
+            }
+            P.ray_n[k] = make_float4(nr.x, nr.y, nr.z, 0.f);
+            P.ray_alb[k] = make_float4(albedo.x, albedo.y, albedo.z, 0.f);
+            P.ray_base[k] = make_float4(emission.x + albedo.x * P.k_bounce * ind.x,
+                                        emission.y + albedo.y * P.k_bounce * ind.y,
+                                        emission.z + albedo.z * P.k_bounce * ind.z, 0.f);
+        }
+    }
+    // append this warp's (ray, light) pairs to the task list with one atomic
+    const int cnt = __popc(gate);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    uint32_t base = 0;
+    if (lane == 31) base = atomicAdd(&P.counters[1], (uint32_t)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    if (base + (uint32_t)total > P.task_capacity) {  // cannot happen with capacity P*R*lights
+        if (lane == 31) atomicOr(&P.counters[3], 1u);
+        return;
+    }
+    uint32_t pos = base + (uint32_t)(incl - cnt);
+    while (gate) {
+        const int l = __ffs(gate) - 1;
+        gate &= gate - 1;
+        P.tasks[pos++] = (k << 5) | (uint32_t)l;
+    }
+}
+
+// ------------------------------------------------------------------ 3. shadow traces
+template <typename T>
+__global__ void __launch_bounds__(kThreads) shadow_kernel(const __grid_constant__ UpdateParams P) {
+    const uint32_t n = min(P.counters[1], P.task_capacity);
+    trace_pool<T>(
+        P.vol, n, &P.counters[2], P.eps_w, P.max_steps,
+        [&](uint32_t j, TraceState& st) {
+            const uint32_t tk = P.tasks[j];
+            const uint32_t k = tk >> 5;
+            const int l = (int)(tk & 31u);
+            const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
+            uint32_t flags;
+            const float3 o = probe_origin(P, p, &flags);
+            const float3 d = ray_direction(i, P.R, P.rot);
+            const float3 x = fma3(P.ray_t[k], d, o);
+            const float4 n4 = P.ray_n[k];
+            st.o = fma3(P.bias_w, f3(n4.x, n4.y, n4.z), x);
+            const LightDev& li = P.lights[l];
+            if (li.type == SDFDDGI_LIGHT_DIRECTIONAL) {
+                st.d = f3(li.v[0], li.v[1], li.v[2]);
+                st.tlimit = P.tmax_w;
+            } else {
+                const float3 Ls = f3(li.v[0], li.v[1], li.v[2]) - st.o;
+                const float ds = sqrtf(dot(Ls, Ls));
+                st.d = (1.f / ds) * Ls;
+                st.tlimit = ds;
+            }
+            st.aux = tk;
+            return true;
+        },
+        [&](const TraceState& st, int ev, int steps, float) {
+            const uint32_t k = st.aux >> 5;
+            atomicAdd(&P.ray_ssteps[k], (uint32_t)steps);
+            if (is_miss(ev)) atomicOr(&P.ray_lit[k], 1u << (st.aux & 31u));  // hit or exhausted: occluded
+        });
+}
+
+// ------------------------------------------------------------------ 4. gather (Eq. 3)
+// The texel weights max(0, u_j . d_i)^e depend on the frame's ray set only, so they are
+// computed once per update: row i (ray) x column j (texel, irradiance first), plus each
+// column's sum, in ray order.
+template <int PEXP>
+__global__ void __launch_bounds__(kThreads) weights_kernel(const __grid_constant__ UpdateParams P) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= kTexels) return;
+    const bool irr = j < kIrrTexels;
+    const int jj = irr ? j : j - kIrrTexels, n = irr ? kIrrN : kDepN;
+    const float3 u = texel_dir(jj % n, jj / n, n);
+    float sw = 0.f;
+    for (int i = 0; i < P.R; ++i) {
+        const float3 d = ray_direction(i, P.R, P.rot);
+        const float c = fmaf(u.x, d.x, fmaf(u.y, d.y, u.z * d.z));
+        float w = 0.f;
+        if (c > 0.f) w = irr ? c : (PEXP == 50 ? pow50(c) : pow_runtime(c, P.depth_exp));
+        sw += w;
+        P.weights[(size_t)i * kTexels + j] = w;
+    }
+    P.weights[(size_t)P.R * kTexels + j] = sw;
+}
+
+// Radiance (visible lights summed in light order) and clamped distance of ray k.
+__device__ __forceinline__ float4 ray_value(const UpdateParams& P, size_t k, int i, float3 o, float3 d,
+                                            uint32_t* lit_out) {
+    const uint32_t es = P.ray_es[k];
+    const int ev = (int)(es & 0xffu);
+    const float t = P.ray_t[k];
+    *lit_out = 0;
+    if (is_miss(ev)) return make_float4(P.sky[0], P.sky[1], P.sky[2], P.tmax_w);
+    const float3 x = fma3(t, d, o);
+    const float4 n4 = P.ray_n[k];
+    const float3 n = f3(n4.x, n4.y, n4.z);
+    const uint32_t lit = P.ray_lit[k];
+    float3 direct = f3(0.f, 0.f, 0.f);
+    for (int l = 0; l < P.n_lights; ++l) {
+        if (!((lit >> l) & 1u)) continue;
+        bool g;
+        const float sc = light_scale(P.lights[l], x, n, &g);
+        direct = fma3(sc, f3(P.lights[l].rgb[0], P.lights[l].rgb[1], P.lights[l].rgb[2]), direct);
+    }
+    const float inv_pi = 0.318309886183790671538f;
+    const float4 a = P.ray_alb[k], b = P.ray_base[k];
+    *lit_out = lit;
+    return make_float4(fmaf(a.x * inv_pi, direct.x, b.x), fmaf(a.y * inv_pi, direct.y, b.y),
+                       fmaf(a.z * inv_pi, direct.z, b.z), fminf(t, P.tmax_w));
+}
+
+// G probes per CTA. Stage a: every ray of the G probes gets its radiance and clamped
+// distance into shared memory (one float4 per ray and probe). Stage b: thread j owns
+// texel j of all G probes and accumulates sum_i W[i][j] v_i over the rays, reading W
+// coalesced and each v_i as a shared-memory broadcast. Stage c: normalise by the column
+// sum, mix with last frame's texel, fill the borders, store each map contiguously.
+template <int G>
+__global__ void __launch_bounds__(kThreads) gather_kernel(const __grid_constant__ UpdateParams P) {
+    extern __shared__ float4 s_val[];  // [R][G]
+    __shared__ float4 s_irr[G][kIrrT * kIrrT];
+    __shared__ __align__(16) float2 s_dep[G][kDepT * kDepT];  // stored out as float4 pairs
+    __shared__ float s_hyst[G];
+    __shared__ uint32_t s_flags[G];
+    __shared__ float3 s_o[G];
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int p0 = blockIdx.x * G;
+    const int ng = min(G, P.P - p0);
+    if (tid < G) {
+        uint32_t flags = 0;
+        float3 o = f3(0.f, 0.f, 0.f);
+        if (tid < ng) o = probe_origin(P, p0 + tid, &flags);
+        s_o[tid] = o;
+        s_flags[tid] = flags;
+        s_hyst[tid] = (tid < ng && P.prev_valid[p0 + tid] && !(flags & SDFDDGI_PROBE_REJECT_HISTORY)) ? P.hyst : 0.f;
+    }
+    __syncthreads();
+
+    // a. per-ray values
+    for (int e = tid; e < P.R * G; e += nt) {
+        const int i = e / G, g = e % G;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (g < ng && (s_flags[g] & SDFDDGI_PROBE_ACTIVE)) {
+            const size_t k = (size_t)(p0 + g) * P.R + i;
+            const float3 d = ray_direction(i, P.R, P.rot);
+            uint32_t lit;
+            v = ray_value(P, k, i, s_o[g], d, &lit);
+            if (P.records) {
+                const uint32_t es = P.ray_es[k];
+                sdfddgi_ray_record rec;
+                rec.t = P.ray_t[k];
+                rec.L[0] = v.x;
+                rec.L[1] = v.y;
+                rec.L[2] = v.z;
+                rec.lit_mask = lit;
+                rec.shadow_steps = P.ray_ssteps[k];
+                rec.steps = (uint16_t)(es >> 8);
+                rec.event = (uint8_t)(es & 0xffu);
+                rec.reserved0 = 0;
+                rec.reserved1 = 0;
+                P.records[k] = rec;
+            }
+        } else if (g < ng && P.records) {
+            sdfddgi_ray_record rec = {};
+            rec.event = kNoRay;
+            P.records[(size_t)(p0 + g) * P.R + i] = rec;
+        }
+        s_val[e] = v;
+    }
+    __syncthreads();
+
+    // b. texel j of every probe: sum over rays of W[i][j] * value
+    if (tid < kTexels) {
+        const int j = tid;
+        const bool irr = j < kIrrTexels;
+        float acc[G][3];
+#pragma unroll
+        for (int g = 0; g < G; ++g) acc[g][0] = acc[g][1] = acc[g][2] = 0.f;
+        const float* W = P.weights + j;
+        if (irr) {
+            for (int i = 0; i < P.R; ++i) {
+                const float w = __ldg(W + (size_t)i * kTexels);
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const float4 v = s_val[i * G + g];
+                    acc[g][0] = fmaf(w, v.x, acc[g][0]);
+                    acc[g][1] = fmaf(w, v.y, acc[g][1]);
+                    acc[g][2] = fmaf(w, v.z, acc[g][2]);
+                }
+            }
+        } else {
+            for (int i = 0; i < P.R; ++i) {
+                const float w = __ldg(W + (size_t)i * kTexels);
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const float t = s_val[i * G + g].w;
+                    acc[g][0] = fmaf(w, t, acc[g][0]);
+                    acc[g][1] = fmaf(w, t * t, acc[g][1]);
+                }
+            }
+        }
+        // c. normalise and mix with the previous texel
+        const float sw = __ldg(P.weights + (size_t)P.R * kTexels + j);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (g >= ng) break;
+            const size_t p = (size_t)(p0 + g);
+            const float hyst = s_hyst[g], keep = 1.f - hyst;
+            if (irr) {
+                const int a = j % kIrrN, b = j / kIrrN, k = (b + 1) * kIrrT + (a + 1);
+                float4 out = __ldg(P.prev_irr + p * (kIrrT * kIrrT) + k);
+                if ((s_flags[g] & SDFDDGI_PROBE_ACTIVE) && sw > 0.f) {
+                    const float inv = 1.f / sw;
+                    out.x = fmaf(hyst, out.x, keep * (acc[g][0] * inv));
+                    out.y = fmaf(hyst, out.y, keep * (acc[g][1] * inv));
+                    out.z = fmaf(hyst, out.z, keep * (acc[g][2] * inv));
+                    out.w = 1.f;
+                }
+                s_irr[g][k] = out;
+            } else {
+                const int jj = j - kIrrTexels, a = jj % kDepN, b = jj / kDepN, k = (b + 1) * kDepT + (a + 1);
+                float2 out = __ldg(P.prev_depth + p * (kDepT * kDepT) + k);
+                if ((s_flags[g] & SDFDDGI_PROBE_ACTIVE) && sw > 0.f) {
+                    const float inv = 1.f / sw;
+                    out.x = fmaf(hyst, out.x, keep * (acc[g][0] * inv));
+                    out.y = fmaf(hyst, out.y, keep * (acc[g][1] * inv));
+                }
+                s_dep[g][k] = out;
+            }
+        }
+    }
+    __syncthreads();
+
+    // borders from the interior (inactive probes: copy of the old map, borders included)
+    for (int e = tid; e < ng * kIrrT * kIrrT; e += nt) {
+        const int g = e / (kIrrT * kIrrT), k = e % (kIrrT * kIrrT);
+        const int y = k / kIrrT, x = k % kIrrT;
+        const int2 s = border_source(y, x, kIrrN);
+        if (!(s_flags[g] & SDFDDGI_PROBE_ACTIVE)) {
+            s_irr[g][k] = __ldg(P.prev_irr + (size_t)(p0 + g) * (kIrrT * kIrrT) + k);
+        } else if (s.x != y || s.y != x) {
+            s_irr[g][k] = s_irr[g][s.x * kIrrT + s.y];
+        }
+    }
+    for (int e = tid; e < ng * kDepT * kDepT; e += nt) {
+        const int g = e / (kDepT * kDepT), k = e % (kDepT * kDepT);
+        const int y = k / kDepT, x = k % kDepT;
+        const int2 s = border_source(y, x, kDepN);
+        if (!(s_flags[g] & SDFDDGI_PROBE_ACTIVE)) {
+            s_dep[g][k] = __ldg(P.prev_depth + (size_t)(p0 + g) * (kDepT * kDepT) + k);
+        } else if (s.x != y || s.y != x) {
+            s_dep[g][k] = s_dep[g][s.x * kDepT + s.y];
+        }
+    }
+    __syncthreads();
+    float4* cur_i = P.cur_irr + (size_t)p0 * (kIrrT * kIrrT);
+    for (int e = tid; e < ng * kIrrT * kIrrT; e += nt) cur_i[e] = (&s_irr[0][0])[e];
+    float4* cur_d4 = reinterpret_cast<float4*>(P.cur_depth + (size_t)p0 * (kDepT * kDepT));
+    const float4* sd4 = reinterpret_cast<const float4*>(&s_dep[0][0]);
+    for (int e = tid; e < ng * kDepT * kDepT / 2; e += nt) cur_d4[e] = sd4[e];
+    if (tid < ng) P.cur_valid[p0 + tid] = (s_flags[tid] & SDFDDGI_PROBE_ACTIVE) ? 1 : P.prev_valid[p0 + tid];
+}
+
+// ------------------------------------------------------------------ launch
+template <typename K>
+static int persistent_blocks(K kernel) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
+    return max(1, sms * max(1, per_sm));
+}
+
+template <int G>
+static cudaError_t launch_gather(const UpdateParams& p, cudaStream_t stream) {
+    const size_t smem = (size_t)p.R * G * sizeof(float4);
+    auto* k = gather_kernel<G>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<p.P, threads, smem, stream>>>(p);
+    k<<<(p.P + G - 1) / G, kThreads, smem, stream>>>(p);
     return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream) {
+    static const int g_primary = persistent_blocks(primary_kernel<T>);
+    static const int g_shadow = persistent_blocks(shadow_kernel<T>);
+    cudaError_t e = cudaMemsetAsync(p.counters, 0, 4 * sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return e;
+    const uint32_t n = (uint32_t)p.P * (uint32_t)p.R;
+    if (p.depth_exp == 50)
+        weights_kernel<50><<<(kTexels + kThreads - 1) / kThreads, kThreads, 0, stream>>>(p);
+    else
+        weights_kernel<0><<<(kTexels + kThreads - 1) / kThreads, kThreads, 0, stream>>>(p);
+    primary_kernel<T><<<g_primary, kThreads, 0, stream>>>(p);
+    prep_kernel<T><<<(n + kThreads - 1) / kThreads, kThreads, 0, stream>>>(p);
+    shadow_kernel<T><<<g_shadow, kThreads, 0, stream>>>(p);
+    // probes per gather CTA: as many as keep the [R][G] values within 32 KiB of shared memory
+    if (p.R <= 256) return launch_gather<8>(p, stream);
+    if (p.R <= 512) return launch_gather<4>(p, stream);
+    return launch_gather<2>(p, stream);
 }
 
 cudaError_t launch_update(const UpdateParams& p, cudaStream_t stream) {
     if (p.P == 0) return cudaSuccess;
-    const int threads = p.R >= kMaxThreads ? kMaxThreads : ((p.R + 31) / 32) * 32;
-    const size_t smem = smem_bytes(p.R, threads, p.n_lights);
-    const bool p50 = p.depth_exp == 50;
-    if (p.vol.dtype == SDFDDGI_F16)
-        return p50 ? launch_typed<__half, 50>(p, threads, smem, stream) : launch_typed<__half, 0>(p, threads, smem, stream);
-    return p50 ? launch_typed<float, 50>(p, threads, smem, stream) : launch_typed<float, 0>(p, threads, smem, stream);
+    return p.vol.dtype == SDFDDGI_F16 ? launch_stages<__half>(p, stream) : launch_stages<float>(p, stream);
 }
 
 }  // namespace sdfddgi

@@ -1,0 +1,48 @@
+// volume.cu -- the device SDF store.
+//
+// Besides the plain [z][y][x] array, the scene keeps the signed-distance values in an
+// "xy-quad" layout: entry (x, y, z) holds the four values (x, y), (x+1, y), (x, y+1),
+// (x+1, y+1) of slice z, indices clamped to the volume. A trilinear sample then reads
+// its eight corners with two vector loads (slices z and z+1) instead of eight scalar
+// loads, which is what bounds the sphere-trace kernels. The values are the same
+// float32 / binary16 numbers, only replicated, so results are unchanged.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace sdfddgi {
+
+template <typename T, typename Q>
+__global__ void build_quads_kernel(const T* __restrict__ sdf, Q* __restrict__ quads, int nx, int ny, int nz) {
+    const size_t n = (size_t)nx * ny * nz;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny);
+        const size_t z = i / ((size_t)nx * ny);
+        const int x1 = min(x + 1, nx - 1), y1 = min(y + 1, ny - 1);
+        const size_t r0 = (z * ny + y) * nx, r1 = (z * ny + y1) * nx;
+        Q q;
+        T* e = reinterpret_cast<T*>(&q);
+        e[0] = sdf[r0 + x];
+        e[1] = sdf[r0 + x1];
+        e[2] = sdf[r1 + x];
+        e[3] = sdf[r1 + x1];
+        quads[i] = q;
+    }
+}
+
+size_t quad_bytes(int dtype, size_t n_voxels) { return n_voxels * (dtype == SDFDDGI_F16 ? 8 : 16); }
+
+cudaError_t build_quads(const void* sdf, void* quads, int dtype, const int dims[3], cudaStream_t stream) {
+    const size_t n = (size_t)dims[0] * dims[1] * dims[2];
+    const int threads = 256;
+    const int blocks = (int)std::min<size_t>((n + threads - 1) / threads, 148 * 64);
+    if (dtype == SDFDDGI_F16)
+        build_quads_kernel<__half, uint2><<<blocks, threads, 0, stream>>>(
+            static_cast<const __half*>(sdf), static_cast<uint2*>(quads), dims[0], dims[1], dims[2]);
+    else
+        build_quads_kernel<float, float4><<<blocks, threads, 0, stream>>>(
+            static_cast<const float*>(sdf), static_cast<float4*>(quads), dims[0], dims[1], dims[2]);
+    return cudaGetLastError();
+}
+
+}  // namespace sdfddgi
