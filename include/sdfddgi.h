@@ -213,6 +213,46 @@ SDFDDGI_API int sdfddgi_write_state(sdfddgi_volume* v, const float* irr, const f
 /* Clears every map and the history (as at creation). */
 SDFDDGI_API int sdfddgi_reset(sdfddgi_volume* v, void* stream);
 
+/* ---- the update without device allocation ------------------------------ */
+
+/* The paper has no counterpart to this entry point; it exists for callers that may not
+ * allocate device memory while they run -- an engine that reserves all GPU memory at
+ * start-up and sub-allocates its own pools, a plug-in inside another framework's memory
+ * manager, or a real-time loop where a cudaMalloc could stall the frame. It computes
+ * exactly what sdfddgi_update_probes computes, with the same kernels, but takes every
+ * input and output from the caller and allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library call. The update's scratch (a copy of the SDF in the kernels'
+ * layout, per-ray buffers, the shadow-task list, texel weights, counters) lives in one
+ * fixed 32 MiB array in device memory that every GPU loading this library holds until
+ * the process exits. An update needs, each part rounded up to 256 bytes: 16 bytes per
+ * SDF voxel (8 at binary16), 64 + 4*max(n_lights,1) bytes per probe ray (P*R), and
+ * 928*(R+1) bytes -- e.g. a 64^3 float32 SDF with 512 probes x 64 rays and 1 light
+ * takes about 6.2 MiB. An update that does not fit in 32 MiB is rejected with
+ * SDFDDGI_ERR_INVALID_ARG before any device work, and sdfddgi_last_error() states the
+ * bytes needed and available.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before capturing any stream.
+ *  - Every call on a device shares the one array and leaves its contents behind (the
+ *    parts that must start at zero are cleared by each call): calls whose work overlaps
+ *    on the GPU (different streams, or different host threads) race; serialise them.
+ * Arguments:
+ *  desc                        -- the probe volume, as for sdfddgi_create_volume.
+ *  sdf, dims, voxel_size, origin, dtype, material
+ *                              -- the scene, as for sdfddgi_upload_sdf, in DEVICE memory.
+ *  lights, n_lights, sky_rgb   -- as for sdfddgi_set_lights (host memory; sky may be NULL).
+ *  frame, rotation             -- as for sdfddgi_update_probes (rotation: host, nullable).
+ *  states                      -- NULL (grid positions, all active) or P device states.
+ *  prev_irr/prev_depth/prev_valid -- the previous maps (device; zeros for no history).
+ *  cur_irr/cur_depth/cur_valid -- receive the new maps (device; must not alias prev_*).
+ *  records                     -- NULL or P*R device records, as for sdfddgi_update_probes.
+ * Map layouts are those of sdfddgi_get_maps. Work is enqueued on `stream`. */
+SDFDDGI_API int sdfddgi_update_probes_noalloc(
+    const sdfddgi_volume_desc* desc, const void* sdf, const int32_t dims[3], float voxel_size,
+    const float origin[3], int32_t dtype, const void* material, const sdfddgi_light* lights, int32_t n_lights,
+    const float sky_rgb[3], uint32_t frame, const float* rotation, const sdfddgi_probe_state* states,
+    const float* prev_irr, const float* prev_depth, const uint8_t* prev_valid, float* cur_irr, float* cur_depth,
+    uint8_t* cur_valid, sdfddgi_ray_record* records, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,9 @@ def _load() -> C.CDLL:
         "sdfddgi_read_state": ([vp, vp, vp, vp, i32, vp], C.c_int),
         "sdfddgi_write_state": ([vp, vp, vp, vp, i32, vp], C.c_int),
         "sdfddgi_reset": ([vp, vp], C.c_int),
+        "sdfddgi_update_probes_noalloc": ([C.POINTER(VolumeDesc), vp, C.POINTER(i32), C.c_float, C.POINTER(C.c_float),
+                                           i32, vp, C.POINTER(Light), i32, C.POINTER(C.c_float), u32, vp, vp,
+                                           vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -84,7 +87,8 @@ def _load() -> C.CDLL:
 
 lib = _load()
 EXPORTED = ("last_error", "create_scene", "destroy_scene", "upload_sdf", "set_lights", "create_volume",
-            "destroy_volume", "volume_probe_count", "frame_rotation", "update_probes", "sample_irradiance",
+            "destroy_volume", "volume_probe_count", "frame_rotation", "update_probes", "update_probes_noalloc",
+            "sample_irradiance",
             "get_maps", "read_state", "write_state", "reset")
 
 
@@ -251,3 +255,35 @@ def write_state(volume, irr, depth, valid, stream=None) -> None:
 
 def reset(volume, stream=None) -> None:
     _check(lib.sdfddgi_reset(volume, _stream(stream)))
+
+
+def update_probes_noalloc(desc: VolumeDesc, sdf, voxel_size: float, origin, lights, sky, prev, cur, frame: int = 0,
+                          rotation=None, material=None, states=None, records=None, stream=None) -> None:
+    """The update for callers that cannot allocate device memory (see include/sdfddgi.h): every
+    buffer is the caller's. sdf [nz,ny,nx] float32/float16 and material [nz,ny,nx,8] float16 are
+    device tensors; prev and cur are (irr [P,8,8,4] f32, depth [P,16,16,2] f32, valid [P] u8)
+    device tensors; states None or a device tensor of P*16 bytes; records None or P*R*32 bytes."""
+    shape = tuple(sdf.shape)
+    name = str(sdf.dtype)
+    dtype = F32 if name.endswith("float32") else F16 if name.endswith("float16") else None
+    if dtype is None or len(shape) != 3:
+        raise ValueError("sdf must be a 3-D float32 or float16 device tensor")
+    for t in (sdf, material, states, records, *prev, *cur):
+        if t is not None and not (_is_torch(t) and t.is_cuda):
+            raise ValueError("update_probes_noalloc: every buffer must be a CUDA tensor")
+    n = len(lights)
+    arr = (Light * max(n, 1))()
+    for i, l in enumerate(lights):
+        arr[i].type = LIGHT_DIRECTIONAL if l["type"] in ("dir", LIGHT_DIRECTIONAL) else LIGHT_POINT
+        arr[i].v = _floats(l["v"], 3)
+        arr[i].rgb = _floats(l["rgb"], 3)
+        arr[i].range = float(l.get("range", 0.0))
+    rot = None
+    if rotation is not None:
+        rot = np.ascontiguousarray(np.asarray(rotation, dtype=np.float32).reshape(9))
+    dims = (C.c_int32 * 3)(shape[2], shape[1], shape[0])
+    _check(lib.sdfddgi_update_probes_noalloc(
+        C.byref(desc), _ptr(sdf)[0], dims, float(voxel_size), _floats(origin, 3), dtype, _ptr(material)[0], arr, n,
+        _floats(sky, 3), int(frame), rot.ctypes.data if rot is not None else None, _ptr(states)[0],
+        _ptr(prev[0])[0], _ptr(prev[1])[0], _ptr(prev[2])[0], _ptr(cur[0])[0], _ptr(cur[1])[0], _ptr(cur[2])[0],
+        _ptr(records)[0], _stream(stream)))

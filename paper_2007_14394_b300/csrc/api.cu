@@ -148,6 +148,8 @@ uint64_t splitmix64_next(uint64_t* state) {
 
 }  // namespace
 
+int sdfddgi::report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 extern "C" {
 
 SDFDDGI_API const char* sdfddgi_last_error(void) { return g_error; }

@@ -94,6 +94,7 @@ struct SampleParams {
 cudaError_t launch_update(const UpdateParams& p, cudaStream_t stream);
 cudaError_t launch_sample(const SampleParams& p, cudaStream_t stream);
 size_t quad_bytes(int dtype, size_t n_voxels);
+int report_error(int code, const char* msg);  // sets the text of sdfddgi_last_error(), returns code
 cudaError_t build_quads(const void* sdf, void* quads, int dtype, const int dims[3], cudaStream_t stream);
 
 }  // namespace sdfddgi
