@@ -15,10 +15,8 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
-import subprocess
 import sys
 import time
 
@@ -33,7 +31,7 @@ METRIC = "probe-rays/s & ms per probe-volume update; learned vs plain rays at eq
 UNIT = "probe-rays/s"
 WORKLOAD = "open256"
 L2_FLUSH_BYTES = 512 << 20
-KERNELS_PER_UPDATE = 4  # primary trace, hit preparation, shadow trace, gather
+KERNELS_PER_UPDATE = 8  # texel weights, weight sums, primary, hit preparation, shadow, finalize, weight image, gather
 
 
 def peaks():
@@ -43,6 +41,15 @@ def peaks():
         return float(m["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6400.0, "fallback"
+
+
+def tensor_peak():
+    """Dense bf16 tensor peak (TFLOP/s), burst: the measured one, else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1800.0, "fallback"
 
 
 def workload_config(pr: W.Preset, rays_traced: int):
@@ -60,57 +67,117 @@ def build_inputs(pr: W.Preset):
 
 
 class Clocks:
-    """nvidia-smi sampler running during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    """SM clock and throttle reasons sampled through NVML every few ms during the timed region."""
+    REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40, "sw_power_cap": 0x4}
 
-    def __init__(self, device_index: int):
-        self.proc = None
-        self.dev = device_index
+    def __init__(self, device_index: int, period_s: float = 0.005):
+        import threading
+        self.samples, self.reasons, self.max_mhz = [], set(), None
+        self._stop = threading.Event()
+        self._thread = None
+        self._proc, self.source = None, None
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            import pynvml
+            pynvml.nvmlInit()
+            self._nv = pynvml
+            self._h = pynvml.nvmlDeviceGetHandleByIndex(device_index)
+            self.max_mhz = float(pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM))
+        except Exception:  # no NVML binding: nvidia-smi every 100 ms instead
+            self._nv = None
+            self._start_smi(device_index)
+            return
+        self._period = period_s
+        self.source = "NVML, 5 ms period"
+        self._thread = threading.Thread(target=self._run, daemon=True)
+        self._thread.start()
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def _start_smi(self, device_index):
+        import subprocess
+        try:
+            self._proc = subprocess.Popen(["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.Q}",
+                                           "--format=csv,noheader,nounits", "-lms", "100"],
+                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._first = self._proc.stdout.readline()  # the sampler is running before the timed region
+            self.source = "nvidia-smi, 100 ms period"
         except OSError:
-            self.proc = None
+            self._proc = None
 
-    def stop(self):
-        if self.proc is None:
-            return None
-        self.proc.terminate()
+    def _stop_smi(self):
+        self._proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-            out, _ = self.proc.communicate()
-        rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
-        sm, mx, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
+            out, _ = self._proc.communicate(timeout=5)
+        except Exception:
+            self._proc.kill()
+            out, _ = self._proc.communicate()
+        names = ["hw_slowdown", "sw_thermal_slowdown", "hw_thermal_slowdown", "sw_power_cap"]
+        for row in out.strip().splitlines():
+            f = [x.strip() for x in row.split(",")]
             try:
-                sm.append(float(r[1]))
-                mx = max(mx, float(r[2]))
+                self.samples.append(float(f[0]))
+                self.max_mhz = max(self.max_mhz or 0.0, float(f[1]))
                 for k, name in enumerate(names):
-                    if r[5 + k].strip().lower() == "active":
-                        reasons.add(name)
+                    if f[2 + k].lower() == "active":
+                        self.reasons.add(name)
             except (ValueError, IndexError):
                 continue
-        if not sm:
+
+    def _run(self):
+        nv = self._nv
+        while not self._stop.is_set():
+            try:
+                self.samples.append(float(nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM)))
+                get = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                    nv.nvmlDeviceGetCurrentClocksThrottleReasons
+                mask = get(self._h)
+                for name, bit in self.REASONS.items():
+                    if mask & bit:
+                        self.reasons.add(name)
+            except Exception:
+                pass
+            self._stop.wait(self._period)
+
+    def stop(self):
+        if self._proc is not None:
+            self._stop_smi()
+        elif self._thread is not None:
+            self._stop.set()
+            self._thread.join()
+        if not self.samples:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(self.samples), "source": self.source}
 
 
-def algorithmic_bytes(rec: np.ndarray, sdf_elem: int, n_probes: int, n_active: int) -> dict:
-    """Bytes the algorithm gathers in one update, from the step counts it actually took:
-    8 corners per SDF sample over the primary trace, the shadow traces and the 6 normal samples;
-    8 material corners (16 B) per shaded hit; 8 probes x 4 texels (16 B) for the bounce term;
-    previous-map reads and current-map writes (3 KiB each per probe) and the probe state."""
+def stage_work(rec: np.ndarray, sdf_elem: int, n_probes: int, rays: int, n_active: int) -> dict:
+    """Algorithmic work of each stage of one update, from the step counts the update took.
+    SDF sample = 8 trilinear corners of sdf_elem bytes. Per stage:
+      primary -- its SDF samples + the 8-byte result of every ray;
+      prep    -- per shaded hit 6 normal samples, 8 material corners (16 B), 8 probes x 4 texels
+                 (16 B) of last frame's irradiance, and 64 B of shading data written;
+      shadow  -- its SDF samples + per task the 4-byte task, the hit's 20 bytes and the result;
+      gather  -- floating-point work of Eq. 3: 2 flops per (texel, ray, channel) over the 36 x 3
+                 irradiance and 196 x 2 moment outputs of every active probe."""
     live = rec["event"] != 255
     shaded = live & ((rec["event"] == 1) | (rec["event"] == 3))
-    samples = int(rec["steps"][live].sum()) + int(rec["shadow_steps"][live].sum()) + 6 * int(shaded.sum())
-    b = samples * 8 * sdf_elem + int(shaded.sum()) * (8 * 16 + 8 * 4 * 16) + n_probes * (2 * 3072 + 16)
-    return {"bytes": b, "sdf_samples": samples, "shaded": int(shaded.sum()), "rays": int(live.sum())}
+    prim = int(rec["steps"][live].sum())
+    shad = int(rec["shadow_steps"][live].sum())
+    hits = int(shaded.sum())
+    corner = 8 * sdf_elem
+    return {
+        "primary": {"bytes": prim * corner + int(live.sum()) * 8, "sdf_samples": prim},
+        "prep": {"bytes": hits * (6 * corner + 8 * 16 + 8 * 4 * 16 + 64), "sdf_samples": 6 * hits},
+        "shadow": {"bytes": shad * corner, "sdf_samples": shad},
+        "gather": {"flops": 2 * rays * (36 * 3 + 196 * 2) * n_active},
+        "rays": int(live.sum()), "hits": hits,
+    }
+
+
+def fp32_peak_tflops(clock_mhz: float) -> float:
+    """FP32 FMA peak from unit counts and clock: 148 SMs x 128 FP32 lanes x 2 flops per cycle."""
+    return 148 * 128 * 2 * clock_mhz * 1e6 / 1e12
 
 
 def run_ours(args, rank, world, local_rank):
@@ -140,7 +207,7 @@ def run_ours(args, rank, world, local_rank):
     S.update_probes(vol, 0, states=states_dev, records=records)
     torch.cuda.synchronize()
     rec = records.cpu().numpy().view(S.RAY_RECORD_DTYPE)
-    algo = algorithmic_bytes(rec, 4 if pr.sdf_dtype == "f32" else 2, P, n_active)
+    work = stage_work(rec, 4 if pr.sdf_dtype == "f32" else 2, P, R, n_active)
     del records
     S.reset(vol)
 
@@ -156,12 +223,19 @@ def run_ours(args, rank, world, local_rank):
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # stage boundaries, recorded by the library on the same stream (events created up front)
+    stage_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    for evs in stage_ev:
+        for e in evs:
+            e.record(stream)
+    torch.cuda.synchronize()
     clocks = Clocks(local_rank)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(float(k))                       # evict the SDF and maps from L2 (not timed)
+        S.set_stage_events(vol, stage_ev[k])
         starts[k].record(stream)
         S.update_probes(vol, frame, states=states_dev, stream=stream)
         ends[k].record(stream)
@@ -170,8 +244,11 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
+    S.set_stage_events(vol, [])
     per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     dev_ms = float(sum(per_step))
+    stage_ms = {name: sum(evs[i].elapsed_time(evs[i + 1]) for evs in stage_ev) / args.steps
+                for i, name in enumerate(S.STAGES)}
 
     # end to end through the C ABI with host buffers: pinned probe states in, both maps out
     host_states = torch.from_numpy(states.view(np.uint8).copy()).pin_memory()
@@ -203,8 +280,36 @@ def run_ours(args, rank, world, local_rank):
     ms = dev_ms / args.steps
     value = world * rays_per_step * args.steps / (dev_ms / 1e3)
     e2e_value = world * rays_per_step * args.steps / (e2e_ms / 1e3)
-    peak, peak_kind = peaks()
-    achieved = algo["bytes"] / (ms / 1e3) / 1e9
+    hbm, peak_kind = peaks()
+    sm_mhz = float((clk or {}).get("sm_max_mhz") or 2032.0)
+    stages = {}
+    for name in S.STAGES:
+        ms_k = stage_ms[name]
+        if name == "gather" and R % 32 == 0:  # the tensor-core gather (3 x tf32 products)
+            ach = work[name]["flops"] / (ms_k / 1e3) / 1e12
+            bf16, bf16_kind = tensor_peak()
+            peak_k = bf16 * 1.1 / 2.25
+            stages[name] = {"ms": ms_k, "bound": "tensor", "achieved": ach, "peak": peak_k, "unit": "TFLOP/s",
+                            "frac": ach / peak_k, "flops_per_launch": work[name]["flops"],
+                            "peak_source": f"{bf16_kind} bf16 burst x nominal tf32/bf16 (1.1/2.25)",
+                            "note": "includes the per-ray finalize and the weight-image pack"}
+        elif name == "gather":
+            ach = work[name]["flops"] / (ms_k / 1e3) / 1e12
+            peak_k = fp32_peak_tflops(sm_mhz)
+            stages[name] = {"ms": ms_k, "bound": "alu", "achieved": ach, "peak": peak_k, "unit": "TFLOP/s",
+                            "frac": ach / peak_k, "flops_per_launch": work[name]["flops"],
+                            "peak_source": f"derived: 148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
+        elif name in work:
+            ach = work[name]["bytes"] / (ms_k / 1e3) / 1e9
+            stages[name] = {"ms": ms_k, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                            "frac": ach / hbm, "bytes_per_launch": work[name]["bytes"],
+                            "sdf_samples_per_launch": work[name]["sdf_samples"],
+                            "peak_source": f"{peak_kind} hbm_gbs"}
+        else:
+            stages[name] = {"ms": ms_k}
+    dominant = max((n for n in S.STAGES if n in work), key=lambda n: stage_ms[n])
+    roof = dict(stages[dominant])
+    roof.update({"kernel": dominant, "traffic": None})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -212,10 +317,8 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": KERNELS_PER_UPDATE * args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": P * 16,
                 "d2h_bytes_per_step": P * (8 * 8 * 4 * 4 + 16 * 16 * 2 * 4 + 1), "ms_per_step": e2e_ms / args.steps},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "probe_update_kernel<float>",
-                     "algorithmic_bytes_per_launch": algo["bytes"], "sdf_samples_per_launch": algo["sdf_samples"],
-                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "roofline": roof,
+        "stages": stages,
         "wall_s_timed_loop": wall,
         "step_ms": {"min": min(per_step), "median": statistics.median(per_step), "max": max(per_step)},
         "clocks": clk,
@@ -242,16 +345,26 @@ def oracle_sample(pr, scene, baked, states, n_probes, seed=0, frame=0, threads=0
     return time.perf_counter() - t0, len(sub) * pr.rays
 
 
-def cpu_baseline(pr, scene, baked, states, budget_s=15.0):
+def cpu_baseline(pr, scene, baked, states, budget_s=10.0):
+    """The oracle as it stands, on all host cores: consecutive frames of the whole workload
+    (each frame starting from the oracle's own previous maps) until about budget_s seconds."""
+    import oracle as O
     cores = os.cpu_count() or 1
+    osc = O.OracleScene(baked.sdf, baked.h, baked.origin, baked.material)
+    g = O.make_grid(pr.probe_dims, pr.probe_origin, pr.probe_spacing, pr.rays, pr.max_steps, pr.eps_vox,
+                    pr.tmax_vox, pr.hysteresis, pr.depth_exponent, pr.k_bounce, pr.bias_vox, scene.sky)
     n_active = int((states["flags"] & 1).sum())
-    calib = max(4, cores)
-    dt, rays = oracle_sample(pr, scene, baked, states, calib)       # calibrate the sample size
-    n = int(max(4, min(n_active, budget_s / max(dt, 1e-3) * calib)))
-    dt, rays = oracle_sample(pr, scene, baked, states, n, seed=1)
-    return {"value": rays / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} random active probes of {pr.name} (frame 0, {pr.rays} rays each), "
-                      f"{dt:.1f} s on {cores} OpenMP threads"}
+    prev, frames, t_total = None, 0, 0.0
+    while t_total < budget_s and frames < 64:
+        t0 = time.perf_counter()
+        out = O.update(osc, g, scene.lights, W.frame_rotation(pr.seed, frames), states, prev=prev, want_rays=False)
+        t_total += time.perf_counter() - t0
+        prev = (out["irr"], out["depth"], out["valid"])
+        frames += 1
+    return {"value": frames * n_active * pr.rays / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{frames} consecutive full frames of {pr.name} ({n_active} active probes x {pr.rays} rays), "
+                      f"{t_total:.1f} s on {cores} OpenMP threads",
+            "ms_per_step": 1e3 * t_total / frames}
 
 
 def run_reference(args):
@@ -260,7 +373,7 @@ def run_reference(args):
     cores = os.cpu_count() or 1
     n_active = int((states["flags"] & 1).sum())
     dt, _ = oracle_sample(pr, scene, baked, states, max(4, cores))
-    per_step_budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step_budget = max(0.05, 60.0 / max(1, args.steps + args.warmup))
     n = int(max(4, min(n_active, (per_step_budget / max(dt, 1e-3)) * max(4, cores))))
     for k in range(args.warmup):
         oracle_sample(pr, scene, baked, states, n, seed=100 + k, frame=k)
@@ -284,12 +397,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.PRESETS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

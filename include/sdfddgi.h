@@ -62,6 +62,7 @@ enum { SDFDDGI_F32 = 0, SDFDDGI_F16 = 1 };                          /* SDF stora
 enum { SDFDDGI_LIGHT_DIRECTIONAL = 0, SDFDDGI_LIGHT_POINT = 1 };    /* light type        */
 enum { SDFDDGI_PROBE_ACTIVE = 1u, SDFDDGI_PROBE_REJECT_HISTORY = 2u }; /* probe flags   */
 enum { SDFDDGI_MAX_LIGHTS = 32, SDFDDGI_MAX_RAYS = 1024, SDFDDGI_MAX_STEPS = 65535 };
+enum { SDFDDGI_STAGE_EVENTS = 6 };
 
 /* Octahedral map sizes (Sec. 3.3: octahedral mapping into the probe atlas):
  * irradiance 6x6 interior texels + 1-texel border = 8x8, RGBA float32 per texel
@@ -186,6 +187,14 @@ SDFDDGI_API int sdfddgi_update_probes(sdfddgi_volume* v, uint32_t frame, const f
                                       const sdfddgi_probe_state* states, int32_t states_on_device,
                                       sdfddgi_ray_record* records, void* stream);
 
+/* Stage timing (a profiling aid; the paper times its stages too, Table 1). With
+ * n = SDFDDGI_STAGE_EVENTS caller-owned CUDA events (cudaEvent_t as void*), every later
+ * update_probes records them on its stream: [0] at the start, [1] after the per-frame
+ * texel weights, [2] after the primary traces, [3] after hit preparation, [4] after the
+ * shadow traces, [5] after the gather (Eq. 3) and border fixup. n = 0 stops recording.
+ * The events must outlive their use; the caller reads them with cudaEventElapsedTime. */
+SDFDDGI_API int sdfddgi_set_stage_events(sdfddgi_volume* v, void* const* events, int32_t n);
+
 /* Interpolated normalised irradiance (Sec. 3.4 probe interpolation, without the
  * per-pixel SDF visibility test) at n world points with unit normals: trilinear
  * over the 8 probes of the grid cell containing the point (clamped to the grid),
@@ -226,7 +235,7 @@ SDFDDGI_API int sdfddgi_reset(sdfddgi_volume* v, void* stream);
  * fixed 32 MiB array in device memory that every GPU loading this library holds until
  * the process exits. An update needs, each part rounded up to 256 bytes: 16 bytes per
  * SDF voxel (8 at binary16), 64 + 4*max(n_lights,1) bytes per probe ray (P*R), and
- * 928*(R+1) bytes -- e.g. a 64^3 float32 SDF with 512 probes x 64 rays and 1 light
+ * 944*R + 928 bytes -- e.g. a 64^3 float32 SDF with 512 probes x 64 rays and 1 light
  * takes about 6.2 MiB. An update that does not fit in 32 MiB is rejected with
  * SDFDDGI_ERR_INVALID_ARG before any device work, and sdfddgi_last_error() states the
  * bytes needed and available.

@@ -74,6 +74,7 @@ def _load() -> C.CDLL:
         "sdfddgi_read_state": ([vp, vp, vp, vp, i32, vp], C.c_int),
         "sdfddgi_write_state": ([vp, vp, vp, vp, i32, vp], C.c_int),
         "sdfddgi_reset": ([vp, vp], C.c_int),
+        "sdfddgi_set_stage_events": ([vp, C.POINTER(vp), i32], C.c_int),
         "sdfddgi_update_probes_noalloc": ([C.POINTER(VolumeDesc), vp, C.POINTER(i32), C.c_float, C.POINTER(C.c_float),
                                            i32, vp, C.POINTER(Light), i32, C.POINTER(C.c_float), u32, vp, vp,
                                            vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
@@ -88,8 +89,15 @@ def _load() -> C.CDLL:
 lib = _load()
 EXPORTED = ("last_error", "create_scene", "destroy_scene", "upload_sdf", "set_lights", "create_volume",
             "destroy_volume", "volume_probe_count", "frame_rotation", "update_probes", "update_probes_noalloc",
-            "sample_irradiance",
-            "get_maps", "read_state", "write_state", "reset")
+            "sample_irradiance", "set_stage_events", "get_maps", "read_state", "write_state", "reset")
+STAGES = ("weights", "primary", "prep", "shadow", "gather")  # intervals between the stage events
+
+
+def set_stage_events(volume, events) -> None:
+    """events: [] to stop, or 6 torch.cuda.Event(enable_timing=True) recorded once already."""
+    n = len(events)
+    arr = (C.c_void_p * max(n, 1))(*[e.cuda_event for e in events])
+    _check(lib.sdfddgi_set_stage_events(volume, arr, n))
 
 
 def last_error() -> str:

@@ -1,6 +1,7 @@
 """Builds libsdfddgi.so in-tree with nvcc for sm_103a (B300).
 
-Usage: python -m paper_2007_14394_b300.build [--force] [--verbose]
+Usage: python paper_2007_14394_b300/build.py [--force] [--verbose]
+(run it as a file: importing the package itself needs the compiled library)
 """
 from __future__ import annotations
 

@@ -53,6 +53,9 @@ struct sdfddgi_volume {
     uint32_t* tasks = nullptr;
     size_t task_capacity = 0;
     float* weights = nullptr;  // texel weights of the frame's ray set and their column sums
+    void* wimage = nullptr;    // the weights as the tensor-core gather's operand image
+    cudaEvent_t stage_events[SDFDDGI_STAGE_EVENTS] = {};  // caller's, recorded at stage boundaries
+    bool has_stage_events = false;
 };
 
 namespace {
@@ -102,9 +105,10 @@ void free_volume_buffers(sdfddgi_volume* v) {
     cudaFree(v->states);
     v->states = nullptr;
     void* scratch[] = {v->ray_t, v->ray_es, v->ray_n, v->ray_alb, v->ray_base, v->ray_lit, v->ray_ssteps,
-                       v->counters, v->tasks, v->weights};
+                       v->counters, v->tasks, v->weights, v->wimage};
     for (void* q : scratch) cudaFree(q);
     v->weights = nullptr;
+    v->wimage = nullptr;
     v->ray_t = nullptr;
     v->ray_es = nullptr;
     v->ray_n = v->ray_alb = v->ray_base = nullptr;
@@ -122,7 +126,8 @@ int alloc_scratch(sdfddgi_volume* v) {
     if (!rc) rc = alloc((void**)&v->ray_lit, n * sizeof(uint32_t));
     if (!rc) rc = alloc((void**)&v->ray_ssteps, n * sizeof(uint32_t));
     if (!rc) rc = alloc((void**)&v->counters, 4 * sizeof(uint32_t));
-    if (!rc) rc = alloc((void**)&v->weights, (size_t)(v->desc.rays_per_probe + 1) * kTexels * sizeof(float));
+    if (!rc) rc = alloc((void**)&v->weights, weights_bytes(v->desc.rays_per_probe));
+    if (!rc) rc = alloc(&v->wimage, wimage_bytes(v->desc.rays_per_probe));
     return rc;
 }
 
@@ -457,9 +462,26 @@ SDFDDGI_API int sdfddgi_update_probes(sdfddgi_volume* v, uint32_t frame, const f
     p.task_capacity = (uint32_t)(v->task_capacity < 0xffffffffu ? v->task_capacity : 0xffffffffu);
     p.counters = v->counters;
     p.weights = v->weights;
-    cudaError_t e = launch_update(p, st);
+    p.wimage = v->wimage;
+    cudaError_t e = launch_update(p, st, v->has_stage_events ? v->stage_events : nullptr);
     if (e != cudaSuccess) return fail(SDFDDGI_ERR_CUDA, "update_probes: launch failed: %s", cudaGetErrorString(e));
     v->cur = next;
+    return SDFDDGI_OK;
+}
+
+SDFDDGI_API int sdfddgi_set_stage_events(sdfddgi_volume* v, void* const* events, int32_t n) {
+    if (!v) return fail(SDFDDGI_ERR_INVALID_ARG, "set_stage_events: volume is NULL");
+    if (n == 0) {
+        v->has_stage_events = false;
+        return SDFDDGI_OK;
+    }
+    if (n != SDFDDGI_STAGE_EVENTS || !events)
+        return fail(SDFDDGI_ERR_INVALID_ARG, "set_stage_events: pass %d events or none", SDFDDGI_STAGE_EVENTS);
+    for (int k = 0; k < n; ++k) {
+        if (!events[k]) return fail(SDFDDGI_ERR_INVALID_ARG, "set_stage_events: event %d is NULL", k);
+        v->stage_events[k] = static_cast<cudaEvent_t>(events[k]);
+    }
+    v->has_stage_events = true;
     return SDFDDGI_OK;
 }
 

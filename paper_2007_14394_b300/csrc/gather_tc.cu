@@ -1,0 +1,335 @@
+// gather_tc.cu -- the gather of Eq. 3 on the 5th-generation tensor cores (tcgen05).
+//
+// For one frame the texel weights W[texel][ray] = max(0, u.d)^e are shared by every probe,
+// so the gather of G probes is one dense contraction
+//     D[texel][probe*6 + c] = sum_ray W[texel][ray] * V[ray][probe*6 + c],
+// c = (radiance r, g, b, distance t, t^2, 1); the last channel makes D hold each texel's
+// weight sum, so that numerator and denominator see the same rounding of W.
+//   A = W, 256 texel rows (irradiance 0..35, depth 36..231, zero padding) as two M = 128
+//       tiles, K-major, prepared once per frame by pack_weights_kernel as a shared-memory
+//       image and brought in per 32-ray chunk with one bulk copy;
+//   B = V for the CTA's 16 probes (N = 96), split by the CTA from the rays' values;
+//   D = two 128 x 96 fp32 accumulators in tensor memory.
+// Precision: fp32 operands split as hi + lo tf32 and multiplied as hi*hi + hi*lo + lo*hi
+// (kind::tf32, fp32 accumulation): products carry about 21 significant bits.
+// One elected thread issues the MMAs; chunks alternate between two shared-memory stages,
+// each guarded by mbarriers (bulk-copy arrival and MMA completion). Every wait is bounded:
+// on timeout the kernel records an error bit, skips the rest and releases its tensor memory.
+#include "device.cuh"
+
+namespace sdfddgi {
+
+namespace tc {
+
+constexpr int kG = 16;                        // probes per CTA
+constexpr int kCh = 6;                        // channels per probe
+constexpr int kN = kG * kCh;                  // 96 accumulator columns per tile
+constexpr int kChunk = 32;                    // rays per K chunk
+constexpr int kTileBytes = 128 * kChunk * 4;  // one tile, one part, one chunk: 16 KiB
+constexpr int kABytes = 2 * 2 * kTileBytes;   // 2 tiles x (hi, lo): 64 KiB per chunk
+constexpr int kBPart = kN * kChunk * 4;       // 12 KiB
+constexpr int kBBytes = 2 * kBPart;           // hi, lo: 24 KiB per chunk
+constexpr int kThreads = 256;
+constexpr int kTmemCols = 256;                // 2 x 96 used
+constexpr uint32_t kSpinLimit = 1u << 22;     // polls per bounded wait (well under a second)
+
+// byte offset of element (row, k) in a K-major, no-swizzle operand of kChunk tf32 per row:
+// 8 x 16-byte core matrices, adjacent along K 128 B apart, adjacent along rows 1024 B apart
+__host__ __device__ constexpr uint32_t core_offset(int row, int k) {
+    return (uint32_t)((row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// shared-memory matrix descriptor: no swizzle, K-major, version 1
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor: D fp32, A and B tf32, both K-major, N = kN, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait (non-blocking polls): false after kSpinLimit polls, or early once any CTA
+// of the launch has recorded a failure in *abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const uint32_t* abort) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+        if (mbar_test_wait(bar, parity)) return true;
+        if ((i & 4095u) == 4095u && (*reinterpret_cast<const volatile uint32_t*>(abort) & 2u)) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive fp32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+}  // namespace tc
+
+// The weight matrix as the A operand's shared-memory image: per 32-ray chunk, per tile,
+// hi then lo part, element (row, k) at tc::core_offset(row, k). Thread per (row, ray).
+__global__ void __launch_bounds__(256) pack_weights_kernel(const __grid_constant__ UpdateParams P) {
+    const int m = threadIdx.x;         // texel row 0..255
+    const int i = blockIdx.x;          // ray
+    const float w = m < kTexels ? P.weights[(size_t)i * kTexels + m] : 0.f;
+    const float hi = tc::to_tf32(w), lo = tc::to_tf32(w - hi);
+    const int c = i / tc::kChunk, k = i % tc::kChunk, t = m >> 7, r = m & 127;
+    unsigned char* base = reinterpret_cast<unsigned char*>(P.wimage) + (size_t)c * tc::kABytes + t * 2 * tc::kTileBytes;
+    *reinterpret_cast<float*>(base + tc::core_offset(r, k)) = hi;
+    *reinterpret_cast<float*>(base + tc::kTileBytes + tc::core_offset(r, k)) = lo;
+}
+
+__global__ void __launch_bounds__(tc::kThreads, 1) gather_tc_kernel(const __grid_constant__ UpdateParams P) {
+    using namespace tc;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA[2] = {smem, smem + kABytes};
+    unsigned char* sB[2] = {smem + 2 * kABytes, smem + 2 * kABytes + kBBytes};
+    __shared__ __align__(8) uint64_t bar_load[2], bar_mma[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+    __shared__ float s_hyst[kG];
+    __shared__ uint32_t s_flags[kG];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int p0 = blockIdx.x * kG;
+    const int ng = min(kG, P.P - p0);
+    const int n_chunks = P.R / kChunk;
+
+    // a launch in which a CTA already gave up does no further work (decided once per CTA)
+    if (tid == 0) s_fail = (int)(*reinterpret_cast<const volatile uint32_t*>(&P.counters[3]) & 2u);
+    __syncthreads();
+    if (s_fail) return;
+
+    if (warp == 0) {  // tensor-memory allocation: one warp, then give up the permit
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&bar_load[0], 1);
+        mbar_init(&bar_load[1], 1);
+        mbar_init(&bar_mma[0], 1);
+        mbar_init(&bar_mma[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < kG) {
+        uint32_t flags = 0;
+        if (tid < ng) flags = P.states ? P.states[p0 + tid].flags : (uint32_t)SDFDDGI_PROBE_ACTIVE;
+        s_flags[tid] = flags;
+        s_hyst[tid] = (tid < ng && P.prev_valid[p0 + tid] && !(flags & SDFDDGI_PROBE_REJECT_HISTORY)) ? P.hyst : 0.f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+
+    // ---- K loop over 32-ray chunks, two stages
+    for (int c = 0; c < n_chunks; ++c) {
+        const int s = c & 1;
+        if (c >= 2 && !mbar_wait(&bar_mma[s], ((c - 2) >> 1) & 1, &P.counters[3])) s_fail = 1;  // stage s free again
+        __syncthreads();
+        if (s_fail) break;
+        if (tid == 0) bulk_copy_g2s(sA[s], reinterpret_cast<const unsigned char*>(P.wimage) + (size_t)c * kABytes,
+                                    kABytes, &bar_load[s]);
+        // B: rays c*32 .. c*32+31 of the CTA's probes, split into tf32 hi + lo
+        for (int e = tid; e < kG * kChunk; e += kThreads) {
+            const int g = e / kChunk, k = e % kChunk;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            float one = 0.f;
+            if (g < ng) {
+                v = P.ray_val[(size_t)(p0 + g) * P.R + c * kChunk + k];
+                one = 1.f;
+            }
+            const float ch[kCh] = {v.x, v.y, v.z, v.w, v.w * v.w, one};
+#pragma unroll
+            for (int q = 0; q < kCh; ++q) {
+                const float hi = to_tf32(ch[q]), lo = to_tf32(ch[q] - hi);
+                const uint32_t off = core_offset(g * kCh + q, k);
+                *reinterpret_cast<float*>(sB[s] + off) = hi;
+                *reinterpret_cast<float*>(sB[s] + kBPart + off) = lo;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+        if (!mbar_wait(&bar_load[s], (c >> 1) & 1, &P.counters[3])) s_fail = 1;
+        __syncthreads();
+        if (s_fail) break;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(sA[s]), b0 = smem_u32(sB[s]);
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+#pragma unroll
+                for (int ks = 0; ks < kChunk / 8; ++ks) {
+                    const uint32_t ak = ks * 256, d = tmem + t * kN;
+                    const uint64_t ahi = make_desc(a0 + t * 2 * kTileBytes + ak, 128, 1024);
+                    const uint64_t alo = make_desc(a0 + t * 2 * kTileBytes + kTileBytes + ak, 128, 1024);
+                    const uint64_t bhi = make_desc(b0 + ak, 128, 1024);
+                    const uint64_t blo = make_desc(b0 + kBPart + ak, 128, 1024);
+                    mma_tf32(d, ahi, bhi, (c > 0 || ks > 0) ? 1u : 0u);
+                    mma_tf32(d, ahi, blo, 1u);
+                    mma_tf32(d, alo, bhi, 1u);
+                }
+            }
+            mma_commit(&bar_mma[s]);
+        }
+    }
+    // ---- all MMAs complete
+    if (!s_fail) {
+        for (int c = max(0, n_chunks - 2); c < n_chunks; ++c)
+            if (!mbar_wait(&bar_mma[c & 1], (c >> 1) & 1, &P.counters[3])) s_fail = 1;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    // ---- epilogue: warp w reads tensor-memory lanes 32*(w%4).. of tile w/4; thread = texel row
+    float4* s_irr = reinterpret_cast<float4*>(smem);                       // [kG][64]   (stages reused)
+    float2* s_dep = reinterpret_cast<float2*>(smem + kG * kIrrT * kIrrT * 16);  // [kG][256]
+    if (!s_fail) {
+        const int t = warp >> 2, row = (warp & 3) * 32 + lane, j = t * 128 + row;
+        const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + t * kN;
+        float acc[48];
+        for (int half = 0; half < 2; ++half) {  // probes 0..7, then 8..15
+            __syncwarp();                        // tcgen05.ld is warp-collective
+            tmem_ld16(lane_addr + half * 48, acc);
+            tmem_ld16(lane_addr + half * 48 + 16, acc + 16);
+            tmem_ld16(lane_addr + half * 48 + 32, acc + 32);
+            if (j >= kTexels) continue;
+#pragma unroll
+            for (int gg = 0; gg < 8; ++gg) {
+                const int g = half * 8 + gg;
+                if (g >= ng) break;
+                const float* a = acc + gg * kCh;
+                const size_t p = (size_t)(p0 + g);
+                const bool live = (s_flags[g] & SDFDDGI_PROBE_ACTIVE) && a[5] > 0.f;
+                const float hyst = s_hyst[g], keep = 1.f - hyst, inv = live ? 1.f / a[5] : 0.f;
+                if (j < kIrrTexels) {
+                    const int k = (j / kIrrN + 1) * kIrrT + (j % kIrrN + 1);
+                    float4 out = __ldg(P.prev_irr + p * (kIrrT * kIrrT) + k);
+                    if (live) {
+                        out.x = fmaf(hyst, out.x, keep * (a[0] * inv));
+                        out.y = fmaf(hyst, out.y, keep * (a[1] * inv));
+                        out.z = fmaf(hyst, out.z, keep * (a[2] * inv));
+                        out.w = 1.f;
+                    }
+                    s_irr[g * kIrrT * kIrrT + k] = out;
+                } else {
+                    const int jj = j - kIrrTexels, k = (jj / kDepN + 1) * kDepT + (jj % kDepN + 1);
+                    float2 out = __ldg(P.prev_depth + p * (kDepT * kDepT) + k);
+                    if (live) {
+                        out.x = fmaf(hyst, out.x, keep * (a[3] * inv));
+                        out.y = fmaf(hyst, out.y, keep * (a[4] * inv));
+                    }
+                    s_dep[g * kDepT * kDepT + k] = out;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    if (s_fail) {
+        if (tid == 0) atomicOr(&P.counters[3], 2u);  // reported by the host as a timeout
+        return;
+    }
+
+    // ---- borders (inactive probes: a copy of the old map), then contiguous stores
+    for (int e = tid; e < ng * kIrrT * kIrrT; e += kThreads) {
+        const int g = e / (kIrrT * kIrrT), k = e % (kIrrT * kIrrT);
+        const int y = k / kIrrT, x = k % kIrrT;
+        const int2 sc = border_source(y, x, kIrrN);
+        if (!(s_flags[g] & SDFDDGI_PROBE_ACTIVE))
+            s_irr[e] = __ldg(P.prev_irr + (size_t)(p0 + g) * (kIrrT * kIrrT) + k);
+        else if (sc.x != y || sc.y != x)
+            s_irr[e] = s_irr[g * kIrrT * kIrrT + sc.x * kIrrT + sc.y];
+    }
+    for (int e = tid; e < ng * kDepT * kDepT; e += kThreads) {
+        const int g = e / (kDepT * kDepT), k = e % (kDepT * kDepT);
+        const int y = k / kDepT, x = k % kDepT;
+        const int2 sc = border_source(y, x, kDepN);
+        if (!(s_flags[g] & SDFDDGI_PROBE_ACTIVE))
+            s_dep[e] = __ldg(P.prev_depth + (size_t)(p0 + g) * (kDepT * kDepT) + k);
+        else if (sc.x != y || sc.y != x)
+            s_dep[e] = s_dep[g * kDepT * kDepT + sc.x * kDepT + sc.y];
+    }
+    __syncthreads();
+    float4* cur_i = P.cur_irr + (size_t)p0 * (kIrrT * kIrrT);
+    for (int e = tid; e < ng * kIrrT * kIrrT; e += kThreads) cur_i[e] = s_irr[e];
+    float4* cur_d4 = reinterpret_cast<float4*>(P.cur_depth + (size_t)p0 * (kDepT * kDepT));
+    const float4* sd4 = reinterpret_cast<const float4*>(s_dep);
+    for (int e = tid; e < ng * kDepT * kDepT / 2; e += kThreads) cur_d4[e] = sd4[e];
+    if (tid < ng) P.cur_valid[p0 + tid] = (s_flags[tid] & SDFDDGI_PROBE_ACTIVE) ? 1 : P.prev_valid[p0 + tid];
+}
+
+bool gather_tc_supported(const UpdateParams& p) { return p.R % tc::kChunk == 0 && p.wimage != nullptr; }
+
+size_t wimage_bytes(int R) { return (size_t)((R + tc::kChunk - 1) / tc::kChunk) * tc::kABytes; }
+
+cudaError_t launch_gather_tc(const UpdateParams& p, cudaStream_t stream) {
+    pack_weights_kernel<<<p.R, 256, 0, stream>>>(p);
+    const size_t smem = 2 * (tc::kABytes + tc::kBBytes);
+    cudaError_t e = cudaFuncSetAttribute(gather_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    gather_tc_kernel<<<(p.P + tc::kG - 1) / tc::kG, tc::kThreads, smem, stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace sdfddgi

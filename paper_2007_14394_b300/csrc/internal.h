@@ -74,7 +74,11 @@ struct UpdateParams {
     uint32_t* tasks;          // shadow tasks (k << 5 | light)
     uint32_t task_capacity;
     uint32_t* counters;       // [0] primary pool, [1] task count, [2] shadow pool, [3] task overflow
-    float* weights;           // [R][kTexels] texel weights of the frame's ray set, then [kTexels] column sums
+    float* weights;           // [R][kTexels] texel weights of the frame's ray set, [kTexels] column sums,
+                              // then room for [R] float4 ray directions (weights_bytes(R) in all)
+    float4* dirs;             // [R] the frame's ray directions (same for every probe), set by launch_update
+    float4* ray_val;          // [P*R] radiance rgb + clamped distance per ray, set by launch_update
+    void* wimage;             // null, or wimage_bytes(R): the weights as the tensor-core gather's operand
 };
 
 constexpr int kTexels = kIrrTexels + kDepTexels;  // 232 gather rows: irradiance texels first
@@ -91,10 +95,16 @@ struct SampleParams {
     int64_t n;
 };
 
-cudaError_t launch_update(const UpdateParams& p, cudaStream_t stream);
+// stage_events: null, or SDFDDGI_STAGE_EVENTS events recorded on `stream` at the stage boundaries
+cudaError_t launch_update(const UpdateParams& p, cudaStream_t stream, cudaEvent_t const* stage_events = nullptr);
 cudaError_t launch_sample(const SampleParams& p, cudaStream_t stream);
 size_t quad_bytes(int dtype, size_t n_voxels);
+inline size_t weights_bytes(int R) { return ((size_t)(R + 1) * kTexels + (size_t)R * 4) * sizeof(float); }
 int report_error(int code, const char* msg);  // sets the text of sdfddgi_last_error(), returns code
+// the gather of Eq. 3 on the tensor cores (R a multiple of 32 and a weight image present)
+bool gather_tc_supported(const UpdateParams& p);
+size_t wimage_bytes(int R);
+cudaError_t launch_gather_tc(const UpdateParams& p, cudaStream_t stream);
 cudaError_t build_quads(const void* sdf, void* quads, int dtype, const int dims[3], cudaStream_t stream);
 
 }  // namespace sdfddgi

@@ -110,7 +110,7 @@ SDFDDGI_API int sdfddgi_update_probes_noalloc(
                             n_rays * 4,   // ray_ssteps
                             n_rays * 4 * (size_t)(n_lights > 0 ? n_lights : 1),  // tasks
                             16,           // counters
-                            (size_t)(R + 1) * kTexels * 4};  // weights
+                            weights_bytes(R)};  // texel weights, their sums, ray directions
     size_t off[sizeof sizes / sizeof sizes[0]], total = 0;
     for (size_t k = 0; k < sizeof sizes / sizeof sizes[0]; ++k) {
         off[k] = total;

@@ -136,6 +136,12 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
     }
 }
 
+// Direction of ray i of the frame (shared by every probe), stored by the weights stage.
+__device__ __forceinline__ float3 ray_dir(const UpdateParams& P, int i) {
+    const float4 d = __ldg(P.dirs + i);
+    return f3(d.x, d.y, d.z);
+}
+
 __device__ __forceinline__ float3 probe_origin(const UpdateParams& P, int p, uint32_t* flags) {
     if (P.states) {
         const sdfddgi_probe_state st = P.states[p];
@@ -185,7 +191,7 @@ __global__ void __launch_bounds__(kThreads) primary_kernel(const __grid_constant
                 P.ray_es[k] = kNoRay;
                 return false;
             }
-            st.d = ray_direction(i, P.R, P.rot);
+            st.d = ray_dir(P, i);
             st.tlimit = P.tmax_w;
             st.aux = k;
             return true;
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(const __grid_constant__ 
             const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
             uint32_t flags;
             const float3 o = probe_origin(P, p, &flags);
-            const float3 d = ray_direction(i, P.R, P.rot);
+            const float3 d = ray_dir(P, i);
             const float3 x = fma3(P.ray_t[k], d, o);
             const float hh = 0.5f * V.h;
             const float gx = sample_sdf<T>(V, f3(x.x + hh, x.y, x.z)) - sample_sdf<T>(V, f3(x.x - hh, x.y, x.z));
@@ -276,7 +282,7 @@ __global__ void __launch_bounds__(kThreads) shadow_kernel(const __grid_constant_
             const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
             uint32_t flags;
             const float3 o = probe_origin(P, p, &flags);
-            const float3 d = ray_direction(i, P.R, P.rot);
+            const float3 d = ray_dir(P, i);
             const float3 x = fma3(P.ray_t[k], d, o);
             const float4 n4 = P.ray_n[k];
             st.o = fma3(P.bias_w, f3(n4.x, n4.y, n4.z), x);
@@ -306,20 +312,26 @@ __global__ void __launch_bounds__(kThreads) shadow_kernel(const __grid_constant_
 // column's sum, in ray order.
 template <int PEXP>
 __global__ void __launch_bounds__(kThreads) weights_kernel(const __grid_constant__ UpdateParams P) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x;  // one ray per block, one texel per thread
+    const int j = threadIdx.x;
     if (j >= kTexels) return;
     const bool irr = j < kIrrTexels;
     const int jj = irr ? j : j - kIrrTexels, n = irr ? kIrrN : kDepN;
     const float3 u = texel_dir(jj % n, jj / n, n);
+    const float3 d = ray_direction(i, P.R, P.rot);
+    if (j == 0) P.dirs[i] = make_float4(d.x, d.y, d.z, 0.f);
+    const float c = fmaf(u.x, d.x, fmaf(u.y, d.y, u.z * d.z));
+    float w = 0.f;
+    if (c > 0.f) w = irr ? c : (PEXP == 50 ? pow50(c) : pow_runtime(c, P.depth_exp));
+    P.weights[(size_t)i * kTexels + j] = w;
+}
+
+// Column sums of the texel weights, in ray order.
+__global__ void __launch_bounds__(kThreads) weight_sums_kernel(const __grid_constant__ UpdateParams P) {
+    const int j = threadIdx.x;
+    if (j >= kTexels) return;
     float sw = 0.f;
-    for (int i = 0; i < P.R; ++i) {
-        const float3 d = ray_direction(i, P.R, P.rot);
-        const float c = fmaf(u.x, d.x, fmaf(u.y, d.y, u.z * d.z));
-        float w = 0.f;
-        if (c > 0.f) w = irr ? c : (PEXP == 50 ? pow50(c) : pow_runtime(c, P.depth_exp));
-        sw += w;
-        P.weights[(size_t)i * kTexels + j] = w;
-    }
+    for (int i = 0; i < P.R; ++i) sw += P.weights[(size_t)i * kTexels + j];
     P.weights[(size_t)P.R * kTexels + j] = sw;
 }
 
@@ -349,11 +361,47 @@ __device__ __forceinline__ float4 ray_value(const UpdateParams& P, size_t k, int
                        fmaf(a.z * inv_pi, direct.z, b.z), fminf(t, P.tmax_w));
 }
 
-// G probes per CTA. Stage a: every ray of the G probes gets its radiance and clamped
-// distance into shared memory (one float4 per ray and probe). Stage b: thread j owns
-// texel j of all G probes and accumulates sum_i W[i][j] v_i over the rays, reading W
-// coalesced and each v_i as a shared-memory broadcast. Stage c: normalise by the column
-// sum, mix with last frame's texel, fill the borders, store each map contiguously.
+// One thread per ray: the ray's value for the gather -- radiance and clamped distance,
+// zero for rays of inactive probes -- written over the ray's normal, which no later stage
+// reads; and the ray's record when records were asked for.
+__global__ void __launch_bounds__(kThreads) finalize_kernel(const __grid_constant__ UpdateParams P) {
+    const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
+    const uint32_t es = P.ray_es[k];
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if ((es & 0xffu) != kNoRay) {
+        uint32_t flags, lit;
+        const float3 o = probe_origin(P, p, &flags);
+        v = ray_value(P, k, i, o, ray_dir(P, i), &lit);
+        if (P.records) {
+            sdfddgi_ray_record rec;
+            rec.t = P.ray_t[k];
+            rec.L[0] = v.x;
+            rec.L[1] = v.y;
+            rec.L[2] = v.z;
+            rec.lit_mask = lit;
+            rec.shadow_steps = P.ray_ssteps[k];
+            rec.steps = (uint16_t)(es >> 8);
+            rec.event = (uint8_t)(es & 0xffu);
+            rec.reserved0 = 0;
+            rec.reserved1 = 0;
+            P.records[k] = rec;
+        }
+    } else if (P.records) {
+        sdfddgi_ray_record rec = {};
+        rec.event = kNoRay;
+        P.records[k] = rec;
+    }
+    P.ray_val[k] = v;
+}
+
+// G probes per CTA. Stage a: the rays' values of the G probes go to shared memory (one
+// float4 per ray and probe). Stage b: thread j owns texel j of all G probes and
+// accumulates sum_i W[i][j] v_i over the rays, reading W coalesced and each v_i as a
+// shared-memory broadcast. Stage c: normalise by the column sum, mix with last frame's
+// texel, fill the borders, store each map contiguously.
 template <int G>
 __global__ void __launch_bounds__(kThreads) gather_kernel(const __grid_constant__ UpdateParams P) {
     extern __shared__ float4 s_val[];  // [R][G]
@@ -376,36 +424,10 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(const __grid_constant_
     }
     __syncthreads();
 
-    // a. per-ray values
+    // a. the rays' values, [ray][probe]
     for (int e = tid; e < P.R * G; e += nt) {
         const int i = e / G, g = e % G;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (g < ng && (s_flags[g] & SDFDDGI_PROBE_ACTIVE)) {
-            const size_t k = (size_t)(p0 + g) * P.R + i;
-            const float3 d = ray_direction(i, P.R, P.rot);
-            uint32_t lit;
-            v = ray_value(P, k, i, s_o[g], d, &lit);
-            if (P.records) {
-                const uint32_t es = P.ray_es[k];
-                sdfddgi_ray_record rec;
-                rec.t = P.ray_t[k];
-                rec.L[0] = v.x;
-                rec.L[1] = v.y;
-                rec.L[2] = v.z;
-                rec.lit_mask = lit;
-                rec.shadow_steps = P.ray_ssteps[k];
-                rec.steps = (uint16_t)(es >> 8);
-                rec.event = (uint8_t)(es & 0xffu);
-                rec.reserved0 = 0;
-                rec.reserved1 = 0;
-                P.records[k] = rec;
-            }
-        } else if (g < ng && P.records) {
-            sdfddgi_ray_record rec = {};
-            rec.event = kNoRay;
-            P.records[(size_t)(p0 + g) * P.R + i] = rec;
-        }
-        s_val[e] = v;
+        s_val[e] = g < ng ? P.ray_val[(size_t)(p0 + g) * P.R + i] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
 
@@ -522,28 +544,50 @@ static cudaError_t launch_gather(const UpdateParams& p, cudaStream_t stream) {
 }
 
 template <typename T>
-static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream) {
+static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cudaEvent_t const* ev) {
     static const int g_primary = persistent_blocks(primary_kernel<T>);
     static const int g_shadow = persistent_blocks(shadow_kernel<T>);
-    cudaError_t e = cudaMemsetAsync(p.counters, 0, 4 * sizeof(uint32_t), stream);
+    auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], stream) : cudaSuccess; };
+    cudaError_t e = mark(0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.counters, 0, 4 * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return e;
     const uint32_t n = (uint32_t)p.P * (uint32_t)p.R;
     if (p.depth_exp == 50)
-        weights_kernel<50><<<(kTexels + kThreads - 1) / kThreads, kThreads, 0, stream>>>(p);
+        weights_kernel<50><<<p.R, kThreads, 0, stream>>>(p);
     else
-        weights_kernel<0><<<(kTexels + kThreads - 1) / kThreads, kThreads, 0, stream>>>(p);
+        weights_kernel<0><<<p.R, kThreads, 0, stream>>>(p);
+    weight_sums_kernel<<<1, kThreads, 0, stream>>>(p);
+    if ((e = mark(1)) != cudaSuccess) return e;
     primary_kernel<T><<<g_primary, kThreads, 0, stream>>>(p);
+    if ((e = mark(2)) != cudaSuccess) return e;
     prep_kernel<T><<<(n + kThreads - 1) / kThreads, kThreads, 0, stream>>>(p);
+    if ((e = mark(3)) != cudaSuccess) return e;
     shadow_kernel<T><<<g_shadow, kThreads, 0, stream>>>(p);
+    if ((e = mark(4)) != cudaSuccess) return e;
+    finalize_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, stream>>>(p);
+    if (gather_tc_supported(p)) {
+        e = launch_gather_tc(p, stream);
+        if (e != cudaSuccess) return e;
+        return mark(5);
+    }
     // probes per gather CTA: as many as keep the [R][G] values within 32 KiB of shared memory
-    if (p.R <= 256) return launch_gather<8>(p, stream);
-    if (p.R <= 512) return launch_gather<4>(p, stream);
-    return launch_gather<2>(p, stream);
+    if (p.R <= 256)
+        e = launch_gather<8>(p, stream);
+    else if (p.R <= 512)
+        e = launch_gather<4>(p, stream);
+    else
+        e = launch_gather<2>(p, stream);
+    if (e != cudaSuccess) return e;
+    return mark(5);
 }
 
-cudaError_t launch_update(const UpdateParams& p, cudaStream_t stream) {
-    if (p.P == 0) return cudaSuccess;
-    return p.vol.dtype == SDFDDGI_F16 ? launch_stages<__half>(p, stream) : launch_stages<float>(p, stream);
+cudaError_t launch_update(const UpdateParams& params, cudaStream_t stream, cudaEvent_t const* stage_events) {
+    if (params.P == 0) return cudaSuccess;
+    UpdateParams p = params;
+    p.dirs = reinterpret_cast<float4*>(p.weights + (size_t)(p.R + 1) * kTexels);  // after the weights
+    p.ray_val = p.ray_n;  // the gather's values replace the normals, dead after the shadow stage
+    return p.vol.dtype == SDFDDGI_F16 ? launch_stages<__half>(p, stream, stage_events)
+                                      : launch_stages<float>(p, stream, stage_events);
 }
 
 }  // namespace sdfddgi

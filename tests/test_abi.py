@@ -4,6 +4,7 @@ with the input generator's implementation of the same published definitions."""
 import os
 import re
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -16,10 +17,19 @@ HEADER = os.path.join(ROOT, "include", "sdfddgi.h")
 
 @pytest.fixture(scope="module")
 def S():
-    from paper_2007_14394_b300 import build
-    build.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_2007_14394_b300 as S
     return S
+
+
+def test_builder_loads_without_the_package():
+    # build() must not import the package (which needs the library it is about to build):
+    # with the package made unimportable, the builder still loads
+    code = ("import sys; sys.modules['paper_2007_14394_b300'] = None; import __graft_entry__ as g; "
+            "b = g._load_builder(); print(b.LIB.endswith('libsdfddgi.so'))")
+    out = subprocess.check_output([sys.executable, "-c", code], cwd=ROOT, text=True)
+    assert out.strip() == "True"
 
 
 def declared_symbols():
