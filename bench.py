@@ -220,7 +220,8 @@ def run_ours(args, rank, world, local_rank):
     S.upload_sdf(sc, baked.sdf, baked.h, baked.origin, material=baked.material)
     S.set_lights(sc, scene.lights, scene.sky)
     desc = S.make_desc(pr.probe_dims, R, pr.probe_origin, pr.probe_spacing, pr.max_steps, pr.depth_exponent,
-                       pr.eps_vox, pr.tmax_vox, pr.hysteresis, pr.k_bounce, pr.bias_vox, seed=pr.seed)
+                       pr.eps_vox, pr.tmax_vox, pr.hysteresis, pr.k_bounce, pr.bias_vox, seed=pr.seed,
+                       flags=S.FLAG_BLEND_BF16 if pr.blend == "bf16" else 0)
     vol = S.create_volume(desc, sc)
     states_dev = torch.from_numpy(states.view(np.uint8).copy()).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -336,7 +337,8 @@ def run_ours(args, rank, world, local_rank):
     roof.update({"kernel": dominant, "traffic": measured_traffic(dominant, args.workload)})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if pr.blend == "f32" and pr.sdf_dtype == "f32" else f"{pr.sdf_dtype} sdf, {pr.blend} gather",
         "data": "synthetic (seeded scene, baked on the host)", "config": workload_config(pr, rays_per_step),
         "gpu_launches": KERNELS_PER_UPDATE * args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": P * 16,

@@ -63,6 +63,13 @@ enum { SDFDDGI_LIGHT_DIRECTIONAL = 0, SDFDDGI_LIGHT_POINT = 1 };    /* light typ
 enum { SDFDDGI_PROBE_ACTIVE = 1u, SDFDDGI_PROBE_REJECT_HISTORY = 2u }; /* probe flags   */
 enum { SDFDDGI_MAX_LIGHTS = 32, SDFDDGI_MAX_RAYS = 1024, SDFDDGI_MAX_STEPS = 65535 };
 enum { SDFDDGI_STAGE_EVENTS = 6 };
+/* Volume flags. BLEND_BF16 -- the precision form of the gather (Eq. 3): texel weights and
+ * ray values rounded to bf16, products accumulated in fp32 on the tensor cores, instead of
+ * the default float32-accurate gather (three tf32 products per term). It applies when
+ * rays_per_probe is a multiple of 32 (otherwise the float32 gather runs). Combine it with a
+ * binary16 SDF (upload_sdf dtype SDFDDGI_F16; stepping stays float32) for the full
+ * precision form. */
+enum { SDFDDGI_FLAG_BLEND_BF16 = 1u };
 
 /* Octahedral map sizes (Sec. 3.3: octahedral mapping into the probe atlas):
  * irradiance 6x6 interior texels + 1-texel border = 8x8, RGBA float32 per texel
@@ -104,7 +111,7 @@ typedef struct {
     float normal_bias;        /* shadow-ray origin offset along the normal, voxels (>= 0) */
     uint32_t seed;            /* seed of the per-frame ray rotation */
     uint32_t volume_id;       /* distinguishes rotations of volumes sharing a seed */
-    uint32_t flags;           /* reserved, must be 0 */
+    uint32_t flags;           /* 0, or SDFDDGI_FLAG_BLEND_BF16 */
 } sdfddgi_volume_desc;
 
 /* Per-ray record of one update (32 bytes), written only when requested:

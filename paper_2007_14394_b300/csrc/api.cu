@@ -316,7 +316,8 @@ SDFDDGI_API int sdfddgi_create_volume(const sdfddgi_volume_desc* d, sdfddgi_scen
         return fail(SDFDDGI_ERR_INVALID_ARG, "create_volume: multibounce_k outside [0, 1]");
     if (!(d->normal_bias >= 0.f) || !std::isfinite(d->normal_bias))
         return fail(SDFDDGI_ERR_INVALID_ARG, "create_volume: normal_bias must be >= 0");
-    if (d->flags != 0) return fail(SDFDDGI_ERR_INVALID_ARG, "create_volume: flags must be 0");
+    if (d->flags & ~(uint32_t)SDFDDGI_FLAG_BLEND_BF16)
+        return fail(SDFDDGI_ERR_INVALID_ARG, "create_volume: unknown flags 0x%x", d->flags);
 
     sdfddgi_volume* v = new (std::nothrow) sdfddgi_volume();
     if (!v) return fail(SDFDDGI_ERR_OOM, "create_volume: host allocation failed");
@@ -463,6 +464,7 @@ SDFDDGI_API int sdfddgi_update_probes(sdfddgi_volume* v, uint32_t frame, const f
     p.counters = v->counters;
     p.weights = v->weights;
     p.wimage = v->wimage;
+    p.blend_bf16 = (d.flags & SDFDDGI_FLAG_BLEND_BF16) ? 1 : 0;
     cudaError_t e = launch_update(p, st, v->has_stage_events ? v->stage_events : nullptr);
     if (e != cudaSuccess) return fail(SDFDDGI_ERR_CUDA, "update_probes: launch failed: %s", cudaGetErrorString(e));
     v->cur = next;

@@ -10,11 +10,16 @@
 //       image and brought in per 32-ray chunk with one bulk copy;
 //   B = V for the CTA's 16 probes (N = 96), split by the CTA from the rays' values;
 //   D = two 128 x 96 fp32 accumulators in tensor memory.
-// Precision: fp32 operands split as hi + lo tf32 and multiplied as hi*hi + hi*lo + lo*hi
-// (kind::tf32, fp32 accumulation): products carry about 21 significant bits.
+// Precision (template parameter): fp32 operands split as hi + lo tf32 and multiplied as
+// hi*hi + hi*lo + lo*hi (kind::tf32, fp32 accumulation; products carry about 21 significant
+// bits), or the precision form: one bf16 x bf16 product (kind::f16, fp32 accumulation).
 // One elected thread issues the MMAs; chunks alternate between two shared-memory stages,
 // each guarded by mbarriers (bulk-copy arrival and MMA completion). Every wait is bounded:
 // on timeout the kernel records an error bit, skips the rest and releases its tensor memory.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
 #include "device.cuh"
 
 namespace sdfddgi {
@@ -25,19 +30,31 @@ constexpr int kG = 16;                        // probes per CTA
 constexpr int kCh = 6;                        // channels per probe
 constexpr int kN = kG * kCh;                  // 96 accumulator columns per tile
 constexpr int kChunk = 32;                    // rays per K chunk
-constexpr int kTileBytes = 128 * kChunk * 4;  // one tile, one part, one chunk: 16 KiB
-constexpr int kABytes = 2 * 2 * kTileBytes;   // 2 tiles x (hi, lo): 64 KiB per chunk
-constexpr int kBPart = kN * kChunk * 4;       // 12 KiB
-constexpr int kBBytes = 2 * kBPart;           // hi, lo: 24 KiB per chunk
 constexpr int kThreads = 256;
 constexpr int kTmemCols = 256;                // 2 x 96 used
 constexpr uint32_t kSpinLimit = 1u << 22;     // polls per bounded wait (well under a second)
 
-// byte offset of element (row, k) in a K-major, no-swizzle operand of kChunk tf32 per row:
-// 8 x 16-byte core matrices, adjacent along K 128 B apart, adjacent along rows 1024 B apart
-__host__ __device__ constexpr uint32_t core_offset(int row, int k) {
-    return (uint32_t)((row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
-}
+// Operand format: 4-byte tf32 in hi + lo parts, or one 2-byte bf16 part. Operands are
+// K-major without swizzle: 8 x 16-byte core matrices, adjacent along K 128 B apart,
+// adjacent along rows kRowBytes * 8 apart; one MMA consumes 32 bytes of K.
+template <bool BF16>
+struct Fmt {
+    static constexpr int kElem = BF16 ? 2 : 4;
+    static constexpr int kParts = BF16 ? 1 : 2;
+    static constexpr int kRowBytes = kChunk * kElem;           // one row of one chunk
+    static constexpr int kSbo = kRowBytes * 8;                 // between 8-row groups
+    static constexpr int kTilePart = 128 * kRowBytes;          // one M = 128 tile, one part
+    static constexpr int kABytes = 2 * kParts * kTilePart;     // both tiles, all parts
+    static constexpr int kBPart = kN * kRowBytes;
+    static constexpr int kBBytes = kParts * kBPart;
+    static constexpr int kKSteps = kRowBytes / 32;
+    // D fp32; A, B tf32 (kind::tf32) or bf16 (kind::f16); K-major; N = kN; M = 128
+    static constexpr uint32_t kIdesc = (1u << 4) | ((BF16 ? 1u : 2u) << 7) | ((BF16 ? 1u : 2u) << 10) |
+                                       ((uint32_t)(kN >> 3) << 17) | ((128u >> 4) << 24);
+    __host__ __device__ static constexpr uint32_t offset(int row, int k) {
+        return (uint32_t)((row >> 3) * kSbo + ((k * kElem) >> 4) * 128 + (row & 7) * 16 + ((k * kElem) & 15));
+    }
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -54,9 +71,6 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
     return (uint64_t)((saddr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | ((uint64_t)1 << 46);
 }
-
-// instruction descriptor: D fp32, A and B tf32, both K-major, N = kN, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
@@ -93,13 +107,32 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
                  : "memory");
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
-        : "memory");
+template <bool BF16>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    if constexpr (BF16) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(Fmt<true>::kIdesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(Fmt<false>::kIdesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
+// one operand element (hi or lo part) at byte offset off of a part
+template <bool BF16>
+__device__ __forceinline__ void put(unsigned char* part, uint32_t off, float v) {
+    if constexpr (BF16)
+        *reinterpret_cast<__nv_bfloat16*>(part + off) = __float2bfloat16_rn(v);
+    else
+        *reinterpret_cast<float*>(part + off) = v;
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -123,20 +156,30 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }  // namespace tc
 
 // The weight matrix as the A operand's shared-memory image: per 32-ray chunk, per tile,
-// hi then lo part, element (row, k) at tc::core_offset(row, k). Thread per (row, ray).
+// its parts (tf32: hi then lo; bf16: one), element (row, k) at Fmt::offset(row, k).
+// Thread per (texel row, ray).
+template <bool BF16>
 __global__ void __launch_bounds__(256) pack_weights_kernel(const __grid_constant__ UpdateParams P) {
+    using F = tc::Fmt<BF16>;
     const int m = threadIdx.x;         // texel row 0..255
     const int i = blockIdx.x;          // ray
     const float w = m < kTexels ? P.weights[(size_t)i * kTexels + m] : 0.f;
-    const float hi = tc::to_tf32(w), lo = tc::to_tf32(w - hi);
     const int c = i / tc::kChunk, k = i % tc::kChunk, t = m >> 7, r = m & 127;
-    unsigned char* base = reinterpret_cast<unsigned char*>(P.wimage) + (size_t)c * tc::kABytes + t * 2 * tc::kTileBytes;
-    *reinterpret_cast<float*>(base + tc::core_offset(r, k)) = hi;
-    *reinterpret_cast<float*>(base + tc::kTileBytes + tc::core_offset(r, k)) = lo;
+    unsigned char* base = reinterpret_cast<unsigned char*>(P.wimage) + (size_t)c * F::kABytes + t * F::kParts * F::kTilePart;
+    if constexpr (BF16) {
+        tc::put<true>(base, F::offset(r, k), w);
+    } else {
+        const float hi = tc::to_tf32(w), lo = tc::to_tf32(w - hi);
+        tc::put<false>(base, F::offset(r, k), hi);
+        tc::put<false>(base + F::kTilePart, F::offset(r, k), lo);
+    }
 }
 
+template <bool BF16>
 __global__ void __launch_bounds__(tc::kThreads, 1) gather_tc_kernel(const __grid_constant__ UpdateParams P) {
     using namespace tc;
+    using F = Fmt<BF16>;
+    constexpr int kABytes = F::kABytes, kBBytes = F::kBBytes, kBPart = F::kBPart, kTilePart = F::kTilePart;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA[2] = {smem, smem + kABytes};
     unsigned char* sB[2] = {smem + 2 * kABytes, smem + 2 * kABytes + kBBytes};
@@ -188,7 +231,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) gather_tc_kernel(const __grid
         if (s_fail) break;
         if (tid == 0) bulk_copy_g2s(sA[s], reinterpret_cast<const unsigned char*>(P.wimage) + (size_t)c * kABytes,
                                     kABytes, &bar_load[s]);
-        // B: rays c*32 .. c*32+31 of the CTA's probes, split into tf32 hi + lo
+        // B: rays c*32 .. c*32+31 of the CTA's probes (tf32: split into hi + lo)
         for (int e = tid; e < kG * kChunk; e += kThreads) {
             const int g = e / kChunk, k = e % kChunk;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -200,10 +243,14 @@ __global__ void __launch_bounds__(tc::kThreads, 1) gather_tc_kernel(const __grid
             const float ch[kCh] = {v.x, v.y, v.z, v.w, v.w * v.w, one};
 #pragma unroll
             for (int q = 0; q < kCh; ++q) {
-                const float hi = to_tf32(ch[q]), lo = to_tf32(ch[q] - hi);
-                const uint32_t off = core_offset(g * kCh + q, k);
-                *reinterpret_cast<float*>(sB[s] + off) = hi;
-                *reinterpret_cast<float*>(sB[s] + kBPart + off) = lo;
+                const uint32_t off = F::offset(g * kCh + q, k);
+                if constexpr (BF16) {
+                    put<true>(sB[s], off, ch[q]);
+                } else {
+                    const float hi = to_tf32(ch[q]), lo = to_tf32(ch[q] - hi);
+                    put<false>(sB[s], off, hi);
+                    put<false>(sB[s] + kBPart, off, lo);
+                }
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
@@ -216,15 +263,17 @@ __global__ void __launch_bounds__(tc::kThreads, 1) gather_tc_kernel(const __grid
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
 #pragma unroll
-                for (int ks = 0; ks < kChunk / 8; ++ks) {
-                    const uint32_t ak = ks * 256, d = tmem + t * kN;
-                    const uint64_t ahi = make_desc(a0 + t * 2 * kTileBytes + ak, 128, 1024);
-                    const uint64_t alo = make_desc(a0 + t * 2 * kTileBytes + kTileBytes + ak, 128, 1024);
-                    const uint64_t bhi = make_desc(b0 + ak, 128, 1024);
-                    const uint64_t blo = make_desc(b0 + kBPart + ak, 128, 1024);
-                    mma_tf32(d, ahi, bhi, (c > 0 || ks > 0) ? 1u : 0u);
-                    mma_tf32(d, ahi, blo, 1u);
-                    mma_tf32(d, alo, bhi, 1u);
+                for (int ks = 0; ks < F::kKSteps; ++ks) {
+                    const uint32_t ak = ks * 256, d = tmem + t * kN;  // 32 bytes of K per MMA
+                    const uint32_t at = a0 + t * F::kParts * kTilePart + ak;
+                    const uint64_t ahi = make_desc(at, 128, F::kSbo), bhi = make_desc(b0 + ak, 128, F::kSbo);
+                    mma<BF16>(d, ahi, bhi, (c > 0 || ks > 0) ? 1u : 0u);
+                    if constexpr (!BF16) {
+                        const uint64_t alo = make_desc(at + kTilePart, 128, F::kSbo);
+                        const uint64_t blo = make_desc(b0 + kBPart + ak, 128, F::kSbo);
+                        mma<false>(d, ahi, blo, 1u);
+                        mma<false>(d, alo, bhi, 1u);
+                    }
                 }
             }
             mma_commit(&bar_mma[s]);
@@ -321,15 +370,23 @@ __global__ void __launch_bounds__(tc::kThreads, 1) gather_tc_kernel(const __grid
 
 bool gather_tc_supported(const UpdateParams& p) { return p.R % tc::kChunk == 0 && p.wimage != nullptr; }
 
-size_t wimage_bytes(int R) { return (size_t)((R + tc::kChunk - 1) / tc::kChunk) * tc::kABytes; }
+size_t wimage_bytes(int R) { return (size_t)((R + tc::kChunk - 1) / tc::kChunk) * tc::Fmt<false>::kABytes; }
+
+template <bool BF16>
+static cudaError_t launch_tc(const UpdateParams& p, cudaStream_t stream) {
+    using F = tc::Fmt<BF16>;
+    pack_weights_kernel<BF16><<<p.R, 256, 0, stream>>>(p);
+    // the two operand stages, reused by the epilogue's map staging (kG probes x 3 KiB)
+    const size_t epilogue = (size_t)tc::kG * (kIrrT * kIrrT * sizeof(float4) + kDepT * kDepT * sizeof(float2));
+    const size_t smem = std::max<size_t>(2 * (F::kABytes + F::kBBytes), epilogue);
+    cudaError_t e = cudaFuncSetAttribute(gather_tc_kernel<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    gather_tc_kernel<BF16><<<(p.P + tc::kG - 1) / tc::kG, tc::kThreads, smem, stream>>>(p);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_gather_tc(const UpdateParams& p, cudaStream_t stream) {
-    pack_weights_kernel<<<p.R, 256, 0, stream>>>(p);
-    const size_t smem = 2 * (tc::kABytes + tc::kBBytes);
-    cudaError_t e = cudaFuncSetAttribute(gather_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    gather_tc_kernel<<<(p.P + tc::kG - 1) / tc::kG, tc::kThreads, smem, stream>>>(p);
-    return cudaGetLastError();
+    return p.blend_bf16 ? launch_tc<true>(p, stream) : launch_tc<false>(p, stream);
 }
 
 }  // namespace sdfddgi

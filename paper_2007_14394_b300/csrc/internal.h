@@ -79,6 +79,7 @@ struct UpdateParams {
     float4* dirs;             // [R] the frame's ray directions (same for every probe), set by launch_update
     float4* ray_val;          // [P*R] radiance rgb + clamped distance per ray, set by launch_update
     void* wimage;             // null, or wimage_bytes(R): the weights as the tensor-core gather's operand
+    int blend_bf16;           // 1: the tensor-core gather multiplies bf16 x bf16 (the precision form)
 };
 
 constexpr int kTexels = kIrrTexels + kDepTexels;  // 232 gather rows: irradiance texels first

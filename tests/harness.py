@@ -125,7 +125,7 @@ def conditioning(geo, vals, dvals, o_map, active):
 class GpuVolume:
     """A scene + probe volume in the CUDA library, built from a Workload."""
 
-    def __init__(self, w: Workload, seed: int = 0):
+    def __init__(self, w: Workload, seed: int = 0, flags: int = 0):
         import torch
         import paper_2007_14394_b300 as S
         self.S, self.torch, self.w = S, torch, w
@@ -135,7 +135,7 @@ class GpuVolume:
         S.set_lights(self.scene, w.lights, w.sky)
         self.desc = S.make_desc(p["probe_dims"], p["rays"], p["probe_origin"], p["probe_spacing"], p["max_steps"],
                                 p["depth_exponent"], p["eps_vox"], p["tmax_vox"], p["hysteresis"], p["k_bounce"],
-                                p["bias_vox"], seed=seed)
+                                p["bias_vox"], seed=seed, flags=flags)
         self.vol = S.create_volume(self.desc, self.scene)
         self.states_dev = torch.from_numpy(w.states.view(np.uint8).copy()).cuda()
         self.records = torch.empty(w.P * p["rays"] * 32, dtype=torch.uint8, device="cuda")
