@@ -356,7 +356,164 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
-def oracle_sample(pr, scene, baked, states, n_probes, seed=0, frame=0, threads=0):
+def run_batch(args, rank, world, local_rank):
+    """A cascade of volumes (Sec. 3.5) as one batch: one CUDA-graph launch per frame after the
+    autotuner has chosen each volume's schedule, against the same volumes updated by one plain
+    launch each (default schedules). One step = one frame of every volume."""
+    import torch
+    import paper_2007_14394_b300 as S
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    c = W.CASCADES[args.workload]
+    base = c.base
+    scene = c.scene()
+    baked = W.bake(scene, base.sdf_dims, base.h, (0.0, 0.0, 0.0), dtype=base.sdf_dtype)
+    states = [W.probe_states(scene, v.probe_dims, v.probe_origin, v.probe_spacing, v.h) for v in c.volumes]
+    n_active = [int((st["flags"] & 1).sum()) for st in states]
+    rays_per_step = sum(a * v.rays for a, v in zip(n_active, c.volumes))
+
+    sc = S.create_scene()
+    S.upload_sdf(sc, baked.sdf, baked.h, baked.origin, material=baked.material)
+    S.set_lights(sc, scene.lights, scene.sky)
+    vols, states_dev = [], []
+    for i, v in enumerate(c.volumes):
+        desc = S.make_desc(v.probe_dims, v.rays, v.probe_origin, v.probe_spacing, v.max_steps, v.depth_exponent,
+                           v.eps_vox, v.tmax_vox, v.hysteresis, v.k_bounce, v.bias_vox, seed=v.seed, volume_id=i)
+        vols.append(S.create_volume(desc, sc))
+        states_dev.append(torch.from_numpy(states[i].view(np.uint8).copy()).to(dev))
+    batch = S.create_batch(vols, states_dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # one recorded plain update per volume (outside any timed region) for the algorithmic work
+    work = []
+    for i, v in enumerate(c.volumes):
+        records = torch.empty(v.n_probes * v.rays * 32, dtype=torch.uint8, device=dev)
+        S.update_probes(vols[i], 0, states=states_dev[i], records=records)
+        torch.cuda.synchronize()
+        rec = records.cpu().numpy().view(S.RAY_RECORD_DTYPE)
+        work.append(stage_work(rec, 4 if base.sdf_dtype == "f32" else 2, v.n_probes, v.rays, n_active[i]))
+        del records
+        S.reset(vols[i])
+    t_tune = time.perf_counter()
+    S.batch_autotune(batch, repeats=3, stream=stream)
+    t_tune = time.perf_counter() - t_tune
+    schedules = [dict(zip(("pool_batch", "blocks_per_sm", "gather", "tuned_ms"), S.batch_schedule(batch, i)))
+                 for i in range(len(vols))]
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(step_fn, frame0):
+        for k in range(args.warmup):
+            step_fn(frame0 + k)
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            step_fn(frame0 + args.warmup + k)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+    def plain(frame):
+        for i in range(len(vols)):
+            S.update_probes(vols[i], frame, states=states_dev[i], stream=stream)
+
+    clocks = Clocks(local_rank)
+    t0 = time.perf_counter()
+    per_step = timed(lambda f: S.update_batch(batch, f, stream=stream), 0)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    seq_step = timed(plain, 10_000)
+
+    # end to end: probe states in from pinned host memory, every volume's maps out
+    host_states = [torch.from_numpy(st.view(np.uint8).copy()).pin_memory() for st in states]
+    outs = [(torch.empty(v.n_probes * 8 * 8 * 4, dtype=torch.float32).pin_memory(),
+             torch.empty(v.n_probes * 16 * 16 * 2, dtype=torch.float32).pin_memory(),
+             torch.empty(v.n_probes, dtype=torch.uint8).pin_memory()) for v in c.volumes]
+
+    def e2e_step(frame):
+        for d, h in zip(states_dev, host_states):
+            d.copy_(h, non_blocking=True)
+        S.update_batch(batch, frame, stream=stream)
+        for vol, (a, b, cc) in zip(vols, outs):
+            S.lib.sdfddgi_read_state(vol, a.data_ptr(), b.data_ptr(), cc.data_ptr(), 0, S._stream(stream))
+    e2e_step_ms = timed(e2e_step, 20_000)
+
+    dev_ms, seq_ms, e2e_ms = float(sum(per_step)), float(sum(seq_step)), float(sum(e2e_step_ms))
+    if world > 1:
+        t = torch.tensor([dev_ms, seq_ms, e2e_ms, wall], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dev_ms, seq_ms, e2e_ms, wall = (float(x) for x in t.tolist())
+    ms = dev_ms / args.steps
+    value = world * rays_per_step * args.steps / (dev_ms / 1e3)
+    hbm, peak_kind = peaks()
+    frame_bytes = sum(w[k]["bytes"] for w in work for k in ("primary", "prep", "shadow"))
+    ach = frame_bytes / (ms / 1e3) / 1e9
+    roof = {"kernel": "frame (all stages of all volumes in one graph)", "bound": "hbm", "achieved": ach,
+            "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "bytes_per_launch": frame_bytes,
+            "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
+            "note": "trace/prep/shadow gathered bytes of every volume over the whole frame's time"}
+    P_all = sum(v.n_probes for v in c.volumes)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"{base.sdf_dtype} sdf, f32 gather", "data": "synthetic (seeded scene, baked on the host)",
+        "config": {"workload": f"{c.name}: {c.description}", "volumes": [
+            {"probes": v.n_probes, "rays_per_probe": v.rays, "active_probes": a, **sch}
+            for v, a, sch in zip(c.volumes, n_active, schedules)],
+            "sdf": "x".join(map(str, base.sdf_dims)) + f" {base.sdf_dtype}", "max_steps": base.max_steps,
+            "active_rays_per_step": rays_per_step, "seed": base.seed,
+            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)", "autotune_s": t_tune},
+        "gpu_launches": KERNELS_PER_UPDATE * len(vols) * args.steps,
+        "sequential": {"ms_per_step": seq_ms / args.steps, "value": world * rays_per_step * args.steps / (seq_ms / 1e3),
+                       "what": "one plain update_probes launch per volume, default schedules, same stream"},
+        "e2e": {"value": world * rays_per_step * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": P_all * 16,
+                "d2h_bytes_per_step": P_all * (8 * 8 * 4 * 4 + 16 * 16 * 2 * 4 + 1),
+                "ms_per_step": e2e_ms / args.steps},
+        "roofline": roof,
+        "wall_s_timed_loop": wall,
+        "step_ms": {"min": min(per_step), "median": statistics.median(per_step), "max": max(per_step)},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cascade_cpu_baseline(c, scene, baked, states, budget_s=args.cpu_budget)
+    S.destroy_batch(batch)
+    for v in vols:
+        S.destroy_volume(v)
+    S.destroy_scene(sc)
+    return line
+
+
+def cascade_cpu_baseline(c, scene, baked, states, budget_s=10.0):
+    """The oracle on a seeded sample of every volume's active probes, about budget_s seconds in
+    all; the frame time is extrapolated linearly in the probe counts."""
+    cores = os.cpu_count() or 1
+    per_vol = budget_s / len(c.volumes)
+    frame_s, rays, samples = 0.0, 0, []
+    for i, (v, st) in enumerate(zip(c.volumes, states)):
+        n_act = int((st["flags"] & 1).sum())
+        dt, _ = oracle_sample(v, scene, baked, st, max(4, cores), volume=i)
+        n = int(max(4, min(n_act, max(4, cores) * per_vol / max(dt, 1e-3))))
+        dt, r = oracle_sample(v, scene, baked, st, n, seed=1, volume=i)
+        frame_s += dt * n_act / n
+        rays += n_act * v.rays
+        samples.append(f"{n}/{n_act}")
+    return {"value": rays / frame_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"seeded active probes per volume {', '.join(samples)} of {c.name}, one frame each; "
+                      f"frame time extrapolated linearly", "ms_per_step": 1e3 * frame_s}
+
+
+def oracle_sample(pr, scene, baked, states, n_probes, seed=0, frame=0, threads=0, volume=0):
     """Times the oracle's update of a seeded sample of active probes; returns (seconds, rays)."""
     import oracle as O
     act = np.flatnonzero(states["flags"] & 1)
@@ -365,7 +522,7 @@ def oracle_sample(pr, scene, baked, states, n_probes, seed=0, frame=0, threads=0
     osc = O.OracleScene(baked.sdf, baked.h, baked.origin, baked.material)
     g = O.make_grid(pr.probe_dims, pr.probe_origin, pr.probe_spacing, pr.rays, pr.max_steps, pr.eps_vox,
                     pr.tmax_vox, pr.hysteresis, pr.depth_exponent, pr.k_bounce, pr.bias_vox, scene.sky)
-    rot = W.frame_rotation(pr.seed, frame)
+    rot = W.frame_rotation(pr.seed, frame, volume)
     t0 = time.perf_counter()
     O.update(osc, g, scene.lights, rot, states, subset=sub, want_rays=False, n_threads=threads)
     return time.perf_counter() - t0, len(sub) * pr.rays
@@ -426,7 +583,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.PRESETS))
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.PRESETS) + sorted(W.CASCADES))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
@@ -437,6 +594,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
+        if args.workload in W.CASCADES:
+            ap.error("the reference arm times single-volume workloads")
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
         return
@@ -445,7 +604,8 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    line = run_ours(args, rank, world, local_rank)
+    run = run_batch if args.workload in W.CASCADES else run_ours
+    line = run(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -57,6 +57,7 @@ typedef enum {
 
 typedef struct sdfddgi_scene sdfddgi_scene;   /* SDF + material volume + lights */
 typedef struct sdfddgi_volume sdfddgi_volume; /* probe grid + ping-pong probe maps */
+typedef struct sdfddgi_batch sdfddgi_batch;   /* volumes updated together (one graph launch) */
 
 enum { SDFDDGI_F32 = 0, SDFDDGI_F16 = 1 };                          /* SDF storage type  */
 enum { SDFDDGI_LIGHT_DIRECTIONAL = 0, SDFDDGI_LIGHT_POINT = 1 };    /* light type        */
@@ -229,6 +230,48 @@ SDFDDGI_API int sdfddgi_write_state(sdfddgi_volume* v, const float* irr, const f
 /* Clears every map and the history (as at creation). */
 SDFDDGI_API int sdfddgi_reset(sdfddgi_volume* v, void* stream);
 
+/* ---- several volumes in one launch ------------------------------------- */
+
+/* Sec. 3.5 (cascade volume) covers a large scene with several probe volumes of
+ * different density -- dense near the camera, sparse far away -- all updated every
+ * frame. A batch updates up to 8 volumes of one scene together: each frame is one
+ * CUDA graph, with one branch per volume, so the volumes' stages overlap on the GPU and
+ * the frame costs one launch. Each volume computes exactly what sdfddgi_update_probes
+ * would compute for it with the same launch shapes (schedule); the results do not
+ * depend on the schedule beyond the rounding order of the gather.
+ *  volumes -- n distinct volumes of the same scene (not owned; they must outlive the
+ *             batch and must not be updated by other calls while the batch is in use).
+ *  states  -- NULL, or n pointers each NULL (grid positions) or P_i DEVICE states that
+ *             the batch reads at every update (the caller may rewrite their contents
+ *             between updates, not the pointers).
+ *  n       -- 1..8.
+ * Errors: SDFDDGI_ERR_INVALID_ARG (NULL, n out of range, a repeated volume, volumes of
+ * different scenes), SDFDDGI_ERR_OOM / SDFDDGI_ERR_CUDA (stream, event or buffer). */
+SDFDDGI_API int sdfddgi_create_batch(sdfddgi_volume* const* volumes, const sdfddgi_probe_state* const* states,
+                                     int32_t n, sdfddgi_batch** out);
+SDFDDGI_API void sdfddgi_destroy_batch(sdfddgi_batch* b);
+
+/* One frame of every volume in the batch, enqueued on `stream` (any stream; NULL is the
+ * legacy default stream). rotation: NULL (each volume's own sdfddgi_frame_rotation of
+ * `frame`) or host float[9*n], volume i's row-major rotation at [9*i]. The graph is built
+ * on first use and rebuilt after the scene changes (upload_sdf / set_lights) or a schedule
+ * changes. Successive calls for one batch must be ordered on the GPU (the same stream,
+ * or streams the caller orders), and not made from two host threads at once. */
+SDFDDGI_API int sdfddgi_update_batch(sdfddgi_batch* b, uint32_t frame, const float* rotation, void* stream);
+
+/* Chooses each volume's schedule by timing `repeats` real updates (plus one warm-up) of
+ * each candidate on `stream`: trace-pool batch (16, 32, 64 tasks per warp claim), resident
+ * CTAs per SM of the trace kernels (4 or the occupancy limit), and gather (tensor cores
+ * when rays_per_probe is a multiple of 32, or SIMT). The trials write only each volume's
+ * spare ping-pong buffer, so the maps and history are unchanged. Synchronises `stream`.
+ * repeats: 1..64. */
+SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* stream);
+
+/* Volume i's schedule: out[0] pool batch, out[1] CTAs per SM (0 = occupancy limit),
+ * out[2] gather (0 automatic, 1 tensor cores, 2 SIMT); tuned_ms (nullable) receives the
+ * autotuner's mean update time of that schedule (0 before tuning). */
+SDFDDGI_API int sdfddgi_batch_schedule(const sdfddgi_batch* b, int32_t i, int32_t out[3], float* tuned_ms);
+
 /* ---- the update without device allocation ------------------------------ */
 
 /* The paper has no counterpart to this entry point; it exists for callers that may not
@@ -247,7 +290,8 @@ SDFDDGI_API int sdfddgi_reset(sdfddgi_volume* v, void* stream);
  * SDFDDGI_ERR_INVALID_ARG before any device work, and sdfddgi_last_error() states the
  * bytes needed and available.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before capturing any stream.
+ *    (cudaGetSymbolAddress) and makes the kernels' one-time set-up (occupancy and
+ *    shared-memory limits); make that first call before capturing any stream.
  *  - Every call on a device shares the one array and leaves its contents behind (the
  *    parts that must start at zero are cleared by each call): calls whose work overlaps
  *    on the GPU (different streams, or different host threads) race; serialise them.

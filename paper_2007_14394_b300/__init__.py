@@ -55,7 +55,7 @@ assert RAY_RECORD_DTYPE.itemsize == 32 and PROBE_STATE_DTYPE.itemsize == 16
 
 def _load() -> C.CDLL:
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2007_14394_b300.build` "
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2007_14394_b300/build.py` "
                           "(the CUDA library is required; there is no fallback)")
     lib = C.CDLL(LIB_PATH)
     vp, i32, u32, i64 = C.c_void_p, C.c_int32, C.c_uint32, C.c_int64
@@ -79,6 +79,11 @@ def _load() -> C.CDLL:
         "sdfddgi_update_probes_noalloc": ([C.POINTER(VolumeDesc), vp, C.POINTER(i32), C.c_float, C.POINTER(C.c_float),
                                            i32, vp, C.POINTER(Light), i32, C.POINTER(C.c_float), u32, vp, vp,
                                            vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
+        "sdfddgi_create_batch": ([C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(vp)], C.c_int),
+        "sdfddgi_destroy_batch": ([vp], None),
+        "sdfddgi_update_batch": ([vp, u32, vp, vp], C.c_int),
+        "sdfddgi_batch_autotune": ([vp, i32, vp], C.c_int),
+        "sdfddgi_batch_schedule": ([vp, i32, C.POINTER(i32), C.POINTER(C.c_float)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -90,7 +95,8 @@ def _load() -> C.CDLL:
 lib = _load()
 EXPORTED = ("last_error", "create_scene", "destroy_scene", "upload_sdf", "set_lights", "create_volume",
             "destroy_volume", "volume_probe_count", "frame_rotation", "update_probes", "update_probes_noalloc",
-            "sample_irradiance", "set_stage_events", "get_maps", "read_state", "write_state", "reset")
+            "sample_irradiance", "set_stage_events", "get_maps", "read_state", "write_state", "reset",
+            "create_batch", "destroy_batch", "update_batch", "batch_autotune", "batch_schedule")
 STAGES = ("weights", "primary", "prep", "shadow", "gather")  # intervals between the stage events
 
 
@@ -296,3 +302,49 @@ def update_probes_noalloc(desc: VolumeDesc, sdf, voxel_size: float, origin, ligh
         _floats(sky, 3), int(frame), rot.ctypes.data if rot is not None else None, _ptr(states)[0],
         _ptr(prev[0])[0], _ptr(prev[1])[0], _ptr(prev[2])[0], _ptr(cur[0])[0], _ptr(cur[1])[0], _ptr(cur[2])[0],
         _ptr(records)[0], _stream(stream)))
+
+
+def create_batch(volumes, states=None) -> C.c_void_p:
+    """volumes: handles of one scene; states: None or one entry per volume, None or a device tensor of
+    P_i * 16 bytes (read at every update_batch)."""
+    n = len(volumes)
+    vols = (C.c_void_p * n)(*[v.value if isinstance(v, C.c_void_p) else v for v in volumes])
+    sts = None
+    if states is not None:
+        if len(states) != n:
+            raise ValueError("one states entry per volume")
+        ptrs = []
+        for s in states:
+            p, dev = _ptr(s)
+            if s is not None and not dev:
+                raise ValueError("batch states must be device tensors")
+            ptrs.append(p)
+        sts = (C.c_void_p * n)(*ptrs)
+    h = C.c_void_p()
+    _check(lib.sdfddgi_create_batch(vols, sts, n, C.byref(h)))
+    return h
+
+
+def destroy_batch(batch) -> None:
+    lib.sdfddgi_destroy_batch(batch)
+
+
+def update_batch(batch, frame: int, rotations=None, stream=None) -> None:
+    """rotations: None (each volume's frame_rotation of `frame`) or float32 [n][3][3] host array."""
+    rot = None
+    if rotations is not None:
+        rot = np.ascontiguousarray(np.asarray(rotations, dtype=np.float32).reshape(-1))
+    _check(lib.sdfddgi_update_batch(batch, int(frame), rot.ctypes.data if rot is not None else None,
+                                    _stream(stream)))
+
+
+def batch_autotune(batch, repeats: int = 3, stream=None) -> None:
+    _check(lib.sdfddgi_batch_autotune(batch, int(repeats), _stream(stream)))
+
+
+def batch_schedule(batch, i: int):
+    """(pool_batch, blocks_per_sm, gather, tuned_ms) of volume i."""
+    out = (C.c_int32 * 3)()
+    ms = C.c_float()
+    _check(lib.sdfddgi_batch_schedule(batch, int(i), out, C.byref(ms)))
+    return out[0], out[1], out[2], ms.value

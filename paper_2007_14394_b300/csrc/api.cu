@@ -9,54 +9,9 @@
 #include <cstring>
 #include <new>
 
-#include "internal.h"
+#include "handles.h"
 
 using namespace sdfddgi;
-
-struct sdfddgi_scene {
-    int device = 0;
-    void* sdf = nullptr;
-    size_t sdf_bytes = 0;
-    void* quads = nullptr;  // xy-quad copy of the SDF read by the trace kernels
-    size_t quads_bytes = 0;
-    void* material = nullptr;
-    size_t material_bytes = 0;
-    int dims[3] = {0, 0, 0};
-    int dtype = SDFDDGI_F32;
-    float h = 0.f;
-    float origin[3] = {0.f, 0.f, 0.f};
-    bool has_sdf = false;
-    bool has_material = false;
-    LightDev lights[SDFDDGI_MAX_LIGHTS] = {};
-    int n_lights = 0;
-    float sky[3] = {0.f, 0.f, 0.f};
-};
-
-struct sdfddgi_volume {
-    sdfddgi_volume_desc desc{};
-    sdfddgi_scene* scene = nullptr;
-    int64_t P = 0;
-    float4* irr[2] = {nullptr, nullptr};
-    float2* depth[2] = {nullptr, nullptr};
-    uint8_t* valid[2] = {nullptr, nullptr};
-    sdfddgi_probe_state* states = nullptr;  // staging for host-side probe states
-    int cur = 0;
-    // per-ray scratch of the staged update (P * R entries each) and the shadow-task list
-    float* ray_t = nullptr;
-    uint32_t* ray_es = nullptr;
-    float4* ray_n = nullptr;
-    float4* ray_alb = nullptr;
-    float4* ray_base = nullptr;
-    uint32_t* ray_lit = nullptr;
-    uint32_t* ray_ssteps = nullptr;
-    uint32_t* counters = nullptr;
-    uint32_t* tasks = nullptr;
-    size_t task_capacity = 0;
-    float* weights = nullptr;  // texel weights of the frame's ray set and their column sums
-    void* wimage = nullptr;    // the weights as the tensor-core gather's operand image
-    cudaEvent_t stage_events[SDFDDGI_STAGE_EVENTS] = {};  // caller's, recorded at stage boundaries
-    bool has_stage_events = false;
-};
 
 namespace {
 
@@ -243,6 +198,7 @@ SDFDDGI_API int sdfddgi_upload_sdf(sdfddgi_scene* s, const void* sdf, const int3
     s->h = voxel_size;
     s->has_sdf = true;
     s->has_material = material != nullptr;
+    s->version++;
     return SDFDDGI_OK;
 }
 
@@ -283,6 +239,7 @@ SDFDDGI_API int sdfddgi_set_lights(sdfddgi_scene* s, const sdfddgi_light* lights
     std::memcpy(s->lights, tmp, sizeof tmp);
     s->n_lights = n;
     std::memcpy(s->sky, sky, sizeof sky);
+    s->version++;
     return SDFDDGI_OK;
 }
 
@@ -339,7 +296,8 @@ SDFDDGI_API int sdfddgi_create_volume(const sdfddgi_volume_desc* d, sdfddgi_scen
     }
     rc = sdfddgi_reset(v, nullptr);
     if (!rc) {
-        cudaError_t e = cudaStreamSynchronize(nullptr);
+        cudaError_t e = prepare_update_kernels();  // so that later updates can be captured
+        if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
         if (e != cudaSuccess) rc = fail(SDFDDGI_ERR_CUDA, "create_volume: %s", cudaGetErrorString(e));
     }
     if (rc) {
@@ -380,35 +338,14 @@ SDFDDGI_API int sdfddgi_frame_rotation(uint32_t seed, uint32_t frame, uint32_t v
     return SDFDDGI_OK;
 }
 
-SDFDDGI_API int sdfddgi_update_probes(sdfddgi_volume* v, uint32_t frame, const float* rotation,
-                                      const sdfddgi_probe_state* states, int32_t states_on_device,
-                                      sdfddgi_ray_record* records, void* stream) {
-    if (!v) return fail(SDFDDGI_ERR_INVALID_ARG, "update_probes: volume is NULL");
-    sdfddgi_scene* s = v->scene;
-    if (!s || !s->has_sdf) return fail(SDFDDGI_ERR_STATE, "update_probes: the scene holds no SDF yet");
-    if (states_on_device != 0 && states_on_device != 1)
-        return fail(SDFDDGI_ERR_INVALID_ARG, "update_probes: states_on_device must be 0 or 1");
-    const sdfddgi_volume_desc& d = v->desc;
-    cudaStream_t st = as_stream(stream);
+}  // extern "C"
 
-    UpdateParams p;
+int sdfddgi::volume_params(sdfddgi_volume* v, UpdateParams* out) {
+    sdfddgi_scene* s = v->scene;
+    if (!s || !s->has_sdf) return fail(SDFDDGI_ERR_STATE, "update: the scene holds no SDF yet");
+    const sdfddgi_volume_desc& d = v->desc;
+    UpdateParams& p = *out;
     std::memset(&p, 0, sizeof p);
-    if (rotation) {
-        for (int k = 0; k < 9; ++k) {
-            if (!std::isfinite(rotation[k])) return fail(SDFDDGI_ERR_INVALID_ARG, "update_probes: rotation not finite");
-            p.rot[k] = rotation[k];
-        }
-    } else {
-        sdfddgi_frame_rotation(d.seed, frame, d.volume_id, p.rot);
-    }
-    if (states) {
-        if (states_on_device) {
-            p.states = states;
-        } else {
-            CUDA_TRY(cudaMemcpyAsync(v->states, states, sizeof(sdfddgi_probe_state) * v->P, cudaMemcpyHostToDevice, st));
-            p.states = v->states;
-        }
-    }
     VolumeView& vol = p.vol;
     vol.sdf = s->sdf;
     vol.quads = s->quads;
@@ -449,7 +386,6 @@ SDFDDGI_API int sdfddgi_update_probes(sdfddgi_volume* v, uint32_t frame, const f
     p.cur_irr = v->irr[next];
     p.cur_depth = v->depth[next];
     p.cur_valid = v->valid[next];
-    p.records = records;
     int rc = ensure_task_capacity(v, s->n_lights);
     if (rc) return rc;
     p.ray_t = v->ray_t;
@@ -465,9 +401,41 @@ SDFDDGI_API int sdfddgi_update_probes(sdfddgi_volume* v, uint32_t frame, const f
     p.weights = v->weights;
     p.wimage = v->wimage;
     p.blend_bf16 = (d.flags & SDFDDGI_FLAG_BLEND_BF16) ? 1 : 0;
+    return SDFDDGI_OK;
+}
+
+extern "C" {
+
+SDFDDGI_API int sdfddgi_update_probes(sdfddgi_volume* v, uint32_t frame, const float* rotation,
+                                      const sdfddgi_probe_state* states, int32_t states_on_device,
+                                      sdfddgi_ray_record* records, void* stream) {
+    if (!v) return fail(SDFDDGI_ERR_INVALID_ARG, "update_probes: volume is NULL");
+    if (states_on_device != 0 && states_on_device != 1)
+        return fail(SDFDDGI_ERR_INVALID_ARG, "update_probes: states_on_device must be 0 or 1");
+    if (rotation)
+        for (int k = 0; k < 9; ++k)
+            if (!std::isfinite(rotation[k])) return fail(SDFDDGI_ERR_INVALID_ARG, "update_probes: rotation not finite");
+    cudaStream_t st = as_stream(stream);
+    UpdateParams p;
+    int rc = volume_params(v, &p);
+    if (rc) return rc;
+    if (rotation) {
+        for (int k = 0; k < 9; ++k) p.rot[k] = rotation[k];
+    } else {
+        sdfddgi_frame_rotation(v->desc.seed, frame, v->desc.volume_id, p.rot);
+    }
+    if (states) {
+        if (states_on_device) {
+            p.states = states;
+        } else {
+            CUDA_TRY(cudaMemcpyAsync(v->states, states, sizeof(sdfddgi_probe_state) * v->P, cudaMemcpyHostToDevice, st));
+            p.states = v->states;
+        }
+    }
+    p.records = records;
     cudaError_t e = launch_update(p, st, v->has_stage_events ? v->stage_events : nullptr);
     if (e != cudaSuccess) return fail(SDFDDGI_ERR_CUDA, "update_probes: launch failed: %s", cudaGetErrorString(e));
-    v->cur = next;
+    v->cur ^= 1;
     return SDFDDGI_OK;
 }
 

@@ -1,0 +1,254 @@
+// batch.cu -- several probe volumes (e.g. the nested cascades of the paper's Sec. 3.5)
+// updated together: one CUDA graph per frame, with one branch per volume, so that the
+// volumes' stages overlap on the GPU (a small volume's pool tails fill with the large
+// volumes' work) and the whole frame is a single launch from the host. The graph is
+// captured once per ping-pong parity and scene version and replayed; the frame's
+// rotations reach it through a small device buffer written before each replay.
+//
+// The autotuner picks each volume's launch shapes (trace-pool batch, resident CTAs per
+// SM of the trace kernels, tensor-core or SIMT gather) by timing real updates of that
+// volume; the trials write only the volume's spare ping-pong buffer.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "handles.h"
+
+using namespace sdfddgi;
+
+namespace {
+
+constexpr int kMaxBatch = 8;
+constexpr int kGraphCache = 4;
+
+struct CachedGraph {
+    uint64_t key = 0;
+    uint64_t version = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+
+int bfail(int code, const char* msg) { return report_error(code, msg); }
+
+}  // namespace
+
+struct sdfddgi_batch {
+    int n = 0;
+    sdfddgi_volume* vols[kMaxBatch] = {};
+    const sdfddgi_probe_state* states[kMaxBatch] = {};  // device, or null (grid positions)
+    Schedule sched[kMaxBatch] = {};
+    float tuned_ms[kMaxBatch] = {};
+    cudaStream_t side[kMaxBatch] = {};
+    cudaStream_t capture = nullptr;  // graphs are captured here (capture needs a non-legacy stream)
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kMaxBatch] = {};
+    float* rot_dev = nullptr;  // [n][9]
+    CachedGraph cache[kGraphCache];
+    int next_slot = 0;
+};
+
+namespace {
+
+void drop_graphs(sdfddgi_batch* b) {
+    for (auto& c : b->cache) {
+        if (c.exec) cudaGraphExecDestroy(c.exec);
+        c = CachedGraph();
+    }
+}
+
+// Records the stages of every volume, one forked stream each, on the capturing stream.
+int record_frame(sdfddgi_batch* b, cudaStream_t st) {
+    cudaError_t e = cudaEventRecord(b->fork, st);
+    for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+        UpdateParams p;
+        int rc = volume_params(b->vols[i], &p);
+        if (rc) return rc;
+        p.rot_dev = b->rot_dev + 9 * i;
+        p.states = b->states[i];
+        p.sched = b->sched[i];
+        e = cudaStreamWaitEvent(b->side[i], b->fork, 0);
+        if (e == cudaSuccess) e = launch_update(p, b->side[i]);
+        if (e == cudaSuccess) e = cudaEventRecord(b->join[i], b->side[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->join[i], 0);
+    }
+    if (e != cudaSuccess) return bfail(SDFDDGI_ERR_CUDA, cudaGetErrorString(e));
+    return SDFDDGI_OK;
+}
+
+uint64_t parity_key(const sdfddgi_batch* b) {
+    uint64_t k = 0;
+    for (int i = 0; i < b->n; ++i) k |= (uint64_t)(b->vols[i]->cur & 1) << i;
+    return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+SDFDDGI_API int sdfddgi_create_batch(sdfddgi_volume* const* volumes, const sdfddgi_probe_state* const* states,
+                                     int32_t n, sdfddgi_batch** out) {
+    if (out) *out = nullptr;
+    if (!out || !volumes) return bfail(SDFDDGI_ERR_INVALID_ARG, "create_batch: NULL argument");
+    if (n < 1 || n > kMaxBatch) return bfail(SDFDDGI_ERR_INVALID_ARG, "create_batch: n must be in [1, 8]");
+    for (int i = 0; i < n; ++i) {
+        if (!volumes[i]) return bfail(SDFDDGI_ERR_INVALID_ARG, "create_batch: a volume is NULL");
+        if (volumes[i]->scene != volumes[0]->scene)
+            return bfail(SDFDDGI_ERR_INVALID_ARG, "create_batch: the volumes must share one scene");
+        for (int j = 0; j < i; ++j)
+            if (volumes[j] == volumes[i]) return bfail(SDFDDGI_ERR_INVALID_ARG, "create_batch: a volume appears twice");
+    }
+    sdfddgi_batch* b = new (std::nothrow) sdfddgi_batch();
+    if (!b) return bfail(SDFDDGI_ERR_OOM, "create_batch: host allocation failed");
+    b->n = n;
+    cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        b->vols[i] = volumes[i];
+        b->states[i] = states ? states[i] : nullptr;
+        e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->rot_dev, sizeof(float) * 9 * n);
+    if (e != cudaSuccess) {
+        sdfddgi_destroy_batch(b);
+        return bfail(e == cudaErrorMemoryAllocation ? SDFDDGI_ERR_OOM : SDFDDGI_ERR_CUDA, cudaGetErrorString(e));
+    }
+    *out = b;
+    return SDFDDGI_OK;
+}
+
+SDFDDGI_API void sdfddgi_destroy_batch(sdfddgi_batch* b) {
+    if (!b) return;
+    drop_graphs(b);
+    for (int i = 0; i < kMaxBatch; ++i) {
+        if (b->side[i]) cudaStreamDestroy(b->side[i]);
+        if (b->join[i]) cudaEventDestroy(b->join[i]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    cudaFree(b->rot_dev);
+    delete b;
+}
+
+SDFDDGI_API int sdfddgi_update_batch(sdfddgi_batch* b, uint32_t frame, const float* rotations, void* stream) {
+    if (!b) return bfail(SDFDDGI_ERR_INVALID_ARG, "update_batch: batch is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float rot[kMaxBatch * 9];
+    for (int i = 0; i < b->n; ++i) {
+        if (rotations) {
+            for (int k = 0; k < 9; ++k) {
+                if (!std::isfinite(rotations[9 * i + k])) return bfail(SDFDDGI_ERR_INVALID_ARG, "update_batch: rotation not finite");
+                rot[9 * i + k] = rotations[9 * i + k];
+            }
+        } else {
+            const sdfddgi_volume_desc& d = b->vols[i]->desc;
+            sdfddgi_frame_rotation(d.seed, frame, d.volume_id, rot + 9 * i);
+        }
+    }
+    // everything the captured work reads from the host side must be current
+    UpdateParams probe;
+    for (int i = 0; i < b->n; ++i) {
+        int rc = volume_params(b->vols[i], &probe);  // also sizes the shadow-task lists
+        if (rc) return rc;
+    }
+    const uint64_t key = parity_key(b), version = b->vols[0]->scene->version;
+    cudaGraphExec_t exec = nullptr;
+    for (auto& c : b->cache)
+        if (c.exec && c.key == key && c.version == version) exec = c.exec;
+    cudaError_t e;
+    if (!exec) {
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return bfail(SDFDDGI_ERR_CUDA, cudaGetErrorString(e));
+        int rc = record_frame(b, b->capture);
+        e = cudaStreamEndCapture(b->capture, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return bfail(SDFDDGI_ERR_CUDA, cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return bfail(SDFDDGI_ERR_CUDA, cudaGetErrorString(e));
+        CachedGraph& slot = b->cache[b->next_slot];
+        b->next_slot = (b->next_slot + 1) % kGraphCache;
+        if (slot.exec) cudaGraphExecDestroy(slot.exec);
+        slot.key = key;
+        slot.version = version;
+        slot.exec = exec;
+    }
+    e = cudaMemcpyAsync(b->rot_dev, rot, sizeof(float) * 9 * b->n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+    if (e != cudaSuccess) return bfail(SDFDDGI_ERR_CUDA, cudaGetErrorString(e));
+    for (int i = 0; i < b->n; ++i) b->vols[i]->cur ^= 1;
+    return SDFDDGI_OK;
+}
+
+SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* stream) {
+    if (!b || repeats < 1 || repeats > 64) return bfail(SDFDDGI_ERR_INVALID_ARG, "batch_autotune: invalid arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return bfail(SDFDDGI_ERR_CUDA, "batch_autotune: cudaEventCreate failed");
+    int rc = SDFDDGI_OK;
+    for (int i = 0; i < b->n && rc == SDFDDGI_OK; ++i) {
+        sdfddgi_volume* v = b->vols[i];
+        const int R = v->desc.rays_per_probe;
+        // every trial reads the current maps and writes the other buffer, which the next
+        // real update overwrites: the volume's state is untouched
+        std::vector<Schedule> cand;
+        for (int pb : {16, 32, 64})
+            for (int bps : {0, 4})
+                for (int g : {1, 2}) {
+                    if (g == 1 && R % 32 != 0) continue;
+                    cand.push_back(Schedule{pb, bps, g});
+                }
+        float best = 1e30f;
+        Schedule best_s = {};
+        for (const Schedule& sc : cand) {
+            float total = 0.f;
+            for (int r = 0; r <= repeats && rc == SDFDDGI_OK; ++r) {  // the first run warms up
+                UpdateParams p;
+                rc = volume_params(v, &p);
+                if (rc) break;
+                sdfddgi_frame_rotation(v->desc.seed, (uint32_t)r, v->desc.volume_id, p.rot);
+                p.states = b->states[i];
+                p.sched = sc;
+                cudaEventRecord(e0, st);
+                cudaError_t e = launch_update(p, st);
+                cudaEventRecord(e1, st);
+                if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = bfail(SDFDDGI_ERR_CUDA, "batch_autotune: trial update failed");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r > 0) total += ms;
+            }
+            if (rc) break;
+            if (total / repeats < best) {
+                best = total / repeats;
+                best_s = sc;
+            }
+        }
+        if (rc == SDFDDGI_OK) {
+            b->sched[i] = best_s;
+            b->tuned_ms[i] = best;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    drop_graphs(b);
+    return rc;
+}
+
+SDFDDGI_API int sdfddgi_batch_schedule(const sdfddgi_batch* b, int32_t i, int32_t out[3], float* tuned_ms) {
+    if (!b || !out || i < 0 || i >= b->n) return bfail(SDFDDGI_ERR_INVALID_ARG, "batch_schedule: invalid arguments");
+    out[0] = b->sched[i].pool_batch;
+    out[1] = b->sched[i].blocks_per_sm;
+    out[2] = b->sched[i].gather;
+    if (tuned_ms) *tuned_ms = b->tuned_ms[i];
+    return SDFDDGI_OK;
+}
+
+}  // extern "C"

@@ -372,16 +372,28 @@ bool gather_tc_supported(const UpdateParams& p) { return p.R % tc::kChunk == 0 &
 
 size_t wimage_bytes(int R) { return (size_t)((R + tc::kChunk - 1) / tc::kChunk) * tc::Fmt<false>::kABytes; }
 
+// dynamic shared memory of the gather: the two operand stages, reused by the epilogue's map
+// staging (kG probes x 3 KiB)
+template <bool BF16>
+static size_t tc_smem() {
+    using F = tc::Fmt<BF16>;
+    const size_t epilogue = (size_t)tc::kG * (kIrrT * kIrrT * sizeof(float4) + kDepT * kDepT * sizeof(float2));
+    return std::max<size_t>(2 * (F::kABytes + F::kBBytes), epilogue);
+}
+
+cudaError_t prepare_gather_tc() {
+    cudaError_t e = cudaFuncSetAttribute(gather_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc_smem<false>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gather_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc_smem<true>());
+    return e;
+}
+
 template <bool BF16>
 static cudaError_t launch_tc(const UpdateParams& p, cudaStream_t stream) {
-    using F = tc::Fmt<BF16>;
     pack_weights_kernel<BF16><<<p.R, 256, 0, stream>>>(p);
-    // the two operand stages, reused by the epilogue's map staging (kG probes x 3 KiB)
-    const size_t epilogue = (size_t)tc::kG * (kIrrT * kIrrT * sizeof(float4) + kDepT * kDepT * sizeof(float2));
-    const size_t smem = std::max<size_t>(2 * (F::kABytes + F::kBBytes), epilogue);
-    cudaError_t e = cudaFuncSetAttribute(gather_tc_kernel<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    gather_tc_kernel<BF16><<<(p.P + tc::kG - 1) / tc::kG, tc::kThreads, smem, stream>>>(p);
+    gather_tc_kernel<BF16><<<(p.P + tc::kG - 1) / tc::kG, tc::kThreads, tc_smem<BF16>(), stream>>>(p);
     return cudaGetLastError();
 }
 

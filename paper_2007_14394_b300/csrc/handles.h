@@ -1,0 +1,58 @@
+// handles.h -- the library's opaque handles (scene, volume) and the helper that turns a
+// volume into the parameters of one update; shared by the C ABI and the batched update.
+#pragma once
+
+#include "internal.h"
+
+struct sdfddgi_scene {
+    uint64_t version = 0;  // bumped by every upload_sdf / set_lights (captured graphs depend on it)
+    int device = 0;
+    void* sdf = nullptr;
+    size_t sdf_bytes = 0;
+    void* quads = nullptr;  // xy-quad copy of the SDF read by the trace kernels
+    size_t quads_bytes = 0;
+    void* material = nullptr;
+    size_t material_bytes = 0;
+    int dims[3] = {0, 0, 0};
+    int dtype = SDFDDGI_F32;
+    float h = 0.f;
+    float origin[3] = {0.f, 0.f, 0.f};
+    bool has_sdf = false;
+    bool has_material = false;
+    sdfddgi::LightDev lights[SDFDDGI_MAX_LIGHTS] = {};
+    int n_lights = 0;
+    float sky[3] = {0.f, 0.f, 0.f};
+};
+
+struct sdfddgi_volume {
+    sdfddgi_volume_desc desc{};
+    sdfddgi_scene* scene = nullptr;
+    int64_t P = 0;
+    float4* irr[2] = {nullptr, nullptr};
+    float2* depth[2] = {nullptr, nullptr};
+    uint8_t* valid[2] = {nullptr, nullptr};
+    sdfddgi_probe_state* states = nullptr;  // staging for host-side probe states
+    int cur = 0;
+    // per-ray scratch of the staged update (P * R entries each) and the shadow-task list
+    float* ray_t = nullptr;
+    uint32_t* ray_es = nullptr;
+    float4* ray_n = nullptr;
+    float4* ray_alb = nullptr;
+    float4* ray_base = nullptr;
+    uint32_t* ray_lit = nullptr;
+    uint32_t* ray_ssteps = nullptr;
+    uint32_t* counters = nullptr;
+    uint32_t* tasks = nullptr;
+    size_t task_capacity = 0;
+    float* weights = nullptr;  // texel weights of the frame's ray set and their column sums
+    void* wimage = nullptr;    // the weights as the tensor-core gather's operand image
+    cudaEvent_t stage_events[SDFDDGI_STAGE_EVENTS] = {};  // caller's, recorded at stage boundaries
+    bool has_stage_events = false;
+};
+
+namespace sdfddgi {
+// Everything of one update of v that follows from the scene and the volume at the current
+// ping-pong parity (rotation, probe states, records and schedule are left zero); ensures the
+// shadow-task capacity. Returns an sdfddgi_status.
+int volume_params(sdfddgi_volume* v, UpdateParams* p);
+}  // namespace sdfddgi

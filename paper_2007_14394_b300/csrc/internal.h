@@ -30,6 +30,13 @@ struct VolumeView {
     float hi[3];
 };
 
+// Launch shapes of one update; zero fields select the defaults.
+struct Schedule {
+    int pool_batch;      // trace tasks a warp claims per atomic: 8, 16, 32 (default) or 64
+    int blocks_per_sm;   // resident CTAs per SM of the persistent trace kernels (default: occupancy limit)
+    int gather;          // 0 automatic (tensor cores when R % 32 == 0), 1 tensor cores, 2 SIMT
+};
+
 struct LightDev {
     int type;
     float v[3];
@@ -80,6 +87,8 @@ struct UpdateParams {
     float4* ray_val;          // [P*R] radiance rgb + clamped distance per ray, set by launch_update
     void* wimage;             // null, or wimage_bytes(R): the weights as the tensor-core gather's operand
     int blend_bf16;           // 1: the tensor-core gather multiplies bf16 x bf16 (the precision form)
+    const float* rot_dev;     // null, or the frame rotation in device memory (read instead of rot)
+    Schedule sched;           // launch shapes (chosen by the autotuner for batches)
 };
 
 constexpr int kTexels = kIrrTexels + kDepTexels;  // 232 gather rows: irradiance texels first
@@ -106,6 +115,11 @@ int report_error(int code, const char* msg);  // sets the text of sdfddgi_last_e
 bool gather_tc_supported(const UpdateParams& p);
 size_t wimage_bytes(int R);
 cudaError_t launch_gather_tc(const UpdateParams& p, cudaStream_t stream);
+cudaError_t prepare_gather_tc();  // dynamic shared-memory limits of the tensor-core gathers
+// one-time per-device set-up of the update's kernels (occupancy, shared-memory limits); the
+// first update makes it otherwise, but it must not happen inside a stream capture
+struct DeviceSetup;
+cudaError_t prepare_update_kernels(const DeviceSetup** out = nullptr);
 cudaError_t build_quads(const void* sdf, void* quads, int dtype, const int dims[3], cudaStream_t stream);
 
 }  // namespace sdfddgi

@@ -54,6 +54,9 @@ int scratch_address(void** out) {
         if (e != cudaSuccess || !p)
             return nofail(SDFDDGI_ERR_CUDA, "update_probes_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
         g_scratch_ptr[dev] = p;
+        e = prepare_update_kernels();  // the kernels' one-time set-up, on the same first call
+        if (e != cudaSuccess)
+            return nofail(SDFDDGI_ERR_CUDA, "update_probes_noalloc: kernel set-up: %s", cudaGetErrorString(e));
     }
     *out = g_scratch_ptr[dev];
     return SDFDDGI_OK;

@@ -19,6 +19,9 @@
 //                         contiguous 16-byte stores.
 // Device-wide pools pay the latency of the longest ray once per launch instead of once
 // per probe.
+#include <mutex>
+#include <type_traits>
+
 #include "device.cuh"
 
 namespace sdfddgi {
@@ -89,7 +92,7 @@ __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, f
 // take part (full-warp votes).
 template <typename T, typename Init, typename Done>
 __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint32_t* counter, float eps,
-                                           int max_steps, Init init, Done done) {
+                                           int max_steps, uint32_t batch, Init init, Done done) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     uint32_t batch_next = 0, batch_end = 0;  // warp-uniform
@@ -100,10 +103,10 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
         if (want) {
             if (batch_next >= batch_end) {
                 uint32_t b = 0;
-                if (lane == 0) b = atomicAdd(counter, (uint32_t)kBatch);
+                if (lane == 0) b = atomicAdd(counter, batch);
                 b = __shfl_sync(full, b, 0);
                 batch_next = b;
-                batch_end = b + kBatch;
+                batch_end = b + batch;
             }
             const uint32_t avail = batch_end - batch_next;
             const uint32_t rank = __popc(want & ((1u << lane) - 1u));
@@ -134,6 +137,10 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
             }
         }
     }
+}
+
+__device__ __forceinline__ uint32_t pool_batch(const UpdateParams& P) {
+    return P.sched.pool_batch > 0 ? (uint32_t)P.sched.pool_batch : (uint32_t)kBatch;
 }
 
 // Direction of ray i of the frame (shared by every probe), stored by the weights stage.
@@ -182,7 +189,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) primary_kernel(const __grid_constant__ UpdateParams P) {
     const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
     trace_pool<T>(
-        P.vol, n, &P.counters[0], P.eps_w, P.max_steps,
+        P.vol, n, &P.counters[0], P.eps_w, P.max_steps, pool_batch(P),
         [&](uint32_t k, TraceState& st) {
             const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
             uint32_t flags;
@@ -274,7 +281,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) shadow_kernel(const __grid_constant__ UpdateParams P) {
     const uint32_t n = min(P.counters[1], P.task_capacity);
     trace_pool<T>(
-        P.vol, n, &P.counters[2], P.eps_w, P.max_steps,
+        P.vol, n, &P.counters[2], P.eps_w, P.max_steps, pool_batch(P),
         [&](uint32_t j, TraceState& st) {
             const uint32_t tk = P.tasks[j];
             const uint32_t k = tk >> 5;
@@ -318,7 +325,7 @@ __global__ void __launch_bounds__(kThreads) weights_kernel(const __grid_constant
     const bool irr = j < kIrrTexels;
     const int jj = irr ? j : j - kIrrTexels, n = irr ? kIrrN : kDepN;
     const float3 u = texel_dir(jj % n, jj / n, n);
-    const float3 d = ray_direction(i, P.R, P.rot);
+    const float3 d = ray_direction(i, P.R, P.rot_dev ? P.rot_dev : P.rot);
     if (j == 0) P.dirs[i] = make_float4(d.x, d.y, d.z, 0.f);
     const float c = fmaf(u.x, d.x, fmaf(u.y, d.y, u.z * d.z));
     float w = 0.f;
@@ -524,31 +531,81 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(const __grid_constant_
 }
 
 // ------------------------------------------------------------------ launch
-template <typename K>
-static int persistent_blocks(K kernel) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
-    return max(1, sms * max(1, per_sm));
+// One-time set-up per device, made outside any stream capture (volume creation calls it):
+// the SM count, the occupancy limits of the persistent pool kernels and the dynamic
+// shared-memory limits of the gathers. Updates then make no such calls, so that they can
+// be captured into a graph.
+struct DeviceSetup {
+    bool done = false;
+    cudaError_t err = cudaSuccess;
+    int sms = 0;
+    int occ_primary[2] = {};  // [float, __half]
+    int occ_shadow[2] = {};
+};
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+DeviceSetup g_setup[kMaxDevices];
+
+template <typename T>
+constexpr int type_slot() { return std::is_same<T, float>::value ? 0 : 1; }
+
+int occupancy(const void* kernel) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, 0) != cudaSuccess) return 1;
+    return max(1, occ);
+}
+
+}  // namespace
+
+cudaError_t prepare_update_kernels(const DeviceSetup** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    DeviceSetup& s = g_setup[dev];
+    if (!s.done) {
+        s.err = cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev);
+        s.occ_primary[0] = occupancy((const void*)primary_kernel<float>);
+        s.occ_primary[1] = occupancy((const void*)primary_kernel<__half>);
+        s.occ_shadow[0] = occupancy((const void*)shadow_kernel<float>);
+        s.occ_shadow[1] = occupancy((const void*)shadow_kernel<__half>);
+        // the SIMT gathers stage [R][G] values: at most 32 KiB for the G chosen per R
+        for (const void* k : {(const void*)gather_kernel<8>, (const void*)gather_kernel<4>, (const void*)gather_kernel<2>})
+            if (s.err == cudaSuccess) s.err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 << 10);
+        if (s.err == cudaSuccess) s.err = prepare_gather_tc();
+        s.done = true;
+    }
+    if (out) *out = &s;
+    return s.err;
+}
+
+// Grid of a persistent pool kernel: resident CTAs per SM (the occupancy limit, or fewer
+// when the schedule asks) times the SM count.
+static int persistent_blocks(const DeviceSetup& s, int occ, int want_per_sm) {
+    const int per_sm = want_per_sm > 0 ? min(occ, want_per_sm) : occ;
+    return max(1, s.sms * per_sm);
 }
 
 template <int G>
 static cudaError_t launch_gather(const UpdateParams& p, cudaStream_t stream) {
-    const size_t smem = (size_t)p.R * G * sizeof(float4);
-    auto* k = gather_kernel<G>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<(p.P + G - 1) / G, kThreads, smem, stream>>>(p);
+    const size_t smem = (size_t)p.R * G * sizeof(float4);  // at most 32 KiB for the G chosen below
+    gather_kernel<G><<<(p.P + G - 1) / G, kThreads, smem, stream>>>(p);
     return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cudaEvent_t const* ev) {
-    static const int g_primary = persistent_blocks(primary_kernel<T>);
-    static const int g_shadow = persistent_blocks(shadow_kernel<T>);
+    const DeviceSetup* setup = nullptr;
+    cudaError_t e = prepare_update_kernels(&setup);
+    if (e != cudaSuccess) return e;
+    const int g_primary = persistent_blocks(*setup, setup->occ_primary[type_slot<T>()], p.sched.blocks_per_sm);
+    const int g_shadow = persistent_blocks(*setup, setup->occ_shadow[type_slot<T>()], p.sched.blocks_per_sm);
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], stream) : cudaSuccess; };
-    cudaError_t e = mark(0);
+    e = mark(0);
     if (e == cudaSuccess) e = cudaMemsetAsync(p.counters, 0, 4 * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return e;
     const uint32_t n = (uint32_t)p.P * (uint32_t)p.R;
@@ -565,7 +622,7 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
     shadow_kernel<T><<<g_shadow, kThreads, 0, stream>>>(p);
     if ((e = mark(4)) != cudaSuccess) return e;
     finalize_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, stream>>>(p);
-    if (gather_tc_supported(p)) {
+    if (gather_tc_supported(p) && p.sched.gather != 2) {
         e = launch_gather_tc(p, stream);
         if (e != cudaSuccess) return e;
         return mark(5);

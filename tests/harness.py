@@ -63,6 +63,18 @@ def make_workload(preset: W.Preset, seed=None, sdf_dtype=None, **overrides) -> W
     return Workload(preset, scene, baked, states, lights, f32v(scene.sky), p)
 
 
+def make_cascade(c: W.Cascade, seed=None) -> list:
+    """One Workload per member volume of a cascade, all sharing one scene and one bake."""
+    first = make_workload(c.base, seed)
+    out = [first]
+    for pr in c.volumes[1:]:
+        p = dict(first.params, rays=pr.rays, probe_dims=pr.probe_dims, probe_origin=f32v(pr.probe_origin),
+                 probe_spacing=f32v(pr.probe_spacing))
+        states = W.probe_states(first.scene, p["probe_dims"], p["probe_origin"], p["probe_spacing"], pr.h)
+        out.append(Workload(pr, first.scene, first.baked, states, first.lights, first.sky, p))
+    return out
+
+
 # ------------------------------------------------------------------------- oracle side
 def oracle_scene(w: Workload) -> O.OracleScene:
     return O.OracleScene(w.baked.sdf, w.baked.h, w.baked.origin, w.baked.material)
@@ -123,19 +135,23 @@ def conditioning(geo, vals, dvals, o_map, active):
 
 # ------------------------------------------------------------------------- GPU side
 class GpuVolume:
-    """A scene + probe volume in the CUDA library, built from a Workload."""
+    """A scene + probe volume in the CUDA library, built from a Workload. With `scene`, the
+    volume is made over that existing library scene (not owned) instead of a new one."""
 
-    def __init__(self, w: Workload, seed: int = 0, flags: int = 0):
+    def __init__(self, w: Workload, seed: int = 0, flags: int = 0, scene=None, volume_id: int = 0):
         import torch
         import paper_2007_14394_b300 as S
         self.S, self.torch, self.w = S, torch, w
         p = w.params
-        self.scene = S.create_scene()
-        S.upload_sdf(self.scene, w.baked.sdf, w.baked.h, w.baked.origin, material=w.baked.material)
-        S.set_lights(self.scene, w.lights, w.sky)
+        self.own_scene = scene is None
+        if scene is None:
+            scene = S.create_scene()
+            S.upload_sdf(scene, w.baked.sdf, w.baked.h, w.baked.origin, material=w.baked.material)
+            S.set_lights(scene, w.lights, w.sky)
+        self.scene = scene
         self.desc = S.make_desc(p["probe_dims"], p["rays"], p["probe_origin"], p["probe_spacing"], p["max_steps"],
                                 p["depth_exponent"], p["eps_vox"], p["tmax_vox"], p["hysteresis"], p["k_bounce"],
-                                p["bias_vox"], seed=seed, flags=flags)
+                                p["bias_vox"], seed=seed, volume_id=volume_id, flags=flags)
         self.vol = S.create_volume(self.desc, self.scene)
         self.states_dev = torch.from_numpy(w.states.view(np.uint8).copy()).cuda()
         self.records = torch.empty(w.P * p["rays"] * 32, dtype=torch.uint8, device="cuda")
@@ -158,7 +174,8 @@ class GpuVolume:
 
     def close(self):
         self.S.destroy_volume(self.vol)
-        self.S.destroy_scene(self.scene)
+        if self.own_scene:
+            self.S.destroy_scene(self.scene)
 
 
 # ------------------------------------------------------------------------- comparison
@@ -247,3 +264,16 @@ def border_is_mirror(maps: np.ndarray) -> bool:
     import oracle
     fixed = np.stack([oracle.border(m.astype(np.float64)) for m in maps])
     return bool(np.array_equal(fixed.astype(np.float32), maps))
+
+
+def assert_bar(s, label=""):
+    assert s["hard"] == 0, (label, s)
+    assert s["class_agree_nongrazing"] >= 0.999, (label, s)
+    assert s["t_err_vox_max"] <= T_TOL_VOX, (label, s)
+    assert s["t_within_tol_frac"] >= 0.99, (label, s)      # ill-conditioned rays are the exception
+    # relative 1e-4 on every well-conditioned texel; on all texels, 1e-4 relative plus the
+    # first-order error of the float32 cosine weights
+    assert s["irr_rel_max"] <= REL_TOL and s["irr_tol_ratio_max"] <= 1.0, (label, s)
+    assert s["depth_rel_max"] <= REL_TOL and s["depth_tol_ratio_max"] <= 1.0, (label, s)
+    assert s["alpha_equal"] and s["valid_equal"], (label, s)
+    assert s["border_irr"] and s["border_depth"], (label, s)

@@ -77,3 +77,20 @@ def test_argument_errors_before_device_work(S):
     assert rc == S.ERR_INVALID_ARG
     with pytest.raises(S.SdfddgiError):
         S.get_maps(None)
+
+
+def test_batch_argument_errors_before_device_work(S):
+    import ctypes as C
+    out = C.c_void_p(1)
+    rc = S.lib.sdfddgi_create_batch(None, None, 1, C.byref(out))
+    assert rc == S.ERR_INVALID_ARG and out.value is None
+    vols = (C.c_void_p * 2)(None, None)
+    for n in (0, 9):
+        assert S.lib.sdfddgi_create_batch(vols, None, n, C.byref(out)) == S.ERR_INVALID_ARG
+        assert "n must be" in S.last_error()
+    assert S.lib.sdfddgi_create_batch(vols, None, 2, C.byref(out)) == S.ERR_INVALID_ARG
+    assert "NULL" in S.last_error()
+    assert S.lib.sdfddgi_update_batch(None, 0, None, None) == S.ERR_INVALID_ARG
+    assert S.lib.sdfddgi_batch_autotune(None, 3, None) == S.ERR_INVALID_ARG
+    assert S.lib.sdfddgi_batch_schedule(None, 0, (C.c_int32 * 3)(), None) == S.ERR_INVALID_ARG
+    S.lib.sdfddgi_destroy_batch(None)

@@ -15,8 +15,8 @@ import pytest
 
 import oracle as O
 import workloads as W
-from harness import (REL_TOL, T_TOL_VOX, T_COND_FACTOR, DELTA_VOX, DELTA_COS, GpuVolume, border_is_mirror, compare,
-                     force_from_records, make_workload, oracle_grid, oracle_scene)
+from harness import (T_TOL_VOX, T_COND_FACTOR, DELTA_VOX, DELTA_COS, GpuVolume, assert_bar, border_is_mirror,
+                     compare, force_from_records, make_workload, oracle_grid, oracle_scene)
 
 pytestmark = pytest.mark.gpu
 
@@ -58,19 +58,6 @@ def run_and_compare(w, frames=1, subset=None, seed_rot=7, prev_gpu=None, record_
     finally:
         gv.close()
     return stats
-
-
-def assert_bar(s, label=""):
-    assert s["hard"] == 0, (label, s)
-    assert s["class_agree_nongrazing"] >= 0.999, (label, s)
-    assert s["t_err_vox_max"] <= T_TOL_VOX, (label, s)
-    assert s["t_within_tol_frac"] >= 0.99, (label, s)      # ill-conditioned rays are the exception
-    # relative 1e-4 on every well-conditioned texel; on all texels, 1e-4 relative plus the
-    # first-order error of the float32 cosine weights
-    assert s["irr_rel_max"] <= REL_TOL and s["irr_tol_ratio_max"] <= 1.0, (label, s)
-    assert s["depth_rel_max"] <= REL_TOL and s["depth_tol_ratio_max"] <= 1.0, (label, s)
-    assert s["alpha_equal"] and s["valid_equal"], (label, s)
-    assert s["border_irr"] and s["border_depth"], (label, s)
 
 
 def test_room64_full_parity():

@@ -311,3 +311,46 @@ PRESETS = {
         probe_spacing=(1.0, 1.0, 1.0), rays=64, max_steps=64, frames=1, seed=7, scene_kind="room",
         sdf_dtype="f16", blend="bf16"),
 }
+
+
+@dataclass
+class Cascade:
+    """Several probe volumes over one scene (Sec. 3.5 cascades), updated together as a
+    batch. Every member is a Preset with the same scene fields; member i is volume id i."""
+    name: str
+    description: str
+    volumes: tuple
+
+    @property
+    def base(self) -> Preset:
+        return self.volumes[0]
+
+    @property
+    def n_rays(self) -> int:
+        return sum(v.n_probes * v.rays for v in self.volumes)
+
+    def scene(self, seed: int | None = None) -> Scene:
+        return self.base.scene(seed)
+
+
+def _cascade_member(name, probe_dims, probe_origin, probe_spacing, rays) -> Preset:
+    return Preset(name, f"{probe_dims} probes at {probe_spacing[0]} m, {rays} rays/probe", world=128.0,
+                  sdf_dims=(512, 512, 512), h=0.25, probe_dims=probe_dims, probe_origin=probe_origin,
+                  probe_spacing=probe_spacing, rays=rays, max_steps=128, frames=8, seed=11, scene_kind="open",
+                  scene_args={"n_prims": 2000}, sdf_dtype="f16")
+
+
+# Four concentric volumes of uneven sizes and ray counts around the centre of a 128 m open
+# world (512^3 binary16 SDF of 2000 primitives, h = 0.25 m, sun + 16 point lights);
+# 6,553,600 probe rays per frame in all.
+CASCADES = {
+    "cascade512": Cascade(
+        "cascade512", "4 volumes over one 512^3 float16 SDF of 2000 primitives: 8^3 @512 rays, 16^3 @256, "
+        "32x8x32 @128, 64x16x64 @64; <=128 steps, sun + 16 point lights",
+        volumes=(
+            _cascade_member("cascade512.0", (8, 8, 8), (57.0, 2.0, 57.0), (2.0, 2.0, 2.0), 512),
+            _cascade_member("cascade512.1", (16, 16, 16), (49.0, 2.0, 49.0), (2.0, 2.0, 2.0), 256),
+            _cascade_member("cascade512.2", (32, 8, 32), (2.0, 2.0, 2.0), (4.0, 4.0, 4.0), 128),
+            _cascade_member("cascade512.3", (64, 16, 64), (1.0, 2.0, 1.0), (2.0, 2.0, 2.0), 64),
+        )),
+}
