@@ -354,3 +354,25 @@ CASCADES = {
             _cascade_member("cascade512.3", (64, 16, 64), (1.0, 2.0, 1.0), (2.0, 2.0, 2.0), 64),
         )),
 }
+
+
+# ---------------------------------------------------------------------------- learned form
+# Layer shapes of the probe denoiser's parameter vector, in order (weights [tap][in][out]).
+DENOISER_SHAPES = (("w1", (9, 35, 64)), ("b1", (64,)), ("w2", (9, 64, 48)), ("b2", (48,)),
+                   ("w3", (9, 48, 3)), ("b3", (3,)))
+
+
+def denoiser_init(seed: int, last_scale: float = 0.1) -> np.ndarray:
+    """Seeded initial parameters (float32 [49219]): He-uniform weights, U(-sqrt(6/fan_in),
+    +sqrt(6/fan_in)) with fan_in = 9 x input channels, the last layer scaled by `last_scale`
+    so that the initial network is close to the identity; zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, shape in DENOISER_SHAPES:
+        if name.startswith("w"):
+            lim = math.sqrt(6.0 / (9 * shape[1]))
+            w = rng.uniform(-lim, lim, shape)
+            parts.append(w * (last_scale if name == "w3" else 1.0))
+        else:
+            parts.append(np.zeros(shape))
+    return np.concatenate([p.reshape(-1) for p in parts]).astype(np.float32)
