@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import sys
@@ -494,6 +495,129 @@ def run_batch(args, rank, world, local_rank):
     return line
 
 
+LEARNED = "learned32"
+DENOISER_FLOPS_PER_PROBE = 2 * 36 * (9 * 35 * 64 + 9 * 64 * 48 + 9 * 48 * 3)  # 3 convs over 36 interior texels
+
+
+def run_learned(args, rank, world, local_rank):
+    """The learned form: the denoiser trained on pairs the plain update makes on 64 room
+    scenes, its error on 8 held-out scenes against plain updates of several ray counts,
+    and the frame time at 32 x 16 x 32 probes of the open scene: a 32-ray update plus the
+    tensor-core denoiser against plain updates at the ray count of equal error and at 256."""
+    import torch
+    import paper_2007_14394_b300 as S
+    from paper_2007_14394_b300 import learned as L
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    room = W.PRESETS["room64"]
+    plain_rays = (48, 64, 96, 128, 192, 256)
+    t0 = time.perf_counter()
+    train = L.make_pairs(room, list(range(1, 65)), plain_rays=plain_rays)
+    held = L.make_pairs(room, list(range(1001, 1009)), plain_rays=plain_rays)
+    t_pairs = time.perf_counter() - t0
+    depth_scale = 4.0
+    d = S.create_denoiser(W.denoiser_init(0), depth_scale)
+    t0 = time.perf_counter()
+    hist = L.train(d, train, steps=args.train_steps, batch_grids=8, lr=3e-4, log_every=max(1, args.train_steps // 8))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    err = L.evaluate(d, held)
+    err_train = L.evaluate(d, train)
+    r_eq = L.equal_error_rays(err)
+
+    # frame times on the open scene's 32 x 16 x 32 grid
+    pr = W.PRESETS["open256"]
+    scene, baked, states = build_inputs(pr)
+    n_active = int((states["flags"] & 1).sum())
+    sc = S.create_scene()
+    S.upload_sdf(sc, baked.sdf, baked.h, baked.origin, material=baked.material)
+    S.set_lights(sc, scene.lights, scene.sky)
+    states_dev = torch.from_numpy(states.view(np.uint8).copy()).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def volume(rays):
+        desc = S.make_desc(pr.probe_dims, rays, pr.probe_origin, pr.probe_spacing, pr.max_steps, pr.depth_exponent,
+                           pr.eps_vox, pr.tmax_vox, pr.hysteresis, pr.k_bounce, pr.bias_vox, seed=pr.seed)
+        return S.create_volume(desc, sc)
+
+    def timed(step_fn):
+        for k in range(args.warmup):
+            step_fn(k)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            step_fn(args.warmup + k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    v32 = volume(32)
+    dn_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    dn_ms = []
+
+    def learned_frame(f):
+        S.update_probes(v32, f, states=states_dev, stream=stream)
+        dn_ev[0].record(stream)
+        S.denoise_volume(d, v32, states_dev, stream=stream)
+        dn_ev[1].record(stream)
+
+    clocks = Clocks(local_rank)
+    learned_steps = []
+    for k in range(args.warmup):
+        learned_frame(k)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        learned_frame(args.warmup + k)
+        b.record(stream)
+        torch.cuda.synchronize()
+        learned_steps.append(a.elapsed_time(b))
+        dn_ms.append(dn_ev[0].elapsed_time(dn_ev[1]))
+    clk = clocks.stop()
+    plain_ms = {}
+    for rays in sorted({256, int(math.ceil(r_eq)) if r_eq else 256}):
+        v = volume(rays)
+        plain_ms[rays] = statistics.median(timed(lambda f: S.update_probes(v, f, states=states_dev, stream=stream)))
+        S.destroy_volume(v)
+    learned_ms = statistics.median(learned_steps)
+    denoise_ms = statistics.median(dn_ms)
+    P = pr.n_probes
+    tc_peak, tc_kind = tensor_peak()
+    ach = DENOISER_FLOPS_PER_PROBE * n_active / (denoise_ms / 1e3) / 1e12
+    eq_rays = r_eq if r_eq else None
+    value = (n_active * eq_rays / (learned_ms / 1e3)) if eq_rays else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "equal-error probe-rays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": learned_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 update, bf16 x bf16 -> f32 denoiser",
+        "data": "synthetic (seeded scenes, baked on the host; pairs made by the plain update)",
+        "config": {"workload": f"{LEARNED}: 32-ray update + denoiser at {pr.probe_dims} probes of {pr.name}; "
+                               "trained on 64 room64 seeds (1..64), evaluated on 8 held-out seeds (1001..1008)",
+                   "probes": P, "active_probes": n_active, "train_steps": args.train_steps, "batch_grids": 8,
+                   "lr": 3e-4, "depth_scale": depth_scale,
+                   "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
+        "gpu_launches": (KERNELS_PER_UPDATE + 2) * args.steps,
+        "rmse_heldout": err, "rmse_train": err_train, "equal_error_rays": r_eq,
+        "ms": {"learned32_frame": learned_ms, "denoise": denoise_ms, "update32": learned_ms - denoise_ms,
+               **{f"plain{r}": t for r, t in plain_ms.items()}},
+        "training": {"pairs_s": t_pairs, "train_s": t_train, "loss": hist},
+        "roofline": {"kernel": "denoise_tc_kernel", "bound": "tensor", "achieved": ach, "peak": tc_peak,
+                     "unit": "TFLOP/s", "frac": ach / tc_peak, "flops_per_launch": DENOISER_FLOPS_PER_PROBE * n_active,
+                     "peak_source": f"{tc_kind} bf16 burst", "traffic": None},
+        "clocks": clk,
+    }
+    S.destroy_volume(v32)
+    S.destroy_scene(sc)
+    S.destroy_denoiser(d)
+    return line
+
+
 def cascade_cpu_baseline(c, scene, baked, states, budget_s=10.0):
     """The oracle on a seeded sample of every volume's active probes, about budget_s seconds in
     all; the frame time is extrapolated linearly in the probe counts."""
@@ -583,7 +707,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.PRESETS) + sorted(W.CASCADES))
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.PRESETS) + sorted(W.CASCADES) + [LEARNED])
+    ap.add_argument("--train-steps", type=int, default=6000, help="training steps of the learned32 workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
@@ -594,7 +719,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
-        if args.workload in W.CASCADES:
+        if args.workload in W.CASCADES or args.workload == LEARNED:
             ap.error("the reference arm times single-volume workloads")
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
@@ -604,7 +729,7 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    run = run_batch if args.workload in W.CASCADES else run_ours
+    run = run_batch if args.workload in W.CASCADES else (run_learned if args.workload == LEARNED else run_ours)
     line = run(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(line), flush=True)

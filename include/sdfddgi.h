@@ -58,6 +58,7 @@ typedef enum {
 typedef struct sdfddgi_scene sdfddgi_scene;   /* SDF + material volume + lights */
 typedef struct sdfddgi_volume sdfddgi_volume; /* probe grid + ping-pong probe maps */
 typedef struct sdfddgi_batch sdfddgi_batch;   /* volumes updated together (one graph launch) */
+typedef struct sdfddgi_denoiser sdfddgi_denoiser; /* learned correction of low-ray updates */
 
 enum { SDFDDGI_F32 = 0, SDFDDGI_F16 = 1 };                          /* SDF storage type  */
 enum { SDFDDGI_LIGHT_DIRECTIONAL = 0, SDFDDGI_LIGHT_POINT = 1 };    /* light type        */
@@ -271,6 +272,81 @@ SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* 
  * out[2] gather (0 automatic, 1 tensor cores, 2 SIMT); tuned_ms (nullable) receives the
  * autotuner's mean update time of that schedule (0 before tuning). */
 SDFDDGI_API int sdfddgi_batch_schedule(const sdfddgi_batch* b, int32_t i, int32_t out[3], float* tuned_ms);
+
+/* ---- the learned form: a denoiser of low-ray-count updates -------------- */
+
+/* The paper has no learned part. A 32-ray update is noisy, and this network corrects it
+ * toward the converged irradiance. It reads a probe's octahedral maps and those of its 6
+ * grid neighbours. Input: 35 channels on the 8x8 bordered grid of the irradiance map.
+ * The first 21 are the irradiance rgb of the probe and of its -x, +x, -y, +y, -z, +z
+ * neighbours. The other 14 are their depth moments (mean / s, mean square / s^2), each
+ * averaged over 2x2 texels of the 16x16 depth map, with s = depth_scale. A neighbour
+ * outside its grid, or one with valid = 0, is replaced by the probe itself.
+ * Network: three 3x3 convolutions 35 -> 64 -> 48 -> 3 over the 6x6 interior, with the
+ * octahedral border fixup (the mirror rule of the maps' borders, Sec. 3.3) as padding
+ * and ReLU between them. Output: irradiance = max(0, own interior irradiance +
+ * residual), then the border fixup. The alpha channel and inactive probes pass through.
+ * Loss: mean squared error over the interior rgb of active probes. Training: Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).
+ * Parameters: SDFDDGI_DENOISER_PARAMS floats, in order w1 [9][35][64], b1 [64],
+ * w2 [9][64][48], b2 [48], w3 [9][48][3], b3 [3], weight [tap][in][out] with tap =
+ * (dy+1)*3 + (dx+1) reading the input at (row+dy, column+dx). */
+enum { SDFDDGI_DENOISER_PARAMS = 49219 };
+
+/* Arithmetic of a denoiser call.
+ *  TENSOR     -- inference only: bf16 weights and layer inputs on the tensor cores, fp32
+ *                accumulation (the deployed form).
+ *  SIMT_BF16  -- the same rounding (weights and each layer's input to bf16) with fp32
+ *                CUDA-core arithmetic; the training mode.
+ *  SIMT_FP32  -- fp32 throughout (for gradient checks). */
+enum { SDFDDGI_DENOISE_TENSOR = 0, SDFDDGI_DENOISE_SIMT_BF16 = 1, SDFDDGI_DENOISE_SIMT_FP32 = 2 };
+
+/* A batch of probe grids and their maps, all in DEVICE memory, as the update leaves them.
+ * P = n_grids * dims[0]*dims[1]*dims[2] probes; grid g holds probes [g*Pg, (g+1)*Pg), x
+ * fastest, and a probe's neighbours are looked up within its own grid. */
+typedef struct {
+    int32_t dims[3];
+    int32_t n_grids;
+    const float* irr;                   /* [P][8][8][4] */
+    const float* depth;                 /* [P][16][16][2] */
+    const uint8_t* valid;               /* [P] 1 = the probe has history */
+    const sdfddgi_probe_state* states;  /* [P] or NULL (all active); flags bit 0 = active */
+} sdfddgi_probe_maps;
+
+/* params: host float[SDFDDGI_DENOISER_PARAMS] (copied); depth_scale > 0 (world units;
+ * e.g. the probe spacing). The Adam state starts at zero. */
+SDFDDGI_API int sdfddgi_create_denoiser(const float* params, float depth_scale, sdfddgi_denoiser** out);
+SDFDDGI_API void sdfddgi_destroy_denoiser(sdfddgi_denoiser* d);
+
+/* Copies the parameters out to `read` and/or in from `write` (host arrays, either NULL).
+ * Writing resets the Adam state. Synchronous. */
+SDFDDGI_API int sdfddgi_denoiser_params(sdfddgi_denoiser* d, float* read, const float* write);
+
+/* out_irr: device [P][8][8][4], the corrected maps (must not alias maps->irr). mode: one
+ * of SDFDDGI_DENOISE_*. The work space grows on demand (device allocation). */
+SDFDDGI_API int sdfddgi_denoise(sdfddgi_denoiser* d, const sdfddgi_probe_maps* maps, float* out_irr, int32_t mode,
+                                void* stream);
+
+/* Corrects volume v's current irradiance maps in place (its grid as one grid; states as
+ * for sdfddgi_update_probes with states_on_device = 1, or NULL). */
+SDFDDGI_API int sdfddgi_denoise_volume(sdfddgi_denoiser* d, sdfddgi_volume* v, const sdfddgi_probe_state* states,
+                                       int32_t mode, void* stream);
+
+/* Forward and backward pass: the loss against target_irr (device [P][8][8][4], interior rgb
+ * of active probes) into *loss and its gradient in the parameters into grad (both
+ * device: float[1] and float[SDFDDGI_DENOISER_PARAMS], overwritten). mode: SIMT_BF16 or
+ * SIMT_FP32 (the gradient is straight-through for the bf16 rounding). */
+SDFDDGI_API int sdfddgi_denoiser_gradients(sdfddgi_denoiser* d, const sdfddgi_probe_maps* maps,
+                                           const float* target_irr, int32_t mode, float* grad, float* loss,
+                                           void* stream);
+
+/* One Adam step with the device gradient grad and learning rate lr. */
+SDFDDGI_API int sdfddgi_denoiser_adam(sdfddgi_denoiser* d, const float* grad, float lr, void* stream);
+
+/* gradients + adam with the denoiser's own gradient buffer; loss: device float[1] or NULL. */
+SDFDDGI_API int sdfddgi_denoiser_train_step(sdfddgi_denoiser* d, const sdfddgi_probe_maps* maps,
+                                            const float* target_irr, int32_t mode, float lr, float* loss,
+                                            void* stream);
 
 /* ---- the update without device allocation ------------------------------ */
 

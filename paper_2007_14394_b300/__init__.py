@@ -36,6 +36,11 @@ class Light(C.Structure):
     _fields_ = [("type", C.c_int32), ("v", C.c_float * 3), ("rgb", C.c_float * 3), ("range", C.c_float)]
 
 
+class ProbeMaps(C.Structure):
+    _fields_ = [("dims", C.c_int32 * 3), ("n_grids", C.c_int32), ("irr", C.c_void_p), ("depth", C.c_void_p),
+                ("valid", C.c_void_p), ("states", C.c_void_p)]
+
+
 class ProbeState(C.Structure):
     _fields_ = [("pos", C.c_float * 3), ("flags", C.c_uint32)]
 
@@ -79,6 +84,14 @@ def _load() -> C.CDLL:
         "sdfddgi_update_probes_noalloc": ([C.POINTER(VolumeDesc), vp, C.POINTER(i32), C.c_float, C.POINTER(C.c_float),
                                            i32, vp, C.POINTER(Light), i32, C.POINTER(C.c_float), u32, vp, vp,
                                            vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
+        "sdfddgi_create_denoiser": ([C.POINTER(C.c_float), C.c_float, C.POINTER(vp)], C.c_int),
+        "sdfddgi_destroy_denoiser": ([vp], None),
+        "sdfddgi_denoiser_params": ([vp, vp, vp], C.c_int),
+        "sdfddgi_denoise": ([vp, C.POINTER(ProbeMaps), vp, i32, vp], C.c_int),
+        "sdfddgi_denoise_volume": ([vp, vp, vp, i32, vp], C.c_int),
+        "sdfddgi_denoiser_gradients": ([vp, C.POINTER(ProbeMaps), vp, i32, vp, vp, vp], C.c_int),
+        "sdfddgi_denoiser_adam": ([vp, vp, C.c_float, vp], C.c_int),
+        "sdfddgi_denoiser_train_step": ([vp, C.POINTER(ProbeMaps), vp, i32, C.c_float, vp, vp], C.c_int),
         "sdfddgi_create_batch": ([C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(vp)], C.c_int),
         "sdfddgi_destroy_batch": ([vp], None),
         "sdfddgi_update_batch": ([vp, u32, vp, vp], C.c_int),
@@ -96,7 +109,11 @@ lib = _load()
 EXPORTED = ("last_error", "create_scene", "destroy_scene", "upload_sdf", "set_lights", "create_volume",
             "destroy_volume", "volume_probe_count", "frame_rotation", "update_probes", "update_probes_noalloc",
             "sample_irradiance", "set_stage_events", "get_maps", "read_state", "write_state", "reset",
-            "create_batch", "destroy_batch", "update_batch", "batch_autotune", "batch_schedule")
+            "create_batch", "destroy_batch", "update_batch", "batch_autotune", "batch_schedule",
+            "create_denoiser", "destroy_denoiser", "denoiser_params", "denoise", "denoise_volume",
+            "denoiser_gradients", "denoiser_adam", "denoiser_train_step")
+DENOISER_PARAMS = 49219
+DENOISE_TENSOR, DENOISE_SIMT_BF16, DENOISE_SIMT_FP32 = 0, 1, 2
 STAGES = ("weights", "primary", "prep", "shadow", "gather")  # intervals between the stage events
 
 
@@ -348,3 +365,67 @@ def batch_schedule(batch, i: int):
     ms = C.c_float()
     _check(lib.sdfddgi_batch_schedule(batch, int(i), out, C.byref(ms)))
     return out[0], out[1], out[2], ms.value
+
+
+# ------------------------------------------------------------------ the learned form
+def _dev_ptr(t, what):
+    if t is None:
+        return None
+    p, dev = _ptr(t)
+    if not dev:
+        raise ValueError(f"{what} must be a device tensor")
+    return p
+
+
+def probe_maps(dims, n_grids, irr, depth, valid, states=None) -> ProbeMaps:
+    """Device tensors irr [P,8,8,4] f32, depth [P,16,16,2] f32, valid [P] u8, states None or P*16 bytes."""
+    return ProbeMaps((C.c_int32 * 3)(*[int(x) for x in dims]), int(n_grids), _dev_ptr(irr, "irr"),
+                     _dev_ptr(depth, "depth"), _dev_ptr(valid, "valid"), _dev_ptr(states, "states"))
+
+
+def create_denoiser(params, depth_scale: float) -> C.c_void_p:
+    a = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+    if a.size != DENOISER_PARAMS:
+        raise ValueError(f"expected {DENOISER_PARAMS} parameters")
+    h = C.c_void_p()
+    _check(lib.sdfddgi_create_denoiser(a.ctypes.data_as(C.POINTER(C.c_float)), float(depth_scale), C.byref(h)))
+    return h
+
+
+def destroy_denoiser(d) -> None:
+    lib.sdfddgi_destroy_denoiser(d)
+
+
+def denoiser_params(d, write=None) -> np.ndarray:
+    """Returns the current parameters (float32); with `write`, sets them first (resets Adam)."""
+    if write is not None:
+        w = np.ascontiguousarray(np.asarray(write, dtype=np.float32).reshape(-1))
+        if w.size != DENOISER_PARAMS:
+            raise ValueError(f"expected {DENOISER_PARAMS} parameters")
+        _check(lib.sdfddgi_denoiser_params(d, None, w.ctypes.data))
+    out = np.empty(DENOISER_PARAMS, np.float32)
+    _check(lib.sdfddgi_denoiser_params(d, out.ctypes.data, None))
+    return out
+
+
+def denoise(d, maps: ProbeMaps, out, mode=DENOISE_TENSOR, stream=None) -> None:
+    _check(lib.sdfddgi_denoise(d, C.byref(maps), _dev_ptr(out, "out"), int(mode), _stream(stream)))
+
+
+def denoise_volume(d, volume, states=None, mode=DENOISE_TENSOR, stream=None) -> None:
+    _check(lib.sdfddgi_denoise_volume(d, volume, _dev_ptr(states, "states"), int(mode), _stream(stream)))
+
+
+def denoiser_gradients(d, maps: ProbeMaps, target, grad, loss, mode=DENOISE_SIMT_BF16, stream=None) -> None:
+    _check(lib.sdfddgi_denoiser_gradients(d, C.byref(maps), _dev_ptr(target, "target"), int(mode),
+                                          _dev_ptr(grad, "grad"), _dev_ptr(loss, "loss"), _stream(stream)))
+
+
+def denoiser_adam(d, grad, lr: float, stream=None) -> None:
+    _check(lib.sdfddgi_denoiser_adam(d, _dev_ptr(grad, "grad"), float(lr), _stream(stream)))
+
+
+def denoiser_train_step(d, maps: ProbeMaps, target, lr: float, loss=None, mode=DENOISE_SIMT_BF16,
+                        stream=None) -> None:
+    _check(lib.sdfddgi_denoiser_train_step(d, C.byref(maps), _dev_ptr(target, "target"), int(mode), float(lr),
+                                           _dev_ptr(loss, "loss"), _stream(stream)))

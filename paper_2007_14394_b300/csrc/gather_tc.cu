@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "device.cuh"
+#include "tcgen05.cuh"
 
 namespace sdfddgi {
 
@@ -32,7 +33,6 @@ constexpr int kN = kG * kCh;                  // 96 accumulator columns per tile
 constexpr int kChunk = 32;                    // rays per K chunk
 constexpr int kThreads = 256;
 constexpr int kTmemCols = 256;                // 2 x 96 used
-constexpr uint32_t kSpinLimit = 1u << 22;     // polls per bounded wait (well under a second)
 
 // Operand format: 4-byte tf32 in hi + lo parts, or one 2-byte bf16 part. Operands are
 // K-major without swizzle: 8 x 16-byte core matrices, adjacent along K 128 B apart,
@@ -55,57 +55,6 @@ struct Fmt {
         return (uint32_t)((row >> 3) * kSbo + ((k * kElem) >> 4) * 128 + (row & 7) * 16 + ((k * kElem) & 15));
     }
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ float to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-// shared-memory matrix descriptor: no swizzle, K-major, version 1
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((saddr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | ((uint64_t)1 << 46);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait (non-blocking polls): false after kSpinLimit polls, or early once any CTA
-// of the launch has recorded a failure in *abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const uint32_t* abort) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
-        if (mbar_test_wait(bar, parity)) return true;
-        if ((i & 4095u) == 4095u && (*reinterpret_cast<const volatile uint32_t*>(abort) & 2u)) return false;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
 
 template <bool BF16>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
@@ -133,24 +82,6 @@ __device__ __forceinline__ void put(unsigned char* part, uint32_t off, float v) 
         *reinterpret_cast<__nv_bfloat16*>(part + off) = __float2bfloat16_rn(v);
     else
         *reinterpret_cast<float*>(part + off) = v;
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-// 16 consecutive fp32 columns of this thread's tensor-memory lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
 }  // namespace tc

@@ -362,10 +362,10 @@ DENOISER_SHAPES = (("w1", (9, 35, 64)), ("b1", (64,)), ("w2", (9, 64, 48)), ("b2
                    ("w3", (9, 48, 3)), ("b3", (3,)))
 
 
-def denoiser_init(seed: int, last_scale: float = 0.1) -> np.ndarray:
+def denoiser_init(seed: int, last_scale: float = 0.0) -> np.ndarray:
     """Seeded initial parameters (float32 [49219]): He-uniform weights, U(-sqrt(6/fan_in),
     +sqrt(6/fan_in)) with fan_in = 9 x input channels, the last layer scaled by `last_scale`
-    so that the initial network is close to the identity; zero biases."""
+    (0 by default: the initial network is the identity, its residual zero); zero biases."""
     rng = np.random.default_rng(seed)
     parts = []
     for name, shape in DENOISER_SHAPES:
