@@ -228,6 +228,14 @@ SDFDDGI_API int sdfddgi_read_state(const sdfddgi_volume* v, float* irr, float* d
 SDFDDGI_API int sdfddgi_write_state(sdfddgi_volume* v, const float* irr, const float* depth,
                                     const uint8_t* valid, int32_t on_device, void* stream);
 
+/* Device-side failures recorded by this volume's updates since the last call, in *flags
+ * (may be NULL): bit 0 -- the shadow-task list overflowed and shadow rays were dropped (the
+ * library sizes the list so that this cannot happen); bit 1 -- a bounded wait of the
+ * tensor-core gather gave up: that update's maps are not valid, and later updates skip
+ * the tensor-core gather (leaving their maps invalid too) until this call clears the bit.
+ * Waits for the device, clears the bits, returns SDFDDGI_ERR_TIMEOUT if bit 1 was set. */
+SDFDDGI_API int sdfddgi_volume_status(sdfddgi_volume* v, uint32_t* flags);
+
 /* Clears every map and the history (as at creation). */
 SDFDDGI_API int sdfddgi_reset(sdfddgi_volume* v, void* stream);
 
@@ -331,6 +339,11 @@ SDFDDGI_API int sdfddgi_denoise(sdfddgi_denoiser* d, const sdfddgi_probe_maps* m
  * for sdfddgi_update_probes with states_on_device = 1, or NULL). */
 SDFDDGI_API int sdfddgi_denoise_volume(sdfddgi_denoiser* d, sdfddgi_volume* v, const sdfddgi_probe_state* states,
                                        int32_t mode, void* stream);
+
+/* Failures of the tensor-core inference since the last call, as sdfddgi_volume_status:
+ * bit 1 -- a bounded wait gave up (those outputs are not valid, and later TENSOR calls do
+ * no work until this call clears the bit). Waits for the device; SDFDDGI_ERR_TIMEOUT if set. */
+SDFDDGI_API int sdfddgi_denoiser_status(sdfddgi_denoiser* d, uint32_t* flags);
 
 /* Forward and backward pass: the loss against target_irr (device [P][8][8][4], interior rgb
  * of active probes) into *loss and its gradient in the parameters into grad (both

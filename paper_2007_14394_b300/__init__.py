@@ -84,6 +84,8 @@ def _load() -> C.CDLL:
         "sdfddgi_update_probes_noalloc": ([C.POINTER(VolumeDesc), vp, C.POINTER(i32), C.c_float, C.POINTER(C.c_float),
                                            i32, vp, C.POINTER(Light), i32, C.POINTER(C.c_float), u32, vp, vp,
                                            vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
+        "sdfddgi_volume_status": ([vp, C.POINTER(u32)], C.c_int),
+        "sdfddgi_denoiser_status": ([vp, C.POINTER(u32)], C.c_int),
         "sdfddgi_create_denoiser": ([C.POINTER(C.c_float), C.c_float, C.POINTER(vp)], C.c_int),
         "sdfddgi_destroy_denoiser": ([vp], None),
         "sdfddgi_denoiser_params": ([vp, vp, vp], C.c_int),
@@ -111,7 +113,7 @@ EXPORTED = ("last_error", "create_scene", "destroy_scene", "upload_sdf", "set_li
             "sample_irradiance", "set_stage_events", "get_maps", "read_state", "write_state", "reset",
             "create_batch", "destroy_batch", "update_batch", "batch_autotune", "batch_schedule",
             "create_denoiser", "destroy_denoiser", "denoiser_params", "denoise", "denoise_volume",
-            "denoiser_gradients", "denoiser_adam", "denoiser_train_step")
+            "denoiser_gradients", "denoiser_adam", "denoiser_train_step", "volume_status", "denoiser_status")
 DENOISER_PARAMS = 49219
 DENOISE_TENSOR, DENOISE_SIMT_BF16, DENOISE_SIMT_FP32 = 0, 1, 2
 STAGES = ("weights", "primary", "prep", "shadow", "gather")  # intervals between the stage events
@@ -429,3 +431,17 @@ def denoiser_train_step(d, maps: ProbeMaps, target, lr: float, loss=None, mode=D
                         stream=None) -> None:
     _check(lib.sdfddgi_denoiser_train_step(d, C.byref(maps), _dev_ptr(target, "target"), int(mode), float(lr),
                                            _dev_ptr(loss, "loss"), _stream(stream)))
+
+
+def volume_status(volume) -> int:
+    """Failure bits recorded by the volume's updates since the last call (cleared);
+    raises SdfddgiError (SDFDDGI_ERR_TIMEOUT) if a tensor-core wait gave up."""
+    f = C.c_uint32()
+    _check(lib.sdfddgi_volume_status(volume, C.byref(f)))
+    return f.value
+
+
+def denoiser_status(d) -> int:
+    f = C.c_uint32()
+    _check(lib.sdfddgi_denoiser_status(d, C.byref(f)))
+    return f.value

@@ -297,6 +297,7 @@ SDFDDGI_API int sdfddgi_create_volume(const sdfddgi_volume_desc* d, sdfddgi_scen
     rc = sdfddgi_reset(v, nullptr);
     if (!rc) {
         cudaError_t e = prepare_update_kernels();  // so that later updates can be captured
+        if (e == cudaSuccess) e = cudaMemset(v->counters, 0, 4 * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
         if (e != cudaSuccess) rc = fail(SDFDDGI_ERR_CUDA, "create_volume: %s", cudaGetErrorString(e));
     }
@@ -510,6 +511,18 @@ SDFDDGI_API int sdfddgi_write_state(sdfddgi_volume* v, const float* irr, const f
     CUDA_TRY(cudaMemcpyAsync(v->depth[v->cur], depth, v->P * kDepBytes, cudaMemcpyDefault, st));
     CUDA_TRY(cudaMemcpyAsync(v->valid[v->cur], valid, (size_t)v->P, cudaMemcpyDefault, st));
     if (!on_device) CUDA_TRY(cudaStreamSynchronize(st));
+    return SDFDDGI_OK;
+}
+
+SDFDDGI_API int sdfddgi_volume_status(sdfddgi_volume* v, uint32_t* flags) {
+    if (flags) *flags = 0;
+    if (!v) return fail(SDFDDGI_ERR_INVALID_ARG, "volume_status: volume is NULL");
+    uint32_t f = 0;
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(&f, v->counters + 3, sizeof f, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(v->counters + 3, 0, sizeof f));
+    if (flags) *flags = f;
+    if (f & 2u) return fail(SDFDDGI_ERR_TIMEOUT, "volume_status: a bounded wait of the tensor-core gather gave up");
     return SDFDDGI_OK;
 }
 

@@ -520,6 +520,19 @@ SDFDDGI_API int sdfddgi_denoise_volume(sdfddgi_denoiser* d, sdfddgi_volume* v, c
     return SDFDDGI_OK;
 }
 
+SDFDDGI_API int sdfddgi_denoiser_status(sdfddgi_denoiser* d, uint32_t* flags) {
+    if (flags) *flags = 0;
+    if (!d) return dfail(SDFDDGI_ERR_INVALID_ARG, "denoiser_status: denoiser is NULL");
+    uint32_t f = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&f, d->tc.status, sizeof f, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(d->tc.status, 0, sizeof f);
+    if (e != cudaSuccess) return dfail(SDFDDGI_ERR_CUDA, cudaGetErrorString(e));
+    if (flags) *flags = f;
+    if (f & 2u) return dfail(SDFDDGI_ERR_TIMEOUT, "denoiser_status: a bounded wait of the tensor-core kernel gave up");
+    return SDFDDGI_OK;
+}
+
 SDFDDGI_API int sdfddgi_denoiser_gradients(sdfddgi_denoiser* d, const sdfddgi_probe_maps* maps,
                                            const float* target_irr, int32_t mode, float* grad, float* loss,
                                            void* stream) {

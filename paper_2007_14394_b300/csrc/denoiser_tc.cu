@@ -14,9 +14,12 @@
 //             the bulk-copy engine and kept in shared memory;
 //   layer 1   K = 35 channels padded to 48, N = 64;  layer 2 K = 64, N = 48;
 //   layer 3   K = 48, N = 16 (3 used); accumulators in tensor-memory columns 0, 64, 112.
-// Per tile: features (the CTA gathers the 7 probes' map texels) -> MMA 1 -> epilogue
+// Per tile: features (the group gathers the 7 probes' map texels) -> MMA 1 -> epilogue
 // (bias, ReLU, bf16, border) -> MMA 2 -> epilogue -> MMA 3 -> residual + output maps.
-// One elected thread issues the MMAs; completion is an mbarrier armed by tcgen05.commit.
+// The CTA's two warp groups (4 warps each, one thread per row of a tile) run independent
+// tile streams with their own activation images, tensor-memory columns and mbarrier, so
+// that one group's MMAs overlap the other's feature gathers and epilogues. The group's
+// first thread issues its MMAs; completion is an mbarrier armed by tcgen05.commit.
 // Every wait is bounded; on timeout the kernel records bit 1 of the status word, releases
 // its tensor memory and returns.
 #include <cuda_bf16.h>
@@ -38,16 +41,19 @@ constexpr int kGuard = 16;                      // guard rows at each end (shift
 constexpr int kBufRows = kRows + 2 * kGuard;    // 160
 constexpr int kK1 = 48, kK2 = 64, kK3 = 48;     // input channels, padded to multiples of 16
 constexpr int kN1 = 64, kN2 = 48, kN3 = 16;     // accumulator columns (layer 3: 3 used)
-constexpr int kCol1 = 0, kCol2 = 64, kCol3 = 112;
-constexpr int kTmemCols = 128;
-constexpr int kThreads = 256;
+constexpr int kCol1 = 0, kCol2 = 64, kCol3 = 112;   // within a warp group's 128 columns
+constexpr int kGroups = 2;                          // warp groups, each with its own tile stream
+constexpr int kGroupThreads = 128;
+constexpr int kGroupCols = 128;
+constexpr int kTmemCols = kGroups * kGroupCols;
+constexpr int kThreads = kGroups * kGroupThreads;
 // B images: per layer, per tap, [K / 8][N][8 channels] bf16 (K-major, no swizzle)
 constexpr int kImg1 = 9 * kK1 * kN1 * 2, kImg2 = 9 * kK2 * kN2 * 2, kImg3 = 9 * kK3 * kN3 * 2;
 constexpr int kImgBytes = kImg1 + kImg2 + kImg3;  // 124,416
 // A images: [K / 8][kBufRows][8 channels] bf16
 constexpr int kActA = kBufRows * kK1 * 2;       // 48 channels: the features, then layer 2's output
 constexpr int kActB = kBufRows * kK2 * 2;       // 64 channels: layer 1's output
-constexpr int kSmemBytes = kImgBytes + kActA + kActB;
+constexpr int kSmemBytes = kImgBytes + kGroups * (kActA + kActB);
 static_assert(kImgBytes % 16 == 0 && kActA % 16 == 0 && kActB % 16 == 0, "16-byte alignment of the images");
 static_assert(kK1 >= kCin && kK3 == kC2 && kK2 == kC1 && kN1 == kC1 && kN2 == kC2 && kN3 >= kCout, "layer shapes");
 
@@ -109,10 +115,10 @@ __device__ __forceinline__ void issue_layer(uint32_t a_img, uint32_t b_img, int 
 
 // Copies into every border row of both probes of a tile, for channel groups [g0, g1), the
 // 16-byte rows of the interior texels they mirror.
-__device__ __forceinline__ void fix_borders(unsigned char* act, int g0, int g1) {
+__device__ __forceinline__ void fix_borders(unsigned char* act, int g0, int g1, int gtid) {
     constexpr int kBorder = kTex - kInt;  // 28
     const int n = kProbesPerTile * kBorder * (g1 - g0);
-    for (int e = threadIdx.x; e < n; e += kThreads) {
+    for (int e = gtid; e < n; e += kGroupThreads) {
         const int g = g0 + e / (kProbesPerTile * kBorder), r = e % (kProbesPerTile * kBorder);
         const int pl = r / kBorder, b = r % kBorder;
         // the b-th border texel in row-major order
@@ -127,18 +133,56 @@ __device__ __forceinline__ bool interior_row(int row) {
     return r >= 1 && r <= kN && c >= 1 && c <= kN;
 }
 
+// barrier of one warp group (128 threads); ids 1 and 2 (0 is __syncthreads)
+__device__ __forceinline__ void group_sync(int g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGroupThreads) : "memory");
+}
+
+// the same barrier, returning the OR of v over the group (one decision for all its threads)
+__device__ __forceinline__ bool group_sync_or(int g, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(1 + g), "r"(kGroupThreads)
+        : "memory");
+    return r != 0;
+}
+
+// Epilogue of a hidden layer for this thread's row: bias, ReLU, bf16, into channels
+// [0, n) of the next layer's A image (interior rows only).
+template <int NCOLS>
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bias, int row, unsigned char* act,
+                                                bool write) {
+    float v[NCOLS];
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < NCOLS; c += 16) tmem_ld16(taddr + c, v + c);
+    if (!write || !interior_row(row)) return;
+#pragma unroll
+    for (int g = 0; g < NCOLS / 8; ++g) {
+        float x[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = fmaxf(v[8 * g + j] + bias[8 * g + j], 0.f);
+        *reinterpret_cast<uint4*>(act + a_off(kGuard + row, 8 * g)) =
+            make_uint4(pack2(x[0], x[1]), pack2(x[2], x[3]), pack2(x[4], x[5]), pack2(x[6], x[7]));
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) denoise_tc_kernel(const __grid_constant__ TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* s_img = smem;
-    unsigned char* s_actA = smem + kImgBytes;              // 48-channel image
-    unsigned char* s_actB = smem + kImgBytes + kActA;      // 64-channel image
-    __shared__ float s_y[kRows * 3];                        // layer 3 outputs of the tile
-    __shared__ __align__(8) uint64_t bar_w, bar_mma;
+    __shared__ float s_y[kGroups][kRows * 3];       // layer 3 outputs of each group's tile
+    __shared__ __align__(8) uint64_t bar_w, bar_mma[kGroups];
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
     __shared__ float s_bias[kC1 + kC2 + kCout];
-    __shared__ uint32_t s_active[kProbesPerTile];
+    __shared__ uint32_t s_active[kGroups][kProbesPerTile];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int grp = tid / kGroupThreads, gtid = tid % kGroupThreads;  // warp group and its thread
 
     if (tid == 0) s_fail = (int)(*reinterpret_cast<const volatile uint32_t*>(a.status) & 2u);
     __syncthreads();
@@ -146,34 +190,45 @@ __global__ void __launch_bounds__(kThreads, 1) denoise_tc_kernel(const __grid_co
     if (warp == 0) tmem_alloc(&s_tmem, kTmemCols);
     if (tid == 0) {
         mbar_init(&bar_w, 1);
-        mbar_init(&bar_mma, 1);
+        for (int g = 0; g < kGroups; ++g) mbar_init(&bar_mma[g], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int i = tid; i < kC1; i += kThreads) s_bias[i] = a.use[kOffB1 + i];
     for (int i = tid; i < kC2; i += kThreads) s_bias[kC1 + i] = a.use[kOffB2 + i];
     if (tid < kCout) s_bias[kC1 + kC2 + tid] = a.use[kOffB3 + tid];
-    // zero both activation images once (guard rows and padding channels stay zero)
-    for (int i = tid; i < (kActA + kActB) / 16; i += kThreads)
-        reinterpret_cast<uint4*>(s_actA)[i] = make_uint4(0u, 0u, 0u, 0u);
+    // zero the activation images once (guard rows and padding channels stay zero)
+    for (int i = tid; i < kGroups * (kActA + kActB) / 16; i += kThreads)
+        reinterpret_cast<uint4*>(smem + kImgBytes)[i] = make_uint4(0u, 0u, 0u, 0u);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = s_tmem;
     if (tid == 0) bulk_copy_g2s(s_img, a.img, kImgBytes, &bar_w);  // all weights, once per CTA
     if (!mbar_wait(&bar_w, 0, a.status)) s_fail = 1;
     __syncthreads();
 
+    // ---- from here on the two warp groups run independent tile streams
+    unsigned char* s_actA = smem + kImgBytes + grp * (kActA + kActB);  // 48 channels: features, layer 2 out
+    unsigned char* s_actB = s_actA + kActA;                             // 64 channels: layer 1 out
     const uint32_t imgA = smem_u32(s_actA), imgB = smem_u32(s_actB), img0 = smem_u32(s_img);
-    uint32_t phase = 0;
+    const uint32_t tmem = s_tmem + (uint32_t)(grp * kGroupCols);
+    uint64_t* bar = &bar_mma[grp];
     const int quarter = warp & 3, row = quarter * 32 + lane;  // this thread's tensor-memory lane
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    const bool leader = gtid == 0;
+    bool fail = s_fail != 0;
+    uint32_t phase = 0;
+    auto wait_mma = [&]() {
+        if (!mbar_wait(bar, phase & 1, a.status)) fail = true;
+        ++phase;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    };
 
-    for (int tile = blockIdx.x; tile < a.n_tiles && !s_fail; tile += gridDim.x) {
+    for (int tile = blockIdx.x * kGroups + grp; tile < a.n_tiles; tile += gridDim.x * kGroups) {
         const int p0 = tile * kProbesPerTile;
-        // ---- features of the tile's 128 texels (threads 0..127), bf16 into image A
-        if (tid < kProbesPerTile) s_active[tid] = (p0 + tid < a.m.P) && probe_active(a.m, p0 + tid);
-        if (tid < kRows) {
-            const int pl = tid / kTex, t = tid % kTex, p = p0 + pl;
+        // ---- features of the tile's 128 texels, bf16 into image A
+        if (gtid < kProbesPerTile) s_active[grp][gtid] = (p0 + gtid < a.m.P) && probe_active(a.m, p0 + gtid);
+        {
+            const int pl = gtid / kTex, t = gtid % kTex, p = p0 + pl;
             float f[kK1];
 #pragma unroll
             for (int c = 0; c < kK1; ++c) f[c] = 0.f;
@@ -197,106 +252,70 @@ __global__ void __launch_bounds__(kThreads, 1) denoise_tc_kernel(const __grid_co
             for (int g = 0; g < kK1 / 8; ++g) {
                 const uint4 v = make_uint4(pack2(f[8 * g], f[8 * g + 1]), pack2(f[8 * g + 2], f[8 * g + 3]),
                                            pack2(f[8 * g + 4], f[8 * g + 5]), pack2(f[8 * g + 6], f[8 * g + 7]));
-                *reinterpret_cast<uint4*>(s_actA + a_off(kGuard + tid, 8 * g)) = v;
+                *reinterpret_cast<uint4*>(s_actA + a_off(kGuard + gtid, 8 * g)) = v;
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
-        __syncthreads();
-        if (tid == 0) issue_layer(imgA, img0, kK1, kN1, tmem + kCol1, &bar_mma);
+        group_sync(grp);
+        if (leader) issue_layer(imgA, img0, kK1, kN1, tmem + kCol1, bar);
 
-        // ---- layer 1 epilogue: bias, ReLU, bf16 into image B (64 channels), then borders
-        if (!mbar_wait(&bar_mma, phase & 1, a.status)) s_fail = 1;
-        ++phase;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        {
-            const int c0 = (warp >> 2) * 32;  // warps 0-3: columns 0..31, warps 4-7: 32..63
-            float v[32];
-            __syncwarp();
-            tmem_ld16(lane_base + kCol1 + c0, v);
-            tmem_ld16(lane_base + kCol1 + c0 + 16, v + 16);
-            if (interior_row(row) && !s_fail) {
-#pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    float x[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) x[j] = fmaxf(v[8 * g + j] + s_bias[c0 + 8 * g + j], 0.f);
-                    *reinterpret_cast<uint4*>(s_actB + a_off(kGuard + row, c0 + 8 * g)) =
-                        make_uint4(pack2(x[0], x[1]), pack2(x[2], x[3]), pack2(x[4], x[5]), pack2(x[6], x[7]));
-                }
-            }
-        }
+        // ---- layer 1 epilogue into image B (64 channels), then its borders
+        wait_mma();
+        hidden_epilogue<kN1>(lane_base + kCol1, s_bias, row, s_actB, !fail);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (s_fail) break;
-        fix_borders(s_actB, 0, kC1 / 8);
+        fail = group_sync_or(grp, fail);
+        if (fail) break;
+        fix_borders(s_actB, 0, kC1 / 8, gtid);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) issue_layer(imgB, img0 + kImg1, kK2, kN2, tmem + kCol2, &bar_mma);
+        group_sync(grp);
+        if (leader) issue_layer(imgB, img0 + kImg1, kK2, kN2, tmem + kCol2, bar);
 
-        // ---- layer 2 epilogue into image A (48 channels; the features are no longer read)
-        if (!mbar_wait(&bar_mma, phase & 1, a.status)) s_fail = 1;
-        ++phase;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        {
-            const int c0 = (warp >> 2) * 32, nc = warp < 4 ? 32 : 16;  // columns 0..31 | 32..47
-            float v[32];
-            __syncwarp();
-            tmem_ld16(lane_base + kCol2 + c0, v);
-            if (warp < 4) tmem_ld16(lane_base + kCol2 + c0 + 16, v + 16);
-            if (interior_row(row) && !s_fail) {
-                for (int g = 0; g < nc / 8; ++g) {
-                    float x[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) x[j] = fmaxf(v[8 * g + j] + s_bias[kC1 + c0 + 8 * g + j], 0.f);
-                    *reinterpret_cast<uint4*>(s_actA + a_off(kGuard + row, c0 + 8 * g)) =
-                        make_uint4(pack2(x[0], x[1]), pack2(x[2], x[3]), pack2(x[4], x[5]), pack2(x[6], x[7]));
-                }
-            }
-        }
+        // ---- layer 2 epilogue into image A (the features are no longer read)
+        wait_mma();
+        hidden_epilogue<kN2>(lane_base + kCol2, s_bias + kC1, row, s_actA, !fail);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (s_fail) break;
-        fix_borders(s_actA, 0, kC2 / 8);
+        fail = group_sync_or(grp, fail);
+        if (fail) break;
+        fix_borders(s_actA, 0, kC2 / 8, gtid);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) issue_layer(imgA, img0 + kImg1 + kImg2, kK3, kN3, tmem + kCol3, &bar_mma);
+        group_sync(grp);
+        if (leader) issue_layer(imgA, img0 + kImg1 + kImg2, kK3, kN3, tmem + kCol3, bar);
 
         // ---- layer 3: residual on the probe's own irradiance, output maps
-        if (!mbar_wait(&bar_mma, phase & 1, a.status)) s_fail = 1;
-        ++phase;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (warp < 4) {
+        wait_mma();
+        {
             float v[16];
             __syncwarp();
             tmem_ld16(lane_base + kCol3, v);
             const int pl = row / kTex, t = row % kTex, p = p0 + pl;
-            if (interior_row(row) && p < a.m.P && !s_fail) {
+            if (interior_row(row) && p < a.m.P && !fail) {
                 const float4 x = a.m.irr[(size_t)p * kTex + t];
-                s_y[row * 3 + 0] = fmaxf(x.x + (v[0] + s_bias[kC1 + kC2 + 0]), 0.f);
-                s_y[row * 3 + 1] = fmaxf(x.y + (v[1] + s_bias[kC1 + kC2 + 1]), 0.f);
-                s_y[row * 3 + 2] = fmaxf(x.z + (v[2] + s_bias[kC1 + kC2 + 2]), 0.f);
+                s_y[grp][row * 3 + 0] = fmaxf(x.x + (v[0] + s_bias[kC1 + kC2 + 0]), 0.f);
+                s_y[grp][row * 3 + 1] = fmaxf(x.y + (v[1] + s_bias[kC1 + kC2 + 1]), 0.f);
+                s_y[grp][row * 3 + 2] = fmaxf(x.z + (v[2] + s_bias[kC1 + kC2 + 2]), 0.f);
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (s_fail) break;
-        if (tid < kRows) {
-            const int pl = tid / kTex, t = tid % kTex, p = p0 + pl;
+        fail = group_sync_or(grp, fail);
+        if (fail) break;
+        {
+            const int pl = gtid / kTex, t = gtid % kTex, p = p0 + pl;
             if (p < a.m.P) {
                 const float4 x = a.m.irr[(size_t)p * kTex + t];
                 float4 y = x;
-                if (s_active[pl]) {
+                if (s_active[grp][pl]) {
                     const int sr = pl * kTex + border_source(t);
-                    y = make_float4(s_y[sr * 3 + 0], s_y[sr * 3 + 1], s_y[sr * 3 + 2], x.w);
+                    y = make_float4(s_y[grp][sr * 3 + 0], s_y[grp][sr * 3 + 1], s_y[grp][sr * 3 + 2], x.w);
                 }
                 a.out[(size_t)p * kTex + t] = y;
             }
         }
-        __syncthreads();  // s_y and s_active are rewritten by the next tile
+        group_sync(grp);  // s_y and s_active are rewritten by the group's next tile
     }
+    if (fail) s_fail = 1;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+    if (warp == 0) tmem_dealloc(s_tmem, kTmemCols);
     if (s_fail && tid == 0) atomicOr(a.status, 2u);
 }
 
@@ -338,7 +357,7 @@ cudaError_t tc_forward(TcState& s, const MapsView& m, float depth_scale, const f
     a.out = out;
     a.status = s.status;
     a.n_tiles = (m.P + kProbesPerTile - 1) / kProbesPerTile;
-    const int grid = std::min(a.n_tiles, std::max(1, s.sms));
+    const int grid = std::min((a.n_tiles + kGroups - 1) / kGroups, std::max(1, s.sms));
     denoise_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
     return cudaGetLastError();
 }

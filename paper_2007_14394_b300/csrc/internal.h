@@ -80,7 +80,8 @@ struct UpdateParams {
     uint32_t* ray_ssteps;     // shadow steps
     uint32_t* tasks;          // shadow tasks (k << 5 | light)
     uint32_t task_capacity;
-    uint32_t* counters;       // [0] primary pool, [1] task count, [2] shadow pool, [3] task overflow
+    uint32_t* counters;       // [0] primary pool, [1] task count, [2] shadow pool (zeroed by each launch),
+                              // [3] failure bits, sticky: 1 task overflow, 2 a tensor-core wait gave up
     float* weights;           // [R][kTexels] texel weights of the frame's ray set, [kTexels] column sums,
                               // then room for [R] float4 ray directions (weights_bytes(R) in all)
     float4* dirs;             // [R] the frame's ray directions (same for every probe), set by launch_update

@@ -201,9 +201,10 @@ SDFDDGI_API int sdfddgi_update_probes_noalloc(
     p.ray_ssteps = reinterpret_cast<uint32_t*>(s + off[7]);
     p.tasks = reinterpret_cast<uint32_t*>(s + off[8]);
     p.task_capacity = (uint32_t)(n_rays * (size_t)(n_lights > 0 ? n_lights : 1));
-    p.counters = reinterpret_cast<uint32_t*>(s + off[9]);  // zeroed by the launch
+    p.counters = reinterpret_cast<uint32_t*>(s + off[9]);
     p.weights = reinterpret_cast<float*>(s + off[10]);
-    e = launch_update(p, st);
+    e = cudaMemsetAsync(p.counters, 0, 4 * sizeof(uint32_t), st);  // the scratch is shared: no sticky bits
+    if (e == cudaSuccess) e = launch_update(p, st);
     if (e != cudaSuccess) return nofail(SDFDDGI_ERR_CUDA, "update_probes_noalloc: launch failed: %s", cudaGetErrorString(e));
     return SDFDDGI_OK;
 }

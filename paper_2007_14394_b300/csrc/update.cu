@@ -606,7 +606,8 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
     const int g_shadow = persistent_blocks(*setup, setup->occ_shadow[type_slot<T>()], p.sched.blocks_per_sm);
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], stream) : cudaSuccess; };
     e = mark(0);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p.counters, 0, 4 * sizeof(uint32_t), stream);
+    // the pool counters start at zero; counters[3] (failure bits) is sticky until read
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.counters, 0, 3 * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return e;
     const uint32_t n = (uint32_t)p.P * (uint32_t)p.R;
     if (p.depth_exp == 50)

@@ -61,6 +61,7 @@ class Twins:
         for i, (a, b) in enumerate(zip(self.batched, self.plain)):
             for x, y, name in zip(a.state(), b.state(), ("irr", "depth", "valid")):
                 assert np.array_equal(x, y), (label, i, name)
+            assert S.volume_status(a.vol) == 0 and S.volume_status(b.vol) == 0, (label, i)
 
     def close(self):
         S.destroy_batch(self.batch)

@@ -55,6 +55,7 @@ def run_and_compare(w, frames=1, subset=None, seed_rot=7, prev_gpu=None, record_
                 gv.update(rot, record=False)
                 again = gv.state()
                 s["records_neutral"] = all(np.array_equal(a, b) for a, b in zip(again, cur))
+        assert gv.S.volume_status(gv.vol) == 0  # no device-side failure recorded
     finally:
         gv.close()
     return stats
