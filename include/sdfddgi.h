@@ -68,7 +68,7 @@ enum { SDFDDGI_STAGE_EVENTS = 6 };
 /* Volume flags. BLEND_BF16 -- the precision form of the gather (Eq. 3): texel weights and
  * ray values rounded to bf16, products accumulated in fp32 on the tensor cores, instead of
  * the default float32-accurate gather (three tf32 products per term). It applies when
- * rays_per_probe is a multiple of 32 (otherwise the float32 gather runs). Combine it with a
+ * rays_per_probe is a multiple of 16 (otherwise the float32 gather runs). Combine it with a
  * binary16 SDF (upload_sdf dtype SDFDDGI_F16; stepping stays float32) for the full
  * precision form. */
 enum { SDFDDGI_FLAG_BLEND_BF16 = 1u };
@@ -271,7 +271,7 @@ SDFDDGI_API int sdfddgi_update_batch(sdfddgi_batch* b, uint32_t frame, const flo
 /* Chooses each volume's schedule by timing `repeats` real updates (plus one warm-up) of
  * each candidate on `stream`: trace-pool batch (16, 32, 64 tasks per warp claim), resident
  * CTAs per SM of the trace kernels (4 or the occupancy limit), and gather (tensor cores
- * when rays_per_probe is a multiple of 32, or SIMT). The trials write only each volume's
+ * when rays_per_probe is a multiple of 16, or SIMT). The trials write only each volume's
  * spare ping-pong buffer, so the maps and history are unchanged. Synchronises `stream`.
  * repeats: 1..64. */
 SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* stream);

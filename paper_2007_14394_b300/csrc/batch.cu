@@ -193,14 +193,17 @@ SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* 
     int rc = SDFDDGI_OK;
     for (int i = 0; i < b->n && rc == SDFDDGI_OK; ++i) {
         sdfddgi_volume* v = b->vols[i];
-        const int R = v->desc.rays_per_probe;
         // every trial reads the current maps and writes the other buffer, which the next
         // real update overwrites: the volume's state is untouched
+        UpdateParams probe;
+        rc = volume_params(v, &probe);
+        if (rc) break;
+        const bool tc_ok = gather_tc_supported(probe);
         std::vector<Schedule> cand;
         for (int pb : {16, 32, 64})
             for (int bps : {0, 4})
                 for (int g : {1, 2}) {
-                    if (g == 1 && R % 32 != 0) continue;
+                    if (g == 1 && !tc_ok) continue;
                     cand.push_back(Schedule{pb, bps, g});
                 }
         float best = 1e30f;

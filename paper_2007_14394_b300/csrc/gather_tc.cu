@@ -7,7 +7,7 @@
 // weight sum, so that numerator and denominator see the same rounding of W.
 //   A = W, 256 texel rows (irradiance 0..35, depth 36..231, zero padding) as two M = 128
 //       tiles, K-major, prepared once per frame by pack_weights_kernel as a shared-memory
-//       image and brought in per 32-ray chunk with one bulk copy;
+//       image and brought in per 16-ray chunk with one bulk copy;
 //   B = V for the CTA's 16 probes (N = 96), split by the CTA from the rays' values;
 //   D = two 128 x 96 fp32 accumulators in tensor memory.
 // Precision (template parameter): fp32 operands split as hi + lo tf32 and multiplied as
@@ -30,7 +30,7 @@ namespace tc {
 constexpr int kG = 16;                        // probes per CTA
 constexpr int kCh = 6;                        // channels per probe
 constexpr int kN = kG * kCh;                  // 96 accumulator columns per tile
-constexpr int kChunk = 32;                    // rays per K chunk
+constexpr int kChunk = 16;                    // rays per K chunk
 constexpr int kThreads = 256;
 constexpr int kTmemCols = 256;                // 2 x 96 used
 
@@ -86,7 +86,7 @@ __device__ __forceinline__ void put(unsigned char* part, uint32_t off, float v) 
 
 }  // namespace tc
 
-// The weight matrix as the A operand's shared-memory image: per 32-ray chunk, per tile,
+// The weight matrix as the A operand's shared-memory image: per 16-ray chunk, per tile,
 // its parts (tf32: hi then lo; bf16: one), element (row, k) at Fmt::offset(row, k).
 // Thread per (texel row, ray).
 template <bool BF16>
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) pack_weights_kernel(const __grid_constant
 }
 
 template <bool BF16>
-__global__ void __launch_bounds__(tc::kThreads, 1) gather_tc_kernel(const __grid_constant__ UpdateParams P) {
+__global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid_constant__ UpdateParams P) {
     using namespace tc;
     using F = Fmt<BF16>;
     constexpr int kABytes = F::kABytes, kBBytes = F::kBBytes, kBPart = F::kBPart, kTilePart = F::kTilePart;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) gather_tc_kernel(const __grid
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
 
-    // ---- K loop over 32-ray chunks, two stages
+    // ---- K loop over 16-ray chunks, two stages (88 KiB: two CTAs per SM)
     for (int c = 0; c < n_chunks; ++c) {
         const int s = c & 1;
         if (c >= 2 && !mbar_wait(&bar_mma[s], ((c - 2) >> 1) & 1, &P.counters[3])) s_fail = 1;  // stage s free again

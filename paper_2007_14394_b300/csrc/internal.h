@@ -34,7 +34,7 @@ struct VolumeView {
 struct Schedule {
     int pool_batch;      // trace tasks a warp claims per atomic: 8, 16, 32 (default) or 64
     int blocks_per_sm;   // resident CTAs per SM of the persistent trace kernels (default: occupancy limit)
-    int gather;          // 0 automatic (tensor cores when R % 32 == 0), 1 tensor cores, 2 SIMT
+    int gather;          // 0 automatic (tensor cores when R % 16 == 0), 1 tensor cores, 2 SIMT
 };
 
 struct LightDev {
@@ -112,7 +112,7 @@ cudaError_t launch_sample(const SampleParams& p, cudaStream_t stream);
 size_t quad_bytes(int dtype, size_t n_voxels);
 inline size_t weights_bytes(int R) { return ((size_t)(R + 1) * kTexels + (size_t)R * 4) * sizeof(float); }
 int report_error(int code, const char* msg);  // sets the text of sdfddgi_last_error(), returns code
-// the gather of Eq. 3 on the tensor cores (R a multiple of 32 and a weight image present)
+// the gather of Eq. 3 on the tensor cores (R a multiple of 16 and a weight image present)
 bool gather_tc_supported(const UpdateParams& p);
 size_t wimage_bytes(int R);
 cudaError_t launch_gather_tc(const UpdateParams& p, cudaStream_t stream);

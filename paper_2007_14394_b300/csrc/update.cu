@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) primary_kernel(const __grid_constant
 
 // ------------------------------------------------------------------ 2. hit preparation
 template <typename T>
-__global__ void __launch_bounds__(kThreads) prep_kernel(const __grid_constant__ UpdateParams P) {
+__global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant__ UpdateParams P) {
     const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;

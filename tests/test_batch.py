@@ -134,7 +134,7 @@ def test_autotune_keeps_state_and_results(cuda_device):
         for i, w in enumerate(t.ws):
             pb, bps, g, ms = S.batch_schedule(t.batch, i)
             assert pb in (16, 32, 64) and bps in (0, 4) and g in (1, 2) and ms > 0, (i, pb, bps, g, ms)
-            assert g == 2 or w.params["rays"] % 32 == 0
+            assert g == 2 or w.params["rays"] % 16 == 0
         # the tuned schedule differs from the default one at most in the gather's rounding
         for frame in (1, 2):
             t.update_batch(frame)
