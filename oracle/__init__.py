@@ -101,6 +101,8 @@ def _load():
                                           dp, dp, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                           C.c_int32]
             lib.oracle_update.restype = C.c_int32
+            lib.oracle_relocate.argtypes = [C.POINTER(Volume), C.POINTER(Grid), C.POINTER(Relocation), C.c_void_p,
+                                            dp, C.c_void_p, C.c_void_p, C.c_void_p]
             _lib = lib
     return _lib
 
@@ -276,3 +278,26 @@ def update(scene: OracleScene, grid: Grid, lights, rot: np.ndarray, probes: np.n
     if rc != 0:
         raise ValueError("oracle_update: invalid arguments")
     return {"irr": ci, "depth": cd, "valid": cv, "rays": rays}
+
+
+# ----------------------------------------------------------------- probe relocation
+class Relocation(C.Structure):
+    _fields_ = [("clearance_vox", C.c_double), ("reject_dist", C.c_double), ("max_offset", C.c_double),
+                ("min_clearance_vox", C.c_double), ("max_iters", C.c_int32), ("pad", C.c_int32)]
+
+
+def relocate(scene: "OracleScene", grid: Grid, clearance_vox: float, reject_dist: float, max_offset: float = 0.45,
+             min_clearance_vox: float = 0.5, max_iters: int = 16, last_pos=None) -> dict:
+    """Probe relocation (Sec. 3.2); returns pos [P,3], flags [P], iters [P], margin [P,2]."""
+    P = int(np.prod(list(grid.dims)))
+    rp = Relocation(float(clearance_vox), float(reject_dist), float(max_offset), float(min_clearance_vox),
+                    int(max_iters), 0)
+    last = None if last_pos is None else np.ascontiguousarray(np.asarray(last_pos, dtype=np.float32).reshape(P, 3))
+    pos = np.zeros((P, 3))
+    flags = np.zeros(P, np.uint32)
+    iters = np.zeros(P, np.int32)
+    margin = np.zeros((P, 2))
+    _load().oracle_relocate(C.byref(scene.vol), C.byref(grid), C.byref(rp),
+                            last.ctypes.data if last is not None else None, _dp(pos), flags.ctypes.data,
+                            iters.ctypes.data, _dp(margin))
+    return {"pos": pos, "flags": flags, "iters": iters, "margin": margin}

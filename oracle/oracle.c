@@ -611,3 +611,59 @@ int32_t oracle_update(const or_volume* vol, const or_grid* g, const or_light* li
     (void)n_threads;
     return 0;
 }
+
+/* ------------------------------------------------ probe relocation (Sec. 3.2) */
+
+/* Gradient of the trilinear field by central differences at +-h/2, per unit length. */
+static void sdf_gradient(const or_volume* vol, const double p[3], double grad[3]) {
+    const double h = vol->h;
+    for (int a = 0; a < 3; ++a) {
+        double pp[3] = {p[0], p[1], p[2]}, pm[3] = {p[0], p[1], p[2]};
+        pp[a] += 0.5 * h;
+        pm[a] -= 0.5 * h;
+        grad[a] = (oracle_sample_sdf(vol, pp) - oracle_sample_sdf(vol, pm)) / h;
+    }
+}
+
+void oracle_relocate(const or_volume* vol, const or_grid* g, const or_relocation* rp, const float* last_pos,
+                     double* out_pos, uint32_t* out_flags, int32_t* out_iters, double* out_margin) {
+    const int32_t P = g->dims[0] * g->dims[1] * g->dims[2];
+    const double h = vol->h, c = rp->clearance_vox * h;
+    for (int32_t p = 0; p < P; ++p) {
+        const int idx[3] = {p % g->dims[0], (p / g->dims[0]) % g->dims[1], p / (g->dims[0] * g->dims[1])};
+        double home[3], pos[3], last[3];
+        for (int a = 0; a < 3; ++a) {
+            home[a] = g->origin[a] + idx[a] * g->spacing[a];
+            pos[a] = home[a];
+            last[a] = last_pos ? (double)last_pos[3 * p + a] : home[a];
+        }
+        int32_t it = 0;
+        if (rp->clearance_vox > 0.0) {
+            while (it < rp->max_iters) {
+                const double s = oracle_sample_sdf(vol, pos);
+                if (s >= c) break;
+                double grad[3];
+                sdf_gradient(vol, pos, grad);
+                const double g2 = dot3(grad, grad);
+                if (!(g2 > 0.0)) break;
+                for (int a = 0; a < 3; ++a) {
+                    const double lim = rp->max_offset * g->spacing[a];
+                    pos[a] = clampd(pos[a] + (c - s) * grad[a] / g2, home[a] - lim, home[a] + lim);
+                }
+                ++it;
+            }
+        }
+        const double s_end = oracle_sample_sdf(vol, pos);
+        const double dist = sqrt((pos[0] - last[0]) * (pos[0] - last[0]) + (pos[1] - last[1]) * (pos[1] - last[1]) +
+                                 (pos[2] - last[2]) * (pos[2] - last[2]));
+        uint32_t flags = s_end > rp->min_clearance_vox * h ? 1u : 0u;
+        if (rp->reject_dist > 0.0 && dist > rp->reject_dist) flags |= 2u;
+        for (int a = 0; a < 3; ++a) out_pos[3 * p + a] = pos[a];
+        out_flags[p] = flags;
+        if (out_iters) out_iters[p] = it;
+        if (out_margin) {
+            out_margin[2 * p] = s_end / h - rp->min_clearance_vox;
+            out_margin[2 * p + 1] = dist - rp->reject_dist;
+        }
+    }
+}

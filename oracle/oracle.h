@@ -153,6 +153,32 @@ int32_t oracle_update(const or_volume* vol, const or_grid* g, const or_light* li
                       const int32_t* subset, int32_t n_subset, const or_force* force, or_ray* rays,
                       int32_t n_threads);
 
+/* Probe relocation (Sec. 3.2, the procedure UpdateProbePos). The paper gives the steps
+ * (query the SDF at the grid position; if below threshold1, move the probe by gradient
+ * descent on the SDF; if it then lies farther than threshold2 from last frame's
+ * position, reject its history) but not the descent itself. Reading taken: Gauss-Newton
+ * steps on E(p) = (c - sdf(p))^2 / 2 toward the level set sdf = c = clearance_vox * h,
+ *     p <- p + (c - sdf(p)) * g / |g|^2,   g = the central-difference gradient of the
+ *     trilinear field at +-h/2 (the shading normal's rule) divided by h,
+ * while sdf(p) < c and |g| > 0, at most max_iters steps, each followed by a clamp of
+ * every coordinate to within max_offset * spacing of the grid position. The probe ends
+ * active iff sdf(p) > min_clearance_vox * h. */
+typedef struct {
+    double clearance_vox;      /* threshold1, voxels; <= 0: no probe moves */
+    double reject_dist;        /* threshold2, world units; <= 0: no rejection */
+    double max_offset;         /* per-axis displacement limit, as a fraction of the spacing */
+    double min_clearance_vox;  /* active iff the final SDF exceeds this (voxels) */
+    int32_t max_iters;
+    int32_t pad;
+} or_relocation;
+
+/* Relocates every probe of grid g. last_pos: NULL (the grid positions) or [P][3] float
+ * positions of the last frame. Outputs [P][3] positions, [P] flags (bit 0 active, bit 1
+ * reject history), [P] steps taken, and [P][2] decision margins: final SDF minus the
+ * active threshold (voxels), and displacement minus threshold2 (world). */
+void oracle_relocate(const or_volume* vol, const or_grid* g, const or_relocation* rp, const float* last_pos,
+                     double* out_pos, uint32_t* out_flags, int32_t* out_iters, double* out_margin);
+
 #ifdef __cplusplus
 }
 #endif
