@@ -204,6 +204,31 @@ SDFDDGI_API int sdfddgi_update_probes(sdfddgi_volume* v, uint32_t frame, const f
  * The events must outlive their use; the caller reads them with cudaEventElapsedTime. */
 SDFDDGI_API int sdfddgi_set_stage_events(sdfddgi_volume* v, void* const* events, int32_t n);
 
+/* Probe relocation (Sec. 3.2, the procedure UpdateProbePos): the paper moves a probe
+ * that lies too near a surface (SDF below threshold1) by gradient descent on the SDF,
+ * and rejects its history when it then lies farther than threshold2 from last frame's
+ * position. The paper does not specify the descent. This library takes Gauss-Newton
+ * steps toward the level set sdf = clearance:
+ *     p <- p + (c - sdf(p)) g / |g|^2,
+ * where g is the gradient of the trilinear SDF by central differences at +-h/2. After
+ * each step every coordinate is clamped to within max_offset * spacing of the grid
+ * position. The steps stop at sdf >= c, at g = 0, or after max_iterations. A probe
+ * ends ACTIVE iff its final SDF exceeds min_clearance, and gets REJECT_HISTORY iff
+ * |p - last| > reject_distance. */
+typedef struct {
+    float clearance;         /* threshold1, voxels; <= 0: no probe moves */
+    float reject_distance;   /* threshold2, world units; <= 0: history is never rejected */
+    float max_offset;        /* per-axis limit of the move, fraction of the probe spacing, [0, 0.5] */
+    float min_clearance;     /* voxels, >= 0 */
+    int32_t max_iterations;  /* 0..64 */
+} sdfddgi_relocation;
+
+/* Writes the P probe states of v's grid to `out` (device). `last`: NULL (last frame's
+ * positions = the grid positions) or P device states of the last frame; out may equal
+ * last. The states feed sdfddgi_update_probes (states_on_device = 1). */
+SDFDDGI_API int sdfddgi_relocate_probes(const sdfddgi_volume* v, const sdfddgi_relocation* r,
+                                        const sdfddgi_probe_state* last, sdfddgi_probe_state* out, void* stream);
+
 /* Interpolated normalised irradiance (Sec. 3.4 probe interpolation, without the
  * per-pixel SDF visibility test) at n world points with unit normals: trilinear
  * over the 8 probes of the grid cell containing the point (clamped to the grid),

@@ -63,7 +63,8 @@ RAY_DTYPE = np.dtype([("t", "f8"), ("L", "f8", (3,)), ("margin_primary", "f8"),
                       ("steps", "i4"), ("natural_event", "i4"), ("natural_steps", "i4"),
                       ("lit_mask", "u4"), ("natural_lit_mask", "u4"), ("traced_mask", "u4"),
                       ("shadow_steps", "i4"), ("forced", "i4"), ("hard", "i4"), ("t_own", "f8"),
-                      ("t_cond", "f8"), ("t_forced", "i4"), ("pad", "i4"), ("dLdt", "f8", (3,))])
+                      ("t_cond", "f8"), ("t_forced", "i4"), ("pad", "i4"), ("dLdt", "f8", (3,)),
+                      ("dLdcos", "f8", (3,))])
 FORCE_DTYPE = np.dtype([("event", "i4"), ("steps", "i4"), ("lit_mask", "u4"), ("t", "f4")])
 
 

@@ -399,10 +399,10 @@ static void shade_at(const or_volume* vol, const or_grid* g, const or_light* lig
     for (int a = 0; a < 3; ++a) xs[a] = x[a] + g->bias_vox * h * n[a];
     const double tmax = g->tmax_vox * h;
 
-    double direct[3] = {0.0, 0.0, 0.0};
+    double direct[3] = {0.0, 0.0, 0.0}, dcos[3] = {0.0, 0.0, 0.0};
     for (int l = 0; l < n_lights; ++l) {
         const or_light* li = &lights[l];
-        double ldir[3], scale = 0.0, tlimit = tmax, m_gate;
+        double ldir[3], scale = 0.0, tlimit = tmax, m_gate, per_cos = 1.0;
         int gate;
         if (li->type == 0) {
             for (int a = 0; a < 3; ++a) ldir[a] = li->v[a];
@@ -422,6 +422,7 @@ static void shade_at(const or_volume* vol, const or_grid* g, const or_light* lig
             m_gate = fmin(fabs(cosv), fabs(1.0 - q4));
             gate = cosv > 0.0 && win > 0.0;
             scale = fmax(cosv, 0.0) * win / (dist * dist);
+            per_cos = win / (dist * dist);
             double Ls[3] = {li->v[0] - xs[0], li->v[1] - xs[1], li->v[2] - xs[2]};
             double ds = sqrt(dot3(Ls, Ls));
             for (int a = 0; a < 3; ++a) ldir[a] = Ls[a] / ds;
@@ -457,8 +458,13 @@ static void shade_at(const or_volume* vol, const or_grid* g, const or_light* lig
         }
         if (!lit) continue;
         rec->lit_mask |= 1u << l;
-        for (int k = 0; k < 3; ++k) direct[k] += li->rgb[k] * scale;
+        for (int k = 0; k < 3; ++k) {
+            direct[k] += li->rgb[k] * scale;
+            dcos[k] += li->rgb[k] * per_cos;
+        }
     }
+    if (!visibility_given)
+        for (int k = 0; k < 3; ++k) rec->dLdcos[k] = albedo[k] / kPi * dcos[k];
 
     double indirect[3] = {0.0, 0.0, 0.0};
     if (g->k_bounce != 0.0) oracle_sample_irradiance(g, prev_irr, prev_valid, x, n, indirect);

@@ -106,6 +106,8 @@ typedef struct {
     int32_t t_forced;        /* 1 if t was taken from the force record (see oracle_set_t_tolerance) */
     int32_t pad;
     double dLdt[3];          /* derivative of L with respect to the hit distance, visibility held fixed */
+    double dLdcos[3];        /* derivative of L with respect to each visible light's cosine n.l, summed
+                                over those lights (sensitivity to the rounding of the shading normal) */
 } or_ray;
 
 /* Spherical-Fibonacci direction i of n (unrotated). */

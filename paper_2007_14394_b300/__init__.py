@@ -36,6 +36,11 @@ class Light(C.Structure):
     _fields_ = [("type", C.c_int32), ("v", C.c_float * 3), ("rgb", C.c_float * 3), ("range", C.c_float)]
 
 
+class Relocation(C.Structure):
+    _fields_ = [("clearance", C.c_float), ("reject_distance", C.c_float), ("max_offset", C.c_float),
+                ("min_clearance", C.c_float), ("max_iterations", C.c_int32)]
+
+
 class ProbeMaps(C.Structure):
     _fields_ = [("dims", C.c_int32 * 3), ("n_grids", C.c_int32), ("irr", C.c_void_p), ("depth", C.c_void_p),
                 ("valid", C.c_void_p), ("states", C.c_void_p)]
@@ -85,6 +90,7 @@ def _load() -> C.CDLL:
                                            i32, vp, C.POINTER(Light), i32, C.POINTER(C.c_float), u32, vp, vp,
                                            vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "sdfddgi_volume_status": ([vp, C.POINTER(u32)], C.c_int),
+        "sdfddgi_relocate_probes": ([vp, C.POINTER(Relocation), vp, vp, vp], C.c_int),
         "sdfddgi_denoiser_status": ([vp, C.POINTER(u32)], C.c_int),
         "sdfddgi_create_denoiser": ([C.POINTER(C.c_float), C.c_float, C.POINTER(vp)], C.c_int),
         "sdfddgi_destroy_denoiser": ([vp], None),
@@ -113,7 +119,8 @@ EXPORTED = ("last_error", "create_scene", "destroy_scene", "upload_sdf", "set_li
             "sample_irradiance", "set_stage_events", "get_maps", "read_state", "write_state", "reset",
             "create_batch", "destroy_batch", "update_batch", "batch_autotune", "batch_schedule",
             "create_denoiser", "destroy_denoiser", "denoiser_params", "denoise", "denoise_volume",
-            "denoiser_gradients", "denoiser_adam", "denoiser_train_step", "volume_status", "denoiser_status")
+            "denoiser_gradients", "denoiser_adam", "denoiser_train_step", "volume_status", "denoiser_status",
+            "relocate_probes")
 DENOISER_PARAMS = 49219
 DENOISE_TENSOR, DENOISE_SIMT_BF16, DENOISE_SIMT_FP32 = 0, 1, 2
 STAGES = ("weights", "primary", "prep", "shadow", "gather")  # intervals between the stage events
@@ -445,3 +452,13 @@ def denoiser_status(d) -> int:
     f = C.c_uint32()
     _check(lib.sdfddgi_denoiser_status(d, C.byref(f)))
     return f.value
+
+
+def relocate_probes(volume, out, clearance=2.0, reject_distance=0.0, max_offset=0.45, min_clearance=0.5,
+                    max_iterations=16, last=None, stream=None) -> None:
+    """Probe relocation (Sec. 3.2) into `out` (device tensor of P*16 bytes); `last`: None or
+    the last frame's states (device, may be `out`)."""
+    r = Relocation(float(clearance), float(reject_distance), float(max_offset), float(min_clearance),
+                   int(max_iterations))
+    _check(lib.sdfddgi_relocate_probes(volume, C.byref(r), _dev_ptr(last, "last"), _dev_ptr(out, "out"),
+                                       _stream(stream)))

@@ -99,6 +99,11 @@ def force_from_records(rec: np.ndarray) -> np.ndarray:
 EPS_COS = 5e-7           # bound of the float32 error of a texel-direction . ray-direction cosine
 WEIGHT_ERR_FACTOR = 4.0  # safety factor on the first-order weight-error term
 TRACE_ERR_FACTOR = 2.0   # safety factor on the first-order effect of the measured hit-distance differences
+# The shading normal is normalised from differences of two trilinear samples h apart; each
+# sample carries a few float32 ulps of the local distances (~1e-7 m below 1 m), so a normal
+# component is good to ~1e-6 and a light's cosine n.l to ~2e-6. Where a light grazes the
+# surface that absolute error is a large relative one; the oracle records dL/d(n.l).
+EPS_SHADE_COS = 2e-6
 
 
 def texel_geometry(rays: int, rot, exponent: int):
@@ -237,7 +242,8 @@ def compare(w: Workload, gpu_state, gpu_rec, orc, subset, h_vox: float, rot=None
     vals = (rays_o["L"], np.stack([that, that * that], axis=-1))
     # first-order effect on each ray's values of the measured hit-distance difference (t within tolerance)
     dt_w = np.where(O.is_miss(ev), 0.0, np.abs(rec["t"].astype(np.float64) - rays_o["t"]))
-    dvals = (np.abs(rays_o["dLdt"]) * dt_w[..., None], np.stack([dt_w, 2.0 * that * dt_w], axis=-1))
+    dvals = (np.abs(rays_o["dLdt"]) * dt_w[..., None] + EPS_SHADE_COS * np.abs(rays_o["dLdcos"]),
+             np.stack([dt_w, 2.0 * that * dt_w], axis=-1))
     for name, g_map, o_map, keep, k in (("irr", ig, io, keep_i, 0), ("depth", dg, do, keep_d, 1)):
         cw = ct = np.zeros_like(o_map)
         if geo is not None:
