@@ -102,6 +102,8 @@ def _load():
                                           dp, dp, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                           C.c_int32]
             lib.oracle_update.restype = C.c_int32
+            lib.oracle_sample_irradiance_visible.argtypes = [C.POINTER(Volume), C.POINTER(Grid), dp, C.c_void_p,
+                                                             C.c_void_p, C.c_double, dp, dp, dp, dp, dp]
             lib.oracle_relocate.argtypes = [C.POINTER(Volume), C.POINTER(Grid), C.POINTER(Relocation), C.c_void_p,
                                             dp, C.c_void_p, C.c_void_p, C.c_void_p]
             _lib = lib
@@ -302,3 +304,16 @@ def relocate(scene: "OracleScene", grid: Grid, clearance_vox: float, reject_dist
                             last.ctypes.data if last is not None else None, _dp(pos), flags.ctypes.data,
                             iters.ctypes.data, _dp(margin))
     return {"pos": pos, "flags": flags, "iters": iters, "margin": margin}
+
+
+def sample_irradiance_visible(scene: "OracleScene", grid: Grid, irr: np.ndarray, valid: np.ndarray, x, nrm,
+                              softness: float, probe_pos=None):
+    """Interpolation with SDF probe visibility (Sec. 3.4); returns (rgb, vis[8], margins[8, 2])."""
+    irr = np.ascontiguousarray(irr, dtype=np.float64)
+    valid = np.ascontiguousarray(valid, dtype=np.uint8)
+    pp = None if probe_pos is None else np.ascontiguousarray(np.asarray(probe_pos, dtype=np.float32))
+    out, vis, marg = np.zeros(3), np.zeros(8), np.zeros(16)
+    _load().oracle_sample_irradiance_visible(C.byref(scene.vol), C.byref(grid), _dp(irr), valid.ctypes.data,
+                                             pp.ctypes.data if pp is not None else None, float(softness),
+                                             _dp(_vec(x)), _dp(_vec(nrm)), _dp(out), _dp(vis), _dp(marg))
+    return out, vis, marg.reshape(8, 2)

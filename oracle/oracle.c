@@ -352,6 +352,78 @@ void oracle_sample_irradiance(const or_grid* g, const double* irr, const uint8_t
     for (int k = 0; k < 3; ++k) out[k] = sw > 0.0 ? acc[k] / sw : 0.0;
 }
 
+/* Visibility of probe position q from x (normal nrm): the soft SDF shadow trace of
+ * oracle_sample_irradiance_visible. */
+static double probe_visibility(const or_volume* vol, const or_grid* g, const double x[3], const double nrm[3],
+                               const double q[3], double softness, double* m_hit, double* m_end) {
+    const double h = vol->h, eps = g->eps_vox * h;
+    double xs[3], v[3];
+    for (int a = 0; a < 3; ++a) {
+        xs[a] = x[a] + g->bias_vox * h * nrm[a];
+        v[a] = q[a] - xs[a];
+    }
+    const double L = sqrt(dot3(v, v));
+    *m_hit = HUGE_MARGIN;
+    *m_end = HUGE_MARGIN;
+    if (!(L > 0.0)) return 1.0;
+    double vis = 1.0, t = 0.0;
+    for (int s = 0; s < g->max_steps; ++s) {
+        if (t >= L) break;
+        double p[3];
+        for (int a = 0; a < 3; ++a) p[a] = xs[a] + t * v[a] / L;
+        const double d = oracle_sample_sdf(vol, p);
+        *m_hit = fmin(*m_hit, fabs(d - eps) / h);
+        if (d < eps) return 0.0;
+        if (t > 0.0) vis = fmin(vis, softness * d / t);
+        t += d;
+        *m_end = fmin(*m_end, fabs(t - L) / h);
+    }
+    return clampd(vis, 0.0, 1.0);
+}
+
+void oracle_sample_irradiance_visible(const or_volume* vol, const or_grid* g, const double* irr,
+                                      const uint8_t* valid, const float* probe_pos, double softness,
+                                      const double x[3], const double nrm[3], double out[3], double vis[8],
+                                      double margins[16]) {
+    int base[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        double c = clampd((x[a] - g->origin[a]) / g->spacing[a], 0.0, (double)(g->dims[a] - 1));
+        int b = (int)floor(c);
+        if (b > g->dims[a] - 2) b = g->dims[a] - 2;
+        if (b < 0) b = 0;
+        base[a] = b;
+        f[a] = g->dims[a] > 1 ? c - b : 0.0;
+    }
+    double sw = 0.0, acc[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < 8; ++c) {
+        int d[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+        double w = 1.0;
+        int idx[3];
+        for (int a = 0; a < 3; ++a) {
+            w *= d[a] ? f[a] : 1.0 - f[a];
+            idx[a] = base[a] + d[a];
+            if (idx[a] > g->dims[a] - 1) idx[a] = g->dims[a] - 1;
+        }
+        size_t p = ((size_t)idx[2] * g->dims[1] + idx[1]) * g->dims[0] + idx[0];
+        w *= valid[p] ? 1.0 : 0.0;
+        vis[c] = -1.0;
+        margins[2 * c] = margins[2 * c + 1] = HUGE_MARGIN;
+        if (w <= 0.0) continue;
+        double q[3];
+        for (int a = 0; a < 3; ++a)
+            q[a] = probe_pos ? (double)probe_pos[3 * p + a] : g->origin[a] + idx[a] * g->spacing[a];
+        vis[c] = probe_visibility(vol, g, x, nrm, q, softness, &margins[2 * c], &margins[2 * c + 1]);
+        w *= vis[c];
+        if (w <= 0.0) continue;
+        double val[3];
+        fetch_oct_bilinear(irr + p * IRR_T * IRR_T * 4, nrm, val);
+        for (int k = 0; k < 3; ++k) acc[k] += w * val[k];
+        sw += w;
+    }
+    for (int k = 0; k < 3; ++k) out[k] = sw > 0.0 ? acc[k] / sw : 0.0;
+}
+
 /* ------------------------------------------------ shading (Sec. 3.3, O12) */
 
 /* Radiance leaving hit point x back along the ray: emission stored with the scene,

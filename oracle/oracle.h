@@ -155,6 +155,21 @@ int32_t oracle_update(const or_volume* vol, const or_grid* g, const or_light* li
                       const int32_t* subset, int32_t n_subset, const or_force* force, or_ray* rays,
                       int32_t n_threads);
 
+/* Per-point interpolation with probe visibility (Sec. 3.4, per-pixel GI shading): each of
+ * the 8 probes of the cell is weighted by trilinear weight x history flag x visibility,
+ * the visibility an SDF shadow trace from the point (offset bias_vox * h along the
+ * normal) toward the probe, soft in the manner of SDF soft shadows: vis = clamp(min over
+ * the march (t > 0) of softness * sdf / t, 0, 1), 0 on a hit (sdf < eps), the march
+ * ending when t reaches the probe's distance or after max_steps. No cosine or other
+ * extra weight. probe_pos: NULL (grid positions) or [P][3] float probe positions.
+ * Outputs the rgb, each corner's visibility (-1 for a corner of weight 0) and, per
+ * corner, the smallest distances of the hit test (|sdf - eps|, voxels) and of the end
+ * test (|t - distance|, voxels) from flipping. */
+void oracle_sample_irradiance_visible(const or_volume* vol, const or_grid* g, const double* irr,
+                                      const uint8_t* valid, const float* probe_pos, double softness,
+                                      const double x[3], const double nrm[3], double out[3], double vis[8],
+                                      double margins[16]);
+
 /* Probe relocation (Sec. 3.2, the procedure UpdateProbePos). The paper gives the steps
  * (query the SDF at the grid position; if below threshold1, move the probe by gradient
  * descent on the SDF; if it then lies farther than threshold2 from last frame's
