@@ -239,6 +239,21 @@ SDFDDGI_API int sdfddgi_relocate_probes(const sdfddgi_volume* v, const sdfddgi_r
 SDFDDGI_API int sdfddgi_sample_irradiance(const sdfddgi_volume* v, const float* points, const float* normals,
                                           int64_t n, float* out_rgb, void* stream);
 
+/* The paper's per-pixel interpolation with probe visibility (Sec. 3.4): as
+ * sdfddgi_sample_irradiance, with each probe's weight also multiplied by its visibility
+ * from the point, and no cosine or other extra weight. The paper tests visibility with
+ * an SDF shadow trace and cites SDF soft shadows; the rule here: march from
+ * x + normal_bias * n toward the probe by sphere tracing (the volume's eps and
+ * max_steps); vis = min over the march (t > 0) of softness * sdf / t, 0 on a hit, clamped
+ * to [0, 1]. The paper's screen-space parts (checkerboard depth, pixel selection, 4x4
+ * de-duplication) need a frame buffer and are not part of this call.
+ *  softness -- > 0; large values approach the binary test.
+ *  states   -- NULL (probes at their grid positions) or P device states (positions used).
+ *  points, normals, out_rgb -- device float[n][3]. */
+SDFDDGI_API int sdfddgi_sample_irradiance_visible(const sdfddgi_volume* v, const float* points, const float* normals,
+                                                  int64_t n, float softness, const sdfddgi_probe_state* states,
+                                                  float* out_rgb, void* stream);
+
 /* Device pointers to the current (latest) maps: irradiance [P][8][8][4] float,
  * depth [P][16][16][2] float, valid [P] uint8 (1 = probe has history). They stay
  * valid until the next update_probes / write_state / destroy. Any may be NULL. */

@@ -352,11 +352,43 @@ void oracle_sample_irradiance(const or_grid* g, const double* irr, const uint8_t
     for (int k = 0; k < 3; ++k) out[k] = sw > 0.0 ? acc[k] / sw : 0.0;
 }
 
-/* Visibility of probe position q from x (normal nrm): the soft SDF shadow trace of
- * oracle_sample_irradiance_visible. */
+/* The march of the soft SDF shadow trace of oracle_sample_irradiance_visible from state
+ * (t, vis, step s0). *m_hit receives how far the hit tests whose other outcome would
+ * change the result lie from flipping (voxels); with branch set, a hit within the
+ * rounding band (g_delta_vox) is also followed the other way to see whether it matters. */
+static double march_visibility(const or_volume* vol, const or_grid* g, const double xs[3], const double dir[3],
+                               double L, double t, double vis, int s0, double softness, int branch,
+                               double* m_hit, double* m_end) {
+    const double h = vol->h, eps = g->eps_vox * h;
+    double near_miss = HUGE_MARGIN;  /* samples just above eps: a flip would give 0 */
+    for (int s = s0; s < g->max_steps; ++s) {
+        if (t >= L) break;
+        double p[3];
+        for (int a = 0; a < 3; ++a) p[a] = xs[a] + t * dir[a];
+        const double d = oracle_sample_sdf(vol, p);
+        if (d < eps) {
+            if (branch && (eps - d) / h < g_delta_vox) {
+                const double vis2 = t > 0.0 ? fmin(vis, softness * d / t) : vis;
+                double mh = HUGE_MARGIN, me = HUGE_MARGIN;
+                if (march_visibility(vol, g, xs, dir, L, t + d, vis2, s + 1, softness, 0, &mh, &me) > 0.0)
+                    *m_hit = fmin(*m_hit, (eps - d) / h);
+            }
+            return 0.0;
+        }
+        near_miss = fmin(near_miss, (d - eps) / h);
+        if (t > 0.0) vis = fmin(vis, softness * d / t);
+        t += d;
+        *m_end = fmin(*m_end, fabs(t - L) / h);
+    }
+    vis = clampd(vis, 0.0, 1.0);
+    if (vis > 0.0) *m_hit = fmin(*m_hit, near_miss);
+    return vis;
+}
+
+/* Visibility of probe position q from x (normal nrm). */
 static double probe_visibility(const or_volume* vol, const or_grid* g, const double x[3], const double nrm[3],
                                const double q[3], double softness, double* m_hit, double* m_end) {
-    const double h = vol->h, eps = g->eps_vox * h;
+    const double h = vol->h;
     double xs[3], v[3];
     for (int a = 0; a < 3; ++a) {
         xs[a] = x[a] + g->bias_vox * h * nrm[a];
@@ -366,19 +398,8 @@ static double probe_visibility(const or_volume* vol, const or_grid* g, const dou
     *m_hit = HUGE_MARGIN;
     *m_end = HUGE_MARGIN;
     if (!(L > 0.0)) return 1.0;
-    double vis = 1.0, t = 0.0;
-    for (int s = 0; s < g->max_steps; ++s) {
-        if (t >= L) break;
-        double p[3];
-        for (int a = 0; a < 3; ++a) p[a] = xs[a] + t * v[a] / L;
-        const double d = oracle_sample_sdf(vol, p);
-        *m_hit = fmin(*m_hit, fabs(d - eps) / h);
-        if (d < eps) return 0.0;
-        if (t > 0.0) vis = fmin(vis, softness * d / t);
-        t += d;
-        *m_end = fmin(*m_end, fabs(t - L) / h);
-    }
-    return clampd(vis, 0.0, 1.0);
+    const double dir[3] = {v[0] / L, v[1] / L, v[2] / L};
+    return march_visibility(vol, g, xs, dir, L, 0.0, 1.0, 0, softness, 1, m_hit, m_end);
 }
 
 void oracle_sample_irradiance_visible(const or_volume* vol, const or_grid* g, const double* irr,

@@ -163,8 +163,10 @@ int32_t oracle_update(const or_volume* vol, const or_grid* g, const or_light* li
  * ending when t reaches the probe's distance or after max_steps. No cosine or other
  * extra weight. probe_pos: NULL (grid positions) or [P][3] float probe positions.
  * Outputs the rgb, each corner's visibility (-1 for a corner of weight 0) and, per
- * corner, the smallest distances of the hit test (|sdf - eps|, voxels) and of the end
- * test (|t - distance|, voxels) from flipping. */
+ * corner, how far the decisions that could change the visibility lie from flipping: the
+ * hit tests whose other outcome changes the result (|sdf - eps|, voxels; a hit within
+ * the rounding band of oracle_set_delta is followed the other way to find out) and the
+ * end test (|t - distance|, voxels). */
 void oracle_sample_irradiance_visible(const or_volume* vol, const or_grid* g, const double* irr,
                                       const uint8_t* valid, const float* probe_pos, double softness,
                                       const double x[3], const double nrm[3], double out[3], double vis[8],

@@ -91,6 +91,7 @@ def _load() -> C.CDLL:
                                            vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "sdfddgi_volume_status": ([vp, C.POINTER(u32)], C.c_int),
         "sdfddgi_relocate_probes": ([vp, C.POINTER(Relocation), vp, vp, vp], C.c_int),
+        "sdfddgi_sample_irradiance_visible": ([vp, vp, vp, i64, C.c_float, vp, vp, vp], C.c_int),
         "sdfddgi_denoiser_status": ([vp, C.POINTER(u32)], C.c_int),
         "sdfddgi_create_denoiser": ([C.POINTER(C.c_float), C.c_float, C.POINTER(vp)], C.c_int),
         "sdfddgi_destroy_denoiser": ([vp], None),
@@ -120,7 +121,7 @@ EXPORTED = ("last_error", "create_scene", "destroy_scene", "upload_sdf", "set_li
             "create_batch", "destroy_batch", "update_batch", "batch_autotune", "batch_schedule",
             "create_denoiser", "destroy_denoiser", "denoiser_params", "denoise", "denoise_volume",
             "denoiser_gradients", "denoiser_adam", "denoiser_train_step", "volume_status", "denoiser_status",
-            "relocate_probes")
+            "relocate_probes", "sample_irradiance_visible")
 DENOISER_PARAMS = 49219
 DENOISE_TENSOR, DENOISE_SIMT_BF16, DENOISE_SIMT_FP32 = 0, 1, 2
 STAGES = ("weights", "primary", "prep", "shadow", "gather")  # intervals between the stage events
@@ -462,3 +463,11 @@ def relocate_probes(volume, out, clearance=2.0, reject_distance=0.0, max_offset=
                    int(max_iterations))
     _check(lib.sdfddgi_relocate_probes(volume, C.byref(r), _dev_ptr(last, "last"), _dev_ptr(out, "out"),
                                        _stream(stream)))
+
+
+def sample_irradiance_visible(volume, points, normals, out, softness=8.0, states=None, stream=None) -> None:
+    """Interpolation with SDF probe visibility (Sec. 3.4); points, normals, out: device float [n, 3]."""
+    n = int(points.numel() // 3) if _is_torch(points) else int(np.asarray(points).size // 3)
+    _check(lib.sdfddgi_sample_irradiance_visible(volume, _dev_ptr(points, "points"), _dev_ptr(normals, "normals"), n,
+                                                 float(softness), _dev_ptr(states, "states"), _dev_ptr(out, "out"),
+                                                 _stream(stream)))

@@ -480,6 +480,57 @@ SDFDDGI_API int sdfddgi_sample_irradiance(const sdfddgi_volume* v, const float* 
     return SDFDDGI_OK;
 }
 
+SDFDDGI_API int sdfddgi_sample_irradiance_visible(const sdfddgi_volume* v, const float* points, const float* normals,
+                                                  int64_t n, float softness, const sdfddgi_probe_state* states,
+                                                  float* out_rgb, void* stream) {
+    if (!v) return fail(SDFDDGI_ERR_INVALID_ARG, "sample_irradiance_visible: volume is NULL");
+    if (n < 0 || n > ((int64_t)1 << 38))
+        return fail(SDFDDGI_ERR_INVALID_ARG, "sample_irradiance_visible: n out of range");
+    if (n > 0 && (!points || !normals || !out_rgb))
+        return fail(SDFDDGI_ERR_INVALID_ARG, "sample_irradiance_visible: NULL array");
+    if (!(softness > 0.f) || !std::isfinite(softness))
+        return fail(SDFDDGI_ERR_INVALID_ARG, "sample_irradiance_visible: softness must be positive and finite");
+    const sdfddgi_scene* s = v->scene;
+    if (!s || !s->has_sdf) return fail(SDFDDGI_ERR_STATE, "sample_irradiance_visible: the scene holds no SDF yet");
+    SampleParams p;
+    std::memset(&p, 0, sizeof p);
+    for (int a = 0; a < 3; ++a) {
+        p.gdims[a] = v->desc.dims[a];
+        p.gorigin[a] = v->desc.origin[a];
+        p.gspacing[a] = v->desc.spacing[a];
+    }
+    p.irr = v->irr[v->cur];
+    p.valid = v->valid[v->cur];
+    p.points = points;
+    p.normals = normals;
+    p.out = out_rgb;
+    p.n = n;
+    VisParams vp;
+    std::memset(&vp, 0, sizeof vp);
+    VolumeView& vol = vp.vol;
+    vol.sdf = s->sdf;
+    vol.quads = s->quads;
+    vol.nx = s->dims[0];
+    vol.ny = s->dims[1];
+    vol.nz = s->dims[2];
+    vol.dtype = s->dtype;
+    vol.h = s->h;
+    vol.inv_h = 1.0f / s->h;
+    for (int a = 0; a < 3; ++a) {
+        vol.lo[a] = s->origin[a];
+        vol.hi[a] = s->origin[a] + (float)s->dims[a] * s->h;
+    }
+    vp.softness = softness;
+    vp.eps_w = v->desc.eps * s->h;
+    vp.bias_w = v->desc.normal_bias * s->h;
+    vp.max_steps = v->desc.max_steps;
+    vp.states = states;
+    cudaError_t e = launch_sample_visible(p, vp, as_stream(stream));
+    if (e != cudaSuccess)
+        return fail(SDFDDGI_ERR_CUDA, "sample_irradiance_visible: launch failed: %s", cudaGetErrorString(e));
+    return SDFDDGI_OK;
+}
+
 SDFDDGI_API int sdfddgi_get_maps(const sdfddgi_volume* v, const float** irr, const float** depth,
                                  const uint8_t** valid) {
     if (!v) return fail(SDFDDGI_ERR_INVALID_ARG, "get_maps: volume is NULL");

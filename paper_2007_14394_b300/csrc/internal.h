@@ -106,9 +106,20 @@ struct SampleParams {
     int64_t n;
 };
 
+// The per-point probe visibility test of sample_irradiance_visible.
+struct VisParams {
+    VolumeView vol;
+    float softness;
+    float eps_w;       // hit threshold, world units
+    float bias_w;      // start offset along the normal, world units
+    int max_steps;
+    const sdfddgi_probe_state* states;  // null: probes at their grid positions
+};
+
 // stage_events: null, or SDFDDGI_STAGE_EVENTS events recorded on `stream` at the stage boundaries
 cudaError_t launch_update(const UpdateParams& p, cudaStream_t stream, cudaEvent_t const* stage_events = nullptr);
 cudaError_t launch_sample(const SampleParams& p, cudaStream_t stream);
+cudaError_t launch_sample_visible(const SampleParams& p, const VisParams& v, cudaStream_t stream);
 size_t quad_bytes(int dtype, size_t n_voxels);
 inline size_t weights_bytes(int R) { return ((size_t)(R + 1) * kTexels + (size_t)R * 4) * sizeof(float); }
 int report_error(int code, const char* msg);  // sets the text of sdfddgi_last_error(), returns code
