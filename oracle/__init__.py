@@ -42,7 +42,12 @@ def build(force: bool = False) -> str:
 class Volume(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("sdf_dtype", C.c_int32),
                 ("h", C.c_double), ("origin", C.c_double * 3),
-                ("sdf", C.c_void_p), ("material", C.c_void_p)]
+                ("sdf", C.c_void_p), ("material", C.c_void_p), ("prims", C.c_void_p),
+                ("n_prims", C.c_int32), ("pad", C.c_int32)]
+
+
+PRIM_DTYPE = np.dtype([("type", "i4"), ("pad", "i4"), ("p", "f8", (7,)), ("albedo", "f8", (3,)),
+                       ("emission", "f8", (3,))])
 
 
 class Light(C.Structure):
@@ -64,8 +69,8 @@ RAY_DTYPE = np.dtype([("t", "f8"), ("L", "f8", (3,)), ("margin_primary", "f8"),
                       ("lit_mask", "u4"), ("natural_lit_mask", "u4"), ("traced_mask", "u4"),
                       ("shadow_steps", "i4"), ("forced", "i4"), ("hard", "i4"), ("t_own", "f8"),
                       ("t_cond", "f8"), ("t_forced", "i4"), ("pad", "i4"), ("dLdt", "f8", (3,)),
-                      ("dLdcos", "f8", (3,))])
-FORCE_DTYPE = np.dtype([("event", "i4"), ("steps", "i4"), ("lit_mask", "u4"), ("t", "f4")])
+                      ("dLdcos", "f8", (3,)), ("owner", "i4"), ("natural_owner", "i4"), ("margin_owner", "f8")])
+FORCE_DTYPE = np.dtype([("event", "i4"), ("steps", "i4"), ("lit_mask", "u4"), ("t", "f4"), ("owner", "i4")])
 
 
 def is_miss(event):
@@ -104,6 +109,8 @@ def _load():
             lib.oracle_update.restype = C.c_int32
             lib.oracle_sample_irradiance_visible.argtypes = [C.POINTER(Volume), C.POINTER(Grid), dp, C.c_void_p,
                                                              C.c_void_p, C.c_double, dp, dp, dp, dp, dp]
+            lib.oracle_analytic_sdf.argtypes = [C.POINTER(Volume), dp, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+            lib.oracle_analytic_sdf.restype = C.c_double
             lib.oracle_relocate.argtypes = [C.POINTER(Volume), C.POINTER(Grid), C.POINTER(Relocation), C.c_void_p,
                                             dp, C.c_void_p, C.c_void_p, C.c_void_p]
             _lib = lib
@@ -139,7 +146,27 @@ class OracleScene:
                 raise ValueError("material must be float16 [nz][ny][nx][8]")
             self.material = m
         self.vol = Volume(nx, ny, nz, dtype_code, float(h), (C.c_double * 3)(*[float(x) for x in origin]),
-                          self.sdf.ctypes.data, self.material.ctypes.data if self.material is not None else None)
+                          self.sdf.ctypes.data, self.material.ctypes.data if self.material is not None else None,
+                          None, 0, 0)
+
+    @classmethod
+    def analytic(cls, types, params, albedo, emission, origin, dims, h: float) -> "OracleScene":
+        """The union of analytic primitives (float32 parameters promoted exactly); the box
+        origin + [0, dims * h] bounds the traces and h is the unit of voxel parameters."""
+        self = cls.__new__(cls)
+        n = len(types)
+        prims = np.zeros(n, dtype=PRIM_DTYPE)
+        prims["type"] = np.asarray(types, dtype=np.int32)
+        prims["p"] = np.asarray(params, dtype=np.float32).reshape(n, -1)[:, :7].astype(np.float64)
+        prims["albedo"] = np.asarray(albedo, dtype=np.float32).astype(np.float64)
+        prims["emission"] = np.asarray(emission, dtype=np.float32).astype(np.float64)
+        self.prims = prims
+        self.sdf = np.zeros(1, np.float32)
+        self.material = None
+        nx, ny, nz = (int(d) for d in dims)
+        self.vol = Volume(nx, ny, nz, 0, float(h), (C.c_double * 3)(*[float(x) for x in origin]),
+                          self.sdf.ctypes.data, None, prims.ctypes.data, n, 0)
+        return self
 
 
 def make_lights(lights) -> tuple:
@@ -317,3 +344,11 @@ def sample_irradiance_visible(scene: "OracleScene", grid: Grid, irr: np.ndarray,
                                              pp.ctypes.data if pp is not None else None, float(softness),
                                              _dp(_vec(x)), _dp(_vec(nrm)), _dp(out), _dp(vis), _dp(marg))
     return out, vis, marg.reshape(8, 2)
+
+
+def analytic_sdf(scene: "OracleScene", p):
+    """(distance, owner index, second-smallest distance) of an analytic scene at p."""
+    own = C.c_int32()
+    sec = C.c_double()
+    d = _load().oracle_analytic_sdf(C.byref(scene.vol), _dp(_vec(p)), C.byref(own), C.byref(sec))
+    return d, own.value, sec.value

@@ -119,7 +119,62 @@ static void trilinear_cell(const or_volume* vol, const double p[3], int i0[3], d
     }
 }
 
+/* Exact Euclidean distance to one primitive (negative inside). */
+static double prim_distance(const or_prim* q, const double x[3]) {
+    const double* a = q->p;
+    switch (q->type) {
+        case 0: { /* sphere */
+            double v[3] = {x[0] - a[0], x[1] - a[1], x[2] - a[2]};
+            return sqrt(dot3(v, v)) - a[3];
+        }
+        case 1: { /* box: distance outside, largest (negative) face distance inside */
+            double e[3], out2 = 0.0, in = -HUGE_VAL;
+            for (int k = 0; k < 3; ++k) {
+                e[k] = fabs(x[k] - a[k]) - a[3 + k];
+                if (e[k] > 0.0) out2 += e[k] * e[k];
+                in = fmax(in, e[k]);
+            }
+            return sqrt(out2) + fmin(in, 0.0);
+        }
+        case 2: { /* capsule: distance to the segment minus the radius */
+            double ab[3] = {a[3] - a[0], a[4] - a[1], a[5] - a[2]};
+            double ax[3] = {x[0] - a[0], x[1] - a[1], x[2] - a[2]};
+            double L2 = dot3(ab, ab);
+            double s = L2 > 0.0 ? clampd(dot3(ax, ab) / L2, 0.0, 1.0) : 0.0;
+            double r[3] = {ax[0] - s * ab[0], ax[1] - s * ab[1], ax[2] - s * ab[2]};
+            return sqrt(dot3(r, r)) - a[6];
+        }
+        case 3: /* solid below y = a[0] */
+            return x[1] - a[0];
+        case 4: { /* solid outside the ball */
+            double v[3] = {x[0] - a[0], x[1] - a[1], x[2] - a[2]};
+            return a[3] - sqrt(dot3(v, v));
+        }
+        default:
+            return HUGE_VAL;
+    }
+}
+
+double oracle_analytic_sdf(const or_volume* vol, const double p[3], int32_t* owner, double* second) {
+    double best = HUGE_VAL, next = HUGE_VAL;
+    int32_t arg = -1;
+    for (int32_t k = 0; k < vol->n_prims; ++k) {
+        const double d = prim_distance(&vol->prims[k], p);
+        if (d < best) {
+            next = best;
+            best = d;
+            arg = k;
+        } else if (d < next) {
+            next = d;
+        }
+    }
+    if (owner) *owner = arg;
+    if (second) *second = next;
+    return best;
+}
+
 double oracle_sample_sdf(const or_volume* vol, const double p[3]) {
+    if (vol->n_prims > 0) return oracle_analytic_sdf(vol, p, NULL, NULL);
     int i0[3];
     double f[3];
     trilinear_cell(vol, p, i0, f);
@@ -132,7 +187,8 @@ double oracle_sample_sdf(const or_volume* vol, const double p[3]) {
     return acc;
 }
 
-/* Albedo and emission at p: the material volume sampled with the same trilinear rule. */
+/* Albedo and emission at p: the material volume sampled with the same trilinear rule
+ * (analytic scenes take the nearest primitive's material, in shade_at). */
 static void sample_material(const or_volume* vol, const double p[3], double albedo[3], double emission[3]) {
     for (int k = 0; k < 3; ++k) albedo[k] = emission[k] = 0.0;
     if (!vol->material) return;
@@ -486,7 +542,32 @@ static void shade_at(const or_volume* vol, const or_grid* g, const or_light* lig
     for (int a = 0; a < 3; ++a) n[a] = glen > 0.0 ? grad[a] / glen : -d[a];
 
     double albedo[3], emission[3];
-    sample_material(vol, x, albedo, emission);
+    if (vol->n_prims > 0) {
+        /* the material of the primitive attaining the distance at the hit; a choice between
+         * primitives within the rounding band follows the other side's record */
+        int32_t own;
+        double second;
+        oracle_analytic_sdf(vol, x, &own, &second);
+        const double best = prim_distance(&vol->prims[own], x);
+        if (!visibility_given) {
+            rec->natural_owner = own + 1;
+            rec->margin_owner = (second - best) / h;
+            if (force && force->owner > 0 && force->owner - 1 != own && force->owner - 1 < vol->n_prims) {
+                rec->forced++;
+                if (!(rec->margin_owner < g_delta_vox)) rec->hard++;
+                own = force->owner - 1;
+            }
+            rec->owner = own + 1;
+        } else if (rec->owner > 0) {
+            own = rec->owner - 1;
+        }
+        for (int k = 0; k < 3; ++k) {
+            albedo[k] = vol->prims[own].albedo[k];
+            emission[k] = vol->prims[own].emission[k];
+        }
+    } else {
+        sample_material(vol, x, albedo, emission);
+    }
 
     double xs[3];
     for (int a = 0; a < 3; ++a) xs[a] = x[a] + g->bias_vox * h * n[a];

@@ -25,12 +25,30 @@ extern "C" {
  * stored [z][y][x]. sdf_dtype 0 = float32, 1 = IEEE binary16 (raw bits).
  * material: [z][y][x][8] binary16 raw bits = albedo r,g,b, unused, emission r,g,b, unused;
  * NULL means albedo 0 and emission 0 everywhere. */
+/* An analytic SDF primitive (the paper's scene representation, Sec. 3.1): type 0 sphere
+ * (centre, radius), 1 axis-aligned box (centre, half-extents), 2 capsule (end a, end b,
+ * radius), 3 half-space below the plane y = p[0], 4 hollow ball (solid outside the sphere
+ * of centre p[0..2] and radius p[3]); albedo and emission per primitive. */
+typedef struct {
+    int32_t type, pad;
+    double p[7];
+    double albedo[3];
+    double emission[3];
+} or_prim;
+
+/* The scene: a voxel SDF (sdf, dtype, trilinear with clamp-to-edge; material volume
+ * optional), or, when n_prims > 0, the union of analytic primitives (the SDF is the
+ * minimum of their distances; the material of a point is that of the primitive attaining
+ * it, ties to the lowest index). Either way the box origin + [0, n*h] bounds the traces,
+ * and h is the unit of the voxel-unit parameters. */
 typedef struct {
     int32_t nx, ny, nz, sdf_dtype;
     double h;
     double origin[3];
     const void* sdf;
     const uint16_t* material;
+    const or_prim* prims;
+    int32_t n_prims, pad;
 } or_volume;
 
 /* Light: type 0 = directional (v = unit direction TOWARD the light, rgb = irradiance E),
@@ -82,6 +100,8 @@ typedef struct {
     int32_t steps;
     uint32_t lit_mask;
     float t;                 /* the other side's hit distance (world) */
+    int32_t owner;           /* analytic scenes: index + 1 of the primitive whose material the hit
+                                took (0: not given) */
 } or_force;
 
 /* Per-ray record of one update (one per (probe, ray)). */
@@ -108,6 +128,9 @@ typedef struct {
     double dLdt[3];          /* derivative of L with respect to the hit distance, visibility held fixed */
     double dLdcos[3];        /* derivative of L with respect to each visible light's cosine n.l, summed
                                 over those lights (sensitivity to the rounding of the shading normal) */
+    int32_t owner;           /* analytic scenes: index + 1 of the primitive whose material was used */
+    int32_t natural_owner;   /* the oracle's own choice */
+    double margin_owner;     /* voxels: second-smallest minus smallest primitive distance at the hit */
 } or_ray;
 
 /* Spherical-Fibonacci direction i of n (unrotated). */
@@ -115,7 +138,10 @@ void oracle_sf_dir(int32_t i, int32_t n, double out[3]);
 /* Octahedral map (pole +z). */
 void oracle_oct_encode(const double v[3], double uv[2]);
 void oracle_oct_decode(const double uv[2], double v[3]);
-/* Trilinear sample of the signed-distance volume at world point p. */
+/* Distance of the union of analytic primitives at p; *owner receives the index of the
+ * primitive attaining it (lowest index on ties) and *second the next smallest distance. */
+double oracle_analytic_sdf(const or_volume* vol, const double p[3], int32_t* owner, double* second);
+/* Trilinear sample of the signed-distance volume at world point p (or the analytic SDF). */
 double oracle_sample_sdf(const or_volume* vol, const double p[3]);
 /* One sphere trace; returns the exit event, writes t (world), steps and margin (voxels). */
 int32_t oracle_trace(const or_volume* vol, const double o[3], const double d[3],
