@@ -120,7 +120,8 @@ typedef struct {
  * the primary trace's exit event (0 left the volume, 1 hit, 2 passed t_max,
  * 3 step budget spent; 255 for rays of inactive probes), its step count, the
  * hit distance (t_max for misses), the radiance carried back, which lights were
- * visible, and the total steps of the shadow rays. */
+ * visible, the total steps of the shadow rays, and (scenes of primitives) the caller's
+ * index + 1 of the primitive whose material the hit took (0 otherwise). */
 typedef struct {
     float t;
     float L[3];
@@ -129,8 +130,27 @@ typedef struct {
     uint16_t steps;
     uint8_t event;
     uint8_t reserved0;
-    uint32_t reserved1;
+    uint32_t material_owner;
 } sdfddgi_ray_record;
+
+/* An analytic SDF primitive (Sec. 3.1: the scene as a set of primitives, each with its
+ * type, transform and material). params:
+ *  SPHERE     centre x y z, radius
+ *  BOX        centre x y z, half-extents x y z (axis-aligned)
+ *  CAPSULE    end a x y z, end b x y z, radius
+ *  PLANE_Y    y: solid below the plane y = params[0]
+ *  INV_SPHERE centre x y z, radius: solid outside the ball (a hollow room)
+ * The scene's SDF is the minimum over its primitives (exact Euclidean distances), and a
+ * hit takes the albedo/emission of the primitive attaining it (the lowest index on ties). */
+enum { SDFDDGI_PRIM_SPHERE = 0, SDFDDGI_PRIM_BOX = 1, SDFDDGI_PRIM_CAPSULE = 2, SDFDDGI_PRIM_PLANE_Y = 3,
+       SDFDDGI_PRIM_INV_SPHERE = 4 };
+typedef struct {
+    int32_t type;
+    float params[7];
+    float albedo[3];
+    float emission[3];
+    float pad[2];
+} sdfddgi_primitive;  /* 64 bytes */
 
 /* Text of the last failure on this thread ("" if none). Never NULL. */
 SDFDDGI_API const char* sdfddgi_last_error(void);
@@ -153,6 +173,23 @@ SDFDDGI_API void sdfddgi_destroy_scene(sdfddgi_scene* s);
 SDFDDGI_API int sdfddgi_upload_sdf(sdfddgi_scene* s, const void* sdf, const int32_t dims[3], float voxel_size,
                                    const float origin[3], int32_t dtype, const void* material,
                                    int32_t is_device_ptr, void* stream);
+
+/* Makes the scene a union of analytic primitives (the paper's representation, Sec. 3.1)
+ * instead of a voxel volume. The library groups the bounded primitives into clusters of
+ * `cluster_size` by the Morton order of their centres, each with a bounding box; an SDF
+ * query takes the unbounded primitives (planes, hollow balls), then visits only the
+ * clusters whose box is no farther than the best distance so far (or contains the point,
+ * once it is inside a primitive), and a sphere trace
+ * starts each query from twice its last distance (the paper's culling, exact: the result
+ * is the minimum over all primitives). cluster_size 0 puts all primitives in one cluster
+ * (a plain loop, the paper's baseline).
+ *  prims, n      -- host array of n >= 1 primitives (copied; the index is the position).
+ *  lo, hi        -- world box that bounds every trace (rays leaving it are misses).
+ *  unit          -- world length of one "voxel" for the voxel-unit parameters (eps, t_max,
+ *                   normal bias, relocation clearances) and the normal's difference step.
+ * Replaces any SDF; bumps the scene version (batches rebuild their graphs). */
+SDFDDGI_API int sdfddgi_upload_primitives(sdfddgi_scene* s, const sdfddgi_primitive* prims, int32_t n,
+                                          const float lo[3], const float hi[3], float unit, int32_t cluster_size);
 
 /* Replaces the scene's lights (host array of n, 0..SDFDDGI_MAX_LIGHTS) and the
  * radiance of rays that leave the scene (sky_rgb, host, may be NULL for black). */

@@ -227,6 +227,15 @@ void oracle_set_t_tolerance(double tol_vox, double factor) {
 
 /* Derivative of the trilinear field along d at p (world units); zero across clamped axes. */
 static double sdf_slope(const or_volume* vol, const double p[3], const double d[3]) {
+    if (vol->n_prims > 0) { /* analytic: central difference of the exact field along d */
+        const double e = 1e-6 * vol->h;
+        double pp[3], pm[3];
+        for (int a = 0; a < 3; ++a) {
+            pp[a] = p[a] + e * d[a];
+            pm[a] = p[a] - e * d[a];
+        }
+        return (oracle_analytic_sdf(vol, pp, NULL, NULL) - oracle_analytic_sdf(vol, pm, NULL, NULL)) / (2.0 * e);
+    }
     int i0[3];
     double f[3], grad[3] = {0.0, 0.0, 0.0};
     trilinear_cell(vol, p, i0, f);

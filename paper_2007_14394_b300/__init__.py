@@ -59,8 +59,11 @@ class VolumeDesc(C.Structure):
 
 PROBE_STATE_DTYPE = np.dtype([("pos", "f4", (3,)), ("flags", "u4")])
 RAY_RECORD_DTYPE = np.dtype([("t", "f4"), ("L", "f4", (3,)), ("lit_mask", "u4"), ("shadow_steps", "u4"),
-                             ("steps", "u2"), ("event", "u1"), ("reserved0", "u1"), ("reserved1", "u4")])
-assert RAY_RECORD_DTYPE.itemsize == 32 and PROBE_STATE_DTYPE.itemsize == 16
+                             ("steps", "u2"), ("event", "u1"), ("reserved0", "u1"), ("material_owner", "u4")])
+PRIMITIVE_DTYPE = np.dtype([("type", "i4"), ("params", "f4", (7,)), ("albedo", "f4", (3,)),
+                            ("emission", "f4", (3,)), ("pad", "f4", (2,))])
+PRIM_SPHERE, PRIM_BOX, PRIM_CAPSULE, PRIM_PLANE_Y, PRIM_INV_SPHERE = 0, 1, 2, 3, 4
+assert RAY_RECORD_DTYPE.itemsize == 32 and PROBE_STATE_DTYPE.itemsize == 16 and PRIMITIVE_DTYPE.itemsize == 64
 
 
 def _load() -> C.CDLL:
@@ -90,6 +93,8 @@ def _load() -> C.CDLL:
                                            i32, vp, C.POINTER(Light), i32, C.POINTER(C.c_float), u32, vp, vp,
                                            vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "sdfddgi_volume_status": ([vp, C.POINTER(u32)], C.c_int),
+        "sdfddgi_upload_primitives": ([vp, vp, i32, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_float, i32],
+                                      C.c_int),
         "sdfddgi_relocate_probes": ([vp, C.POINTER(Relocation), vp, vp, vp], C.c_int),
         "sdfddgi_sample_irradiance_visible": ([vp, vp, vp, i64, C.c_float, vp, vp, vp], C.c_int),
         "sdfddgi_denoiser_status": ([vp, C.POINTER(u32)], C.c_int),
@@ -121,7 +126,7 @@ EXPORTED = ("last_error", "create_scene", "destroy_scene", "upload_sdf", "set_li
             "create_batch", "destroy_batch", "update_batch", "batch_autotune", "batch_schedule",
             "create_denoiser", "destroy_denoiser", "denoiser_params", "denoise", "denoise_volume",
             "denoiser_gradients", "denoiser_adam", "denoiser_train_step", "volume_status", "denoiser_status",
-            "relocate_probes", "sample_irradiance_visible")
+            "relocate_probes", "sample_irradiance_visible", "upload_primitives")
 DENOISER_PARAMS = 49219
 DENOISE_TENSOR, DENOISE_SIMT_BF16, DENOISE_SIMT_FP32 = 0, 1, 2
 STAGES = ("weights", "primary", "prep", "shadow", "gather")  # intervals between the stage events
@@ -471,3 +476,18 @@ def sample_irradiance_visible(volume, points, normals, out, softness=8.0, states
     _check(lib.sdfddgi_sample_irradiance_visible(volume, _dev_ptr(points, "points"), _dev_ptr(normals, "normals"), n,
                                                  float(softness), _dev_ptr(states, "states"), _dev_ptr(out, "out"),
                                                  _stream(stream)))
+
+
+def upload_primitives(scene, types, params, albedo, emission, lo, hi, unit: float, cluster_size: int = 8) -> None:
+    """The scene as a union of analytic primitives (Sec. 3.1): types [n], params [n, >=7 or fewer]
+    (float32), albedo / emission [n, 3]; the box lo..hi bounds every trace, `unit` is the length
+    of one voxel for the voxel-unit parameters; cluster_size 0 disables the cluster culling."""
+    n = len(types)
+    arr = np.zeros(n, dtype=PRIMITIVE_DTYPE)
+    arr["type"] = np.asarray(types, dtype=np.int32)
+    par = np.asarray(params, dtype=np.float32).reshape(n, -1)
+    arr["params"][:, :min(7, par.shape[1])] = par[:, :7]
+    arr["albedo"] = np.asarray(albedo, dtype=np.float32).reshape(n, 3)
+    arr["emission"] = np.asarray(emission, dtype=np.float32).reshape(n, 3)
+    _check(lib.sdfddgi_upload_primitives(scene, arr.ctypes.data, n, _floats(lo, 3), _floats(hi, 3), float(unit),
+                                         int(cluster_size)))

@@ -134,6 +134,8 @@ SDFDDGI_API void sdfddgi_destroy_scene(sdfddgi_scene* s) {
     cudaFree(s->sdf);
     cudaFree(s->quads);
     cudaFree(s->material);
+    cudaFree(s->prims);
+    cudaFree(s->clusters);
     delete s;
 }
 
@@ -201,6 +203,34 @@ SDFDDGI_API int sdfddgi_upload_sdf(sdfddgi_scene* s, const void* sdf, const int3
     s->version++;
     return SDFDDGI_OK;
 }
+
+}  // extern "C"
+
+void sdfddgi::scene_view(const sdfddgi_scene* s, VolumeView* v) {
+    std::memset(v, 0, sizeof *v);
+    v->dtype = s->dtype;
+    v->nx = s->dims[0];
+    v->ny = s->dims[1];
+    v->nz = s->dims[2];
+    v->h = s->h;
+    v->inv_h = 1.0f / s->h;
+    for (int a = 0; a < 3; ++a) {
+        v->lo[a] = s->origin[a];
+        v->hi[a] = s->origin[a] + (float)s->dims[a] * s->h;
+    }
+    if (s->dtype == kAnalytic) {
+        v->prims = s->prims;
+        v->clusters = s->clusters;
+        v->n_unbounded = s->n_unbounded;
+        v->n_clusters = s->n_clusters;
+    } else {
+        v->sdf = s->sdf;
+        v->quads = s->quads;
+        v->material = s->has_material ? static_cast<const uint4*>(s->material) : nullptr;
+    }
+}
+
+extern "C" {
 
 SDFDDGI_API int sdfddgi_set_lights(sdfddgi_scene* s, const sdfddgi_light* lights, int32_t n, const float sky_rgb[3]) {
     if (!s) return fail(SDFDDGI_ERR_INVALID_ARG, "set_lights: scene is NULL");
@@ -347,20 +377,7 @@ int sdfddgi::volume_params(sdfddgi_volume* v, UpdateParams* out) {
     const sdfddgi_volume_desc& d = v->desc;
     UpdateParams& p = *out;
     std::memset(&p, 0, sizeof p);
-    VolumeView& vol = p.vol;
-    vol.sdf = s->sdf;
-    vol.quads = s->quads;
-    vol.material = s->has_material ? static_cast<const uint4*>(s->material) : nullptr;
-    vol.nx = s->dims[0];
-    vol.ny = s->dims[1];
-    vol.nz = s->dims[2];
-    vol.dtype = s->dtype;
-    vol.h = s->h;
-    vol.inv_h = 1.0f / s->h;
-    for (int a = 0; a < 3; ++a) {
-        vol.lo[a] = s->origin[a];
-        vol.hi[a] = s->origin[a] + (float)s->dims[a] * s->h;
-    }
+    scene_view(s, &p.vol);
     std::memcpy(p.lights, s->lights, sizeof p.lights);
     p.n_lights = s->n_lights;
     for (int a = 0; a < 3; ++a) {
@@ -507,19 +524,7 @@ SDFDDGI_API int sdfddgi_sample_irradiance_visible(const sdfddgi_volume* v, const
     p.n = n;
     VisParams vp;
     std::memset(&vp, 0, sizeof vp);
-    VolumeView& vol = vp.vol;
-    vol.sdf = s->sdf;
-    vol.quads = s->quads;
-    vol.nx = s->dims[0];
-    vol.ny = s->dims[1];
-    vol.nz = s->dims[2];
-    vol.dtype = s->dtype;
-    vol.h = s->h;
-    vol.inv_h = 1.0f / s->h;
-    for (int a = 0; a < 3; ++a) {
-        vol.lo[a] = s->origin[a];
-        vol.hi[a] = s->origin[a] + (float)s->dims[a] * s->h;
-    }
+    scene_view(s, &vp.vol);
     vp.softness = softness;
     vp.eps_w = v->desc.eps * s->h;
     vp.bias_w = v->desc.normal_bias * s->h;

@@ -70,6 +70,89 @@ __device__ __forceinline__ float sample_sdf(const VolumeView& v, float3 p) {
     return lerp(lerp(x00, x10, c.fy), lerp(x01, x11, c.fy), c.fz);
 }
 
+// ------------------------------------------------------------------ analytic scene (Sec. 3.1)
+struct Analytic {};  // the SDF-type tag of a scene made of primitives
+
+// Exact Euclidean distance to one primitive (negative inside), float32.
+__device__ __forceinline__ float prim_distance(const PrimDev& q, float3 x) {
+    switch (q.type) {
+        case SDFDDGI_PRIM_SPHERE: {
+            const float3 v = x - f3(q.p[0], q.p[1], q.p[2]);
+            return sqrtf(dot(v, v)) - q.p[3];
+        }
+        case SDFDDGI_PRIM_BOX: {
+            const float ex = fabsf(x.x - q.p[0]) - q.p[3], ey = fabsf(x.y - q.p[1]) - q.p[4],
+                        ez = fabsf(x.z - q.p[2]) - q.p[5];
+            const float ox = fmaxf(ex, 0.f), oy = fmaxf(ey, 0.f), oz = fmaxf(ez, 0.f);
+            return sqrtf(ox * ox + oy * oy + oz * oz) + fminf(fmaxf(ex, fmaxf(ey, ez)), 0.f);
+        }
+        case SDFDDGI_PRIM_CAPSULE: {
+            const float3 a = f3(q.p[0], q.p[1], q.p[2]), ab = f3(q.p[3], q.p[4], q.p[5]) - a, ax = x - a;
+            const float l2 = dot(ab, ab);
+            const float s = l2 > 0.f ? fminf(fmaxf(dot(ax, ab) / l2, 0.f), 1.f) : 0.f;
+            const float3 r = ax - s * ab;
+            return sqrtf(dot(r, r)) - q.p[6];
+        }
+        case SDFDDGI_PRIM_PLANE_Y:
+            return x.y - q.p[0];
+        case SDFDDGI_PRIM_INV_SPHERE: {
+            const float3 v = x - f3(q.p[0], q.p[1], q.p[2]);
+            return q.p[3] - sqrtf(dot(v, v));
+        }
+        default:
+            return INFINITY;
+    }
+}
+
+__device__ __forceinline__ void take(const PrimDev& q, float d, float* best, int* who) {
+    if (d < *best || (d == *best && q.index < *who)) {
+        *best = d;
+        *who = q.index;
+    }
+}
+
+// Distance of the union of primitives at p (the paper's cluster query): the unbounded
+// primitives, then every cluster whose box lies no farther than the best distance so far
+// (or contains p, once p is inside a primitive),
+// starting from `bound` (an upper bound known beforehand: +inf, or about twice the last
+// distance of a sphere trace). The result is the minimum over all primitives whenever
+// bound is one. *who (optional) receives the caller's index of the primitive attaining
+// it (the lowest among equals), *slot its position in the primitive array.
+__device__ __forceinline__ float analytic_sdf(const VolumeView& v, float3 p, float bound, int* who = nullptr,
+                                              int* slot = nullptr) {
+    float best = bound;
+    int idx = 0x7fffffff, at = -1;
+    for (int k = 0; k < v.n_unbounded; ++k) {
+        const PrimDev& q = v.prims[k];
+        const int before = idx;
+        take(q, prim_distance(q, p), &best, &idx);
+        if (idx != before) at = k;
+    }
+    for (int c = 0; c < v.n_clusters; ++c) {
+        const ClusterDev cl = v.clusters[c];
+        const float dx = fmaxf(fmaxf(cl.lo[0] - p.x, p.x - cl.hi[0]), 0.f);
+        const float dy = fmaxf(fmaxf(cl.lo[1] - p.y, p.y - cl.hi[1]), 0.f);
+        const float dz = fmaxf(fmaxf(cl.lo[2] - p.z, p.z - cl.hi[2]), 0.f);
+        // every primitive inside lies at least the box distance away; a point already inside a
+        // primitive (best < 0) must still visit each box that contains it
+        if (sqrtf(dx * dx + dy * dy + dz * dz) > fmaxf(best, 0.f)) continue;
+        for (int k = cl.first; k < cl.first + cl.count; ++k) {
+            const PrimDev& q = v.prims[k];
+            const int before = idx;
+            take(q, prim_distance(q, p), &best, &idx);
+            if (idx != before) at = k;
+        }
+    }
+    if (who) *who = idx;
+    if (slot) *slot = at;
+    return best;
+}
+
+template <>
+__device__ __forceinline__ float sample_sdf<Analytic>(const VolumeView& v, float3 p) {
+    return analytic_sdf(v, p, INFINITY);
+}
+
 // Albedo and emission: the material volume under the same trilinear rule.
 __device__ __forceinline__ void sample_material(const VolumeView& v, float3 p, float3* albedo, float3* emission) {
     *albedo = f3(0.f, 0.f, 0.f);

@@ -19,6 +19,10 @@ struct sdfddgi_scene {
     float origin[3] = {0.f, 0.f, 0.f};
     bool has_sdf = false;
     bool has_material = false;
+    // a scene of analytic primitives (dtype kAnalytic) instead of a voxel volume
+    sdfddgi::PrimDev* prims = nullptr;  // unbounded primitives first, then each cluster's run
+    sdfddgi::ClusterDev* clusters = nullptr;
+    int n_prims = 0, n_unbounded = 0, n_clusters = 0;
     sdfddgi::LightDev lights[SDFDDGI_MAX_LIGHTS] = {};
     int n_lights = 0;
     float sky[3] = {0.f, 0.f, 0.f};
@@ -51,6 +55,8 @@ struct sdfddgi_volume {
 };
 
 namespace sdfddgi {
+// The scene's SDF as the kernels read it (voxel volume or primitives).
+void scene_view(const sdfddgi_scene* s, VolumeView* v);
 // Everything of one update of v that follows from the scene and the volume at the current
 // ping-pong parity (rotation, probe states, records and schedule are left zero); ensures the
 // shadow-task capacity. Returns an sdfddgi_status.

@@ -18,16 +18,43 @@ constexpr int kDepTexels = kDepN * kDepN;        // 196 interior depth texels
 
 enum Event : uint8_t { kLeftVolume = 0, kHit = 1, kPastLimit = 2, kExhausted = 3, kNoRay = 255 };
 
-// The signed-distance volume and its material volume as the kernels read them.
+// One analytic primitive as the kernels read it (64 bytes): type and parameters as in
+// sdfddgi_primitive, the caller's index (material ties go to the lowest), material.
+struct PrimDev {
+    int type;
+    int index;
+    float p[7];
+    float albedo[3];
+    float emission[3];
+    float pad;
+};
+
+// A cluster of primitives: its box (inflated so that float rounding never culls a primitive
+// that attains the minimum) and its run [first, first + count) of the primitive array.
+struct ClusterDev {
+    float lo[3];
+    int first;
+    float hi[3];
+    int count;
+};
+
+constexpr int kAnalytic = 2;  // VolumeView::dtype of a scene made of primitives
+
+// The scene's SDF as the kernels read it: a voxel volume (float or binary16, with its
+// material volume) or, with dtype kAnalytic, a union of analytic primitives in clusters.
 struct VolumeView {
     const void* sdf;          // float or __half, [nz][ny][nx]
     const void* quads;        // xy-quads of the same values: float4 or 4 x __half per voxel
     const uint4* material;    // 8 x binary16 per voxel (albedo rgb, -, emission rgb, -), or null
     int nx, ny, nz;
-    int dtype;                // SDFDDGI_F32 / SDFDDGI_F16
-    float h, inv_h;
-    float lo[3];              // world box of the volume
+    int dtype;                // SDFDDGI_F32 / SDFDDGI_F16 / kAnalytic
+    float h, inv_h;           // voxel size (analytic: the unit of voxel parameters)
+    float lo[3];              // world box of the volume (bounds every trace)
     float hi[3];
+    const PrimDev* prims;     // analytic: unbounded primitives first, then each cluster's run
+    const ClusterDev* clusters;
+    int n_unbounded;
+    int n_clusters;
 };
 
 // Launch shapes of one update; zero fields select the defaults.

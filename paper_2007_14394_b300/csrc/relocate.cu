@@ -89,19 +89,8 @@ extern "C" SDFDDGI_API int sdfddgi_relocate_probes(const sdfddgi_volume* v, cons
     if (!s || !s->has_sdf) return report_error(SDFDDGI_ERR_STATE, "relocate_probes: the scene holds no SDF yet");
     if (v->P == 0) return SDFDDGI_OK;
     RelocArgs a{};
-    VolumeView& vol = a.vol;
-    vol.sdf = s->sdf;
-    vol.quads = s->quads;
-    vol.material = nullptr;
-    vol.nx = s->dims[0];
-    vol.ny = s->dims[1];
-    vol.nz = s->dims[2];
-    vol.dtype = s->dtype;
-    vol.h = s->h;
-    vol.inv_h = 1.0f / s->h;
+    scene_view(s, &a.vol);
     for (int k = 0; k < 3; ++k) {
-        vol.lo[k] = s->origin[k];
-        vol.hi[k] = s->origin[k] + (float)s->dims[k] * s->h;
         a.gdims[k] = v->desc.dims[k];
         a.gorigin[k] = v->desc.origin[k];
         a.gspacing[k] = v->desc.spacing[k];
@@ -116,7 +105,9 @@ extern "C" SDFDDGI_API int sdfddgi_relocate_probes(const sdfddgi_volume* v, cons
     a.out = out;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const unsigned blocks = (unsigned)((a.P + 255) / 256);
-    if (s->dtype == SDFDDGI_F16)
+    if (s->dtype == kAnalytic)
+        relocate_kernel<Analytic><<<blocks, 256, 0, st>>>(a);
+    else if (s->dtype == SDFDDGI_F16)
         relocate_kernel<__half><<<blocks, 256, 0, st>>>(a);
     else
         relocate_kernel<float><<<blocks, 256, 0, st>>>(a);

@@ -112,7 +112,9 @@ cudaError_t launch_sample_visible(const SampleParams& p, const VisParams& v, cud
     if (p.n == 0) return cudaSuccess;
     const int threads = 256;
     const int64_t blocks = (p.n + threads - 1) / threads;
-    if (v.vol.dtype == SDFDDGI_F16)
+    if (v.vol.dtype == kAnalytic)
+        sample_visible_kernel<Analytic><<<(unsigned)blocks, threads, 0, stream>>>(p, v);
+    else if (v.vol.dtype == SDFDDGI_F16)
         sample_visible_kernel<__half><<<(unsigned)blocks, threads, 0, stream>>>(p, v);
     else
         sample_visible_kernel<float><<<(unsigned)blocks, threads, 0, stream>>>(p, v);

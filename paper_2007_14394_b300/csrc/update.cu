@@ -48,9 +48,27 @@ __device__ __forceinline__ float pow_runtime(float c, int p) {
 struct TraceState {
     float3 o, d;
     float t, tlimit;
+    float last;    // the previous sample's distance (scenes of primitives: bounds the next query)
     int s;
     uint32_t aux;  // task payload kept for the completion handler
 };
+
+// The SDF at p on a sphere trace. For a scene of primitives the query starts from twice the
+// last distance (the field is 1-Lipschitz and the step was that distance; the slack covers
+// float rounding), and falls back to a full query if nothing lies below that bound, so the
+// result is always the minimum over all primitives.
+template <typename T>
+__device__ __forceinline__ float trace_sample(const VolumeView& v, TraceState& st, float3 p) {
+    if constexpr (std::is_same<T, Analytic>::value) {
+        const float bound = st.last < INFINITY ? fmaf(2.002f, st.last, 1e-4f * v.h) : INFINITY;
+        float sd = analytic_sdf(v, p, bound);
+        if (!(sd < bound)) sd = analytic_sdf(v, p, INFINITY);
+        st.last = sd;
+        return sd;
+    } else {
+        return sample_sdf<T>(v, p);
+    }
+}
 
 // Advances a sphere trace by one step, with the tests of sphere_trace() in device.cuh
 // in the same order (leave the box, hit, pass the limit, spend the budget). Returns the
@@ -65,7 +83,7 @@ __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, f
         *t_end = st.tlimit;
         return kLeftVolume;
     }
-    const float sd = sample_sdf<T>(v, p);
+    const float sd = trace_sample<T>(v, st, p);
     if (sd < eps) {
         *steps = st.s + 1;
         *t_end = st.t;
@@ -118,6 +136,7 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
                 } else if (init(k, st)) {
                     st.t = 0.f;
                     st.s = 0;
+                    st.last = INFINITY;
                     busy = true;
                 } else {
                     need = true;  // nothing to trace for this task: take another
@@ -235,7 +254,17 @@ __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant
             const float glen = sqrtf(gx * gx + gy * gy + gz * gz);
             const float3 nr = glen > 0.f ? f3(gx / glen, gy / glen, gz / glen) : f3(-d.x, -d.y, -d.z);
             float3 albedo, emission;
-            sample_material(V, x, &albedo, &emission);
+            uint32_t owner = 0;  // scenes of primitives: the caller's index + 1 of the material's primitive
+            if constexpr (std::is_same<T, Analytic>::value) {
+                int slot;
+                analytic_sdf(V, x, INFINITY, nullptr, &slot);
+                const PrimDev& q = V.prims[slot];
+                albedo = f3(q.albedo[0], q.albedo[1], q.albedo[2]);
+                emission = f3(q.emission[0], q.emission[1], q.emission[2]);
+                owner = (uint32_t)q.index + 1u;
+            } else {
+                sample_material(V, x, &albedo, &emission);
+            }
             float3 ind = f3(0.f, 0.f, 0.f);
             if (P.k_bounce != 0.f)
                 ind = interpolate_irradiance(P.gdims, P.gorigin, P.gspacing, P.prev_irr, P.prev_valid, x, nr);
@@ -245,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant
                 if (g) gate |= 1u << l;
             }
             P.ray_n[k] = make_float4(nr.x, nr.y, nr.z, 0.f);
-            P.ray_alb[k] = make_float4(albedo.x, albedo.y, albedo.z, 0.f);
+            P.ray_alb[k] = make_float4(albedo.x, albedo.y, albedo.z, __uint_as_float(owner));
             P.ray_base[k] = make_float4(emission.x + albedo.x * P.k_bounce * ind.x,
                                         emission.y + albedo.y * P.k_bounce * ind.y,
                                         emission.z + albedo.z * P.k_bounce * ind.z, 0.f);
@@ -393,7 +422,7 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(const __grid_constan
             rec.steps = (uint16_t)(es >> 8);
             rec.event = (uint8_t)(es & 0xffu);
             rec.reserved0 = 0;
-            rec.reserved1 = 0;
+            rec.material_owner = is_miss((int)(es & 0xffu)) ? 0u : __float_as_uint(P.ray_alb[k].w);
             P.records[k] = rec;
         }
     } else if (P.records) {
@@ -539,8 +568,8 @@ struct DeviceSetup {
     bool done = false;
     cudaError_t err = cudaSuccess;
     int sms = 0;
-    int occ_primary[2] = {};  // [float, __half]
-    int occ_shadow[2] = {};
+    int occ_primary[3] = {};  // [float, __half, Analytic]
+    int occ_shadow[3] = {};
 };
 
 namespace {
@@ -550,7 +579,7 @@ std::mutex g_setup_mutex;
 DeviceSetup g_setup[kMaxDevices];
 
 template <typename T>
-constexpr int type_slot() { return std::is_same<T, float>::value ? 0 : 1; }
+constexpr int type_slot() { return std::is_same<T, float>::value ? 0 : (std::is_same<T, __half>::value ? 1 : 2); }
 
 int occupancy(const void* kernel) {
     int occ = 0;
@@ -573,6 +602,8 @@ cudaError_t prepare_update_kernels(const DeviceSetup** out) {
         s.occ_primary[1] = occupancy((const void*)primary_kernel<__half>);
         s.occ_shadow[0] = occupancy((const void*)shadow_kernel<float>);
         s.occ_shadow[1] = occupancy((const void*)shadow_kernel<__half>);
+        s.occ_primary[2] = occupancy((const void*)primary_kernel<Analytic>);
+        s.occ_shadow[2] = occupancy((const void*)shadow_kernel<Analytic>);
         // the SIMT gathers stage [R][G] values: at most 32 KiB for the G chosen per R
         for (const void* k : {(const void*)gather_kernel<8>, (const void*)gather_kernel<4>, (const void*)gather_kernel<2>})
             if (s.err == cudaSuccess) s.err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 << 10);
@@ -644,6 +675,7 @@ cudaError_t launch_update(const UpdateParams& params, cudaStream_t stream, cudaE
     UpdateParams p = params;
     p.dirs = reinterpret_cast<float4*>(p.weights + (size_t)(p.R + 1) * kTexels);  // after the weights
     p.ray_val = p.ray_n;  // the gather's values replace the normals, dead after the shadow stage
+    if (p.vol.dtype == kAnalytic) return launch_stages<Analytic>(p, stream, stage_events);
     return p.vol.dtype == SDFDDGI_F16 ? launch_stages<__half>(p, stream, stage_events)
                                       : launch_stages<float>(p, stream, stage_events);
 }

@@ -76,7 +76,13 @@ def make_cascade(c: W.Cascade, seed=None) -> list:
 
 
 # ------------------------------------------------------------------------- oracle side
-def oracle_scene(w: Workload) -> O.OracleScene:
+def oracle_scene(w: Workload, analytic: bool = False) -> O.OracleScene:
+    """The oracle's scene: the baked volume, or (analytic) the primitives themselves over the
+    same box, with the voxel size as the unit."""
+    if analytic:
+        t, prm = w.scene.arrays()
+        return O.OracleScene.analytic(t, prm, w.scene.albedo, w.scene.emission, w.baked.origin,
+                                      w.preset.sdf_dims, w.baked.h)
     return O.OracleScene(w.baked.sdf, w.baked.h, w.baked.origin, w.baked.material)
 
 
@@ -93,6 +99,7 @@ def force_from_records(rec: np.ndarray) -> np.ndarray:
     f["steps"] = rec["steps"].astype(np.int32)
     f["lit_mask"] = rec["lit_mask"]
     f["t"] = rec["t"]
+    f["owner"] = rec["material_owner"].astype(np.int32)
     return f
 
 
@@ -143,7 +150,8 @@ class GpuVolume:
     """A scene + probe volume in the CUDA library, built from a Workload. With `scene`, the
     volume is made over that existing library scene (not owned) instead of a new one."""
 
-    def __init__(self, w: Workload, seed: int = 0, flags: int = 0, scene=None, volume_id: int = 0):
+    def __init__(self, w: Workload, seed: int = 0, flags: int = 0, scene=None, volume_id: int = 0,
+                 analytic: bool = False, cluster_size: int = 8):
         import torch
         import paper_2007_14394_b300 as S
         self.S, self.torch, self.w = S, torch, w
@@ -151,7 +159,14 @@ class GpuVolume:
         self.own_scene = scene is None
         if scene is None:
             scene = S.create_scene()
-            S.upload_sdf(scene, w.baked.sdf, w.baked.h, w.baked.origin, material=w.baked.material)
+            if analytic:  # the primitives themselves over the baked volume's box, unit = voxel size
+                t, prm = w.scene.arrays()
+                lo = np.asarray(w.baked.origin, dtype=np.float64)
+                hi = lo + np.asarray(w.preset.sdf_dims) * w.baked.h
+                S.upload_primitives(scene, t, prm, w.scene.albedo, w.scene.emission, lo, hi, w.baked.h,
+                                    cluster_size)
+            else:
+                S.upload_sdf(scene, w.baked.sdf, w.baked.h, w.baked.origin, material=w.baked.material)
             S.set_lights(scene, w.lights, w.sky)
         self.scene = scene
         self.desc = S.make_desc(p["probe_dims"], p["rays"], p["probe_origin"], p["probe_spacing"], p["max_steps"],
