@@ -495,6 +495,102 @@ def run_batch(args, rank, world, local_rank):
     return line
 
 
+ANALYTIC = {"open256_analytic": "open256", "room64_analytic": "room64"}
+
+
+def run_analytic(args, rank, world, local_rank):
+    """The preset's scene as analytic SDF primitives (Sec. 3.1) instead of a voxel volume: the
+    update with the paper's cluster culling (8 primitives per cluster, queries along a trace
+    bounded by twice the last distance), against the same update with culling off (one cluster:
+    the plain loop over all primitives, the paper's baseline) and against the voxel volume."""
+    import torch
+    import paper_2007_14394_b300 as S
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pr = W.PRESETS[ANALYTIC[args.workload]]
+    scene, baked, states = build_inputs(pr)
+    P, R = pr.n_probes, pr.rays
+    n_active = int((states["flags"] & 1).sum())
+    rays_per_step = n_active * R
+    t, prm = scene.arrays()
+    hi = np.asarray(pr.sdf_dims, dtype=np.float64) * pr.h
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    states_dev = torch.from_numpy(states.view(np.uint8).copy()).to(dev)
+    desc = S.make_desc(pr.probe_dims, R, pr.probe_origin, pr.probe_spacing, pr.max_steps, pr.depth_exponent,
+                       pr.eps_vox, pr.tmax_vox, pr.hysteresis, pr.k_bounce, pr.bias_vox, seed=pr.seed)
+
+    def measure(setup, steps, with_stages=False, with_clocks=False):
+        sc = S.create_scene()
+        setup(sc)
+        S.set_lights(sc, scene.lights, scene.sky)
+        vol = S.create_volume(desc, sc)
+        for k in range(args.warmup):
+            S.update_probes(vol, k, states=states_dev, stream=stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        stage_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(steps)]
+        for evs in stage_ev:
+            for e in evs:
+                e.record(stream)
+        torch.cuda.synchronize()
+        clocks = Clocks(local_rank) if with_clocks else None
+        for k in range(steps):
+            flush.fill_(float(k))
+            if with_stages:
+                S.set_stage_events(vol, stage_ev[k])
+            ev[k][0].record(stream)
+            S.update_probes(vol, args.warmup + k, states=states_dev, stream=stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        S.set_stage_events(vol, [])
+        ms = [a.elapsed_time(b) for a, b in ev]
+        stages = None
+        if with_stages:
+            stages = {name: sum(e[i].elapsed_time(e[i + 1]) for e in stage_ev) / steps for i, name in enumerate(S.STAGES)}
+        assert S.volume_status(vol) == 0
+        S.destroy_volume(vol)
+        S.destroy_scene(sc)
+        return ms, stages, clk
+
+    def prims(cluster_size):
+        return lambda sc: S.upload_primitives(sc, t, prm, scene.albedo, scene.emission, (0.0, 0.0, 0.0), hi, pr.h,
+                                              cluster_size)
+
+    ms_c, stages, clk = measure(prims(8), args.steps, with_stages=True, with_clocks=True)
+    ms_b, _, _ = measure(prims(0), max(3, args.steps // 4))
+    ms_v, _, _ = measure(lambda sc: S.upload_sdf(sc, baked.sdf, baked.h, baked.origin, material=baked.material),
+                         max(3, args.steps // 4))
+    ms = float(np.mean(ms_c))
+    if world > 1:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    dominant = max(("primary", "prep", "shadow"), key=lambda n: stages[n])
+    line = {
+        "metric": METRIC, "value": world * rays_per_step / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scene of analytic primitives)",
+        "config": dict(workload_config(pr, rays_per_step), workload=f"{args.workload}: the {pr.name} scene as "
+                       f"{len(t)} analytic primitives, clusters of 8", primitives=len(t)),
+        "gpu_launches": KERNELS_PER_UPDATE * args.steps,
+        "clusters": {"ms_per_update": ms, "brute_force_ms_per_update": float(np.mean(ms_b)),
+                     "speedup": float(np.mean(ms_b)) / ms,
+                     "note": "culling on (8 primitives per cluster, traces bounded by twice the last distance) "
+                             "vs one cluster holding every primitive (the plain loop)"},
+        "voxel_ms_per_update": float(np.mean(ms_v)),
+        "stages_ms": stages,
+        "roofline": {"kernel": dominant, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+                     "traffic": None, "note": "primitive queries run from L1 (the primitives take a few KiB); "
+                                              "no byte or flop model is reported for them"},
+        "e2e": None,
+        "clocks": clk,
+    }
+    return line
+
+
 LEARNED = "learned32"
 DENOISER_FLOPS_PER_PROBE = 2 * 36 * (9 * 35 * 64 + 9 * 64 * 48 + 9 * 48 * 3)  # 3 convs over 36 interior texels
 
@@ -707,7 +803,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.PRESETS) + sorted(W.CASCADES) + [LEARNED])
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=sorted(W.PRESETS) + sorted(W.CASCADES) + [LEARNED] + sorted(ANALYTIC))
     ap.add_argument("--train-steps", type=int, default=6000, help="training steps of the learned32 workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
@@ -719,7 +816,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
-        if args.workload in W.CASCADES or args.workload == LEARNED:
+        if args.workload in W.CASCADES or args.workload == LEARNED or args.workload in ANALYTIC:
             ap.error("the reference arm times single-volume workloads")
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
@@ -729,7 +826,8 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    run = run_batch if args.workload in W.CASCADES else (run_learned if args.workload == LEARNED else run_ours)
+    run = (run_batch if args.workload in W.CASCADES else run_learned if args.workload == LEARNED
+           else run_analytic if args.workload in ANALYTIC else run_ours)
     line = run(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(line), flush=True)
