@@ -80,7 +80,7 @@ int alloc_scratch(sdfddgi_volume* v) {
     if (!rc) rc = alloc((void**)&v->ray_base, n * sizeof(float4));
     if (!rc) rc = alloc((void**)&v->ray_lit, n * sizeof(uint32_t));
     if (!rc) rc = alloc((void**)&v->ray_ssteps, n * sizeof(uint32_t));
-    if (!rc) rc = alloc((void**)&v->counters, 4 * sizeof(uint32_t));
+    if (!rc) rc = alloc((void**)&v->counters, kCounterWords * sizeof(uint32_t));
     if (!rc) rc = alloc((void**)&v->weights, weights_bytes(v->desc.rays_per_probe));
     if (!rc) rc = alloc(&v->wimage, wimage_bytes(v->desc.rays_per_probe));
     return rc;
@@ -327,7 +327,7 @@ SDFDDGI_API int sdfddgi_create_volume(const sdfddgi_volume_desc* d, sdfddgi_scen
     rc = sdfddgi_reset(v, nullptr);
     if (!rc) {
         cudaError_t e = prepare_update_kernels();  // so that later updates can be captured
-        if (e == cudaSuccess) e = cudaMemset(v->counters, 0, 4 * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMemset(v->counters, 0, kCounterWords * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
         if (e != cudaSuccess) rc = fail(SDFDDGI_ERR_CUDA, "create_volume: %s", cudaGetErrorString(e));
     }
@@ -575,8 +575,8 @@ SDFDDGI_API int sdfddgi_volume_status(sdfddgi_volume* v, uint32_t* flags) {
     if (!v) return fail(SDFDDGI_ERR_INVALID_ARG, "volume_status: volume is NULL");
     uint32_t f = 0;
     CUDA_TRY(cudaDeviceSynchronize());
-    CUDA_TRY(cudaMemcpy(&f, v->counters + 3, sizeof f, cudaMemcpyDeviceToHost));
-    CUDA_TRY(cudaMemset(v->counters + 3, 0, sizeof f));
+    CUDA_TRY(cudaMemcpy(&f, v->counters + kFailWord, sizeof f, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(v->counters + kFailWord, 0, sizeof f));
     if (flags) *flags = f;
     if (f & 2u) return fail(SDFDDGI_ERR_TIMEOUT, "volume_status: a bounded wait of the tensor-core gather gave up");
     return SDFDDGI_OK;

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
     const int n_chunks = P.R / kChunk;
 
     // a launch in which a CTA already gave up does no further work (decided once per CTA)
-    if (tid == 0) s_fail = (int)(*reinterpret_cast<const volatile uint32_t*>(&P.counters[3]) & 2u);
+    if (tid == 0) s_fail = (int)(*reinterpret_cast<const volatile uint32_t*>(&P.counters[kFailWord]) & 2u);
     __syncthreads();
     if (s_fail) return;
 
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
     // ---- K loop over 16-ray chunks, two stages (88 KiB: two CTAs per SM)
     for (int c = 0; c < n_chunks; ++c) {
         const int s = c & 1;
-        if (c >= 2 && !mbar_wait(&bar_mma[s], ((c - 2) >> 1) & 1, &P.counters[3])) s_fail = 1;  // stage s free again
+        if (c >= 2 && !mbar_wait(&bar_mma[s], ((c - 2) >> 1) & 1, &P.counters[kFailWord])) s_fail = 1;  // stage s free again
         __syncthreads();
         if (s_fail) break;
         if (tid == 0) bulk_copy_g2s(sA[s], reinterpret_cast<const unsigned char*>(P.wimage) + (size_t)c * kABytes,
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
-        if (!mbar_wait(&bar_load[s], (c >> 1) & 1, &P.counters[3])) s_fail = 1;
+        if (!mbar_wait(&bar_load[s], (c >> 1) & 1, &P.counters[kFailWord])) s_fail = 1;
         __syncthreads();
         if (s_fail) break;
         if (tid == 0) {
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
     // ---- all MMAs complete
     if (!s_fail) {
         for (int c = max(0, n_chunks - 2); c < n_chunks; ++c)
-            if (!mbar_wait(&bar_mma[c & 1], (c >> 1) & 1, &P.counters[3])) s_fail = 1;
+            if (!mbar_wait(&bar_mma[c & 1], (c >> 1) & 1, &P.counters[kFailWord])) s_fail = 1;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     if (s_fail) {
-        if (tid == 0) atomicOr(&P.counters[3], 2u);  // reported by the host as a timeout
+        if (tid == 0) atomicOr(&P.counters[kFailWord], 2u);  // reported by the host as a timeout
         return;
     }
 

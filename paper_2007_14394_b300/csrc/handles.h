@@ -45,7 +45,7 @@ struct sdfddgi_volume {
     float4* ray_base = nullptr;
     uint32_t* ray_lit = nullptr;
     uint32_t* ray_ssteps = nullptr;
-    uint32_t* counters = nullptr;
+    uint32_t* counters = nullptr;  // kCounterWords words (see UpdateParams)
     uint32_t* tasks = nullptr;
     size_t task_capacity = 0;
     float* weights = nullptr;  // texel weights of the frame's ray set and their column sums

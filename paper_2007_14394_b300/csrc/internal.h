@@ -107,8 +107,8 @@ struct UpdateParams {
     uint32_t* ray_ssteps;     // shadow steps
     uint32_t* tasks;          // shadow tasks (k << 5 | light)
     uint32_t task_capacity;
-    uint32_t* counters;       // [0] primary pool, [1] task count, [2] shadow pool (zeroed by each launch),
-                              // [3] failure bits, sticky: 1 task overflow, 2 a tensor-core wait gave up
+    uint32_t* counters;       // kCounterWords words: pools and counts (zeroed by each launch), then at
+                              // kFailWord the failure bits, sticky: 1 task overflow, 2 a tensor-core wait gave up
     float* weights;           // [R][kTexels] texel weights of the frame's ray set, [kTexels] column sums,
                               // then room for [R] float4 ray directions (weights_bytes(R) in all)
     float4* dirs;             // [R] the frame's ray directions (same for every probe), set by launch_update
@@ -120,6 +120,12 @@ struct UpdateParams {
 };
 
 constexpr int kTexels = kIrrTexels + kDepTexels;  // 232 gather rows: irradiance texels first
+
+// Words of UpdateParams::counters: 0 primary pool, 1 shadow-task count, 2 shadow pool;
+// words 0..kFailWord-1 are zeroed by every launch.
+constexpr int kPrimaryPool = 0, kTaskCount = 1, kShadowPool = 2;
+constexpr int kFailWord = 7;
+constexpr int kCounterWords = 8;
 
 struct SampleParams {
     int gdims[3];

@@ -112,7 +112,7 @@ SDFDDGI_API int sdfddgi_update_probes_noalloc(
                             n_rays * 4,   // ray_lit
                             n_rays * 4,   // ray_ssteps
                             n_rays * 4 * (size_t)(n_lights > 0 ? n_lights : 1),  // tasks
-                            16,           // counters
+                            kCounterWords * 4,  // counters
                             weights_bytes(R)};  // texel weights, their sums, ray directions
     size_t off[sizeof sizes / sizeof sizes[0]], total = 0;
     for (size_t k = 0; k < sizeof sizes / sizeof sizes[0]; ++k) {
@@ -203,7 +203,7 @@ SDFDDGI_API int sdfddgi_update_probes_noalloc(
     p.task_capacity = (uint32_t)(n_rays * (size_t)(n_lights > 0 ? n_lights : 1));
     p.counters = reinterpret_cast<uint32_t*>(s + off[9]);
     p.weights = reinterpret_cast<float*>(s + off[10]);
-    e = cudaMemsetAsync(p.counters, 0, 4 * sizeof(uint32_t), st);  // the scratch is shared: no sticky bits
+    e = cudaMemsetAsync(p.counters, 0, kCounterWords * sizeof(uint32_t), st);  // the scratch is shared: no sticky bits
     if (e == cudaSuccess) e = launch_update(p, st);
     if (e != cudaSuccess) return nofail(SDFDDGI_ERR_CUDA, "update_probes_noalloc: launch failed: %s", cudaGetErrorString(e));
     return SDFDDGI_OK;

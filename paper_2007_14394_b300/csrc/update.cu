@@ -208,7 +208,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) primary_kernel(const __grid_constant__ UpdateParams P) {
     const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
     trace_pool<T>(
-        P.vol, n, &P.counters[0], P.eps_w, P.max_steps, pool_batch(P),
+        P.vol, n, &P.counters[kPrimaryPool], P.eps_w, P.max_steps, pool_batch(P),
         [&](uint32_t k, TraceState& st) {
             const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
             uint32_t flags;
@@ -229,18 +229,42 @@ __global__ void __launch_bounds__(kThreads) primary_kernel(const __grid_constant
 }
 
 // ------------------------------------------------------------------ 2. hit preparation
+constexpr int kPrepRays = 2048;  // rays per hit-preparation CTA
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant__ UpdateParams P) {
+    // The CTA's rays to shade (hit, or step budget spent) are first gathered into shared
+    // memory, so that the shading below runs in full warps instead of one thread per ray
+    // with the misses idle.
+    __shared__ uint32_t s_rays[kPrepRays];
+    __shared__ int s_count;
     const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t first = blockIdx.x * (uint32_t)kPrepRays;
     const int lane = threadIdx.x & 31;
-    uint32_t gate = 0;
-    if (k < n) {
-        const uint32_t es = P.ray_es[k];
-        const int ev = (int)(es & 0xffu);
-        P.ray_lit[k] = 0;
-        P.ray_ssteps[k] = 0;
-        if (ev != kNoRay && !is_miss(ev)) {
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < kPrepRays; r += kThreads) {
+        const uint32_t k = first + (uint32_t)r;
+        bool shade = false;
+        if (k < n) {
+            const int ev = (int)(P.ray_es[k] & 0xffu);
+            shade = ev != kNoRay && !is_miss(ev);
+        }
+        const unsigned want = __ballot_sync(0xffffffffu, shade);
+        int base = 0;
+        if (lane == 0 && want) base = atomicAdd(&s_count, __popc(want));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (shade) s_rays[base + __popc(want & ((1u << lane) - 1u))] = k;
+    }
+    __syncthreads();
+    const int n_shade = s_count;
+    for (int j0 = 0; j0 < n_shade; j0 += kThreads) {
+        const int j = j0 + threadIdx.x;
+        uint32_t gate = 0, k = 0;
+        if (j < n_shade) {
+            k = s_rays[j];
+            P.ray_lit[k] = 0;
+            P.ray_ssteps[k] = 0;
             const VolumeView& V = P.vol;
             const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
             uint32_t flags;
@@ -279,38 +303,38 @@ __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant
                                         emission.y + albedo.y * P.k_bounce * ind.y,
                                         emission.z + albedo.z * P.k_bounce * ind.z, 0.f);
         }
-    }
-    // append this warp's (ray, light) pairs to the task list with one atomic
-    const int cnt = __popc(gate);
-    int incl = cnt;
+        // append this warp's (ray, light) pairs to the task list with one atomic
+        const int cnt = __popc(gate);
+        int incl = cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (total == 0) return;
-    uint32_t base = 0;
-    if (lane == 31) base = atomicAdd(&P.counters[1], (uint32_t)total);
-    base = __shfl_sync(0xffffffffu, base, 31);
-    if (base + (uint32_t)total > P.task_capacity) {  // cannot happen with capacity P*R*lights
-        if (lane == 31) atomicOr(&P.counters[3], 1u);
-        return;
-    }
-    uint32_t pos = base + (uint32_t)(incl - cnt);
-    while (gate) {
-        const int l = __ffs(gate) - 1;
-        gate &= gate - 1;
-        P.tasks[pos++] = (k << 5) | (uint32_t)l;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total == 0) continue;
+        uint32_t base = 0;
+        if (lane == 31) base = atomicAdd(&P.counters[kTaskCount], (uint32_t)total);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        if (base + (uint32_t)total > P.task_capacity) {  // cannot happen with capacity P*R*lights
+            if (lane == 31) atomicOr(&P.counters[kFailWord], 1u);
+            continue;
+        }
+        uint32_t pos = base + (uint32_t)(incl - cnt);
+        while (gate) {
+            const int l = __ffs(gate) - 1;
+            gate &= gate - 1;
+            P.tasks[pos++] = (k << 5) | (uint32_t)l;
+        }
     }
 }
 
 // ------------------------------------------------------------------ 3. shadow traces
 template <typename T>
 __global__ void __launch_bounds__(kThreads) shadow_kernel(const __grid_constant__ UpdateParams P) {
-    const uint32_t n = min(P.counters[1], P.task_capacity);
+    const uint32_t n = min(P.counters[kTaskCount], P.task_capacity);
     trace_pool<T>(
-        P.vol, n, &P.counters[2], P.eps_w, P.max_steps, pool_batch(P),
+        P.vol, n, &P.counters[kShadowPool], P.eps_w, P.max_steps, pool_batch(P),
         [&](uint32_t j, TraceState& st) {
             const uint32_t tk = P.tasks[j];
             const uint32_t k = tk >> 5;
@@ -418,7 +442,7 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(const __grid_constan
             rec.L[1] = v.y;
             rec.L[2] = v.z;
             rec.lit_mask = lit;
-            rec.shadow_steps = P.ray_ssteps[k];
+            rec.shadow_steps = is_miss((int)(es & 0xffu)) ? 0u : P.ray_ssteps[k];
             rec.steps = (uint16_t)(es >> 8);
             rec.event = (uint8_t)(es & 0xffu);
             rec.reserved0 = 0;
@@ -637,8 +661,8 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
     const int g_shadow = persistent_blocks(*setup, setup->occ_shadow[type_slot<T>()], p.sched.blocks_per_sm);
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], stream) : cudaSuccess; };
     e = mark(0);
-    // the pool counters start at zero; counters[3] (failure bits) is sticky until read
-    if (e == cudaSuccess) e = cudaMemsetAsync(p.counters, 0, 3 * sizeof(uint32_t), stream);
+    // the pools and counts start at zero; the failure bits are sticky until read
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.counters, 0, kFailWord * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return e;
     const uint32_t n = (uint32_t)p.P * (uint32_t)p.R;
     if (p.depth_exp == 50)
@@ -649,7 +673,7 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
     if ((e = mark(1)) != cudaSuccess) return e;
     primary_kernel<T><<<g_primary, kThreads, 0, stream>>>(p);
     if ((e = mark(2)) != cudaSuccess) return e;
-    prep_kernel<T><<<(n + kThreads - 1) / kThreads, kThreads, 0, stream>>>(p);
+    prep_kernel<T><<<(n + kPrepRays - 1) / kPrepRays, kThreads, 0, stream>>>(p);
     if ((e = mark(3)) != cudaSuccess) return e;
     shadow_kernel<T><<<g_shadow, kThreads, 0, stream>>>(p);
     if ((e = mark(4)) != cudaSuccess) return e;
