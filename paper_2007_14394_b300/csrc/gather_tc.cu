@@ -154,27 +154,33 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
 
-    // ---- K loop over 16-ray chunks, two stages (88 KiB: two CTAs per SM)
+    // ---- K loop over 16-ray chunks, two stages (88 KiB: two CTAs per SM). Each thread owns
+    // one (probe, ray) element of every chunk's B operand and loads the next chunk's value
+    // into a register one iteration ahead; the weight image of chunk c+1 is copied into the
+    // other stage as soon as the MMAs of chunk c-1 that read it are done. Both latencies
+    // thus overlap the current chunk's operand build and MMAs.
+    static_assert(kG * kChunk == kThreads, "one B element per thread and chunk");
+    const int g_own = tid / kChunk, k_own = tid % kChunk;
+    const bool own_live = g_own < ng;
+    const float4* own_src = P.ray_val + (size_t)(p0 + (own_live ? g_own : 0)) * P.R + k_own;
+    float4 v_next = own_live ? own_src[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+    int last_copy = -1;  // thread 0: the last chunk whose weight copy it issued
+    if (tid == 0 && n_chunks > 0) {
+        bulk_copy_g2s(sA[0], P.wimage, kABytes, &bar_load[0]);
+        last_copy = 0;
+    }
     for (int c = 0; c < n_chunks; ++c) {
         const int s = c & 1;
-        if (c >= 2 && !mbar_wait(&bar_mma[s], ((c - 2) >> 1) & 1, &P.counters[kFailWord])) s_fail = 1;  // stage s free again
-        __syncthreads();
+        const float4 v = v_next;
+        if (own_live && c + 1 < n_chunks) v_next = own_src[(size_t)(c + 1) * kChunk];
+        __syncthreads();  // the MMAs of chunk c-2 (stage s) are done: waited by thread 0 last iteration
         if (s_fail) break;
-        if (tid == 0) bulk_copy_g2s(sA[s], reinterpret_cast<const unsigned char*>(P.wimage) + (size_t)c * kABytes,
-                                    kABytes, &bar_load[s]);
-        // B: rays c*32 .. c*32+31 of the CTA's probes (tf32: split into hi + lo)
-        for (int e = tid; e < kG * kChunk; e += kThreads) {
-            const int g = e / kChunk, k = e % kChunk;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            float one = 0.f;
-            if (g < ng) {
-                v = P.ray_val[(size_t)(p0 + g) * P.R + c * kChunk + k];
-                one = 1.f;
-            }
+        {
+            const float one = own_live ? 1.f : 0.f;
             const float ch[kCh] = {v.x, v.y, v.z, v.w, v.w * v.w, one};
 #pragma unroll
             for (int q = 0; q < kCh; ++q) {
-                const uint32_t off = F::offset(g * kCh + q, k);
+                const uint32_t off = F::offset(g_own * kCh + q, k_own);
                 if constexpr (BF16) {
                     put<true>(sB[s], off, ch[q]);
                 } else {
@@ -208,7 +214,22 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
                 }
             }
             mma_commit(&bar_mma[s]);
+            // the weights of chunk c+1 into stage s^1, free once the MMAs of chunk c-1 are done
+            if (c + 1 < n_chunks) {
+                if (c >= 1 && !mbar_wait(&bar_mma[s ^ 1], ((c - 1) >> 1) & 1, &P.counters[kFailWord])) s_fail = 1;
+                if (!s_fail) {
+                    bulk_copy_g2s(sA[s ^ 1], reinterpret_cast<const unsigned char*>(P.wimage) + (size_t)(c + 1) * kABytes,
+                                  kABytes, &bar_load[s ^ 1]);
+                    last_copy = c + 1;
+                }
+            }
         }
+    }
+    // after a failure, no copy of this CTA may still be writing its shared memory (bounded,
+    // and not cut short by the launch's failure bit)
+    if (s_fail && tid == 0 && last_copy >= 0) {
+        const uint32_t no_abort = 0;
+        mbar_wait(&bar_load[last_copy & 1], (last_copy >> 1) & 1, &no_abort);
     }
     // ---- all MMAs complete
     if (!s_fail) {
