@@ -421,40 +421,71 @@ __device__ __forceinline__ float4 ray_value(const UpdateParams& P, size_t k, int
                        fmaf(a.z * inv_pi, direct.z, b.z), fminf(t, P.tmax_w));
 }
 
-// One thread per ray: the ray's value for the gather -- radiance and clamped distance,
-// zero for rays of inactive probes -- written over the ray's normal, which no later stage
-// reads; and the ray's record when records were asked for.
+// The ray's record, when records were asked for.
+__device__ __forceinline__ void write_record(const UpdateParams& P, uint32_t k, uint32_t es, float4 v, uint32_t lit) {
+    const int ev = (int)(es & 0xffu);
+    sdfddgi_ray_record rec = {};
+    rec.event = (uint8_t)ev;
+    if (ev != kNoRay) {
+        rec.t = P.ray_t[k];
+        rec.L[0] = v.x;
+        rec.L[1] = v.y;
+        rec.L[2] = v.z;
+        rec.lit_mask = lit;
+        rec.shadow_steps = is_miss(ev) ? 0u : P.ray_ssteps[k];
+        rec.steps = (uint16_t)(es >> 8);
+        rec.material_owner = is_miss(ev) ? 0u : __float_as_uint(P.ray_alb[k].w);
+    }
+    P.records[k] = rec;
+}
+
+constexpr int kFinalRays = 2048;  // rays per finalize CTA
+
+// The rays' values for the gather -- radiance and clamped distance, zero for rays of
+// inactive probes -- written over the rays' normals, which no later stage reads; and the
+// rays' records when records were asked for. A CTA takes 2048 rays: misses and rays of
+// inactive probes are written directly, the rays to shade are gathered in shared memory
+// and shaded in full warps (the light loop would otherwise leave the misses' lanes idle).
 __global__ void __launch_bounds__(kThreads) finalize_kernel(const __grid_constant__ UpdateParams P) {
+    __shared__ uint32_t s_rays[kFinalRays];
+    __shared__ int s_count;
     const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
-    const uint32_t es = P.ray_es[k];
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if ((es & 0xffu) != kNoRay) {
+    const uint32_t first = blockIdx.x * (uint32_t)kFinalRays;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < kFinalRays; r += kThreads) {
+        const uint32_t k = first + (uint32_t)r;
+        bool shade = false;
+        if (k < n) {
+            const uint32_t es = P.ray_es[k];
+            const int ev = (int)(es & 0xffu);
+            if (ev == kNoRay || is_miss(ev)) {
+                const float4 v = ev == kNoRay ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                              : make_float4(P.sky[0], P.sky[1], P.sky[2], P.tmax_w);
+                P.ray_val[k] = v;
+                if (P.records) write_record(P, k, es, v, 0u);
+            } else {
+                shade = true;
+            }
+        }
+        const unsigned want = __ballot_sync(0xffffffffu, shade);
+        int base = 0;
+        if (lane == 0 && want) base = atomicAdd(&s_count, __popc(want));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (shade) s_rays[base + __popc(want & ((1u << lane) - 1u))] = k;
+    }
+    __syncthreads();
+    const int n_shade = s_count;
+    for (int j = threadIdx.x; j < n_shade; j += kThreads) {
+        const uint32_t k = s_rays[j];
+        const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
         uint32_t flags, lit;
         const float3 o = probe_origin(P, p, &flags);
-        v = ray_value(P, k, i, o, ray_dir(P, i), &lit);
-        if (P.records) {
-            sdfddgi_ray_record rec;
-            rec.t = P.ray_t[k];
-            rec.L[0] = v.x;
-            rec.L[1] = v.y;
-            rec.L[2] = v.z;
-            rec.lit_mask = lit;
-            rec.shadow_steps = is_miss((int)(es & 0xffu)) ? 0u : P.ray_ssteps[k];
-            rec.steps = (uint16_t)(es >> 8);
-            rec.event = (uint8_t)(es & 0xffu);
-            rec.reserved0 = 0;
-            rec.material_owner = is_miss((int)(es & 0xffu)) ? 0u : __float_as_uint(P.ray_alb[k].w);
-            P.records[k] = rec;
-        }
-    } else if (P.records) {
-        sdfddgi_ray_record rec = {};
-        rec.event = kNoRay;
-        P.records[k] = rec;
+        const float4 v = ray_value(P, k, i, o, ray_dir(P, i), &lit);
+        P.ray_val[k] = v;
+        if (P.records) write_record(P, k, P.ray_es[k], v, lit);
     }
-    P.ray_val[k] = v;
 }
 
 // G probes per CTA. Stage a: the rays' values of the G probes go to shared memory (one
@@ -677,7 +708,7 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
     if ((e = mark(3)) != cudaSuccess) return e;
     shadow_kernel<T><<<g_shadow, kThreads, 0, stream>>>(p);
     if ((e = mark(4)) != cudaSuccess) return e;
-    finalize_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, stream>>>(p);
+    finalize_kernel<<<(n + kFinalRays - 1) / kFinalRays, kThreads, 0, stream>>>(p);
     if (gather_tc_supported(p) && p.sched.gather != 2) {
         e = launch_gather_tc(p, stream);
         if (e != cudaSuccess) return e;
