@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA[2] = {smem, smem + kABytes};
     unsigned char* sB[2] = {smem + 2 * kABytes, smem + 2 * kABytes + kBBytes};
-    __shared__ __align__(8) uint64_t bar_load[2], bar_mma[2];
+    __shared__ __align__(8) uint64_t bar_load[2], bar_mma[2], bar_prev;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
     __shared__ float s_hyst[kG];
@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
         mbar_init(&bar_load[1], 1);
         mbar_init(&bar_mma[0], 1);
         mbar_init(&bar_mma[1], 1);
+        mbar_init(&bar_prev, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (tid < kG) {
@@ -240,9 +241,18 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    // ---- epilogue: warp w reads tensor-memory lanes 32*(w%4).. of tile w/4; thread = texel row
+    // ---- epilogue. The CTA's probes are consecutive, so their previous maps are two contiguous
+    // blocks; bulk copies bring them into the staging buffers (the free operand stages) while
+    // the accumulators come out of tensor memory, and each texel is blended in place.
     float4* s_irr = reinterpret_cast<float4*>(smem);                       // [kG][64]   (stages reused)
     float2* s_dep = reinterpret_cast<float2*>(smem + kG * kIrrT * kIrrT * 16);  // [kG][256]
+    const uint32_t prev_bytes = (uint32_t)ng * (kIrrT * kIrrT * 16 + kDepT * kDepT * 8);
+    const bool prev_issued = !s_fail;  // thread 0 issues the copies exactly when this holds
+    if (prev_issued && tid == 0) {
+        bulk_expect(&bar_prev, prev_bytes);
+        bulk_copy(s_irr, P.prev_irr + (size_t)p0 * (kIrrT * kIrrT), (uint32_t)ng * kIrrT * kIrrT * 16, &bar_prev);
+        bulk_copy(s_dep, P.prev_depth + (size_t)p0 * (kDepT * kDepT), (uint32_t)ng * kDepT * kDepT * 8, &bar_prev);
+    }
     if (!s_fail) {
         const int t = warp >> 2, row = (warp & 3) * 32 + lane, j = t * 128 + row;
         const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + t * kN;
@@ -252,7 +262,8 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
             tmem_ld16(lane_addr + half * 48, acc);
             tmem_ld16(lane_addr + half * 48 + 16, acc + 16);
             tmem_ld16(lane_addr + half * 48 + 32, acc + 32);
-            if (j >= kTexels) continue;
+            if (half == 0 && !mbar_wait(&bar_prev, 0, &P.counters[kFailWord])) s_fail = 1;
+            if (j >= kTexels || s_fail) continue;
 #pragma unroll
             for (int gg = 0; gg < 8; ++gg) {
                 const int g = half * 8 + gg;
@@ -263,7 +274,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
                 const float hyst = s_hyst[g], keep = 1.f - hyst, inv = live ? 1.f / a[5] : 0.f;
                 if (j < kIrrTexels) {
                     const int k = (j / kIrrN + 1) * kIrrT + (j % kIrrN + 1);
-                    float4 out = __ldg(P.prev_irr + p * (kIrrT * kIrrT) + k);
+                    float4 out = s_irr[g * kIrrT * kIrrT + k];  // last frame's texel
                     if (live) {
                         out.x = fmaf(hyst, out.x, keep * (a[0] * inv));
                         out.y = fmaf(hyst, out.y, keep * (a[1] * inv));
@@ -273,7 +284,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
                     s_irr[g * kIrrT * kIrrT + k] = out;
                 } else {
                     const int jj = j - kIrrTexels, k = (jj / kDepN + 1) * kDepT + (jj % kDepN + 1);
-                    float2 out = __ldg(P.prev_depth + p * (kDepT * kDepT) + k);
+                    float2 out = s_dep[g * kDepT * kDepT + k];  // last frame's texel
                     if (live) {
                         out.x = fmaf(hyst, out.x, keep * (a[3] * inv));
                         out.y = fmaf(hyst, out.y, keep * (a[4] * inv));
@@ -288,27 +299,29 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     if (s_fail) {
-        if (tid == 0) atomicOr(&P.counters[kFailWord], 2u);  // reported by the host as a timeout
+        if (tid == 0) {
+            // the copies of last frame's maps may still be in flight (bounded, not cut short)
+            const uint32_t no_abort = 0;
+            if (prev_issued) mbar_wait(&bar_prev, 0, &no_abort);
+            atomicOr(&P.counters[kFailWord], 2u);  // reported by the host as a timeout
+        }
         return;
     }
 
-    // ---- borders (inactive probes: a copy of the old map), then contiguous stores
+    // ---- borders of active probes (an inactive probe's staged map is its old map), then
+    // contiguous stores
     for (int e = tid; e < ng * kIrrT * kIrrT; e += kThreads) {
         const int g = e / (kIrrT * kIrrT), k = e % (kIrrT * kIrrT);
         const int y = k / kIrrT, x = k % kIrrT;
         const int2 sc = border_source(y, x, kIrrN);
-        if (!(s_flags[g] & SDFDDGI_PROBE_ACTIVE))
-            s_irr[e] = __ldg(P.prev_irr + (size_t)(p0 + g) * (kIrrT * kIrrT) + k);
-        else if (sc.x != y || sc.y != x)
+        if ((s_flags[g] & SDFDDGI_PROBE_ACTIVE) && (sc.x != y || sc.y != x))
             s_irr[e] = s_irr[g * kIrrT * kIrrT + sc.x * kIrrT + sc.y];
     }
     for (int e = tid; e < ng * kDepT * kDepT; e += kThreads) {
         const int g = e / (kDepT * kDepT), k = e % (kDepT * kDepT);
         const int y = k / kDepT, x = k % kDepT;
         const int2 sc = border_source(y, x, kDepN);
-        if (!(s_flags[g] & SDFDDGI_PROBE_ACTIVE))
-            s_dep[e] = __ldg(P.prev_depth + (size_t)(p0 + g) * (kDepT * kDepT) + k);
-        else if (sc.x != y || sc.y != x)
+        if ((s_flags[g] & SDFDDGI_PROBE_ACTIVE) && (sc.x != y || sc.y != x))
             s_dep[e] = s_dep[g * kDepT * kDepT + sc.x * kDepT + sc.y];
     }
     __syncthreads();
