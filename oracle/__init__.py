@@ -111,6 +111,12 @@ def _load():
                                                              C.c_void_p, C.c_double, dp, dp, dp, dp, dp]
             lib.oracle_analytic_sdf.argtypes = [C.POINTER(Volume), dp, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
             lib.oracle_analytic_sdf.restype = C.c_double
+            lib.oracle_mvc.argtypes = [dp, C.c_int32, C.c_void_p, C.c_int32, dp, dp]
+            lib.oracle_mvc.restype = C.c_int32
+            lib.oracle_cascade_weight.argtypes = [C.POINTER(Grid), dp]
+            lib.oracle_cascade_weight.restype = C.c_double
+            lib.oracle_sample_irradiance_cascade.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, dp, dp,
+                                                             dp, C.POINTER(C.c_double), C.POINTER(C.c_int32)]
             lib.oracle_relocate.argtypes = [C.POINTER(Volume), C.POINTER(Grid), C.POINTER(Relocation), C.c_void_p,
                                             dp, C.c_void_p, C.c_void_p, C.c_void_p]
             _lib = lib
@@ -352,3 +358,33 @@ def analytic_sdf(scene: "OracleScene", p):
     sec = C.c_double()
     d = _load().oracle_analytic_sdf(C.byref(scene.vol), _dp(_vec(p)), C.byref(own), C.byref(sec))
     return d, own.value, sec.value
+
+
+# ----------------------------------------------------------------- cascade blending
+def mvc(verts, tris, x):
+    """Mean value coordinates of x over a closed triangle mesh; returns (lambda, on_mesh)."""
+    v = np.ascontiguousarray(np.asarray(verts, dtype=np.float64).reshape(-1, 3))
+    t = np.ascontiguousarray(np.asarray(tris, dtype=np.int32).reshape(-1, 3))
+    lam = np.zeros(len(v))
+    on = _load().oracle_mvc(_dp(v), len(v), t.ctypes.data, len(t), _dp(_vec(x)), _dp(lam))
+    return lam, bool(on)
+
+
+def cascade_weight(grid: Grid, x) -> float:
+    return _load().oracle_cascade_weight(C.byref(grid), _dp(_vec(x)))
+
+
+def sample_irradiance_cascade(grids, irrs, valids, x, nrm):
+    """Cascade interpolation (Sec. 3.5) over grids[0] (finest) .. grids[-1]; returns (rgb, w, level)."""
+    n = len(grids)
+    irrs = [np.ascontiguousarray(a, dtype=np.float64) for a in irrs]
+    valids = [np.ascontiguousarray(a, dtype=np.uint8) for a in valids]
+    gp = (C.c_void_p * n)(*[C.cast(C.pointer(g), C.c_void_p) for g in grids])
+    ip = (C.c_void_p * n)(*[a.ctypes.data for a in irrs])
+    vp = (C.c_void_p * n)(*[a.ctypes.data for a in valids])
+    out = np.zeros(3)
+    w = C.c_double()
+    lvl = C.c_int32()
+    _load().oracle_sample_irradiance_cascade(gp, ip, vp, n, _dp(_vec(x)), _dp(_vec(nrm)), _dp(out), C.byref(w),
+                                             C.byref(lvl))
+    return out, w.value, lvl.value

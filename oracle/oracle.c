@@ -856,3 +856,154 @@ void oracle_relocate(const or_volume* vol, const or_grid* g, const or_relocation
         }
     }
 }
+
+/* ------------------------------------------------ cascade blending (Sec. 3.5) */
+
+static void cross3(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+int32_t oracle_mvc(const double* verts, int32_t nv, const int32_t* tris, int32_t nt, const double x[3],
+                   double* lambda) {
+    const double tiny = 1e-12;
+    double* d = (double*)malloc(sizeof(double) * (size_t)nv);
+    double* u = (double*)malloc(sizeof(double) * 3 * (size_t)nv);
+    for (int32_t j = 0; j < nv; ++j) {
+        lambda[j] = 0.0;
+        double v[3] = {verts[3 * j] - x[0], verts[3 * j + 1] - x[1], verts[3 * j + 2] - x[2]};
+        d[j] = sqrt(dot3(v, v));
+        if (d[j] < tiny) { /* x at a vertex */
+            lambda[j] = 1.0;
+            free(d);
+            free(u);
+            return 1;
+        }
+        for (int a = 0; a < 3; ++a) u[3 * j + a] = v[a] / d[j];
+    }
+    for (int32_t t = 0; t < nt; ++t) {
+        const int32_t id[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
+        double th[3], c[3], sn[3];
+        for (int i = 0; i < 3; ++i) { /* angle at x between the two other corners */
+            const double* a = &u[3 * id[(i + 1) % 3]];
+            const double* b = &u[3 * id[(i + 2) % 3]];
+            double e[3] = {a[0] - b[0], a[1] - b[1], a[2] - b[2]};
+            th[i] = 2.0 * asin(fmin(1.0, sqrt(dot3(e, e)) / 2.0));
+        }
+        const double hh = 0.5 * (th[0] + th[1] + th[2]);
+        if (M_PI - hh < tiny) { /* x on this triangle: barycentric coordinates */
+            double w[3], sw = 0.0;
+            for (int i = 0; i < 3; ++i) {
+                w[i] = sin(th[i]) * d[id[(i + 2) % 3]] * d[id[(i + 1) % 3]];
+                sw += w[i];
+            }
+            for (int32_t j = 0; j < nv; ++j) lambda[j] = 0.0;
+            for (int i = 0; i < 3; ++i) lambda[id[i]] += w[i] / sw;
+            free(d);
+            free(u);
+            return 1;
+        }
+        double cr[3];
+        cross3(&u[3 * id[0]], &u[3 * id[1]], cr);
+        const double det = dot3(cr, &u[3 * id[2]]);
+        const double sgn = det >= 0.0 ? 1.0 : -1.0;
+        int skip = 0;
+        for (int i = 0; i < 3; ++i) {
+            c[i] = 2.0 * sin(hh) * sin(hh - th[i]) / (sin(th[(i + 1) % 3]) * sin(th[(i + 2) % 3])) - 1.0;
+            sn[i] = sgn * sqrt(fmax(0.0, 1.0 - c[i] * c[i]));
+            if (fabs(sn[i]) <= tiny) skip = 1; /* x in the triangle's plane, outside it */
+        }
+        if (skip) continue;
+        for (int i = 0; i < 3; ++i) {
+            const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+            lambda[id[i]] += (th[i] - c[i1] * th[i2] - c[i2] * th[i1]) / (d[id[i]] * sin(th[i1]) * sn[i2]);
+        }
+    }
+    double sw = 0.0;
+    for (int32_t j = 0; j < nv; ++j) sw += lambda[j];
+    for (int32_t j = 0; j < nv; ++j) lambda[j] /= sw;
+    free(d);
+    free(u);
+    return 0;
+}
+
+/* The 12 triangles of an axis-aligned box, counter-clockwise seen from outside (corner c has
+ * coordinates lo/hi by the bits x = c&1, y = c&2, z = c&4), or reversed. */
+static void box_triangles(int base, int reversed, int32_t* tris) {
+    static const int32_t faces[6][4] = {{0, 4, 6, 2}, {1, 3, 7, 5}, {0, 1, 5, 4},
+                                        {2, 6, 7, 3}, {0, 2, 3, 1}, {4, 5, 7, 6}};
+    for (int f = 0; f < 6; ++f) {
+        const int32_t* q = faces[f];
+        int32_t t0[3] = {q[0], q[1], q[2]}, t1[3] = {q[0], q[2], q[3]};
+        for (int k = 0; k < 3; ++k) {
+            tris[6 * f + k] = base + (reversed ? t0[2 - k] : t0[k]);
+            tris[6 * f + 3 + k] = base + (reversed ? t1[2 - k] : t1[k]);
+        }
+    }
+}
+
+static void box_corners(const double lo[3], const double hi[3], double* v) {
+    for (int c = 0; c < 8; ++c) {
+        v[3 * c] = (c & 1) ? hi[0] : lo[0];
+        v[3 * c + 1] = (c & 2) ? hi[1] : lo[1];
+        v[3 * c + 2] = (c & 4) ? hi[2] : lo[2];
+    }
+}
+
+static void probe_box(const or_grid* g, double lo[3], double hi[3]) {
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = g->origin[a];
+        hi[a] = g->origin[a] + (g->dims[a] - 1) * g->spacing[a];
+    }
+}
+
+double oracle_cascade_weight(const or_grid* g, const double x[3]) {
+    double lo[3], hi[3], ilo[3], ihi[3];
+    probe_box(g, lo, hi);
+    for (int a = 0; a < 3; ++a) {
+        if (g->dims[a] < 3) return 1.0; /* no inner box: no transition */
+        ilo[a] = lo[a] + g->spacing[a];
+        ihi[a] = hi[a] - g->spacing[a];
+    }
+    int inside_inner = 1;
+    for (int a = 0; a < 3; ++a)
+        if (x[a] < ilo[a] || x[a] > ihi[a]) inside_inner = 0;
+    if (inside_inner) return 1.0;
+    double v[48];
+    int32_t tris[72];
+    box_corners(lo, hi, v);
+    box_corners(ilo, ihi, v + 24);
+    box_triangles(0, 0, tris);
+    box_triangles(8, 1, tris + 36);
+    double lam[16];
+    oracle_mvc(v, 16, tris, 24, x, lam);
+    double w = 0.0;
+    for (int j = 8; j < 16; ++j) w += lam[j];
+    return clampd(w, 0.0, 1.0);
+}
+
+void oracle_sample_irradiance_cascade(const or_grid* const* grids, const double* const* irr,
+                                      const uint8_t* const* valid, int32_t n, const double x[3],
+                                      const double nrm[3], double out[3], double* w_out, int32_t* level_out) {
+    int32_t k = n - 1;
+    for (int32_t i = 0; i < n; ++i) {
+        double lo[3], hi[3];
+        probe_box(grids[i], lo, hi);
+        if (x[0] >= lo[0] && x[0] <= hi[0] && x[1] >= lo[1] && x[1] <= hi[1] && x[2] >= lo[2] && x[2] <= hi[2]) {
+            k = i;
+            break;
+        }
+    }
+    double w = k < n - 1 ? oracle_cascade_weight(grids[k], x) : 1.0;
+    double ek[3];
+    oracle_sample_irradiance(grids[k], irr[k], valid[k], x, nrm, ek);
+    for (int a = 0; a < 3; ++a) out[a] = ek[a];
+    if (w < 1.0) {
+        double ec[3];
+        oracle_sample_irradiance(grids[k + 1], irr[k + 1], valid[k + 1], x, nrm, ec);
+        for (int a = 0; a < 3; ++a) out[a] = w * ek[a] + (1.0 - w) * ec[a];
+    }
+    *w_out = w;
+    *level_out = k;
+}

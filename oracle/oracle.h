@@ -198,6 +198,28 @@ void oracle_sample_irradiance_visible(const or_volume* vol, const or_grid* g, co
                                       const double x[3], const double nrm[3], double out[3], double vis[8],
                                       double margins[16]);
 
+/* Mean value coordinates (Floater, Kos and Reimers 2005; Ju, Schaefer and Warren 2005)
+ * of x with respect to a closed, consistently oriented triangle mesh (nv vertices [nv][3],
+ * nt triangles [nt][3] of vertex indices, counter-clockwise seen from outside the domain):
+ * lambda [nv] with sum 1 and sum lambda_j p_j = x. Returns 0, or 1 when x lies on the mesh
+ * (lambda then holds the barycentric coordinates of its triangle or the vertex delta). */
+int32_t oracle_mvc(const double* verts, int32_t nv, const int32_t* tris, int32_t nt, const double x[3],
+                   double* lambda);
+
+/* Cascade blending (Sec. 3.5): the transition weight of volume k at x. The shell between its
+ * probe box (outer) and that box shrunk by one probe spacing (inner) is a closed surface
+ * (inner faces reversed); w = the sum of the mean value coordinates of the 8 inner corners,
+ * 1 on and inside the inner box, 0 on the outer box, clamped to [0, 1]. */
+double oracle_cascade_weight(const or_grid* g, const double x[3]);
+
+/* Irradiance at x (normal nrm) from volumes grids[0] (finest) .. grids[n-1] (coarsest), each
+ * with its maps: the finest volume k whose probe box holds x (the coarsest if none),
+ * E = w E_k + (1 - w) E_{k+1} with w = oracle_cascade_weight(grids[k], x) (w = 1 for the
+ * coarsest), E_i the plain interpolation rule of volume i. Writes *w_out and *level_out. */
+void oracle_sample_irradiance_cascade(const or_grid* const* grids, const double* const* irr,
+                                      const uint8_t* const* valid, int32_t n, const double x[3],
+                                      const double nrm[3], double out[3], double* w_out, int32_t* level_out);
+
 /* Probe relocation (Sec. 3.2, the procedure UpdateProbePos). The paper gives the steps
  * (query the SDF at the grid position; if below threshold1, move the probe by gradient
  * descent on the SDF; if it then lies farther than threshold2 from last frame's
