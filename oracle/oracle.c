@@ -859,73 +859,80 @@ void oracle_relocate(const or_volume* vol, const or_grid* g, const or_relocation
 
 /* ------------------------------------------------ cascade blending (Sec. 3.5) */
 
-static void cross3(const double a[3], const double b[3], double c[3]) {
-    c[0] = a[1] * b[2] - a[2] * b[1];
-    c[1] = a[2] * b[0] - a[0] * b[2];
-    c[2] = a[0] * b[1] - a[1] * b[0];
-}
-
+/* Evaluated in long double (a 64-bit significand on x86-64): in FP64 the closed form loses
+ * up to 1e-5 at points within 1e-7 spacings of a face's plane, where the per-triangle term is
+ * a difference of nearly equal quantities. The angles come from atan2(|a x b|, a . b), which
+ * keeps its accuracy near 0 and near pi, unlike the chord's arcsine. */
 int32_t oracle_mvc(const double* verts, int32_t nv, const int32_t* tris, int32_t nt, const double x[3],
                    double* lambda) {
-    const double tiny = 1e-12;
-    double* d = (double*)malloc(sizeof(double) * (size_t)nv);
-    double* u = (double*)malloc(sizeof(double) * 3 * (size_t)nv);
+    typedef long double ld;
+    const ld tiny = 1e-15L, pi = 3.141592653589793238462643383279502884L;
+    ld* d = (ld*)malloc(sizeof(ld) * (size_t)nv);
+    ld* u = (ld*)malloc(sizeof(ld) * 3 * (size_t)nv);
+    ld* lam = (ld*)malloc(sizeof(ld) * (size_t)nv);
+    int32_t on = 0;
     for (int32_t j = 0; j < nv; ++j) {
         lambda[j] = 0.0;
-        double v[3] = {verts[3 * j] - x[0], verts[3 * j + 1] - x[1], verts[3 * j + 2] - x[2]};
-        d[j] = sqrt(dot3(v, v));
+        lam[j] = 0.0L;
+    }
+    for (int32_t j = 0; j < nv && !on; ++j) {
+        ld v[3] = {(ld)verts[3 * j] - x[0], (ld)verts[3 * j + 1] - x[1], (ld)verts[3 * j + 2] - x[2]};
+        d[j] = sqrtl(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         if (d[j] < tiny) { /* x at a vertex */
             lambda[j] = 1.0;
-            free(d);
-            free(u);
-            return 1;
+            on = 1;
+            break;
         }
         for (int a = 0; a < 3; ++a) u[3 * j + a] = v[a] / d[j];
     }
-    for (int32_t t = 0; t < nt; ++t) {
+    for (int32_t t = 0; t < nt && !on; ++t) {
         const int32_t id[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
-        double th[3], c[3], sn[3];
+        ld th[3], c[3], sn[3];
         for (int i = 0; i < 3; ++i) { /* angle at x between the two other corners */
-            const double* a = &u[3 * id[(i + 1) % 3]];
-            const double* b = &u[3 * id[(i + 2) % 3]];
-            double e[3] = {a[0] - b[0], a[1] - b[1], a[2] - b[2]};
-            th[i] = 2.0 * asin(fmin(1.0, sqrt(dot3(e, e)) / 2.0));
+            const ld* a = &u[3 * id[(i + 1) % 3]];
+            const ld* b = &u[3 * id[(i + 2) % 3]];
+            const ld cr[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+            th[i] = atan2l(sqrtl(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]), a[0] * b[0] + a[1] * b[1] + a[2] * b[2]);
         }
-        const double hh = 0.5 * (th[0] + th[1] + th[2]);
-        if (M_PI - hh < tiny) { /* x on this triangle: barycentric coordinates */
-            double w[3], sw = 0.0;
+        const ld hh = 0.5L * (th[0] + th[1] + th[2]);
+        if (pi - hh < tiny) { /* x on this triangle: barycentric coordinates */
+            ld w[3], sw = 0.0L;
             for (int i = 0; i < 3; ++i) {
-                w[i] = sin(th[i]) * d[id[(i + 2) % 3]] * d[id[(i + 1) % 3]];
+                w[i] = sinl(th[i]) * d[id[(i + 2) % 3]] * d[id[(i + 1) % 3]];
                 sw += w[i];
             }
             for (int32_t j = 0; j < nv; ++j) lambda[j] = 0.0;
-            for (int i = 0; i < 3; ++i) lambda[id[i]] += w[i] / sw;
-            free(d);
-            free(u);
-            return 1;
+            for (int i = 0; i < 3; ++i) lambda[id[i]] += (double)(w[i] / sw);
+            on = 1;
+            break;
         }
-        double cr[3];
-        cross3(&u[3 * id[0]], &u[3 * id[1]], cr);
-        const double det = dot3(cr, &u[3 * id[2]]);
-        const double sgn = det >= 0.0 ? 1.0 : -1.0;
+        const ld* p0 = &u[3 * id[0]];
+        const ld* p1 = &u[3 * id[1]];
+        const ld* p2 = &u[3 * id[2]];
+        const ld det = (p0[1] * p1[2] - p0[2] * p1[1]) * p2[0] + (p0[2] * p1[0] - p0[0] * p1[2]) * p2[1] +
+                       (p0[0] * p1[1] - p0[1] * p1[0]) * p2[2];
+        const ld sgn = det >= 0.0L ? 1.0L : -1.0L;
         int skip = 0;
         for (int i = 0; i < 3; ++i) {
-            c[i] = 2.0 * sin(hh) * sin(hh - th[i]) / (sin(th[(i + 1) % 3]) * sin(th[(i + 2) % 3])) - 1.0;
-            sn[i] = sgn * sqrt(fmax(0.0, 1.0 - c[i] * c[i]));
-            if (fabs(sn[i]) <= tiny) skip = 1; /* x in the triangle's plane, outside it */
+            c[i] = 2.0L * sinl(hh) * sinl(hh - th[i]) / (sinl(th[(i + 1) % 3]) * sinl(th[(i + 2) % 3])) - 1.0L;
+            sn[i] = sgn * sqrtl(fmaxl(0.0L, 1.0L - c[i] * c[i]));
+            if (fabsl(sn[i]) <= tiny) skip = 1; /* x in the triangle's plane, outside it */
         }
         if (skip) continue;
         for (int i = 0; i < 3; ++i) {
             const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
-            lambda[id[i]] += (th[i] - c[i1] * th[i2] - c[i2] * th[i1]) / (d[id[i]] * sin(th[i1]) * sn[i2]);
+            lam[id[i]] += (th[i] - c[i1] * th[i2] - c[i2] * th[i1]) / (d[id[i]] * sinl(th[i1]) * sn[i2]);
         }
     }
-    double sw = 0.0;
-    for (int32_t j = 0; j < nv; ++j) sw += lambda[j];
-    for (int32_t j = 0; j < nv; ++j) lambda[j] /= sw;
+    if (!on) {
+        ld sw = 0.0L;
+        for (int32_t j = 0; j < nv; ++j) sw += lam[j];
+        for (int32_t j = 0; j < nv; ++j) lambda[j] = (double)(lam[j] / sw);
+    }
     free(d);
     free(u);
-    return 0;
+    free(lam);
+    return on;
 }
 
 /* The 12 triangles of an axis-aligned box, counter-clockwise seen from outside (corner c has
@@ -962,7 +969,9 @@ double oracle_cascade_weight(const or_grid* g, const double x[3]) {
     double lo[3], hi[3], ilo[3], ihi[3];
     probe_box(g, lo, hi);
     for (int a = 0; a < 3; ++a) {
-        if (g->dims[a] < 3) return 1.0; /* no inner box: no transition */
+        /* with fewer than 4 probes along an axis the inner box is empty or flat; a flat one
+         * would make the shell a slit box whose weight is 0 off the plate: no transition */
+        if (g->dims[a] < 4) return 1.0;
         ilo[a] = lo[a] + g->spacing[a];
         ihi[a] = hi[a] - g->spacing[a];
     }

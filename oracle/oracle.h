@@ -209,7 +209,8 @@ int32_t oracle_mvc(const double* verts, int32_t nv, const int32_t* tris, int32_t
 /* Cascade blending (Sec. 3.5): the transition weight of volume k at x. The shell between its
  * probe box (outer) and that box shrunk by one probe spacing (inner) is a closed surface
  * (inner faces reversed); w = the sum of the mean value coordinates of the 8 inner corners,
- * 1 on and inside the inner box, 0 on the outer box, clamped to [0, 1]. */
+ * 1 on and inside the inner box, 0 on the outer box, clamped to [0, 1]; 1 everywhere when an
+ * axis has fewer than 4 probes (no inner box of positive volume). */
 double oracle_cascade_weight(const or_grid* g, const double x[3]);
 
 /* Irradiance at x (normal nrm) from volumes grids[0] (finest) .. grids[n-1] (coarsest), each

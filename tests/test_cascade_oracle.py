@@ -6,9 +6,12 @@ faces. On a convex box they equal the defining spherical integral, lambda_j = th
 integral of phi_j(p(w)) / r(w) over the integral of 1 / r(w), where r is the distance
 along direction w to the surface and phi_j the barycentric weight of vertex j at the hit.
 That integral is evaluated here by brute-force quadrature over a Fibonacci sphere, a
-computation that shares nothing with the closed form. The cascade weight is 1 inside the
-inner box and 0 on the outer box, and the blended irradiance reduces to one volume's
-plain interpolation wherever the weight is 0 or 1.
+computation that shares nothing with the closed form. On the cascade's shell the same
+integral, taken face by face over the surface by adaptive quadrature, pins the weight to
+1e-10, also beside the faces' planes where the closed form cancels. The cascade weight is
+1 inside the inner box and 0 on the outer box (1 everywhere without an inner box of
+positive volume), and the blended irradiance reduces to one volume's plain interpolation
+wherever the weight is 0 or 1.
 """
 import numpy as np
 
@@ -145,3 +148,58 @@ def test_cascade_sample_reduces_to_one_volume():
     out, w, lvl = O.sample_irradiance_cascade([fine, coarse], irr, valid, x, n)
     ef, ec = O.sample_irradiance(fine, irr[0], valid[0], x, n), O.sample_irradiance(coarse, irr[1], valid[1], x, n)
     assert lvl == 0 and 0 < w < 1 and np.allclose(out, w * ef + (1 - w) * ec, rtol=0, atol=1e-15)
+
+
+def _weight_by_quadrature(lo, hi, sp, x):
+    """The cascade weight from the integral that defines mean value coordinates, face by face.
+
+    lambda_j = W_j / sum W with W_j the integral over the surface of phi_j / r over the sphere
+    of directions; with d(omega) = h / r^3 dA that is the integral of phi_j h / r^4 over the
+    surface (h the signed distance of the face's plane along its outward normal). The hats of
+    a face's corners sum to 1 on it, so the inner corners' total is the ratio of the inner
+    faces' integrals of h / r^4 to all 12 faces' ones, each integrated here by adaptive 2-D
+    quadrature.
+    """
+    from scipy import integrate
+    lo, hi, sp = (np.asarray(v, float) for v in (lo, hi, sp))
+    ilo, ihi = lo + sp, hi - sp
+    num = den = 0.0
+    for inner, (L, H) in ((False, (lo, hi)), (True, (ilo, ihi))):
+        for ax in range(3):
+            p, q = [k for k in range(3) if k != ax]
+            for side in (0, 1):
+                n = (1.0 if side else -1.0) * (-1.0 if inner else 1.0)   # outward from the shell
+                h = n * ((H if side else L)[ax] - x[ax])
+                f = lambda b, a, h=h: h / (h * h + a * a + b * b) ** 2
+                val = integrate.dblquad(f, L[p] - x[p], H[p] - x[p], L[q] - x[q], H[q] - x[q],
+                                        epsabs=1e-15, epsrel=1e-12)[0]
+                den += val
+                num += val if inner else 0.0
+    return num / den
+
+
+def test_cascade_weight_equals_the_surface_integral():
+    """Generic shell points and points within 1e-7 spacings of an inner face's plane (outside
+    the face), where the per-triangle closed form is a difference of nearly equal terms (an
+    FP64 evaluation of it is off by 2e-8 at the first point of the large volume); the bar
+    is the quadrature's accuracy."""
+    cases = []
+    dims, origin, sp = (7, 5, 9), np.array([1.0, -2.0, 0.5]), np.array([0.5, 0.5, 0.5])
+    cases.append((dims, origin, sp, [[1.2, -1.1, 2.0], [3.7, -0.4, 1.3], [2.0, -0.3, 4.3], [1.25, -1.75, 0.8],
+                                     [1.2, -1.5 + 5e-8, 2.2], [2.1, -1.5 - 1.5e-7, 0.65]]))
+    dims, origin, sp = (32, 16, 32), np.array([-60.0, -2.0, -64.0]), np.array([4.0, 4.0, 4.0])
+    cases.append((dims, origin, sp, [[-58.0, 2.0 + 4e-7, -20.0], [61.5, 10.0, -60.0 - 4e-7], [0.0, 54.0 + 2e-7, 59.0],
+                                     [-57.5, -0.5, 3.25], [10.0, 56.0, 50.0]]))
+    for dims, origin, sp, pts in cases:
+        g = _grid(dims, origin, sp)
+        lo, hi = origin, origin + (np.array(dims) - 1) * sp
+        for x in map(np.array, pts):
+            ref = _weight_by_quadrature(lo, hi, sp, x)
+            got = O.cascade_weight(g, x)
+            assert abs(got - ref) < 1e-10, (x, got, ref)
+
+
+def test_flat_inner_box_means_no_transition():
+    g = _grid((3, 6, 5), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))      # inner box flat in x
+    for x in ([0.5, 2.5, 2.0], [1.0, 0.2, 3.9], [1.7, 4.8, 0.1]):
+        assert O.cascade_weight(g, np.array(x)) == 1.0
