@@ -862,7 +862,8 @@ void oracle_relocate(const or_volume* vol, const or_grid* g, const or_relocation
 /* Evaluated in long double (a 64-bit significand on x86-64): in FP64 the closed form loses
  * up to 1e-5 at points within 1e-7 spacings of a face's plane, where the per-triangle term is
  * a difference of nearly equal quantities. The angles come from atan2(|a x b|, a . b), which
- * keeps its accuracy near 0 and near pi, unlike the chord's arcsine. */
+ * keeps its accuracy near 0 and near pi, unlike the chord's arcsine, and the sines of the
+ * spherical triangle's corner angles from the triple product (spherical law of sines). */
 int32_t oracle_mvc(const double* verts, int32_t nv, const int32_t* tris, int32_t nt, const double x[3],
                    double* lambda) {
     typedef long double ld;
@@ -895,30 +896,34 @@ int32_t oracle_mvc(const double* verts, int32_t nv, const int32_t* tris, int32_t
             th[i] = atan2l(sqrtl(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]), a[0] * b[0] + a[1] * b[1] + a[2] * b[2]);
         }
         const ld hh = 0.5L * (th[0] + th[1] + th[2]);
-        if (pi - hh < tiny) { /* x on this triangle: barycentric coordinates */
-            ld w[3], sw = 0.0L;
-            for (int i = 0; i < 3; ++i) {
-                w[i] = sinl(th[i]) * d[id[(i + 2) % 3]] * d[id[(i + 1) % 3]];
-                sw += w[i];
-            }
-            for (int32_t j = 0; j < nv; ++j) lambda[j] = 0.0;
-            for (int i = 0; i < 3; ++i) lambda[id[i]] += (double)(w[i] / sw);
-            on = 1;
-            break;
-        }
         const ld* p0 = &u[3 * id[0]];
         const ld* p1 = &u[3 * id[1]];
         const ld* p2 = &u[3 * id[2]];
         const ld det = (p0[1] * p1[2] - p0[2] * p1[1]) * p2[0] + (p0[2] * p1[0] - p0[0] * p1[2]) * p2[1] +
                        (p0[0] * p1[1] - p0[1] * p1[0]) * p2[2];
-        const ld sgn = det >= 0.0L ? 1.0L : -1.0L;
-        int skip = 0;
-        for (int i = 0; i < 3; ++i) {
-            c[i] = 2.0L * sinl(hh) * sinl(hh - th[i]) / (sinl(th[(i + 1) % 3]) * sinl(th[(i + 2) % 3])) - 1.0L;
-            sn[i] = sgn * sqrtl(fmaxl(0.0L, 1.0L - c[i] * c[i]));
-            if (fabsl(sn[i]) <= tiny) skip = 1; /* x in the triangle's plane, outside it */
+        /* x in the triangle's plane: the triple product vanishes (to first order in the distance
+         * to the plane; the angle sum's gap to 2 pi only to second order) */
+        if (fabsl(det) <= tiny) {
+            if (pi - hh < 1e-9L) { /* inside the triangle: barycentric coordinates */
+                ld w[3], sw = 0.0L;
+                for (int i = 0; i < 3; ++i) {
+                    w[i] = sinl(th[i]) * d[id[(i + 2) % 3]] * d[id[(i + 1) % 3]];
+                    sw += w[i];
+                }
+                for (int32_t j = 0; j < nv; ++j) lambda[j] = 0.0;
+                for (int i = 0; i < 3; ++i) lambda[id[i]] += (double)(w[i] / sw);
+                on = 1;
+                break;
+            }
+            continue; /* outside it: no contribution */
         }
-        if (skip) continue;
+        for (int i = 0; i < 3; ++i) {
+            const ld s1 = sinl(th[(i + 1) % 3]), s2 = sinl(th[(i + 2) % 3]);
+            c[i] = 2.0L * sinl(hh) * sinl(hh - th[i]) / (s1 * s2) - 1.0L;
+            /* sign(det) sqrt(1 - c^2) by the spherical law of sines, without its cancellation
+             * where c is near -1 or 1 (x next to a face, or in a face's plane) */
+            sn[i] = det / (s1 * s2);
+        }
         for (int i = 0; i < 3; ++i) {
             const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
             lam[id[i]] += (th[i] - c[i1] * th[i2] - c[i2] * th[i1]) / (d[id[i]] * sinl(th[i1]) * sn[i2]);

@@ -203,3 +203,26 @@ def test_flat_inner_box_means_no_transition():
     g = _grid((3, 6, 5), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))      # inner box flat in x
     for x in ([0.5, 2.5, 2.0], [1.0, 0.2, 3.9], [1.7, 4.8, 0.1]):
         assert O.cascade_weight(g, np.array(x)) == 1.0
+
+
+def test_weight_is_smooth_up_to_the_faces():
+    """Mean value coordinates are smooth up to the interior of a face, so approaching an inner
+    face (weight 1 on it) or the probe box's face (weight 0) from the shell, (1 - w) / h and
+    w / h tend to the normal derivative: at distances 1e-6 .. 1e-10 spacings they agree with
+    their value at 1e-5 to first order. A test for x on a face by the angle sum alone (whose
+    gap to 2 pi is second order in the distance) reads such points as on the face."""
+    dims, origin, sp = (32, 16, 32), np.array([1.0, -2.0, 0.5]), np.array([4.0, 4.0, 4.0])
+    g = _grid(dims, origin, sp)
+    lo, hi = origin, origin + (np.array(dims) - 1) * sp
+    ilo = lo + sp
+    foot = np.array([78.7, 0.0, 47.9])
+    for face_y, sign, inner in ((ilo[1], -1.0, True), (lo[1], 1.0, False)):
+        def gap(h):
+            x = foot.copy()
+            x[1] = face_y + sign * h
+            w = O.cascade_weight(g, x)
+            return ((1.0 - w) if inner else w) / h
+        ref = gap(1e-5 * sp[1])
+        for k in range(6, 11):
+            h = 10.0 ** -k * sp[1]
+            assert abs(gap(h) / ref - 1.0) < 1e-4, (inner, k, gap(h), ref)
