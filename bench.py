@@ -44,26 +44,28 @@ def peaks():
         return 6400.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+def source_hash(patterns) -> str:
+    """Hash of the files matching the glob patterns (repository-relative)."""
     import glob
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2007_14394_b300", "csrc", "*"))) + \
-            [os.path.join(ROOT, "include", "sdfddgi.h")]:
+    files = sorted({f for pat in patterns for f in glob.glob(os.path.join(ROOT, pat))})
+    for f in files:
+        h.update(os.path.relpath(f, ROOT).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def measured_traffic(stage: str, workload: str):
-    """DRAM bytes per launch of `stage` from the committed ncu capture, or None when the
-    kernels changed since that capture (or it covers another workload)."""
+    """DRAM bytes per launch of `stage` from the committed ncu capture of `workload`
+    (profiles/traffic_<workload>.json), or None when a source it covers changed since."""
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", f"traffic_{workload}.json")) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
-    if t.get("source_hash") != kernel_source_hash() or t.get("workload") != workload:
+    if t.get("source_hash") != source_hash(t.get("sources", [])):
         return None
     return t["dram_bytes_per_launch"].get(stage)
 
@@ -495,6 +497,146 @@ def run_batch(args, rank, world, local_rank):
     return line
 
 
+CASCADE_QUERY = "cascade512_query"
+
+
+def touched_map_bytes(c, pts, level, weight):
+    """Irradiance-map and history bytes of the distinct probes the points interpolate from (the
+    8 probes of the point's cell in its level, and in the next level where it blends)."""
+    total = 0
+    for i, v in enumerate(c.volumes):
+        use = (level == i) | ((level == i - 1) & (weight < 1.0))
+        if not use.any():
+            continue
+        d, o, sp = np.array(v.probe_dims), np.array(v.probe_origin), np.array(v.probe_spacing)
+        g = np.clip((pts[use] - o) / sp, 0, d - 1)
+        b = np.clip(np.floor(g).astype(np.int64), 0, np.maximum(d - 2, 0))
+        ids = []
+        for k in range(8):
+            q = np.minimum(b + [(k >> a) & 1 for a in range(3)], d - 1)
+            ids.append((q[:, 2] * d[1] + q[:, 1]) * d[0] + q[:, 0])
+        total += np.unique(np.concatenate(ids)).size * (8 * 8 * 16 + 1)
+    return total
+
+
+def run_cascade_query(args, rank, world, local_rank):
+    """Irradiance queries against a cascade of volumes (Sec. 3.5): the four volumes of the
+    cascade512 workload (finest first, their maps random), 2,073,600 points per step; each
+    point takes the finest volume holding it, blended toward the next across that volume's
+    border with the mean-value-coordinate weight."""
+    import torch
+    import paper_2007_14394_b300 as S
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    c = W.CASCADES["cascade512"]
+    sc = S.create_scene()
+    vols, host_maps = [], W.cascade_query_maps(c)
+    for i, v in enumerate(c.volumes):
+        desc = S.make_desc(v.probe_dims, v.rays, v.probe_origin, v.probe_spacing, v.max_steps, volume_id=i)
+        vols.append(S.create_volume(desc, sc))
+        irr, valid = host_maps[i]
+        S.write_state(vols[i], irr, np.zeros((v.n_probes, 16, 16, 2), np.float32), valid)
+    n = W.QUERY_POINTS
+    pts, nrm = W.cascade_query_points(n)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    p_d, n_d = torch.from_numpy(pts).to(dev), torch.from_numpy(nrm).to(dev)
+    out = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    lvl = torch.empty(n, dtype=torch.int32, device=dev)
+    wgt = torch.empty(n, dtype=torch.float32, device=dev)
+    S.sample_irradiance_cascade(vols, p_d, n_d, out, lvl, wgt, stream=stream)
+    torch.cuda.synchronize()
+    level, weight = lvl.cpu().numpy(), wgt.cpu().numpy()
+    blend = (weight < 1.0) & (level < len(vols) - 1)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(step_fn):
+        for _ in range(args.warmup):
+            step_fn()
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            step_fn()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+    clocks = Clocks(local_rank)
+    per_step = timed(lambda: S.sample_irradiance_cascade(vols, p_d, n_d, out, stream=stream))
+    clk = clocks.stop()
+    # end to end: points and normals in from pinned host memory, the irradiance out
+    hp, hn = torch.from_numpy(pts).pin_memory(), torch.from_numpy(nrm).pin_memory()
+    ho = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        p_d.copy_(hp, non_blocking=True)
+        n_d.copy_(hn, non_blocking=True)
+        S.sample_irradiance_cascade(vols, p_d, n_d, out, stream=stream)
+        ho.copy_(out, non_blocking=True)
+    e2e_ms = timed(e2e_step)
+    ms, e2e = float(np.mean(per_step)), float(np.mean(e2e_ms))
+    if world > 1:
+        t = torch.tensor([ms, e2e], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, e2e = (float(x) for x in t.tolist())
+    hbm, peak_kind = peaks()
+    alg = n * (24 + 12) + touched_map_bytes(c, pts, level, weight)
+    ach = alg / (ms / 1e3) / 1e9
+    line = {
+        "metric": "irradiance queries/s through a cascade of probe volumes", "value": world * n / (ms / 1e3),
+        "unit": "points/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (random maps, seeded points)",
+        "config": {"workload": f"{CASCADE_QUERY}: {n} points (1920x1080) against the 4 volumes of cascade512 "
+                               "(8^3, 16^3 @2 m; 32x8x32 @4 m; 64x16x64 @2 m)",
+                   "points": n, "levels": np.bincount(level, minlength=len(vols)).tolist(),
+                   "blending_points": int(blend.sum()),
+                   "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
+        "gpu_launches": args.steps,
+        "e2e": {"value": world * n / (e2e / 1e3), "unit": "points/s", "h2d_bytes_per_step": n * 24,
+                "d2h_bytes_per_step": n * 12, "ms_per_step": e2e},
+        "roofline": {"kernel": "cascade_kernel", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                     "frac": ach / hbm, "bytes_per_launch": alg, "peak_source": f"{peak_kind} hbm_gbs",
+                     "traffic": measured_traffic("cascade", CASCADE_QUERY),
+                     "note": "36 B per point plus the maps of the distinct probes touched. The kernel is bound "
+                             "by FP32 issue, not memory: each blending point's weight is 48 closed-form "
+                             "face-edge terms (4 arctangents per lane of a warp)"},
+        "step_ms": {"min": min(per_step), "median": statistics.median(per_step), "max": max(per_step)},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cascade_query_cpu_baseline(c, host_maps, pts, nrm, args.cpu_budget)
+    for v in vols:
+        S.destroy_volume(v)
+    S.destroy_scene(sc)
+    return line
+
+
+def cascade_query_cpu_baseline(c, host_maps, pts, nrm, budget_s):
+    import oracle as O
+    grids = [O.make_grid(v.probe_dims, v.probe_origin, v.probe_spacing, v.rays, v.max_steps, v.eps_vox, v.tmax_vox,
+                         v.hysteresis) for v in c.volumes]
+    irr = [m[0].astype(np.float64) for m in host_maps]
+    valid = [m[1] for m in host_maps]
+    t0, k = time.perf_counter(), 0
+    while time.perf_counter() - t0 < budget_s and k < len(pts):
+        O.sample_irradiance_cascade(grids, irr, valid, pts[k].astype(np.float64), nrm[k].astype(np.float64))
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": f"the first {k} of the step's points, one oracle call each ({dt:.1f} s)"}
+
+
 ANALYTIC = {"open256_analytic": "open256", "room64_analytic": "room64"}
 
 
@@ -804,7 +946,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=sorted(W.PRESETS) + sorted(W.CASCADES) + [LEARNED] + sorted(ANALYTIC))
+                    choices=sorted(W.PRESETS) + sorted(W.CASCADES) + [LEARNED] + sorted(ANALYTIC) + [CASCADE_QUERY])
     ap.add_argument("--train-steps", type=int, default=6000, help="training steps of the learned32 workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
@@ -816,7 +958,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
-        if args.workload in W.CASCADES or args.workload == LEARNED or args.workload in ANALYTIC:
+        if args.workload in W.CASCADES or args.workload in (LEARNED, CASCADE_QUERY) or args.workload in ANALYTIC:
             ap.error("the reference arm times single-volume workloads")
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
@@ -827,7 +969,8 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     run = (run_batch if args.workload in W.CASCADES else run_learned if args.workload == LEARNED
-           else run_analytic if args.workload in ANALYTIC else run_ours)
+           else run_analytic if args.workload in ANALYTIC else run_cascade_query if args.workload == CASCADE_QUERY
+           else run_ours)
     line = run(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(line), flush=True)

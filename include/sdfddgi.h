@@ -291,6 +291,34 @@ SDFDDGI_API int sdfddgi_sample_irradiance_visible(const sdfddgi_volume* v, const
                                                   int64_t n, float softness, const sdfddgi_probe_state* states,
                                                   float* out_rgb, void* stream);
 
+/* Irradiance from a cascade of probe volumes (Sec. 3.5: nested volumes of falling density,
+ * blended across each volume's border with mean value coordinates instead of trilinear
+ * weights, and no visibility test in the farthest one). volumes[0..n-1] run from the finest
+ * to the coarsest (1 <= n <= 8; a host array of handles). For each point: k = the first
+ * volume whose probe box (grid origin to origin + (dims - 1) * spacing, closed) holds it,
+ * else n - 1; E = w E_k + (1 - w) E_{k+1}, w = 1 for k = n - 1. E_i is
+ * sdfddgi_sample_irradiance's rule on volume i when softness = 0 or i = n - 1, else
+ * sdfddgi_sample_irradiance_visible's rule (Sec. 3.4) with this softness, volume i's scene
+ * and states[i]. The weight w is the sum of the mean value coordinates of the 8 corners of
+ * volume k's probe box shrunk by one spacing (the inner box) over the closed shell between
+ * the two boxes: 1 on and inside the inner box, 0 on the probe box's faces, smooth in
+ * between; w = 1 everywhere when an axis of volume k has fewer than 4 probes (no inner box
+ * of positive volume).
+ *  points, normals, out_rgb -- device float[n_pts][3];
+ *  softness -- 0 (no visibility test) or > 0 (finite);
+ *  states -- NULL or a host array of n pointers, each NULL (probes at their grid positions)
+ *            or that volume's P device probe states (positions used; only with softness > 0);
+ *  out_level -- NULL or device int32[n_pts]: k;  out_weight -- NULL or device float[n_pts]: w.
+ * Errors: INVALID_ARG for a NULL handle or array, n outside [1, 8], n_pts outside [0, 2^38]
+ * or a negative or non-finite softness; STATE when softness > 0 and the scene of a volume
+ * but the last holds no SDF; CUDA when the launch fails. Reads the volumes' current maps on
+ * `stream`. */
+SDFDDGI_API int sdfddgi_sample_irradiance_cascade(const sdfddgi_volume* const* volumes, int32_t n,
+                                                  const float* points, const float* normals, int64_t n_pts,
+                                                  float softness, const sdfddgi_probe_state* const* states,
+                                                  float* out_rgb, int32_t* out_level, float* out_weight,
+                                                  void* stream);
+
 /* Device pointers to the current (latest) maps: irradiance [P][8][8][4] float,
  * depth [P][16][16][2] float, valid [P] uint8 (1 = probe has history). They stay
  * valid until the next update_probes / write_state / destroy. Any may be NULL. */

@@ -117,6 +117,9 @@ def _load():
             lib.oracle_cascade_weight.restype = C.c_double
             lib.oracle_sample_irradiance_cascade.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, dp, dp,
                                                              dp, C.POINTER(C.c_double), C.POINTER(C.c_int32)]
+            lib.oracle_sample_irradiance_cascade_visible.argtypes = [
+                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, dp, dp, dp,
+                C.POINTER(C.c_double), C.POINTER(C.c_int32), dp]
             lib.oracle_relocate.argtypes = [C.POINTER(Volume), C.POINTER(Grid), C.POINTER(Relocation), C.c_void_p,
                                             dp, C.c_void_p, C.c_void_p, C.c_void_p]
             _lib = lib
@@ -388,3 +391,25 @@ def sample_irradiance_cascade(grids, irrs, valids, x, nrm):
     _load().oracle_sample_irradiance_cascade(gp, ip, vp, n, _dp(_vec(x)), _dp(_vec(nrm)), _dp(out), C.byref(w),
                                              C.byref(lvl))
     return out, w.value, lvl.value
+
+
+def sample_irradiance_cascade_visible(scenes, grids, irrs, valids, x, nrm, softness, probe_pos=None):
+    """Cascade interpolation with probe visibility in every level but the farthest (Sec. 3.4,
+    3.5); scenes: one OracleScene per level; probe_pos: None or per level None / float32 [P, 3].
+    Returns (rgb, w, level, margins [2, 8, 2]) (levels k and k + 1)."""
+    n = len(grids)
+    irrs = [np.ascontiguousarray(a, dtype=np.float64) for a in irrs]
+    valids = [np.ascontiguousarray(a, dtype=np.uint8) for a in valids]
+    pps = [None if probe_pos is None or probe_pos[i] is None
+           else np.ascontiguousarray(np.asarray(probe_pos[i], dtype=np.float32)) for i in range(n)]
+    sp = (C.c_void_p * n)(*[C.cast(C.pointer(sc.vol), C.c_void_p) for sc in scenes])
+    gp = (C.c_void_p * n)(*[C.cast(C.pointer(g), C.c_void_p) for g in grids])
+    ip = (C.c_void_p * n)(*[a.ctypes.data for a in irrs])
+    vp = (C.c_void_p * n)(*[a.ctypes.data for a in valids])
+    pp = (C.c_void_p * n)(*[None if a is None else a.ctypes.data for a in pps])
+    out, marg = np.zeros(3), np.zeros(32)
+    w = C.c_double()
+    lvl = C.c_int32()
+    _load().oracle_sample_irradiance_cascade_visible(sp, gp, ip, vp, pp, n, float(softness), _dp(_vec(x)),
+                                                     _dp(_vec(nrm)), _dp(out), C.byref(w), C.byref(lvl), _dp(marg))
+    return out, w.value, lvl.value, marg.reshape(2, 8, 2)

@@ -997,9 +997,27 @@ double oracle_cascade_weight(const or_grid* g, const double x[3]) {
     return clampd(w, 0.0, 1.0);
 }
 
-void oracle_sample_irradiance_cascade(const or_grid* const* grids, const double* const* irr,
-                                      const uint8_t* const* valid, int32_t n, const double x[3],
-                                      const double nrm[3], double out[3], double* w_out, int32_t* level_out) {
+/* E_i of one cascade level: the plain rule, or (vols given, softness > 0, not the farthest
+ * level) the rule with probe visibility, whose 16 margins go to m (HUGE_MARGIN otherwise). */
+static void cascade_level_value(const or_volume* const* vols, const or_grid* const* grids,
+                                const double* const* irr, const uint8_t* const* valid,
+                                const float* const* probe_pos, int32_t n, double softness, int32_t i,
+                                const double x[3], const double nrm[3], double e[3], double m[16]) {
+    if (vols && softness > 0.0 && i < n - 1) {
+        double vis[8];
+        oracle_sample_irradiance_visible(vols[i], grids[i], irr[i], valid[i], probe_pos ? probe_pos[i] : NULL,
+                                         softness, x, nrm, e, vis, m);
+        return;
+    }
+    oracle_sample_irradiance(grids[i], irr[i], valid[i], x, nrm, e);
+    for (int k = 0; k < 16; ++k) m[k] = HUGE_MARGIN;
+}
+
+void oracle_sample_irradiance_cascade_visible(const or_volume* const* vols, const or_grid* const* grids,
+                                              const double* const* irr, const uint8_t* const* valid,
+                                              const float* const* probe_pos, int32_t n, double softness,
+                                              const double x[3], const double nrm[3], double out[3], double* w_out,
+                                              int32_t* level_out, double margins[32]) {
     int32_t k = n - 1;
     for (int32_t i = 0; i < n; ++i) {
         double lo[3], hi[3];
@@ -1011,13 +1029,21 @@ void oracle_sample_irradiance_cascade(const or_grid* const* grids, const double*
     }
     double w = k < n - 1 ? oracle_cascade_weight(grids[k], x) : 1.0;
     double ek[3];
-    oracle_sample_irradiance(grids[k], irr[k], valid[k], x, nrm, ek);
+    cascade_level_value(vols, grids, irr, valid, probe_pos, n, softness, k, x, nrm, ek, margins);
     for (int a = 0; a < 3; ++a) out[a] = ek[a];
+    for (int j = 16; j < 32; ++j) margins[j] = HUGE_MARGIN;
     if (w < 1.0) {
         double ec[3];
-        oracle_sample_irradiance(grids[k + 1], irr[k + 1], valid[k + 1], x, nrm, ec);
+        cascade_level_value(vols, grids, irr, valid, probe_pos, n, softness, k + 1, x, nrm, ec, margins + 16);
         for (int a = 0; a < 3; ++a) out[a] = w * ek[a] + (1.0 - w) * ec[a];
     }
     *w_out = w;
     *level_out = k;
+}
+
+void oracle_sample_irradiance_cascade(const or_grid* const* grids, const double* const* irr,
+                                      const uint8_t* const* valid, int32_t n, const double x[3],
+                                      const double nrm[3], double out[3], double* w_out, int32_t* level_out) {
+    double m[32];
+    oracle_sample_irradiance_cascade_visible(NULL, grids, irr, valid, NULL, n, 0.0, x, nrm, out, w_out, level_out, m);
 }

@@ -221,6 +221,17 @@ void oracle_sample_irradiance_cascade(const or_grid* const* grids, const double*
                                       const uint8_t* const* valid, int32_t n, const double x[3],
                                       const double nrm[3], double out[3], double* w_out, int32_t* level_out);
 
+/* The same with the paper's probe visibility (Sec. 3.4) in every level but the farthest
+ * (Sec. 3.5): with vols != NULL and softness > 0, level i < n - 1 takes
+ * oracle_sample_irradiance_visible on vols[i] (probe positions probe_pos[i], or the grid
+ * positions where probe_pos or probe_pos[i] is NULL). margins[0..15] are that call's margins
+ * for level k, margins[16..31] for level k + 1 (HUGE where no visibility test ran). */
+void oracle_sample_irradiance_cascade_visible(const or_volume* const* vols, const or_grid* const* grids,
+                                              const double* const* irr, const uint8_t* const* valid,
+                                              const float* const* probe_pos, int32_t n, double softness,
+                                              const double x[3], const double nrm[3], double out[3], double* w_out,
+                                              int32_t* level_out, double margins[32]);
+
 /* Probe relocation (Sec. 3.2, the procedure UpdateProbePos). The paper gives the steps
  * (query the SDF at the grid position; if below threshold1, move the probe by gradient
  * descent on the SDF; if it then lies farther than threshold2 from last frame's

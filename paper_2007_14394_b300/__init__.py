@@ -97,6 +97,7 @@ def _load() -> C.CDLL:
                                       C.c_int),
         "sdfddgi_relocate_probes": ([vp, C.POINTER(Relocation), vp, vp, vp], C.c_int),
         "sdfddgi_sample_irradiance_visible": ([vp, vp, vp, i64, C.c_float, vp, vp, vp], C.c_int),
+        "sdfddgi_sample_irradiance_cascade": ([vp, C.c_int32, vp, vp, i64, C.c_float, vp, vp, vp, vp, vp], C.c_int),
         "sdfddgi_denoiser_status": ([vp, C.POINTER(u32)], C.c_int),
         "sdfddgi_create_denoiser": ([C.POINTER(C.c_float), C.c_float, C.POINTER(vp)], C.c_int),
         "sdfddgi_destroy_denoiser": ([vp], None),
@@ -126,7 +127,7 @@ EXPORTED = ("last_error", "create_scene", "destroy_scene", "upload_sdf", "set_li
             "create_batch", "destroy_batch", "update_batch", "batch_autotune", "batch_schedule",
             "create_denoiser", "destroy_denoiser", "denoiser_params", "denoise", "denoise_volume",
             "denoiser_gradients", "denoiser_adam", "denoiser_train_step", "volume_status", "denoiser_status",
-            "relocate_probes", "sample_irradiance_visible", "upload_primitives")
+            "relocate_probes", "sample_irradiance_visible", "upload_primitives", "sample_irradiance_cascade")
 DENOISER_PARAMS = 49219
 DENOISE_TENSOR, DENOISE_SIMT_BF16, DENOISE_SIMT_FP32 = 0, 1, 2
 STAGES = ("weights", "primary", "prep", "shadow", "gather")  # intervals between the stage events
@@ -476,6 +477,24 @@ def sample_irradiance_visible(volume, points, normals, out, softness=8.0, states
     _check(lib.sdfddgi_sample_irradiance_visible(volume, _dev_ptr(points, "points"), _dev_ptr(normals, "normals"), n,
                                                  float(softness), _dev_ptr(states, "states"), _dev_ptr(out, "out"),
                                                  _stream(stream)))
+
+
+def sample_irradiance_cascade(volumes, points, normals, out, level=None, weight=None, softness=0.0, states=None,
+                              stream=None) -> None:
+    """Irradiance from a cascade of volumes (Sec. 3.5), finest first; points, normals, out: device
+    float [n, 3]; level (int32 [n]) and weight (float [n]): None or device tensors. softness > 0
+    weights the probes of every level but the farthest by their visibility (Sec. 3.4); states:
+    None or one entry per volume, each None or that volume's device probe states."""
+    vols = list(volumes)
+    arr = (C.c_void_p * max(len(vols), 1))(*vols)
+    st = None
+    if states is not None:
+        st = (C.c_void_p * max(len(vols), 1))(*[_dev_ptr(x, "states") for x in states])
+    n = int(points.numel() // 3) if _is_torch(points) else int(np.asarray(points).size // 3)
+    _check(lib.sdfddgi_sample_irradiance_cascade(arr, len(vols), _dev_ptr(points, "points"),
+                                                 _dev_ptr(normals, "normals"), n, float(softness), st,
+                                                 _dev_ptr(out, "out"), _dev_ptr(level, "level"),
+                                                 _dev_ptr(weight, "weight"), _stream(stream)))
 
 
 def upload_primitives(scene, types, params, albedo, emission, lo, hi, unit: float, cluster_size: int = 8) -> None:

@@ -321,4 +321,79 @@ __device__ __forceinline__ float3 ray_direction(int i, int R, const float rot[9]
               fmaf(rot[6], d.x, fmaf(rot[7], d.y, rot[8] * d.z)));
 }
 
+// ------------------------------------------------------------------ probe visibility
+// Visibility of probe position q from x (normal n), the paper's per-pixel visibility test
+// (Sec. 3.4) as a soft SDF shadow trace: from x + bias * n toward q, vis = min over the
+// march (t > 0) of softness * sdf / t, 0 on a hit (sdf < eps), clamped to [0, 1]; the march
+// ends when t reaches |q - x_s| or after max_steps.
+template <typename T>
+__device__ float probe_visibility(const VisParams& V, float3 x, float3 n, float3 q) {
+    const float3 xs = fma3(V.bias_w, n, x);
+    const float3 v = q - xs;
+    const float L = sqrtf(dot(v, v));
+    if (!(L > 0.f)) return 1.f;
+    const float inv_l = 1.0f / L;
+    const float3 d = f3(v.x * inv_l, v.y * inv_l, v.z * inv_l);
+    float vis = 1.f, t = 0.f;
+    for (int s = 0; s < V.max_steps; ++s) {
+        if (t >= L) break;
+        const float sd = sample_sdf<T>(V.vol, fma3(t, d, xs));
+        if (sd < V.eps_w) return 0.f;
+        if (t > 0.f) vis = fminf(vis, V.softness * sd / t);
+        t += sd;
+    }
+    return fminf(fmaxf(vis, 0.f), 1.f);
+}
+
+// The interpolation of interpolate_irradiance with each probe's weight times its visibility
+// from x; probes at their grid positions or at V.states' positions.
+template <typename T>
+__device__ float3 interpolate_irradiance_visible(const int gd[3], const float go[3], const float gs[3],
+                                                 const float4* irr, const uint8_t* valid, const VisParams& V,
+                                                 float3 x, float3 nrm) {
+    const float xs[3] = {x.x, x.y, x.z};
+    int base[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float c = fminf(fmaxf((xs[a] - go[a]) / gs[a], 0.f), (float)(gd[a] - 1));
+        int b = (int)floorf(c);
+        b = max(0, min(b, gd[a] - 2));
+        base[a] = b;
+        f[a] = gd[a] > 1 ? c - (float)b : 0.f;
+    }
+    const float2 uv = oct_encode(nrm);
+    const float cx = fmaf(uv.x, (float)kIrrN, 0.5f), cy = fmaf(uv.y, (float)kIrrN, 0.5f);
+    const int x0 = min((int)floorf(cx), kIrrN), y0 = min((int)floorf(cy), kIrrN);
+    const float fx = cx - (float)x0, fy = cy - (float)y0;
+    float sw = 0.f, r = 0.f, g = 0.f, bl = 0.f;
+    for (int k = 0; k < 8; ++k) {
+        const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+        const int ix = min(base[0] + dx, gd[0] - 1), iy = min(base[1] + dy, gd[1] - 1), iz = min(base[2] + dz, gd[2] - 1);
+        const size_t p = ((size_t)iz * gd[1] + iy) * gd[0] + ix;
+        float w = (dx ? f[0] : 1.f - f[0]) * (dy ? f[1] : 1.f - f[1]) * (dz ? f[2] : 1.f - f[2]);
+        if (!__ldg(valid + p)) w = 0.f;
+        if (!(w > 0.f)) continue;
+        float3 q;
+        if (V.states) {
+            q = f3(V.states[p].pos[0], V.states[p].pos[1], V.states[p].pos[2]);
+        } else {
+            q = f3(fmaf((float)ix, gs[0], go[0]), fmaf((float)iy, gs[1], go[1]), fmaf((float)iz, gs[2], go[2]));
+        }
+        w *= probe_visibility<T>(V, x, nrm, q);
+        if (!(w > 0.f)) continue;
+        const float4* m = irr + p * (kIrrT * kIrrT);
+        const float4 t00 = __ldg(m + y0 * kIrrT + x0), t01 = __ldg(m + y0 * kIrrT + x0 + 1);
+        const float4 t10 = __ldg(m + (y0 + 1) * kIrrT + x0), t11 = __ldg(m + (y0 + 1) * kIrrT + x0 + 1);
+        const float w00 = (1.f - fx) * (1.f - fy), w01 = fx * (1.f - fy), w10 = (1.f - fx) * fy, w11 = fx * fy;
+        r = fmaf(w, w00 * t00.x + w01 * t01.x + w10 * t10.x + w11 * t11.x, r);
+        g = fmaf(w, w00 * t00.y + w01 * t01.y + w10 * t10.y + w11 * t11.y, g);
+        bl = fmaf(w, w00 * t00.z + w01 * t01.z + w10 * t10.z + w11 * t11.z, bl);
+        sw += w;
+    }
+    if (!(sw > 0.f)) return f3(0.f, 0.f, 0.f);
+    const float inv = 1.0f / sw;
+    return f3(r * inv, g * inv, bl * inv);
+}
+
 }  // namespace sdfddgi

@@ -269,7 +269,6 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
                 const int g = half * 8 + gg;
                 if (g >= ng) break;
                 const float* a = acc + gg * kCh;
-                const size_t p = (size_t)(p0 + g);
                 const bool live = (s_flags[g] & SDFDDGI_PROBE_ACTIVE) && a[5] > 0.f;
                 const float hyst = s_hyst[g], keep = 1.f - hyst, inv = live ? 1.f / a[5] : 0.f;
                 if (j < kIrrTexels) {

@@ -226,3 +226,39 @@ def test_weight_is_smooth_up_to_the_faces():
         for k in range(6, 11):
             h = 10.0 ** -k * sp[1]
             assert abs(gap(h) / ref - 1.0) < 1e-4, (inner, k, gap(h), ref)
+
+
+def test_cascade_with_visibility_composes_the_pinned_rules():
+    """With probe visibility (Sec. 3.4), every level but the farthest takes the visibility rule
+    and the farthest the plain one (Sec. 3.5): inside the fine inner box the result is the
+    fine volume's visibility interpolation, in its shell the weight's blend of that and the
+    coarse plain interpolation, outside it the coarse plain interpolation; softness 0 is
+    the plain cascade."""
+    import workloads as W
+    h = 0.125
+    s = W.Scene()
+    s.add(W.BOX, [4.0, 4.0, 4.0, h, 10.0, 10.0], (0.5, 0.5, 0.5))   # a wall at x = 4
+    baked = W.bake(s, (64, 64, 64), h)
+    sc = O.OracleScene(baked.sdf, h, (0, 0, 0), None)
+    fine = O.make_grid((5, 5, 5), (3.0, 3.0, 3.0), (0.5, 0.5, 0.5), 8, 128, 0.01, 300.0, 0.97)   # [3, 5]^3
+    coarse = O.make_grid((5, 5, 5), (1.0, 1.0, 1.0), (1.5, 1.5, 1.5), 8, 128, 0.01, 300.0, 0.97)  # [1, 7]^3
+    rng = np.random.default_rng(4)
+    irr = [rng.uniform(0.1, 1.0, (125, 8, 8, 4)) for _ in range(2)]
+    valid = [np.ones(125, np.uint8), np.ones(125, np.uint8)]
+    grids, scenes = [fine, coarse], [sc, sc]
+    n = np.array([0.0, 0.6, 0.8])
+    for x, where in (([3.7, 4.1, 3.9], "inner"), ([3.2, 4.0, 4.3], "shell"), ([6.0, 2.0, 3.0], "outside")):
+        x = np.array(x)
+        out, w, lvl, m = O.sample_irradiance_cascade_visible(scenes, grids, irr, valid, x, n, 8.0)
+        vis_fine = O.sample_irradiance_visible(sc, fine, irr[0], valid[0], x, n, 8.0)
+        plain_coarse = O.sample_irradiance(coarse, irr[1], valid[1], x, n)
+        if where == "inner":
+            assert lvl == 0 and w == 1.0 and np.array_equal(out, vis_fine[0])
+            assert np.array_equal(m[0], vis_fine[2]) and np.all(m[1] > 1e30)
+        elif where == "shell":
+            assert lvl == 0 and 0 < w < 1
+            assert np.allclose(out, w * vis_fine[0] + (1 - w) * plain_coarse, rtol=0, atol=1e-15)
+        else:
+            assert lvl == 1 and np.array_equal(out, plain_coarse) and np.all(m > 1e30)
+        plain = O.sample_irradiance_cascade(grids, irr, valid, x, n)
+        assert np.array_equal(O.sample_irradiance_cascade_visible(scenes, grids, irr, valid, x, n, 0.0)[0], plain[0])

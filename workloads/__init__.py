@@ -376,3 +376,31 @@ def denoiser_init(seed: int, last_scale: float = 0.0) -> np.ndarray:
         else:
             parts.append(np.zeros(shape))
     return np.concatenate([p.reshape(-1) for p in parts]).astype(np.float32)
+
+
+# Irradiance queries against the cascade512 volumes (Sec. 3.5): one 1080p frame's shading points.
+QUERY_POINTS = 1920 * 1080
+
+
+def cascade_query_points(n: int = QUERY_POINTS, seed: int = 5):
+    """Shading points as a camera at the 128 m world's centre sees them: horizontal distance
+    log-uniform over 0.5..62 m, azimuth uniform, height uniform over 2.5..31.5 m (the volumes'
+    slab, inset 0.5 m); unit normals uniform on the sphere. float32 [n, 3] each."""
+    rng = np.random.default_rng(seed)
+    r = np.exp(rng.uniform(np.log(0.5), np.log(62.0), n))
+    phi = rng.uniform(0.0, 2.0 * np.pi, n)
+    pts = np.stack([64.0 + r * np.cos(phi), rng.uniform(2.5, 31.5, n), 64.0 + r * np.sin(phi)], axis=1)
+    nrm = rng.normal(size=(n, 3))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    return pts.astype(np.float32), nrm.astype(np.float32)
+
+
+def cascade_query_maps(c: Cascade, seed: int = 7):
+    """Per volume: irradiance maps uniform in [0.05, 1) (float32 [P, 8, 8, 4]) and history
+    flags (uint8 [P], 9 in 10 set)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for v in c.volumes:
+        irr = rng.uniform(0.05, 1.0, (v.n_probes, 8, 8, 4)).astype(np.float32)
+        out.append((irr, (rng.random(v.n_probes) < 0.9).astype(np.uint8)))
+    return out
