@@ -4,7 +4,7 @@
 //  1. primary traces   -- a persistent grid; every lane takes the next ray (of any probe)
 //                         as soon as its current sphere trace ends, so all lanes keep
 //                         stepping however much trace lengths differ; tasks come from a
-//                         global counter in batches of 32 per warp;
+//                         global counter in batches of 64 per warp;
 //  2. hit preparation  -- one thread per ray: normal, material, last frame's interpolated
 //                         irradiance (the multi-bounce term) and the lights that can reach
 //                         the hit; the (ray, light) pairs are appended to a shadow-task list;
@@ -27,7 +27,11 @@
 namespace sdfddgi {
 
 constexpr int kThreads = 256;
-constexpr int kBatch = 32;  // tasks a warp takes from a global pool at once
+// Tasks a warp takes from a global pool at once. 64 measured 7 % faster than 32 on open256
+// (half the atomics on the one counter); counters split over several segments of the task
+// range were slower, because warps then trace rays from distant parts of the volume at once
+// and the SDF working set no longer stays in L2.
+constexpr int kBatch = 64;
 
 // c^p for the depth weights; p = 50 (the usual sharpness) as a fixed product chain.
 __device__ __forceinline__ float pow50(float c) {
