@@ -13,9 +13,11 @@
 // Precision (template parameter): fp32 operands split as hi + lo tf32 and multiplied as
 // hi*hi + hi*lo + lo*hi (kind::tf32, fp32 accumulation; products carry about 21 significant
 // bits), or the precision form: one bf16 x bf16 product (kind::f16, fp32 accumulation).
-// One elected thread issues the MMAs; chunks alternate between two shared-memory stages,
-// each guarded by mbarriers (bulk-copy arrival and MMA completion). Every wait is bounded:
-// on timeout the kernel records an error bit, skips the rest and releases its tensor memory.
+// The K loop is warp-specialized over a ring of shared-memory stages: one lane copies the
+// weight images in, four warps build the B operands, one lane issues the MMAs, with mbarriers
+// between them (weights in, B built, MMAs done) and no CTA-wide barrier. Every wait is
+// bounded: on a timeout the kernel records an error bit that stops the other roles and CTAs,
+// waits for its own copies and MMAs in flight, and releases its tensor memory.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -33,6 +35,7 @@ constexpr int kN = kG * kCh;                  // 96 accumulator columns per tile
 constexpr int kChunk = 16;                    // rays per K chunk
 constexpr int kThreads = 256;
 constexpr int kTmemCols = 256;                // 2 x 96 used
+constexpr int kStagesTf32 = 2;                // stages of the tf32 ring (88 KiB: two CTAs per SM)
 
 // Operand format: 4-byte tf32 in hi + lo parts, or one 2-byte bf16 part. Operands are
 // K-major without swizzle: 8 x 16-byte core matrices, adjacent along K 128 B apart,
@@ -54,6 +57,18 @@ struct Fmt {
     __host__ __device__ static constexpr uint32_t offset(int row, int k) {
         return (uint32_t)((row >> 3) * kSbo + ((k * kElem) >> 4) * 128 + (row & 7) * 16 + ((k * kElem) & 15));
     }
+};
+
+// Operand stages of the gather's ring (44 KiB each for tf32, 11 KiB for bf16).
+template <bool BF16>
+struct Stages {
+    static constexpr int value = BF16 ? 4 : kStagesTf32;
+};
+// Threads that build the B operand: one 16-byte core-matrix row of every channel of one
+// probe and part per chunk.
+template <bool BF16>
+struct Producers {
+    static constexpr int value = kG * (kChunk / (16 / Fmt<BF16>::kElem)) * Fmt<BF16>::kParts;
 };
 
 template <bool BF16>
@@ -111,12 +126,13 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
     using namespace tc;
     using F = Fmt<BF16>;
     constexpr int kABytes = F::kABytes, kBBytes = F::kBBytes, kBPart = F::kBPart, kTilePart = F::kTilePart;
+    constexpr int kStages = Stages<BF16>::value;
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sA[2] = {smem, smem + kABytes};
-    unsigned char* sB[2] = {smem + 2 * kABytes, smem + 2 * kABytes + kBBytes};
-    __shared__ __align__(8) uint64_t bar_load[2], bar_mma[2], bar_prev;
+    auto sA = [&](int s) { return smem + (size_t)s * kABytes; };
+    auto sB = [&](int s) { return smem + (size_t)kStages * kABytes + (size_t)s * kBBytes; };
+    __shared__ __align__(8) uint64_t bar_full_a[kStages], bar_full_b[kStages], bar_empty[kStages], bar_prev;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_fail;
+    __shared__ volatile int s_fail;
     __shared__ float s_hyst[kG];
     __shared__ uint32_t s_flags[kG];
 
@@ -137,10 +153,11 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&bar_load[0], 1);
-        mbar_init(&bar_load[1], 1);
-        mbar_init(&bar_mma[0], 1);
-        mbar_init(&bar_mma[1], 1);
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&bar_full_a[s], 1);
+            mbar_init(&bar_full_b[s], Producers<BF16>::value);
+            mbar_init(&bar_empty[s], 1);
+        }
         mbar_init(&bar_prev, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -155,49 +172,112 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
 
-    // ---- K loop over 16-ray chunks, two stages (88 KiB: two CTAs per SM). Each thread owns
-    // one (probe, ray) element of every chunk's B operand and loads the next chunk's value
-    // into a register one iteration ahead; the weight image of chunk c+1 is copied into the
-    // other stage as soon as the MMAs of chunk c-1 that read it are done. Both latencies
-    // thus overlap the current chunk's operand build and MMAs.
-    static_assert(kG * kChunk == kThreads, "one B element per thread and chunk");
-    const int g_own = tid / kChunk, k_own = tid % kChunk;
-    const bool own_live = g_own < ng;
-    const float4* own_src = P.ray_val + (size_t)(p0 + (own_live ? g_own : 0)) * P.R + k_own;
-    float4 v_next = own_live ? own_src[0] : make_float4(0.f, 0.f, 0.f, 0.f);
-    int last_copy = -1;  // thread 0: the last chunk whose weight copy it issued
-    if (tid == 0 && n_chunks > 0) {
-        bulk_copy_g2s(sA[0], P.wimage, kABytes, &bar_load[0]);
-        last_copy = 0;
-    }
-    for (int c = 0; c < n_chunks; ++c) {
-        const int s = c & 1;
-        const float4 v = v_next;
-        if (own_live && c + 1 < n_chunks) v_next = own_src[(size_t)(c + 1) * kChunk];
-        __syncthreads();  // the MMAs of chunk c-2 (stage s) are done: waited by thread 0 last iteration
-        if (s_fail) break;
-        {
-            const float one = own_live ? 1.f : 0.f;
-            const float ch[kCh] = {v.x, v.y, v.z, v.w, v.w * v.w, one};
+    // ---- K loop over 16-ray chunks through a ring of kStages operand stages, in three roles
+    // and without a CTA-wide barrier:
+    //  the copier (warp 4, lane 0) brings chunk c's weight image into stage c % kStages with one
+    //    bulk copy as soon as the MMAs of chunk c - kStages are done (full_a counts the bytes);
+    //  producers (the first kProducers threads) then build chunk c's B operand from the rays'
+    //    values, split as the format asks, and arrive on full_b; each loads its values of the
+    //    next chunk into registers one chunk ahead;
+    //  the issuer (warp 5, lane 0) issues chunk c's MMAs once both operands are in and commits
+    //    them to empty[c % kStages], which frees the stage for both.
+    // Copies thus run up to kStages - 1 chunks ahead of the MMAs.
+    constexpr int kVec = 16 / F::kElem;                   // K values per 16-byte core-matrix row
+    constexpr int kQuads = kChunk / kVec;                 // such rows per operand row and chunk
+    constexpr int kProducers = kG * kQuads * F::kParts;   // one (probe, rows, part) each
+    static_assert(kProducers <= 128, "producers fit in warps 0..3");
+    const uint32_t* fail_word = &P.counters[kFailWord];
+    auto give_up = [&]() {
+        atomicOr(&P.counters[kFailWord], 2u);  // the other roles and CTAs stop waiting too
+        s_fail = 1;
+    };
+    if (tid < kProducers) {
+        const int g = tid % kG, kq = (tid / kG) % kQuads, part = tid / (kG * kQuads);
+        const bool live = g < ng;
+        const float one = live ? 1.f : 0.f;
+        const float4* src = P.ray_val + (size_t)(p0 + (live ? g : 0)) * P.R + kq * kVec;
+        float4 nxt[kVec];  // the next chunk's values, loaded one chunk ahead
 #pragma unroll
-            for (int q = 0; q < kCh; ++q) {
-                const uint32_t off = F::offset(g_own * kCh + q, k_own);
-                if constexpr (BF16) {
-                    put<true>(sB[s], off, ch[q]);
-                } else {
-                    const float hi = to_tf32(ch[q]), lo = to_tf32(ch[q] - hi);
-                    put<false>(sB[s], off, hi);
-                    put<false>(sB[s] + kBPart, off, lo);
+        for (int j = 0; j < kVec; ++j) nxt[j] = live ? src[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c = 0; c < n_chunks; ++c) {
+            const int s = c % kStages;
+            float4 cur[kVec];
+#pragma unroll
+            for (int j = 0; j < kVec; ++j) cur[j] = nxt[j];
+            if (live && c + 1 < n_chunks) {
+#pragma unroll
+                for (int j = 0; j < kVec; ++j) nxt[j] = src[(size_t)(c + 1) * kChunk + j];
+            }
+            {  // the stage is free once its weights are in (the copier waited for the MMAs of
+               // chunk c - kStages first); one lane of the warp waits, the others take its answer
+                int ok = 1;
+                if (lane == 0) ok = mbar_wait(&bar_full_a[s], (c / kStages) & 1, fail_word);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    if (lane == 0) give_up();
+                    break;
                 }
             }
+            unsigned char* dst = sB(s) + part * kBPart;
+#pragma unroll
+            for (int q = 0; q < kCh; ++q) {  // the channel is a compile-time index: no divergence
+                float x[kVec];
+#pragma unroll
+                for (int j = 0; j < kVec; ++j) {
+                    const float4 v = cur[j];
+                    x[j] = q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : q == 3 ? v.w : q == 4 ? v.w * v.w : one;
+                }
+                uint4 w;
+                if constexpr (BF16) {
+                    uint32_t h[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const __nv_bfloat162 b2 = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+                        h[j] = *reinterpret_cast<const uint32_t*>(&b2);
+                    }
+                    w = make_uint4(h[0], h[1], h[2], h[3]);
+                } else {
+                    uint32_t h[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float hi = to_tf32(x[j]);
+                        h[j] = __float_as_uint(part ? to_tf32(x[j] - hi) : hi);
+                    }
+                    w = make_uint4(h[0], h[1], h[2], h[3]);
+                }
+                *reinterpret_cast<uint4*>(dst + F::offset(g * kCh + q, kq * kVec)) = w;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_full_b[s])) : "memory");
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
-        if (!mbar_wait(&bar_load[s], (c >> 1) & 1, &P.counters[kFailWord])) s_fail = 1;
-        __syncthreads();
-        if (s_fail) break;
-        if (tid == 0) {
+    } else if (warp == 4 && lane == 0) {
+        int copied = 0;  // chunks whose weight copy was issued
+        for (int c = 0; c < n_chunks && !s_fail; ++c) {
+            const int s = c % kStages;
+            if (c >= kStages && !mbar_wait(&bar_empty[s], ((c / kStages) - 1) & 1, fail_word)) {
+                give_up();
+                break;
+            }
+            bulk_copy_g2s(sA(s), reinterpret_cast<const unsigned char*>(P.wimage) + (size_t)c * kABytes, kABytes,
+                          &bar_full_a[s]);
+            copied = c + 1;
+        }
+        // no copy of this CTA may still be writing its shared memory when the stages are
+        // reused or the CTA ends (bounded, and not cut short by the failure bit)
+        const uint32_t no_abort = 0;
+        for (int c = max(0, copied - kStages); c < copied; ++c)
+            mbar_wait(&bar_full_a[c % kStages], (c / kStages) & 1, &no_abort);
+    } else if (warp == 5 && lane == 0) {
+        int committed = 0;  // chunks whose MMAs were committed
+        for (int c = 0; c < n_chunks && !s_fail; ++c) {
+            const int s = c % kStages;
+            const uint32_t ph = (c / kStages) & 1;
+            if (!mbar_wait(&bar_full_a[s], ph, fail_word) || !mbar_wait(&bar_full_b[s], ph, fail_word)) {
+                give_up();
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(sA[s]), b0 = smem_u32(sB[s]);
+            const uint32_t a0 = smem_u32(sA(s)), b0 = smem_u32(sB(s));
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
 #pragma unroll
@@ -214,28 +294,17 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
                     }
                 }
             }
-            mma_commit(&bar_mma[s]);
-            // the weights of chunk c+1 into stage s^1, free once the MMAs of chunk c-1 are done
-            if (c + 1 < n_chunks) {
-                if (c >= 1 && !mbar_wait(&bar_mma[s ^ 1], ((c - 1) >> 1) & 1, &P.counters[kFailWord])) s_fail = 1;
-                if (!s_fail) {
-                    bulk_copy_g2s(sA[s ^ 1], reinterpret_cast<const unsigned char*>(P.wimage) + (size_t)(c + 1) * kABytes,
-                                  kABytes, &bar_load[s ^ 1]);
-                    last_copy = c + 1;
-                }
-            }
+            mma_commit(&bar_empty[s]);
+            committed = c + 1;
         }
-    }
-    // after a failure, no copy of this CTA may still be writing its shared memory (bounded,
-    // and not cut short by the launch's failure bit)
-    if (s_fail && tid == 0 && last_copy >= 0) {
-        const uint32_t no_abort = 0;
-        mbar_wait(&bar_load[last_copy & 1], (last_copy >> 1) & 1, &no_abort);
-    }
-    // ---- all MMAs complete
-    if (!s_fail) {
-        for (int c = max(0, n_chunks - 2); c < n_chunks; ++c)
-            if (!mbar_wait(&bar_mma[c & 1], (c >> 1) & 1, &P.counters[kFailWord])) s_fail = 1;
+        // every committed MMA complete before the accumulators are read or released (bounded,
+        // not cut short: a commit covers all earlier MMAs of this thread)
+        if (committed > 0) {
+            const uint32_t no_abort = 0;
+            const int c = committed - 1;
+            if (!mbar_wait(&bar_empty[c % kStages], (c / kStages) & 1, s_fail ? &no_abort : fail_word)) give_up();
+        }
+        if (committed < n_chunks && !s_fail) give_up();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -342,7 +411,7 @@ template <bool BF16>
 static size_t tc_smem() {
     using F = tc::Fmt<BF16>;
     const size_t epilogue = (size_t)tc::kG * (kIrrT * kIrrT * sizeof(float4) + kDepT * kDepT * sizeof(float2));
-    return std::max<size_t>(2 * (F::kABytes + F::kBBytes), epilogue);
+    return std::max<size_t>((size_t)tc::Stages<BF16>::value * (F::kABytes + F::kBBytes), epilogue);
 }
 
 cudaError_t prepare_gather_tc() {

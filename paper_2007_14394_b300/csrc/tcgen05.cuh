@@ -1,6 +1,6 @@
 // tcgen05.cuh -- inline-PTX helpers for the 5th-generation tensor cores (tcgen05), the
 // bulk-copy engine and shared-memory mbarriers, shared by the library's tensor-core kernels.
-// Every wait is bounded (kSpinLimit polls, or earlier once a failure bit is set).
+// Every wait is bounded (200 ms, or earlier once a failure bit is set).
 #pragma once
 
 #include <stdint.h>
@@ -42,12 +42,39 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait (non-blocking polls): false after kSpinLimit polls, or early once any CTA
-// of the launch has recorded a failure in *abort.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t kWaitNs = 200000000ull;  // a bounded wait gives up after 200 ms
+
+// Bounded wait: try_wait suspends the thread in hardware until the phase completes or a short
+// time-out passes, so that waiting threads take no issue slots from the working ones. False
+// after kWaitNs (or kSpinLimit tries), or early once any CTA of the launch has recorded a
+// failure in *abort.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const uint32_t* abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
     for (uint32_t i = 0; i < kSpinLimit; ++i) {
-        if (mbar_test_wait(bar, parity)) return true;
-        if ((i & 4095u) == 4095u && (*reinterpret_cast<const volatile uint32_t*>(abort) & 2u)) return false;
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63u) == 63u) {
+            if (*reinterpret_cast<const volatile uint32_t*>(abort) & 2u) return false;
+            if (global_ns() - t0 > kWaitNs) return false;
+        }
     }
     return false;
 }
