@@ -72,6 +72,10 @@ enum { SDFDDGI_STAGE_EVENTS = 6 };
  * binary16 SDF (upload_sdf dtype SDFDDGI_F16; stepping stays float32) for the full
  * precision form. */
 enum { SDFDDGI_FLAG_BLEND_BF16 = 1u };
+/* For tests of the failure detection only: the tensor-core gather leaves the first chunk's
+ * weight copy out, so that its bounded waits run out (after about 0.2 s). The update then
+ * reports SDFDDGI_ERR_TIMEOUT through sdfddgi_volume_status, and its maps are not valid. */
+enum { SDFDDGI_FLAG_TEST_GATHER_STALL = 1u << 30 };
 
 /* Octahedral map sizes (Sec. 3.3: octahedral mapping into the probe atlas):
  * irradiance 6x6 interior texels + 1-texel border = 8x8, RGBA float32 per texel
@@ -113,7 +117,7 @@ typedef struct {
     float normal_bias;        /* shadow-ray origin offset along the normal, voxels (>= 0) */
     uint32_t seed;            /* seed of the per-frame ray rotation */
     uint32_t volume_id;       /* distinguishes rotations of volumes sharing a seed */
-    uint32_t flags;           /* 0, or SDFDDGI_FLAG_BLEND_BF16 */
+    uint32_t flags;           /* 0, or SDFDDGI_FLAG_BLEND_BF16 (SDFDDGI_FLAG_TEST_GATHER_STALL: tests) */
 } sdfddgi_volume_desc;
 
 /* Per-ray record of one update (32 bytes), written only when requested:

@@ -21,6 +21,7 @@ F32, F16 = 0, 1
 LIGHT_DIRECTIONAL, LIGHT_POINT = 0, 1
 PROBE_ACTIVE, PROBE_REJECT_HISTORY = 1, 2
 FLAG_BLEND_BF16 = 1  # volume flag: the precision form of the gather (bf16 tensor-core products)
+FLAG_TEST_GATHER_STALL = 1 << 30  # volume flag for failure tests: the gather's bounded waits run out
 MAX_LIGHTS, MAX_RAYS, MAX_STEPS = 32, 1024, 65535
 IRR_SIDE, DEPTH_SIDE = 8, 16
 EVENT_LEFT_VOLUME, EVENT_HIT, EVENT_PAST_LIMIT, EVENT_EXHAUSTED, EVENT_NO_RAY = 0, 1, 2, 3, 255

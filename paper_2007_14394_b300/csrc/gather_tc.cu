@@ -251,22 +251,24 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_full_b[s])) : "memory");
         }
     } else if (warp == 4 && lane == 0) {
-        int copied = 0;  // chunks whose weight copy was issued
+        int last[kStages];  // per stage, the last chunk whose weight copy was issued into it
+        for (int s = 0; s < kStages; ++s) last[s] = -1;
         for (int c = 0; c < n_chunks && !s_fail; ++c) {
             const int s = c % kStages;
             if (c >= kStages && !mbar_wait(&bar_empty[s], ((c / kStages) - 1) & 1, fail_word)) {
                 give_up();
                 break;
             }
+            if (c == 0 && P.test_stall) continue;  // failure tests: chunk 0's weights never arrive
             bulk_copy_g2s(sA(s), reinterpret_cast<const unsigned char*>(P.wimage) + (size_t)c * kABytes, kABytes,
                           &bar_full_a[s]);
-            copied = c + 1;
+            last[s] = c;
         }
         // no copy of this CTA may still be writing its shared memory when the stages are
         // reused or the CTA ends (bounded, and not cut short by the failure bit)
         const uint32_t no_abort = 0;
-        for (int c = max(0, copied - kStages); c < copied; ++c)
-            mbar_wait(&bar_full_a[c % kStages], (c / kStages) & 1, &no_abort);
+        for (int s = 0; s < kStages; ++s)
+            if (last[s] >= 0) mbar_wait(&bar_full_a[s], (last[s] / kStages) & 1, &no_abort);
     } else if (warp == 5 && lane == 0) {
         int committed = 0;  // chunks whose MMAs were committed
         for (int c = 0; c < n_chunks && !s_fail; ++c) {
