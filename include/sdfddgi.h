@@ -72,6 +72,17 @@ enum { SDFDDGI_STAGE_EVENTS = 6 };
  * binary16 SDF (upload_sdf dtype SDFDDGI_F16; stepping stays float32) for the full
  * precision form. */
 enum { SDFDDGI_FLAG_BLEND_BF16 = 1u };
+/* RELAXED_PRIMARY, RELAXED_SHADOW -- the primary or the shadow traces take over-relaxed
+ * steps (the paper's accelerated sphere tracing, Sec. 3.3, after enhanced sphere tracing): a
+ * step is SDFDDGI_RELAX_OMEGA times the sampled distance; when the new sample's sphere and
+ * the previous one's do not overlap (sdf + previous sdf < step), or the step left the volume
+ * box, the trace returns to the previous point's plain step and stays plain for the rest of
+ * the ray (the discarded sample counts toward max_steps). Hits are found with the same eps
+ * test; the paths differ from plain sphere tracing, so hit distances differ within about eps.
+ * Relaxation pays for rays that run far through free space (shadow rays toward the lights);
+ * rays that meet a surface within a few steps pay a discarded step instead. */
+enum { SDFDDGI_FLAG_RELAXED_SHADOW = 2u, SDFDDGI_FLAG_RELAXED_PRIMARY = 4u };
+#define SDFDDGI_RELAX_OMEGA 1.6f
 /* For tests of the failure detection only: the tensor-core gather leaves the first chunk's
  * weight copy out, so that its bounded waits run out (after about 0.2 s). The update then
  * reports SDFDDGI_ERR_TIMEOUT through sdfddgi_volume_status, and its maps are not valid. */
@@ -117,7 +128,8 @@ typedef struct {
     float normal_bias;        /* shadow-ray origin offset along the normal, voxels (>= 0) */
     uint32_t seed;            /* seed of the per-frame ray rotation */
     uint32_t volume_id;       /* distinguishes rotations of volumes sharing a seed */
-    uint32_t flags;           /* 0, or SDFDDGI_FLAG_BLEND_BF16 (SDFDDGI_FLAG_TEST_GATHER_STALL: tests) */
+    uint32_t flags;           /* 0, or SDFDDGI_FLAG_BLEND_BF16 | SDFDDGI_FLAG_RELAXED_SHADOW |
+                                 SDFDDGI_FLAG_RELAXED_PRIMARY (SDFDDGI_FLAG_TEST_GATHER_STALL: tests) */
 } sdfddgi_volume_desc;
 
 /* Per-ray record of one update (32 bytes), written only when requested:

@@ -60,7 +60,8 @@ class Grid(C.Structure):
                 ("origin", C.c_double * 3), ("spacing", C.c_double * 3),
                 ("max_steps", C.c_int32), ("depth_exponent", C.c_int32),
                 ("eps_vox", C.c_double), ("tmax_vox", C.c_double), ("hysteresis", C.c_double),
-                ("k_bounce", C.c_double), ("bias_vox", C.c_double), ("sky", C.c_double * 3)]
+                ("k_bounce", C.c_double), ("bias_vox", C.c_double), ("sky", C.c_double * 3),
+                ("omega_primary", C.c_double), ("omega_shadow", C.c_double)]
 
 
 RAY_DTYPE = np.dtype([("t", "f8"), ("L", "f8", (3,)), ("margin_primary", "f8"),
@@ -96,6 +97,9 @@ def _load():
             lib.oracle_trace.argtypes = [C.POINTER(Volume), dp, dp, C.c_double, C.c_double, C.c_int32,
                                          dp, C.POINTER(C.c_int32), dp]
             lib.oracle_trace.restype = C.c_int32
+            lib.oracle_trace_relaxed.argtypes = [C.POINTER(Volume), dp, dp, C.c_double, C.c_double, C.c_int32,
+                                                 C.c_double, dp, C.POINTER(C.c_int32), dp]
+            lib.oracle_trace_relaxed.restype = C.c_int32
             lib.oracle_border.argtypes = [dp, C.c_int32, C.c_int32]
             lib.oracle_sample_irradiance.argtypes = [C.POINTER(Grid), dp, C.c_void_p, dp, dp, dp]
             lib.oracle_shade.argtypes = [C.POINTER(Volume), C.POINTER(Grid), C.POINTER(Light), C.c_int32,
@@ -191,11 +195,13 @@ def make_lights(lights) -> tuple:
 
 
 def make_grid(dims, origin, spacing, rays, max_steps, eps_vox, tmax_vox, hysteresis,
-              depth_exponent=50, k_bounce=1.0, bias_vox=1.0, sky=(0.0, 0.0, 0.0)) -> Grid:
+              depth_exponent=50, k_bounce=1.0, bias_vox=1.0, sky=(0.0, 0.0, 0.0), omega_primary=1.0,
+              omega_shadow=1.0) -> Grid:
     return Grid((C.c_int32 * 3)(*[int(x) for x in dims]), int(rays),
                 (C.c_double * 3)(*[float(x) for x in origin]), (C.c_double * 3)(*[float(x) for x in spacing]),
                 int(max_steps), int(depth_exponent), float(eps_vox), float(tmax_vox), float(hysteresis),
-                float(k_bounce), float(bias_vox), (C.c_double * 3)(*[float(x) for x in sky]))
+                float(k_bounce), float(bias_vox), (C.c_double * 3)(*[float(x) for x in sky]), float(omega_primary),
+                float(omega_shadow))
 
 
 # ----------------------------------------------------------------- elementary functions
@@ -231,13 +237,18 @@ def set_t_tolerance(tol_vox: float = 1e-3, factor: float = 8.0) -> None:
     _load().oracle_set_t_tolerance(float(tol_vox), float(factor))
 
 
-def trace(scene: OracleScene, o, d, eps_vox: float, tlimit: float, max_steps: int):
-    """Returns (event, t, steps, margin_vox)."""
+def trace(scene: OracleScene, o, d, eps_vox: float, tlimit: float, max_steps: int, omega: float = 1.0):
+    """Returns (event, t, steps, margin_vox); omega > 1: the over-relaxed trace."""
     t = C.c_double()
     m = C.c_double()
     s = C.c_int32()
-    cls = _load().oracle_trace(C.byref(scene.vol), _dp(_vec(o)), _dp(_vec(d)), float(eps_vox),
-                               float(tlimit), int(max_steps), C.byref(t), C.byref(s), C.byref(m))
+    if omega > 1.0:
+        cls = _load().oracle_trace_relaxed(C.byref(scene.vol), _dp(_vec(o)), _dp(_vec(d)), float(eps_vox),
+                                           float(tlimit), int(max_steps), float(omega), C.byref(t), C.byref(s),
+                                           C.byref(m))
+    else:
+        cls = _load().oracle_trace(C.byref(scene.vol), _dp(_vec(o)), _dp(_vec(d)), float(eps_vox),
+                                   float(tlimit), int(max_steps), C.byref(t), C.byref(s), C.byref(m))
     return int(cls), t.value, s.value, m.value
 
 

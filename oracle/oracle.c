@@ -259,20 +259,36 @@ static double sdf_slope(const or_volume* vol, const double p[3], const double d[
  * outcome. With fe >= 0 the path follows the given event (fe) and step count (fs)
  * instead of its own tests; every test so overridden increments *forced, and
  * *hard as well when its margin was at least delta. *cond receives the first-order
- * float32 rounding bound of the returned t (voxels), see oracle_set_t_tolerance. */
-static int32_t trace_path(const or_volume* vol, const double o[3], const double d[3], double eps_vox,
-                          double tlimit, int32_t max_steps, int32_t fe, int32_t fs, double* t_out,
-                          int32_t* steps_out, double* margin_vox, int32_t* forced, int32_t* hard, double* cond) {
+ * float32 rounding bound of the returned t (voxels), see oracle_set_t_tolerance.
+ *
+ * With omega > 1 the steps are over-relaxed (the accelerated sphere tracing of Sec. 3.3,
+ * after enhanced sphere tracing): a step is omega times the sampled distance, and a sample
+ * whose sphere does not overlap the previous sample's (sdf + previous sdf < step), or a step
+ * that left the volume box, is discarded: the trace returns to the previous point plus its
+ * sampled distance (the plain step) and stays plain (omega = 1) from there. The discarded
+ * sample counts as a step.
+ * Every such overlap test that lies within delta of the other outcome is "in band"; bit j of
+ * `flip` reverses the j-th in-band test on the path (counted in *forced), and *n_inband
+ * receives the number of in-band tests met. */
+static int32_t trace_relaxed(const or_volume* vol, const double o[3], const double d[3], double eps_vox,
+                             double tlimit, int32_t max_steps, double omega, int32_t fe, int32_t fs, uint32_t flip,
+                             int32_t* n_inband, double* t_out, int32_t* steps_out, double* margin_vox,
+                             int32_t* forced, int32_t* hard, double* cond) {
     const double h = vol->h, eps = eps_vox * h, band = g_delta_vox * h, u32 = ldexp(1.0, -24);
     const double lo[3] = {vol->origin[0], vol->origin[1], vol->origin[2]};
     const double hi[3] = {vol->origin[0] + vol->nx * h, vol->origin[1] + vol->ny * h,
                           vol->origin[2] + vol->nz * h};
     double t = 0.0, margin = HUGE_MARGIN, dt = 0.0;
+    double w = omega > 1.0 ? omega : 1.0;  /* the current relaxation factor */
+    double prev_r = 0.0, step = 0.0;        /* the previous sample's distance and the last step */
+    double dt_prev = 0.0, slope_prev = 0.0; /* t's rounding bound and the slope at the previous point */
+    int32_t inband = 0;
 #define DECIDE(natural, wanted_if_forced, m)                      \
     ((fe < 0) ? (natural) : ((wanted_if_forced) != (natural)      \
                                  ? (++*forced, *hard += (m) >= band, (wanted_if_forced)) \
                                  : (natural)))
     *cond = 0.0;
+    if (n_inband) *n_inband = 0;
     for (int32_t s = 0; s < max_steps; ++s) {
         double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
         int outside = 0;
@@ -283,13 +299,41 @@ static int32_t trace_path(const or_volume* vol, const double o[3], const double 
             pmax = fmax(pmax, fmax(fabs(p[a]), fabs(p[a] - lo[a])));
         }
         margin = fmin(margin, m_out);
-        if (DECIDE(outside, fe == OR_LEFT_VOLUME && s == fs, m_out)) {
+        if (w > 1.0) { /* over-relaxed: a step that left the box failed (in band: either way) */
+            if (m_out < band) {
+                if ((flip >> inband) & 1u) {
+                    outside = !outside;
+                    ++*forced;
+                }
+                ++inband;
+            }
+        } else if (DECIDE(outside, fe == OR_LEFT_VOLUME && s == fs, m_out)) {
             *t_out = tlimit;
             *steps_out = s;
             *margin_vox = margin / h;
+            if (n_inband) *n_inband = inband;
             return OR_LEFT_VOLUME;
         }
-        double sd = oracle_sample_sdf(vol, p);
+        double sd = outside ? 0.0 : oracle_sample_sdf(vol, p);
+        if (w > 1.0) { /* over-relaxed: does this sample's sphere overlap the previous one's? */
+            const double m_sor = outside ? HUGE_MARGIN : fabs(sd + prev_r - step);
+            int back = outside || sd + prev_r < step;
+            margin = fmin(margin, m_sor);
+            if (m_sor < band) {
+                if ((flip >> inband) & 1u) {
+                    back = !back;
+                    ++*forced;
+                }
+                ++inband;
+            }
+            if (back) { /* discard the sample: the previous point's plain step instead */
+                dt = dt_prev * fabs(1.0 + slope_prev) + u32 * (2.0 * pmax + 2.0 * fabs(step) + 2.0 * h + t);
+                t = t - step + prev_r;
+                step = prev_r;
+                w = 1.0;
+                continue; /* the budget test of this step is the loop's own */
+            }
+        }
         double m_hit = fabs(sd - eps);
         margin = fmin(margin, m_hit);
         if (DECIDE(sd < eps, fe == OR_HIT && s == fs - 1, m_hit)) {
@@ -297,18 +341,25 @@ static int32_t trace_path(const or_volume* vol, const double o[3], const double 
             *steps_out = s + 1;
             *margin_vox = margin / h;
             *cond = dt / h;
+            if (n_inband) *n_inband = inband;
             return OR_HIT;
         }
         /* first-order propagation of a perturbation of t through this step, plus the
          * float32 rounding of this step's point, sample and sum */
-        dt = dt * fabs(1.0 + sdf_slope(vol, p, d)) + u32 * (2.0 * pmax + 2.0 * fabs(sd) + 2.0 * h + t);
-        t += sd;
+        const double slope = sdf_slope(vol, p, d);
+        dt_prev = dt;
+        slope_prev = slope;
+        dt = dt * fabs(1.0 + w * slope) + u32 * (2.0 * pmax + 2.0 * fabs(w * sd) + 2.0 * h + t);
+        prev_r = sd;
+        step = w * sd;
+        t += step;
         double m_lim = fabs(t - tlimit);
         margin = fmin(margin, m_lim);
         if (DECIDE(t > tlimit, fe == OR_PAST_LIMIT && s == fs - 1, m_lim)) {
             *t_out = tlimit;
             *steps_out = s + 1;
             *margin_vox = margin / h;
+            if (n_inband) *n_inband = inband;
             return OR_PAST_LIMIT;
         }
     }
@@ -321,7 +372,50 @@ static int32_t trace_path(const or_volume* vol, const double o[3], const double 
     *steps_out = max_steps;
     *margin_vox = margin / h;
     *cond = dt / h;
+    if (n_inband) *n_inband = inband;
     return OR_EXHAUSTED;
+}
+
+static int32_t trace_path(const or_volume* vol, const double o[3], const double d[3], double eps_vox,
+                          double tlimit, int32_t max_steps, int32_t fe, int32_t fs, double* t_out,
+                          int32_t* steps_out, double* margin_vox, int32_t* forced, int32_t* hard, double* cond) {
+    return trace_relaxed(vol, o, d, eps_vox, tlimit, max_steps, 1.0, fe, fs, 0u, NULL, t_out, steps_out, margin_vox,
+                         forced, hard, cond);
+}
+
+/* A path that follows the other side's event (fe) and step count (fs). Over-relaxed traces
+ * also try reversing their in-band overlap tests (those within delta of the other outcome),
+ * fewest reversals first, and take the first path whose forced tests are all in band. */
+static int32_t trace_follow(const or_volume* vol, const double o[3], const double d[3], double eps_vox,
+                            double tlimit, int32_t max_steps, double omega, int32_t fe, int32_t fs, int32_t n_inband,
+                            double* t_out, int32_t* steps_out, double* margin_vox, int32_t* forced, int32_t* hard,
+                            double* cond) {
+    int32_t f0 = 0, h0 = 0, nb;
+    int32_t ev = trace_relaxed(vol, o, d, eps_vox, tlimit, max_steps, omega, fe, fs, 0u, &nb, t_out, steps_out,
+                               margin_vox, &f0, &h0, cond);
+    const int32_t bits = n_inband < 6 ? n_inband : 6;
+    if (h0 > 0 && omega > 1.0 && bits > 0) {
+        for (int32_t k = 1; k <= bits; ++k)
+            for (uint32_t mask = 1; mask < (1u << bits); ++mask) {
+                if (__builtin_popcount(mask) != k) continue;
+                int32_t f1 = 0, h1 = 0;
+                double t1, m1, c1;
+                int32_t s1;
+                const int32_t e1 = trace_relaxed(vol, o, d, eps_vox, tlimit, max_steps, omega, fe, fs, mask, NULL, &t1,
+                                                 &s1, &m1, &f1, &h1, &c1);
+                if (h1 == 0) {
+                    *t_out = t1;
+                    *steps_out = s1;
+                    *margin_vox = m1;
+                    *cond = c1;
+                    *forced += f1;
+                    return e1;
+                }
+            }
+    }
+    *forced += f0;
+    *hard += h0;
+    return ev;
 }
 
 int32_t oracle_trace(const or_volume* vol, const double o[3], const double d[3],
@@ -331,6 +425,15 @@ int32_t oracle_trace(const or_volume* vol, const double o[3], const double d[3],
     double cond;
     return trace_path(vol, o, d, eps_vox, tlimit, max_steps, -1, 0, t_out, steps_out, margin_vox, &forced,
                       &hard, &cond);
+}
+
+int32_t oracle_trace_relaxed(const or_volume* vol, const double o[3], const double d[3], double eps_vox,
+                             double tlimit, int32_t max_steps, double omega, double* t_out, int32_t* steps_out,
+                             double* margin_vox) {
+    int32_t forced = 0, hard = 0;
+    double cond;
+    return trace_relaxed(vol, o, d, eps_vox, tlimit, max_steps, omega, -1, 0, 0u, NULL, t_out, steps_out, margin_vox,
+                         &forced, &hard, &cond);
 }
 
 static int is_miss(int32_t event) { return event == OR_LEFT_VOLUME || event == OR_PAST_LIMIT; }
@@ -623,8 +726,8 @@ static void shade_at(const or_volume* vol, const or_grid* g, const or_light* lig
             double ts;
             int32_t st, f0 = 0, h0 = 0;
             double c0;
-            int32_t ev = trace_path(vol, xs, ldir, g->eps_vox, tlimit, g->max_steps, -1, 0, &ts, &st, &m_sh,
-                                    &f0, &h0, &c0);
+            int32_t ev = trace_relaxed(vol, xs, ldir, g->eps_vox, tlimit, g->max_steps, g->omega_shadow, -1, 0, 0u, NULL,
+                                       &ts, &st, &m_sh, &f0, &h0, &c0);
             rec->traced_mask |= 1u << l;
             rec->shadow_steps += st;
             rec->margin_shadow = fmin(rec->margin_shadow, m_sh);
@@ -726,15 +829,16 @@ static void update_one_probe(const or_volume* vol, const or_grid* g, const or_li
         rec.margin_decision = HUGE_MARGIN;
         const or_force* fi = force ? &force[i] : NULL;
         double t;
-        rec.natural_event = trace_path(vol, o, d, g->eps_vox, tmax, g->max_steps, -1, 0, &t,
-                                       &rec.natural_steps, &rec.margin_primary, &rec.forced, &rec.hard,
-                                       &rec.t_cond);
+        int32_t n_inband = 0;
+        rec.natural_event = trace_relaxed(vol, o, d, g->eps_vox, tmax, g->max_steps, g->omega_primary, -1, 0, 0u, &n_inband,
+                                          &t, &rec.natural_steps, &rec.margin_primary, &rec.forced, &rec.hard,
+                                          &rec.t_cond);
         rec.event = rec.natural_event;
         rec.steps = rec.natural_steps;
         if (fi && (fi->event != rec.natural_event || fi->steps != rec.natural_steps)) {
             double m_unused;
-            rec.event = trace_path(vol, o, d, g->eps_vox, tmax, g->max_steps, fi->event, fi->steps, &t,
-                                   &rec.steps, &m_unused, &rec.forced, &rec.hard, &rec.t_cond);
+            rec.event = trace_follow(vol, o, d, g->eps_vox, tmax, g->max_steps, g->omega_primary, fi->event, fi->steps,
+                                     n_inband, &t, &rec.steps, &m_unused, &rec.forced, &rec.hard, &rec.t_cond);
         }
         rec.t_own = t;
         if (fi && !is_miss(rec.event)) {

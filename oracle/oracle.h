@@ -74,6 +74,8 @@ typedef struct {
     double k_bounce;           /* gain of the previous-frame (multi-bounce) term */
     double bias_vox;           /* shadow-ray origin offset along the normal, voxels */
     double sky[3];             /* radiance of rays that miss */
+    double omega_primary;      /* relaxation of the primary traces (1: plain sphere tracing) */
+    double omega_shadow;       /* relaxation of the shadow traces */
 } or_grid;
 
 /* Probe state: world position and flags (bit 0 active, bit 1 reject history). */
@@ -147,6 +149,13 @@ double oracle_sample_sdf(const or_volume* vol, const double p[3]);
 int32_t oracle_trace(const or_volume* vol, const double o[3], const double d[3],
                      double eps_vox, double tlimit, int32_t max_steps,
                      double* t, int32_t* steps, double* margin_vox);
+
+/* The same trace over-relaxed by omega > 1 (Sec. 3.3 accelerated sphere tracing): steps of
+ * omega * sdf; a sample whose sphere misses the previous sample's (sdf + previous sdf < step)
+ * is discarded for the previous point's plain step, and the rest of the ray is plain. */
+int32_t oracle_trace_relaxed(const or_volume* vol, const double o[3], const double d[3], double eps_vox,
+                             double tlimit, int32_t max_steps, double omega, double* t_out, int32_t* steps_out,
+                             double* margin_vox);
 /* Border fixup of one (n+2)x(n+2)xC map in place. */
 void oracle_border(double* map, int32_t n, int32_t channels);
 /* Interpolated normalised irradiance at world point x with unit normal nrm. */

@@ -21,6 +21,9 @@ F32, F16 = 0, 1
 LIGHT_DIRECTIONAL, LIGHT_POINT = 0, 1
 PROBE_ACTIVE, PROBE_REJECT_HISTORY = 1, 2
 FLAG_BLEND_BF16 = 1  # volume flag: the precision form of the gather (bf16 tensor-core products)
+FLAG_RELAXED_SHADOW = 2   # volume flag: over-relaxed shadow traces (RELAX_OMEGA)
+FLAG_RELAXED_PRIMARY = 4  # volume flag: over-relaxed primary traces
+RELAX_OMEGA = float(np.float32(1.6))  # the relaxation factor of FLAG_RELAXED_TRACE (float32 1.6)
 FLAG_TEST_GATHER_STALL = 1 << 30  # volume flag for failure tests: the gather's bounded waits run out
 MAX_LIGHTS, MAX_RAYS, MAX_STEPS = 32, 1024, 65535
 IRR_SIDE, DEPTH_SIDE = 8, 16

@@ -303,7 +303,8 @@ SDFDDGI_API int sdfddgi_create_volume(const sdfddgi_volume_desc* d, sdfddgi_scen
         return fail(SDFDDGI_ERR_INVALID_ARG, "create_volume: multibounce_k outside [0, 1]");
     if (!(d->normal_bias >= 0.f) || !std::isfinite(d->normal_bias))
         return fail(SDFDDGI_ERR_INVALID_ARG, "create_volume: normal_bias must be >= 0");
-    if (d->flags & ~(uint32_t)(SDFDDGI_FLAG_BLEND_BF16 | SDFDDGI_FLAG_TEST_GATHER_STALL))
+    if (d->flags & ~(uint32_t)(SDFDDGI_FLAG_BLEND_BF16 | SDFDDGI_FLAG_RELAXED_SHADOW | SDFDDGI_FLAG_RELAXED_PRIMARY |
+                               SDFDDGI_FLAG_TEST_GATHER_STALL))
         return fail(SDFDDGI_ERR_INVALID_ARG, "create_volume: unknown flags 0x%x", d->flags);
 
     sdfddgi_volume* v = new (std::nothrow) sdfddgi_volume();
@@ -420,6 +421,8 @@ int sdfddgi::volume_params(sdfddgi_volume* v, UpdateParams* out) {
     p.wimage = v->wimage;
     p.blend_bf16 = (d.flags & SDFDDGI_FLAG_BLEND_BF16) ? 1 : 0;
     p.test_stall = (d.flags & SDFDDGI_FLAG_TEST_GATHER_STALL) ? 1 : 0;
+    p.omega_primary = (d.flags & SDFDDGI_FLAG_RELAXED_PRIMARY) ? SDFDDGI_RELAX_OMEGA : 1.f;
+    p.omega_shadow = (d.flags & SDFDDGI_FLAG_RELAXED_SHADOW) ? SDFDDGI_RELAX_OMEGA : 1.f;
     return SDFDDGI_OK;
 }
 

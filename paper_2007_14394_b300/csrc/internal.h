@@ -116,6 +116,8 @@ struct UpdateParams {
     void* wimage;             // null, or wimage_bytes(R): the weights as the tensor-core gather's operand
     int blend_bf16;           // 1: the tensor-core gather multiplies bf16 x bf16 (the precision form)
     int test_stall;           // 1: the tensor-core gather leaves chunk 0's weight copy out (failure tests)
+    float omega_primary;      // relaxation factor of the primary traces (1: plain sphere tracing)
+    float omega_shadow;       // relaxation factor of the shadow traces
     const float* rot_dev;     // null, or the frame rotation in device memory (read instead of rot)
     Schedule sched;           // launch shapes (chosen by the autotuner for batches)
 };

@@ -53,18 +53,23 @@ struct TraceState {
     float3 o, d;
     float t, tlimit;
     float last;    // the previous sample's distance (scenes of primitives: bounds the next query)
+    float moved;   // how far the trace moved since that sample (scenes of primitives)
+    float prev_r;  // over-relaxed stepping: the previous sample's distance,
+    float step;    //   the last step taken,
+    float omega;   //   and the relaxation factor (1: plain sphere tracing)
     int s;
     uint32_t aux;  // task payload kept for the completion handler
 };
 
-// The SDF at p on a sphere trace. For a scene of primitives the query starts from twice the
-// last distance (the field is 1-Lipschitz and the step was that distance; the slack covers
-// float rounding), and falls back to a full query if nothing lies below that bound, so the
-// result is always the minimum over all primitives.
+// The SDF at p on a sphere trace. For a scene of primitives the query starts from the last
+// distance plus the distance moved since (the field is 1-Lipschitz; a plain step moved by the
+// last distance, so the bound is twice it; the slack covers float rounding), and falls back to
+// a full query if nothing lies below that bound, so the result is always the minimum over all
+// primitives.
 template <typename T>
 __device__ __forceinline__ float trace_sample(const VolumeView& v, TraceState& st, float3 p) {
     if constexpr (std::is_same<T, Analytic>::value) {
-        const float bound = st.last < INFINITY ? fmaf(2.002f, st.last, 1e-4f * v.h) : INFINITY;
+        const float bound = st.last < INFINITY ? fmaf(1.001f, st.last + st.moved, 1e-4f * v.h) : INFINITY;
         float sd = analytic_sdf(v, p, bound);
         if (!(sd < bound)) sd = analytic_sdf(v, p, INFINITY);
         st.last = sd;
@@ -74,26 +79,57 @@ __device__ __forceinline__ float trace_sample(const VolumeView& v, TraceState& s
     }
 }
 
-// Advances a sphere trace by one step, with the tests of sphere_trace() in device.cuh
-// in the same order (leave the box, hit, pass the limit, spend the budget). Returns the
-// event, or -1 while the trace continues; on an event *steps and *t_end receive the step
-// count and the recorded distance.
-template <typename T>
+// Advances a sphere trace by one step. The tests come in the order leave the box, hit, pass
+// the limit, spend the budget. Returns the event, or -1 while the trace continues; on an
+// event *steps and *t_end receive the step count and the recorded distance.
+// With omega > 1 the steps are over-relaxed (the paper's accelerated sphere tracing, Sec. 3.3,
+// after Keinert et al.'s enhanced sphere tracing): step omega * sdf; when the sphere of the new
+// sample and that of the previous one do not overlap (sdf + previous sdf < step), or when the
+// step left the volume box, the step may have passed a surface, so the trace goes back to the
+// previous point's plain step and stays plain (omega = 1) for the rest of the ray; the
+// discarded sample counts as a step.
+template <typename T, bool Relax>
 __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, float eps, int max_steps,
                                           int* steps, float* t_end) {
     const float3 p = fma3(st.t, st.d, st.o);
-    if (p.x < v.lo[0] || p.x > v.hi[0] || p.y < v.lo[1] || p.y > v.hi[1] || p.z < v.lo[2] || p.z > v.hi[2]) {
+    const bool outside =
+        p.x < v.lo[0] || p.x > v.hi[0] || p.y < v.lo[1] || p.y > v.hi[1] || p.z < v.lo[2] || p.z > v.hi[2];
+    if (outside && !(Relax && st.omega > 1.f)) {
         *steps = st.s;
         *t_end = st.tlimit;
         return kLeftVolume;
     }
-    const float sd = trace_sample<T>(v, st, p);
+    // a relaxed step that left the box failed like one whose spheres do not overlap
+    const float sd = outside ? 0.f : trace_sample<T>(v, st, p);
+    if constexpr (Relax) {
+        if (st.omega > 1.f && (outside || sd + st.prev_r < st.step)) {
+            const float back = st.prev_r - st.step;
+            st.t += back;
+            st.moved = -back;
+            st.step = st.prev_r;
+            st.omega = 1.f;
+            if (++st.s == max_steps) {
+                *steps = max_steps;
+                *t_end = st.t;
+                return kExhausted;
+            }
+            return -1;
+        }
+    }
     if (sd < eps) {
         *steps = st.s + 1;
         *t_end = st.t;
         return kHit;
     }
-    st.t += sd;
+    if constexpr (Relax) {
+        st.prev_r = sd;
+        st.step = st.omega * sd;
+        st.moved = st.step;
+        st.t += st.step;
+    } else {
+        st.moved = sd;
+        st.t += sd;
+    }
     if (st.t > st.tlimit) {
         *steps = st.s + 1;
         *t_end = st.tlimit;
@@ -112,9 +148,9 @@ __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, f
 // init(k, st) returns false for a task that needs no trace (it is then complete),
 // done(st, event, steps, t) consumes a finished trace. Every lane of the warp must
 // take part (full-warp votes).
-template <typename T, typename Init, typename Done>
+template <typename T, bool Relax, typename Init, typename Done>
 __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint32_t* counter, float eps,
-                                           int max_steps, uint32_t batch, Init init, Done done) {
+                                           int max_steps, float omega, uint32_t batch, Init init, Done done) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     uint32_t batch_next = 0, batch_end = 0;  // warp-uniform
@@ -141,6 +177,10 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
                     st.t = 0.f;
                     st.s = 0;
                     st.last = INFINITY;
+                    st.moved = 0.f;
+                    st.prev_r = 0.f;
+                    st.step = 0.f;
+                    st.omega = omega;
                     busy = true;
                 } else {
                     need = true;  // nothing to trace for this task: take another
@@ -152,7 +192,7 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
         if (busy) {
             int steps;
             float t_end;
-            const int ev = trace_step<T>(v, st, eps, max_steps, &steps, &t_end);
+            const int ev = trace_step<T, Relax>(v, st, eps, max_steps, &steps, &t_end);
             if (ev >= 0) {
                 done(st, ev, steps, t_end);
                 busy = false;
@@ -208,11 +248,11 @@ __device__ __forceinline__ float light_scale(const LightDev& li, float3 x, float
 }
 
 // ------------------------------------------------------------------ 1. primary traces
-template <typename T>
-__global__ void __launch_bounds__(kThreads) primary_kernel(const __grid_constant__ UpdateParams P) {
+template <typename T, bool Relax>
+__global__ void __launch_bounds__(kThreads, 8) primary_kernel(const __grid_constant__ UpdateParams P) {
     const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
-    trace_pool<T>(
-        P.vol, n, &P.counters[kPrimaryPool], P.eps_w, P.max_steps, pool_batch(P),
+    trace_pool<T, Relax>(
+        P.vol, n, &P.counters[kPrimaryPool], P.eps_w, P.max_steps, P.omega_primary, pool_batch(P),
         [&](uint32_t k, TraceState& st) {
             const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
             uint32_t flags;
@@ -334,11 +374,11 @@ __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant
 }
 
 // ------------------------------------------------------------------ 3. shadow traces
-template <typename T>
-__global__ void __launch_bounds__(kThreads) shadow_kernel(const __grid_constant__ UpdateParams P) {
+template <typename T, bool Relax>
+__global__ void __launch_bounds__(kThreads, 8) shadow_kernel(const __grid_constant__ UpdateParams P) {
     const uint32_t n = min(P.counters[kTaskCount], P.task_capacity);
-    trace_pool<T>(
-        P.vol, n, &P.counters[kShadowPool], P.eps_w, P.max_steps, pool_batch(P),
+    trace_pool<T, Relax>(
+        P.vol, n, &P.counters[kShadowPool], P.eps_w, P.max_steps, P.omega_shadow, pool_batch(P),
         [&](uint32_t j, TraceState& st) {
             const uint32_t tk = P.tasks[j];
             const uint32_t k = tk >> 5;
@@ -627,8 +667,8 @@ struct DeviceSetup {
     bool done = false;
     cudaError_t err = cudaSuccess;
     int sms = 0;
-    int occ_primary[3] = {};  // [float, __half, Analytic]
-    int occ_shadow[3] = {};
+    int occ_primary[2][3] = {};  // [plain, relaxed][float, __half, Analytic]
+    int occ_shadow[2][3] = {};
 };
 
 namespace {
@@ -657,12 +697,18 @@ cudaError_t prepare_update_kernels(const DeviceSetup** out) {
     DeviceSetup& s = g_setup[dev];
     if (!s.done) {
         s.err = cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev);
-        s.occ_primary[0] = occupancy((const void*)primary_kernel<float>);
-        s.occ_primary[1] = occupancy((const void*)primary_kernel<__half>);
-        s.occ_shadow[0] = occupancy((const void*)shadow_kernel<float>);
-        s.occ_shadow[1] = occupancy((const void*)shadow_kernel<__half>);
-        s.occ_primary[2] = occupancy((const void*)primary_kernel<Analytic>);
-        s.occ_shadow[2] = occupancy((const void*)shadow_kernel<Analytic>);
+        s.occ_primary[0][0] = occupancy((const void*)primary_kernel<float, false>);
+        s.occ_primary[0][1] = occupancy((const void*)primary_kernel<__half, false>);
+        s.occ_primary[0][2] = occupancy((const void*)primary_kernel<Analytic, false>);
+        s.occ_shadow[0][0] = occupancy((const void*)shadow_kernel<float, false>);
+        s.occ_shadow[0][1] = occupancy((const void*)shadow_kernel<__half, false>);
+        s.occ_shadow[0][2] = occupancy((const void*)shadow_kernel<Analytic, false>);
+        s.occ_primary[1][0] = occupancy((const void*)primary_kernel<float, true>);
+        s.occ_primary[1][1] = occupancy((const void*)primary_kernel<__half, true>);
+        s.occ_primary[1][2] = occupancy((const void*)primary_kernel<Analytic, true>);
+        s.occ_shadow[1][0] = occupancy((const void*)shadow_kernel<float, true>);
+        s.occ_shadow[1][1] = occupancy((const void*)shadow_kernel<__half, true>);
+        s.occ_shadow[1][2] = occupancy((const void*)shadow_kernel<Analytic, true>);
         // the SIMT gathers stage [R][G] values: at most 32 KiB for the G chosen per R
         for (const void* k : {(const void*)gather_kernel<8>, (const void*)gather_kernel<4>, (const void*)gather_kernel<2>})
             if (s.err == cudaSuccess) s.err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 << 10);
@@ -692,8 +738,9 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
     const DeviceSetup* setup = nullptr;
     cudaError_t e = prepare_update_kernels(&setup);
     if (e != cudaSuccess) return e;
-    const int g_primary = persistent_blocks(*setup, setup->occ_primary[type_slot<T>()], p.sched.blocks_per_sm);
-    const int g_shadow = persistent_blocks(*setup, setup->occ_shadow[type_slot<T>()], p.sched.blocks_per_sm);
+    const int rp = p.omega_primary > 1.f ? 1 : 0, rs = p.omega_shadow > 1.f ? 1 : 0;
+    const int g_primary = persistent_blocks(*setup, setup->occ_primary[rp][type_slot<T>()], p.sched.blocks_per_sm);
+    const int g_shadow = persistent_blocks(*setup, setup->occ_shadow[rs][type_slot<T>()], p.sched.blocks_per_sm);
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], stream) : cudaSuccess; };
     e = mark(0);
     // the pools and counts start at zero; the failure bits are sticky until read
@@ -706,11 +753,17 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
         weights_kernel<0><<<p.R, kThreads, 0, stream>>>(p);
     weight_sums_kernel<<<1, kThreads, 0, stream>>>(p);
     if ((e = mark(1)) != cudaSuccess) return e;
-    primary_kernel<T><<<g_primary, kThreads, 0, stream>>>(p);
+    if (rp)
+        primary_kernel<T, true><<<g_primary, kThreads, 0, stream>>>(p);
+    else
+        primary_kernel<T, false><<<g_primary, kThreads, 0, stream>>>(p);
     if ((e = mark(2)) != cudaSuccess) return e;
     prep_kernel<T><<<(n + kPrepRays - 1) / kPrepRays, kThreads, 0, stream>>>(p);
     if ((e = mark(3)) != cudaSuccess) return e;
-    shadow_kernel<T><<<g_shadow, kThreads, 0, stream>>>(p);
+    if (rs)
+        shadow_kernel<T, true><<<g_shadow, kThreads, 0, stream>>>(p);
+    else
+        shadow_kernel<T, false><<<g_shadow, kThreads, 0, stream>>>(p);
     if ((e = mark(4)) != cudaSuccess) return e;
     finalize_kernel<<<(n + kFinalRays - 1) / kFinalRays, kThreads, 0, stream>>>(p);
     if (gather_tc_supported(p) && p.sched.gather != 2) {
@@ -732,6 +785,8 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
 cudaError_t launch_update(const UpdateParams& params, cudaStream_t stream, cudaEvent_t const* stage_events) {
     if (params.P == 0) return cudaSuccess;
     UpdateParams p = params;
+    if (!(p.omega_primary > 1.f)) p.omega_primary = 1.f;  // plain sphere tracing unless relaxation was asked for
+    if (!(p.omega_shadow > 1.f)) p.omega_shadow = 1.f;
     p.dirs = reinterpret_cast<float4*>(p.weights + (size_t)(p.R + 1) * kTexels);  // after the weights
     p.ray_val = p.ray_n;  // the gather's values replace the normals, dead after the shadow stage
     if (p.vol.dtype == kAnalytic) return launch_stages<Analytic>(p, stream, stage_events);

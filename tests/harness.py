@@ -86,11 +86,11 @@ def oracle_scene(w: Workload, analytic: bool = False) -> O.OracleScene:
     return O.OracleScene(w.baked.sdf, w.baked.h, w.baked.origin, w.baked.material)
 
 
-def oracle_grid(w: Workload) -> O.Grid:
+def oracle_grid(w: Workload, omega_primary: float = 1.0, omega_shadow: float = 1.0) -> O.Grid:
     p = w.params
     return O.make_grid(p["probe_dims"], p["probe_origin"], p["probe_spacing"], p["rays"], p["max_steps"],
                        p["eps_vox"], p["tmax_vox"], p["hysteresis"], p["depth_exponent"], p["k_bounce"],
-                       p["bias_vox"], w.sky)
+                       p["bias_vox"], w.sky, omega_primary=omega_primary, omega_shadow=omega_shadow)
 
 
 def force_from_records(rec: np.ndarray) -> np.ndarray:
