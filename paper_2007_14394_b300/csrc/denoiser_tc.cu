@@ -6,7 +6,7 @@
 // with one row per texel. A tile is 128 rows = the 64 texels of 2 probes. The layer input
 // lives in shared memory as a K-major image without swizzle: 8 channels of one texel per
 // 16-byte row, rows consecutive, so a shifted operand is the same image read from a start
-// address 16 * tap_k bytes further on (16 guard rows at both ends absorb the shift). Rows of
+// address 16 * tap_k bytes further on (10 guard rows at both ends absorb the shift). Rows of
 // border texels (and rows a shift carries into the neighbouring probe) produce values that
 // are discarded: the epilogue keeps the 36 interior rows of each probe and rebuilds the
 // border with the octahedral fixup, which is the next layer's padding.
@@ -16,9 +16,10 @@
 //   layer 3   K = 48, N = 16 (3 used); accumulators in tensor-memory columns 0, 64, 112.
 // Per tile: features (the group gathers the 7 probes' map texels) -> MMA 1 -> epilogue
 // (bias, ReLU, bf16, border) -> MMA 2 -> epilogue -> MMA 3 -> residual + output maps.
-// The CTA's two warp groups (4 warps each, one thread per row of a tile) run independent
+// The CTA's three warp groups (4 warps each, one thread per row of a tile) run independent
 // tile streams with their own activation images, tensor-memory columns and mbarrier, so
-// that one group's MMAs overlap the other's feature gathers and epilogues. The group's
+// that one group's MMAs overlap the others' feature gathers and epilogues (three streams
+// fill the shared memory: 121.5 KiB of weights + 3 x 32.4 KiB of activation images). The group's
 // first thread issues its MMAs; completion is an mbarrier armed by tcgen05.commit.
 // Every wait is bounded; on timeout the kernel records bit 1 of the status word, releases
 // its tensor memory and returns.
@@ -37,15 +38,15 @@ using namespace sdfddgi::tc;
 
 constexpr int kRows = 128;                      // texel rows per tile: 2 probes x 64
 constexpr int kProbesPerTile = kRows / kTex;
-constexpr int kGuard = 16;                      // guard rows at each end (shifts reach +-9)
-constexpr int kBufRows = kRows + 2 * kGuard;    // 160
+constexpr int kGuard = 10;                      // guard rows at each end (shifts reach +-9)
+constexpr int kBufRows = kRows + 2 * kGuard;    // 148
 constexpr int kK1 = 48, kK2 = 64, kK3 = 48;     // input channels, padded to multiples of 16
 constexpr int kN1 = 64, kN2 = 48, kN3 = 16;     // accumulator columns (layer 3: 3 used)
 constexpr int kCol1 = 0, kCol2 = 64, kCol3 = 112;   // within a warp group's 128 columns
-constexpr int kGroups = 2;                          // warp groups, each with its own tile stream
+constexpr int kGroups = 3;                          // warp groups, each with its own tile stream
 constexpr int kGroupThreads = 128;
 constexpr int kGroupCols = 128;
-constexpr int kTmemCols = kGroups * kGroupCols;
+constexpr int kTmemCols = 512;                      // 3 x 128 used; allocations are powers of 2
 constexpr int kThreads = kGroups * kGroupThreads;
 // B images: per layer, per tap, [K / 8][N][8 channels] bf16 (K-major, no swizzle)
 constexpr int kImg1 = 9 * kK1 * kN1 * 2, kImg2 = 9 * kK2 * kN2 * 2, kImg3 = 9 * kK3 * kN3 * 2;
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1) denoise_tc_kernel(const __grid_co
     if (!mbar_wait(&bar_w, 0, a.status)) s_fail = 1;
     __syncthreads();
 
-    // ---- from here on the two warp groups run independent tile streams
+    // ---- from here on the three warp groups run independent tile streams
     unsigned char* s_actA = smem + kImgBytes + grp * (kActA + kActB);  // 48 channels: features, layer 2 out
     unsigned char* s_actB = s_actA + kActA;                             // 64 channels: layer 1 out
     const uint32_t imgA = smem_u32(s_actA), imgB = smem_u32(s_actB), img0 = smem_u32(s_img);
