@@ -35,6 +35,12 @@ L2_FLUSH_BYTES = 512 << 20
 KERNELS_PER_UPDATE = 8  # texel weights, weight sums, primary, hit preparation, shadow, finalize, weight image, gather
 
 
+def kernels_per_update(slabs: int) -> int:
+    """Kernel launches of one update run as `slabs` slab branches (tensor-core gather): the
+    weights, their sums and the weight image once, then five stage kernels per slab."""
+    return KERNELS_PER_UPDATE if slabs <= 1 else 3 + 5 * slabs
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -226,6 +232,7 @@ def run_ours(args, rank, world, local_rank):
                        pr.eps_vox, pr.tmax_vox, pr.hysteresis, pr.k_bounce, pr.bias_vox, seed=pr.seed,
                        flags=S.FLAG_BLEND_BF16 if pr.blend == "bf16" else 0)
     vol = S.create_volume(desc, sc)
+    S.set_slabs(vol, args.slabs)
     states_dev = torch.from_numpy(states.view(np.uint8).copy()).to(dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -251,19 +258,13 @@ def run_ours(args, rank, world, local_rank):
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    # stage boundaries, recorded by the library on the same stream (events created up front)
-    stage_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
-    for evs in stage_ev:
-        for e in evs:
-            e.record(stream)
-    torch.cuda.synchronize()
+    slabs = S.volume_slabs(vol)  # the library's automatic schedule: slab branches for an update this size
     clocks = Clocks(local_rank)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(float(k))                       # evict the SDF and maps from L2 (not timed)
-        S.set_stage_events(vol, stage_ev[k])
         starts[k].record(stream)
         S.update_probes(vol, frame, states=states_dev, stream=stream)
         ends[k].record(stream)
@@ -272,11 +273,27 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
-    S.set_stage_events(vol, [])
     per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     dev_ms = float(sum(per_step))
-    stage_ms = {name: sum(evs[i].elapsed_time(evs[i + 1]) for evs in stage_ev) / args.steps
+
+    # stage times: the same updates with stage events, which run them serially (one slab), so
+    # that every stage kernel is timed alone on the update's stream
+    n_s = max(10, min(args.steps, 200))
+    stage_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(n_s)]
+    for evs in stage_ev:
+        for e in evs:
+            e.record(stream)
+    torch.cuda.synchronize()
+    for k in range(n_s):
+        flush.fill_(float(k))
+        S.set_stage_events(vol, stage_ev[k])
+        S.update_probes(vol, frame, states=states_dev, stream=stream)
+        frame += 1
+    torch.cuda.synchronize()
+    S.set_stage_events(vol, [])
+    stage_ms = {name: sum(evs[i].elapsed_time(evs[i + 1]) for evs in stage_ev) / n_s
                 for i, name in enumerate(S.STAGES)}
+    serial_ms = sum(evs[0].elapsed_time(evs[5]) for evs in stage_ev) / n_s
 
     # end to end through the C ABI with host buffers: pinned probe states in, both maps out
     host_states = torch.from_numpy(states.view(np.uint8).copy()).pin_memory()
@@ -372,14 +389,17 @@ def run_ours(args, rank, world, local_rank):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if pr.blend == "f32" and pr.sdf_dtype == "f32" else f"{pr.sdf_dtype} sdf, {pr.blend} gather",
         "data": "synthetic (seeded scene, baked on the host)", "config": workload_config(pr, rays_per_step),
-        "gpu_launches": KERNELS_PER_UPDATE * args.steps,
+        "gpu_launches": kernels_per_update(slabs) * args.steps,
+        "schedule": {"slabs": slabs, "serial_ms_per_update": serial_ms, "stage_updates": n_s,
+                     "note": "value: updates as the library runs them by default (slab branches); stages and "
+                             "roofline: the same updates run serially with stage events, L2 flushed"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": P * 16,
                 "d2h_bytes_per_step": P * (8 * 8 * 4 * 4 + 16 * 16 * 2 * 4 + 1), "ms_per_step": e2e_ms / args.steps},
         "roofline": roof,
         "stages": stages,
         "relaxed_trace_variants": dict(relaxed, omega=S.RELAX_OMEGA,
-                                       note="SDFDDGI_FLAG_RELAXED_* volumes, same workload, stage events; "
-                                            "plain path above: " + f"{ms:.4f} ms"),
+                                       note="SDFDDGI_FLAG_RELAXED_* volumes, same workload, stage events (serial); "
+                                            "plain serial path: " + f"{serial_ms:.4f} ms"),
         "wall_s_timed_loop": wall,
         "step_ms": {"min": min(per_step), "median": statistics.median(per_step), "max": max(per_step)},
         "clocks": clk,
@@ -981,6 +1001,8 @@ def main():
                     choices=sorted(W.PRESETS) + sorted(W.CASCADES) + [LEARNED] + sorted(ANALYTIC) + [CASCADE_QUERY])
     ap.add_argument("--train-steps", type=int, default=6000, help="training steps of the learned32 workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--slabs", type=int, default=0,
+                    help="slab branches per update of the open256 volume (0: the library's automatic choice)")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:

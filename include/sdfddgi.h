@@ -65,6 +65,7 @@ enum { SDFDDGI_LIGHT_DIRECTIONAL = 0, SDFDDGI_LIGHT_POINT = 1 };    /* light typ
 enum { SDFDDGI_PROBE_ACTIVE = 1u, SDFDDGI_PROBE_REJECT_HISTORY = 2u }; /* probe flags   */
 enum { SDFDDGI_MAX_LIGHTS = 32, SDFDDGI_MAX_RAYS = 1024, SDFDDGI_MAX_STEPS = 65535 };
 enum { SDFDDGI_STAGE_EVENTS = 6 };
+#define SDFDDGI_MAX_SLABS 4
 /* Volume flags. BLEND_BF16 -- the precision form of the gather (Eq. 3): texel weights and
  * ray values rounded to bf16, products accumulated in fp32 on the tensor cores, instead of
  * the default float32-accurate gather (three tf32 products per term). It applies when
@@ -254,8 +255,25 @@ SDFDDGI_API int sdfddgi_update_probes(sdfddgi_volume* v, uint32_t frame, const f
  * update_probes records them on its stream: [0] at the start, [1] after the per-frame
  * texel weights, [2] after the primary traces, [3] after hit preparation, [4] after the
  * shadow traces, [5] after the gather (Eq. 3) and border fixup. n = 0 stops recording.
- * The events must outlive their use; the caller reads them with cudaEventElapsedTime. */
+ * The events must outlive their use; the caller reads them with cudaEventElapsedTime.
+ * While stage events are set, updates run serially (one slab, see sdfddgi_set_slabs). */
 SDFDDGI_API int sdfddgi_set_stage_events(sdfddgi_volume* v, void* const* events, int32_t n);
+
+/* Slab branches (a scheduling choice; the results are the same bit for bit). An update can
+ * run its probes as `slabs` z-slabs of the probe grid (slab c: z-layers c*nz/slabs up to
+ * (c+1)*nz/slabs), each slab's traces, shading, gather and fixup a chain of its own: slab 0,
+ * 2 on the caller's stream, slab 1, 3 on a second stream owned by the volume, forked from
+ * and joined back into the caller's stream (so the update stays one stream-ordered unit,
+ * also under graph capture). The pools of a stage end with a few long rays that keep few
+ * lanes busy; the other slab's kernels fill the SMs meanwhile. The texel weights are
+ * computed once, before the fork. Each slab has its own pool counters and part of the
+ * shadow-task list; the multi-bounce lookup still reads the whole volume's last maps.
+ *  slabs -- 0: automatic (2 when P*R >= 2^20 rays, else 1), 1: serial, up to
+ *           SDFDDGI_MAX_SLABS (at most nz slabs are used).
+ * Returns SDFDDGI_ERR_INVALID_ARG outside [0, SDFDDGI_MAX_SLABS]. */
+SDFDDGI_API int sdfddgi_set_slabs(sdfddgi_volume* v, int32_t slabs);
+/* The number of slabs the next update_probes of v runs as (1 while stage events are set). */
+SDFDDGI_API int sdfddgi_volume_slabs(const sdfddgi_volume* v, int32_t* slabs);
 
 /* Probe relocation (Sec. 3.2, the procedure UpdateProbePos): the paper moves a probe
  * that lies too near a surface (SDF below threshold1) by gradient descent on the SDF,
@@ -494,9 +512,9 @@ SDFDDGI_API int sdfddgi_denoiser_train_step(sdfddgi_denoiser* d, const sdfddgi_p
  * layout, per-ray buffers, the shadow-task list, texel weights, counters) lives in one
  * fixed 32 MiB array in device memory that every GPU loading this library holds until
  * the process exits. An update needs, each part rounded up to 256 bytes: 16 bytes per
- * SDF voxel (8 at binary16), 64 + 4*max(n_lights,1) bytes per probe ray (P*R), and
+ * SDF voxel (8 at binary16), 64 + 16*max(n_lights,1) bytes per probe ray (P*R), and
  * 944*R + 928 bytes -- e.g. a 64^3 float32 SDF with 512 probes x 64 rays and 1 light
- * takes about 6.2 MiB. An update that does not fit in 32 MiB is rejected with
+ * takes about 6.6 MiB. An update that does not fit in 32 MiB is rejected with
  * SDFDDGI_ERR_INVALID_ARG before any device work, and sdfddgi_last_error() states the
  * bytes needed and available.
  *  - The first call on a device looks up the array's device address

@@ -93,6 +93,8 @@ def _load() -> C.CDLL:
         "sdfddgi_write_state": ([vp, vp, vp, vp, i32, vp], C.c_int),
         "sdfddgi_reset": ([vp, vp], C.c_int),
         "sdfddgi_set_stage_events": ([vp, C.POINTER(vp), i32], C.c_int),
+        "sdfddgi_set_slabs": ([vp, i32], C.c_int),
+        "sdfddgi_volume_slabs": ([vp, C.POINTER(i32)], C.c_int),
         "sdfddgi_update_probes_noalloc": ([C.POINTER(VolumeDesc), vp, C.POINTER(i32), C.c_float, C.POINTER(C.c_float),
                                            i32, vp, C.POINTER(Light), i32, C.POINTER(C.c_float), u32, vp, vp,
                                            vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
@@ -131,7 +133,9 @@ EXPORTED = ("last_error", "create_scene", "destroy_scene", "upload_sdf", "set_li
             "create_batch", "destroy_batch", "update_batch", "batch_autotune", "batch_schedule",
             "create_denoiser", "destroy_denoiser", "denoiser_params", "denoise", "denoise_volume",
             "denoiser_gradients", "denoiser_adam", "denoiser_train_step", "volume_status", "denoiser_status",
-            "relocate_probes", "sample_irradiance_visible", "upload_primitives", "sample_irradiance_cascade")
+            "relocate_probes", "sample_irradiance_visible", "upload_primitives", "sample_irradiance_cascade",
+            "set_slabs", "volume_slabs")
+MAX_SLABS = 4
 DENOISER_PARAMS = 49219
 DENOISE_TENSOR, DENOISE_SIMT_BF16, DENOISE_SIMT_FP32 = 0, 1, 2
 STAGES = ("weights", "primary", "prep", "shadow", "gather")  # intervals between the stage events
@@ -142,6 +146,18 @@ def set_stage_events(volume, events) -> None:
     n = len(events)
     arr = (C.c_void_p * max(n, 1))(*[e.cuda_event for e in events])
     _check(lib.sdfddgi_set_stage_events(volume, arr, n))
+
+
+def set_slabs(volume, slabs: int) -> None:
+    """Slab branches per update of `volume`: 0 automatic, 1 serial, up to MAX_SLABS."""
+    _check(lib.sdfddgi_set_slabs(volume, int(slabs)))
+
+
+def volume_slabs(volume) -> int:
+    """The number of slabs the next update of `volume` runs as."""
+    n = C.c_int32()
+    _check(lib.sdfddgi_volume_slabs(volume, C.byref(n)))
+    return n.value
 
 
 def last_error() -> str:

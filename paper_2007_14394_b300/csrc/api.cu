@@ -62,12 +62,19 @@ void free_volume_buffers(sdfddgi_volume* v) {
     void* scratch[] = {v->ray_t, v->ray_es, v->ray_n, v->ray_alb, v->ray_base, v->ray_lit, v->ray_ssteps,
                        v->counters, v->tasks, v->weights, v->wimage};
     for (void* q : scratch) cudaFree(q);
+    for (int c = 0; c < kMaxSlabs - 1; ++c) {
+        if (v->lanes.side[c]) cudaStreamDestroy(v->lanes.side[c]);
+        if (v->lanes.join[c]) cudaEventDestroy(v->lanes.join[c]);
+    }
+    if (v->lanes.fork) cudaEventDestroy(v->lanes.fork);
+    v->lanes = {};
     v->weights = nullptr;
     v->wimage = nullptr;
     v->ray_t = nullptr;
     v->ray_es = nullptr;
     v->ray_n = v->ray_alb = v->ray_base = nullptr;
-    v->ray_lit = v->ray_ssteps = v->counters = v->tasks = nullptr;
+    v->ray_lit = v->ray_ssteps = v->counters = nullptr;
+    v->tasks = nullptr;
     v->task_capacity = 0;
 }
 
@@ -80,7 +87,7 @@ int alloc_scratch(sdfddgi_volume* v) {
     if (!rc) rc = alloc((void**)&v->ray_base, n * sizeof(float4));
     if (!rc) rc = alloc((void**)&v->ray_lit, n * sizeof(uint32_t));
     if (!rc) rc = alloc((void**)&v->ray_ssteps, n * sizeof(uint32_t));
-    if (!rc) rc = alloc((void**)&v->counters, kCounterWords * sizeof(uint32_t));
+    if (!rc) rc = alloc((void**)&v->counters, kMaxSlabs * kSlabCounterStride * sizeof(uint32_t));
     if (!rc) rc = alloc((void**)&v->weights, weights_bytes(v->desc.rays_per_probe));
     if (!rc) rc = alloc(&v->wimage, wimage_bytes(v->desc.rays_per_probe));
     return rc;
@@ -93,7 +100,7 @@ int ensure_task_capacity(sdfddgi_volume* v, int n_lights) {
     cudaFree(v->tasks);
     v->tasks = nullptr;
     v->task_capacity = 0;
-    int rc = alloc((void**)&v->tasks, need * sizeof(uint32_t));
+    int rc = alloc((void**)&v->tasks, need * sizeof(float4));
     if (!rc) v->task_capacity = need;
     return rc;
 }
@@ -320,6 +327,14 @@ SDFDDGI_API int sdfddgi_create_volume(const sdfddgi_volume_desc* d, sdfddgi_scen
     }
     if (!rc) rc = alloc((void**)&v->states, sizeof(sdfddgi_probe_state) * P);
     if (!rc) rc = alloc_scratch(v);
+    if (!rc) {
+        cudaError_t e = cudaEventCreateWithFlags(&v->lanes.fork, cudaEventDisableTiming);
+        for (int c = 0; c < kMaxSlabs - 1 && e == cudaSuccess; ++c) {
+            e = cudaStreamCreateWithFlags(&v->lanes.side[c], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->lanes.join[c], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) rc = fail(SDFDDGI_ERR_CUDA, "create_volume: %s", cudaGetErrorString(e));
+    }
     if (rc) {
         free_volume_buffers(v);
         delete v;
@@ -328,7 +343,7 @@ SDFDDGI_API int sdfddgi_create_volume(const sdfddgi_volume_desc* d, sdfddgi_scen
     rc = sdfddgi_reset(v, nullptr);
     if (!rc) {
         cudaError_t e = prepare_update_kernels();  // so that later updates can be captured
-        if (e == cudaSuccess) e = cudaMemset(v->counters, 0, kCounterWords * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMemset(v->counters, 0, kMaxSlabs * kSlabCounterStride * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
         if (e != cudaSuccess) rc = fail(SDFDDGI_ERR_CUDA, "create_volume: %s", cudaGetErrorString(e));
     }
@@ -350,6 +365,26 @@ SDFDDGI_API void sdfddgi_destroy_volume(sdfddgi_volume* v) {
 SDFDDGI_API int sdfddgi_volume_probe_count(const sdfddgi_volume* v, int64_t* n) {
     if (!v || !n) return fail(SDFDDGI_ERR_INVALID_ARG, "volume_probe_count: NULL argument");
     *n = v->P;
+    return SDFDDGI_OK;
+}
+
+SDFDDGI_API int sdfddgi_set_slabs(sdfddgi_volume* v, int32_t slabs) {
+    if (!v) return fail(SDFDDGI_ERR_INVALID_ARG, "set_slabs: volume is NULL");
+    if (slabs < 0 || slabs > SDFDDGI_MAX_SLABS)
+        return fail(SDFDDGI_ERR_INVALID_ARG, "set_slabs: slabs must be in [0, %d]", SDFDDGI_MAX_SLABS);
+    v->slabs = slabs;
+    return SDFDDGI_OK;
+}
+
+SDFDDGI_API int sdfddgi_volume_slabs(const sdfddgi_volume* v, int32_t* slabs) {
+    if (!v || !slabs) return fail(SDFDDGI_ERR_INVALID_ARG, "volume_slabs: NULL argument");
+    UpdateParams p;
+    std::memset(&p, 0, sizeof p);
+    for (int a = 0; a < 3; ++a) p.gdims[a] = v->desc.dims[a];
+    p.P = (int)v->P;
+    p.R = v->desc.rays_per_probe;
+    p.sched.slabs = v->slabs;
+    *slabs = slab_count(p, true, v->has_stage_events);
     return SDFDDGI_OK;
 }
 
@@ -455,7 +490,8 @@ SDFDDGI_API int sdfddgi_update_probes(sdfddgi_volume* v, uint32_t frame, const f
         }
     }
     p.records = records;
-    cudaError_t e = launch_update(p, st, v->has_stage_events ? v->stage_events : nullptr);
+    p.sched.slabs = v->slabs;
+    cudaError_t e = launch_update(p, st, v->has_stage_events ? v->stage_events : nullptr, &v->lanes);
     if (e != cudaSuccess) return fail(SDFDDGI_ERR_CUDA, "update_probes: launch failed: %s", cudaGetErrorString(e));
     v->cur ^= 1;
     return SDFDDGI_OK;
@@ -577,10 +613,14 @@ SDFDDGI_API int sdfddgi_write_state(sdfddgi_volume* v, const float* irr, const f
 SDFDDGI_API int sdfddgi_volume_status(sdfddgi_volume* v, uint32_t* flags) {
     if (flags) *flags = 0;
     if (!v) return fail(SDFDDGI_ERR_INVALID_ARG, "volume_status: volume is NULL");
-    uint32_t f = 0;
+    uint32_t words[kMaxSlabs * kSlabCounterStride];
     CUDA_TRY(cudaDeviceSynchronize());
-    CUDA_TRY(cudaMemcpy(&f, v->counters + kFailWord, sizeof f, cudaMemcpyDeviceToHost));
-    CUDA_TRY(cudaMemset(v->counters + kFailWord, 0, sizeof f));
+    CUDA_TRY(cudaMemcpy(words, v->counters, sizeof words, cudaMemcpyDeviceToHost));
+    uint32_t f = 0;  // the failure bits of every slab's counters
+    for (int c = 0; c < kMaxSlabs; ++c) {
+        f |= words[c * kSlabCounterStride + kFailWord];
+        CUDA_TRY(cudaMemset(v->counters + c * kSlabCounterStride + kFailWord, 0, sizeof(uint32_t)));
+    }
     if (flags) *flags = f;
     if (f & 2u) return fail(SDFDDGI_ERR_TIMEOUT, "volume_status: a bounded wait of the tensor-core gather gave up");
     return SDFDDGI_OK;

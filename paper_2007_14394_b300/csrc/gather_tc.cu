@@ -426,14 +426,18 @@ cudaError_t prepare_gather_tc() {
 }
 
 template <bool BF16>
-static cudaError_t launch_tc(const UpdateParams& p, cudaStream_t stream) {
-    pack_weights_kernel<BF16><<<p.R, 256, 0, stream>>>(p);
-    gather_tc_kernel<BF16><<<(p.P + tc::kG - 1) / tc::kG, tc::kThreads, tc_smem<BF16>(), stream>>>(p);
+static cudaError_t launch_tc(const UpdateParams& p, cudaStream_t stream, bool pack, bool gather) {
+    if (pack) pack_weights_kernel<BF16><<<p.R, 256, 0, stream>>>(p);
+    if (gather) gather_tc_kernel<BF16><<<(p.P + tc::kG - 1) / tc::kG, tc::kThreads, tc_smem<BF16>(), stream>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_tc(const UpdateParams& p, cudaStream_t stream) {
-    return p.blend_bf16 ? launch_tc<true>(p, stream) : launch_tc<false>(p, stream);
+cudaError_t launch_gather_tc(const UpdateParams& p, cudaStream_t stream, bool pack) {
+    return p.blend_bf16 ? launch_tc<true>(p, stream, pack, true) : launch_tc<false>(p, stream, pack, true);
+}
+
+cudaError_t launch_pack_weights(const UpdateParams& p, cudaStream_t stream) {
+    return p.blend_bf16 ? launch_tc<true>(p, stream, true, false) : launch_tc<false>(p, stream, true, false);
 }
 
 }  // namespace sdfddgi

@@ -45,13 +45,15 @@ struct sdfddgi_volume {
     float4* ray_base = nullptr;
     uint32_t* ray_lit = nullptr;
     uint32_t* ray_ssteps = nullptr;
-    uint32_t* counters = nullptr;  // kCounterWords words (see UpdateParams)
-    uint32_t* tasks = nullptr;
+    uint32_t* counters = nullptr;  // kMaxSlabs slabs' kCounterWords words, kSlabCounterStride apart
+    float4* tasks = nullptr;
     size_t task_capacity = 0;
     float* weights = nullptr;  // texel weights of the frame's ray set and their column sums
     void* wimage = nullptr;    // the weights as the tensor-core gather's operand image
     cudaEvent_t stage_events[SDFDDGI_STAGE_EVENTS] = {};  // caller's, recorded at stage boundaries
     bool has_stage_events = false;
+    int slabs = 0;                    // slab branches per update (0 automatic)
+    sdfddgi::SlabLanes lanes = {};    // the second stream and fork/join events of slab branches
 };
 
 namespace sdfddgi {

@@ -62,7 +62,10 @@ struct Schedule {
     int pool_batch;      // trace tasks a warp claims per atomic: 8, 16, 32 or 64 (default)
     int blocks_per_sm;   // resident CTAs per SM of the persistent trace kernels (default: occupancy limit)
     int gather;          // 0 automatic (tensor cores when R % 16 == 0), 1 tensor cores, 2 SIMT
+    int slabs;           // z-slabs of probes run as concurrent branches: 0 automatic, 1 (serial) .. kMaxSlabs
 };
+
+constexpr int kMaxSlabs = SDFDDGI_MAX_SLABS;
 
 struct LightDev {
     int type;
@@ -79,7 +82,8 @@ struct UpdateParams {
     int gdims[3];
     float gorigin[3];
     float gspacing[3];
-    int P;                    // probe count
+    int P;                    // probe count (of this launch: the volume, or one slab of it)
+    int p_begin;              // the volume's index of probe 0 of this launch (a slab's first probe)
     int R;                    // rays per probe
     int max_steps;
     int depth_exp;
@@ -93,6 +97,8 @@ struct UpdateParams {
     const float4* prev_irr;   // [P][8][8]
     const float2* prev_depth; // [P][16][16]
     const uint8_t* prev_valid;
+    const float4* look_irr;   // the whole volume's previous irradiance and validity (multi-bounce
+    const uint8_t* look_valid;// lookups reach any probe); null: prev_irr / prev_valid
     float4* cur_irr;
     float2* cur_depth;
     uint8_t* cur_valid;
@@ -105,7 +111,7 @@ struct UpdateParams {
     float4* ray_base;         // emission + k * albedo * last-frame irradiance
     uint32_t* ray_lit;        // visible-light mask
     uint32_t* ray_ssteps;     // shadow steps
-    uint32_t* tasks;          // shadow tasks (k << 5 | light)
+    float4* tasks;            // shadow tasks: origin xyz, bits of (k << 5 | light)
     uint32_t task_capacity;
     uint32_t* counters;       // kCounterWords words: pools and counts (zeroed by each launch), then at
                               // kFailWord the failure bits, sticky: 1 task overflow, 2 a tensor-core wait gave up
@@ -129,6 +135,9 @@ constexpr int kTexels = kIrrTexels + kDepTexels;  // 232 gather rows: irradiance
 constexpr int kPrimaryPool = 0, kTaskCount = 1, kShadowPool = 2;
 constexpr int kFailWord = 7;
 constexpr int kCounterWords = 8;
+// The slabs of one update keep their counters 256 bytes apart, so that concurrent slab
+// branches' atomics do not meet in one L2 line.
+constexpr int kSlabCounterStride = 64;
 
 struct SampleParams {
     int gdims[3];
@@ -152,8 +161,20 @@ struct VisParams {
     const sdfddgi_probe_state* states;  // null: probes at their grid positions
 };
 
+// The streams and events with which one update forks its slab branches off `stream` and joins
+// them again (owned by the volume): slab c > 0 runs on side[c - 1].
+struct SlabLanes {
+    cudaStream_t side[SDFDDGI_MAX_SLABS - 1];
+    cudaEvent_t fork;
+    cudaEvent_t join[SDFDDGI_MAX_SLABS - 1];
+};
+
 // stage_events: null, or SDFDDGI_STAGE_EVENTS events recorded on `stream` at the stage boundaries
-cudaError_t launch_update(const UpdateParams& p, cudaStream_t stream, cudaEvent_t const* stage_events = nullptr);
+// (the update then runs serially); lanes: null (serial), or the streams for slab branches.
+cudaError_t launch_update(const UpdateParams& p, cudaStream_t stream, cudaEvent_t const* stage_events = nullptr,
+                          const SlabLanes* lanes = nullptr);
+// The number of slab branches launch_update runs p as (1 = serial).
+int slab_count(const UpdateParams& p, bool have_lanes, bool stage_events);
 cudaError_t launch_sample(const SampleParams& p, cudaStream_t stream);
 cudaError_t launch_sample_visible(const SampleParams& p, const VisParams& v, cudaStream_t stream);
 size_t quad_bytes(int dtype, size_t n_voxels);
@@ -162,7 +183,10 @@ int report_error(int code, const char* msg);  // sets the text of sdfddgi_last_e
 // the gather of Eq. 3 on the tensor cores (R a multiple of 16 and a weight image present)
 bool gather_tc_supported(const UpdateParams& p);
 size_t wimage_bytes(int R);
-cudaError_t launch_gather_tc(const UpdateParams& p, cudaStream_t stream);
+// The tensor-core gather; with pack, first the frame's weight image (otherwise already packed
+// by launch_pack_weights on a stream this one waits for).
+cudaError_t launch_gather_tc(const UpdateParams& p, cudaStream_t stream, bool pack = true);
+cudaError_t launch_pack_weights(const UpdateParams& p, cudaStream_t stream);
 cudaError_t prepare_gather_tc();  // dynamic shared-memory limits of the tensor-core gathers
 // one-time per-device set-up of the update's kernels (occupancy, shared-memory limits); the
 // first update makes it otherwise, but it must not happen inside a stream capture

@@ -111,7 +111,7 @@ SDFDDGI_API int sdfddgi_update_probes_noalloc(
                             n_rays * 16,  // ray_base
                             n_rays * 4,   // ray_lit
                             n_rays * 4,   // ray_ssteps
-                            n_rays * 4 * (size_t)(n_lights > 0 ? n_lights : 1),  // tasks
+                            n_rays * 16 * (size_t)(n_lights > 0 ? n_lights : 1),  // tasks
                             kCounterWords * 4,  // counters
                             weights_bytes(R)};  // texel weights, their sums, ray directions
     size_t off[sizeof sizes / sizeof sizes[0]], total = 0;
@@ -199,7 +199,7 @@ SDFDDGI_API int sdfddgi_update_probes_noalloc(
     p.ray_base = reinterpret_cast<float4*>(s + off[5]);
     p.ray_lit = reinterpret_cast<uint32_t*>(s + off[6]);
     p.ray_ssteps = reinterpret_cast<uint32_t*>(s + off[7]);
-    p.tasks = reinterpret_cast<uint32_t*>(s + off[8]);
+    p.tasks = reinterpret_cast<float4*>(s + off[8]);
     p.task_capacity = (uint32_t)(n_rays * (size_t)(n_lights > 0 ? n_lights : 1));
     p.counters = reinterpret_cast<uint32_t*>(s + off[9]);
     p.weights = reinterpret_cast<float*>(s + off[10]);

@@ -145,12 +145,14 @@ __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, f
 
 // Device-wide pool of sphere traces. Tasks 0..n-1 are claimed from *counter by whole
 // warps in batches of kBatch and handed to lanes as they finish their current trace;
-// init(k, st) returns false for a task that needs no trace (it is then complete),
-// done(st, event, steps, t) consumes a finished trace. Every lane of the warp must
-// take part (full-warp votes).
-template <typename T, bool Relax, typename Init, typename Done>
+// claim(b) runs on every lane of the warp when it has claimed tasks b..b+batch-1 (work
+// shared by the whole batch is done there once), init(k, st) returns false for a task
+// that needs no trace (it is then complete), done(st, event, steps, t) consumes a
+// finished trace. Every lane of the warp must take part (full-warp votes).
+template <typename T, bool Relax, typename Claim, typename Init, typename Done>
 __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint32_t* counter, float eps,
-                                           int max_steps, float omega, uint32_t batch, Init init, Done done) {
+                                           int max_steps, float omega, uint32_t batch, Claim claim, Init init,
+                                           Done done) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     uint32_t batch_next = 0, batch_end = 0;  // warp-uniform
@@ -165,6 +167,7 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
                 b = __shfl_sync(full, b, 0);
                 batch_next = b;
                 batch_end = b + batch;
+                claim(b);
             }
             const uint32_t avail = batch_end - batch_next;
             const uint32_t rank = __popc(want & ((1u << lane) - 1u));
@@ -218,7 +221,8 @@ __device__ __forceinline__ float3 probe_origin(const UpdateParams& P, int p, uin
         *flags = st.flags;
         return f3(st.pos[0], st.pos[1], st.pos[2]);
     }
-    const int ix = p % P.gdims[0], iy = (p / P.gdims[0]) % P.gdims[1], iz = p / (P.gdims[0] * P.gdims[1]);
+    const int g = p + P.p_begin;  // grid positions follow the volume's index (a slab starts at p_begin)
+    const int ix = g % P.gdims[0], iy = (g / P.gdims[0]) % P.gdims[1], iz = g / (P.gdims[0] * P.gdims[1]);
     *flags = SDFDDGI_PROBE_ACTIVE;
     return f3(fmaf((float)ix, P.gspacing[0], P.gorigin[0]), fmaf((float)iy, P.gspacing[1], P.gorigin[1]),
               fmaf((float)iz, P.gspacing[2], P.gorigin[2]));
@@ -248,15 +252,41 @@ __device__ __forceinline__ float light_scale(const LightDev& li, float3 x, float
 }
 
 // ------------------------------------------------------------------ 1. primary traces
+// A claimed batch of tasks lies within one probe whenever R is a multiple of the batch
+// size, so the probe's origin and flags are decoded once per batch, by lane 0 into its
+// warp's slot; a task outside the slot's probe decodes its own.
 template <typename T, bool Relax>
 __global__ void __launch_bounds__(kThreads, 8) primary_kernel(const __grid_constant__ UpdateParams P) {
+    __shared__ float4 s_origin[kThreads / 32];  // probe origin, its first task index (bits)
+    __shared__ uint32_t s_flags[kThreads / 32];
     const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
+    const int warp = threadIdx.x >> 5;
     trace_pool<T, Relax>(
         P.vol, n, &P.counters[kPrimaryPool], P.eps_w, P.max_steps, P.omega_primary, pool_batch(P),
+        [&](uint32_t b) {
+            __syncwarp();  // every lane has read the previous batch's slot
+            if ((threadIdx.x & 31) == 0 && b < n) {
+                const uint32_t p = b / (uint32_t)P.R;
+                uint32_t flags;
+                const float3 o = probe_origin(P, (int)p, &flags);
+                s_origin[warp] = make_float4(o.x, o.y, o.z, __uint_as_float(p * (uint32_t)P.R));
+                s_flags[warp] = flags;
+            }
+            __syncwarp();
+        },
         [&](uint32_t k, TraceState& st) {
-            const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
+            const float4 so = s_origin[warp];
+            const uint32_t rel = k - __float_as_uint(so.w);
+            int i;
             uint32_t flags;
-            st.o = probe_origin(P, p, &flags);
+            if (rel < (uint32_t)P.R) {
+                i = (int)rel;
+                flags = s_flags[warp];
+                st.o = f3(so.x, so.y, so.z);
+            } else {
+                i = (int)(k % (uint32_t)P.R);
+                st.o = probe_origin(P, (int)(k / (uint32_t)P.R), &flags);
+            }
             if (!(flags & SDFDDGI_PROBE_ACTIVE)) {
                 P.ray_es[k] = kNoRay;
                 return false;
@@ -305,6 +335,7 @@ __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant
     for (int j0 = 0; j0 < n_shade; j0 += kThreads) {
         const int j = j0 + threadIdx.x;
         uint32_t gate = 0, k = 0;
+        float3 so = f3(0.f, 0.f, 0.f);  // the shadow rays' origin: the hit lifted off the surface
         if (j < n_shade) {
             k = s_rays[j];
             P.ray_lit[k] = 0;
@@ -335,12 +366,13 @@ __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant
             }
             float3 ind = f3(0.f, 0.f, 0.f);
             if (P.k_bounce != 0.f)
-                ind = interpolate_irradiance(P.gdims, P.gorigin, P.gspacing, P.prev_irr, P.prev_valid, x, nr);
+                ind = interpolate_irradiance(P.gdims, P.gorigin, P.gspacing, P.look_irr, P.look_valid, x, nr);
             for (int l = 0; l < P.n_lights; ++l) {
                 bool g;
                 light_scale(P.lights[l], x, nr, &g);
                 if (g) gate |= 1u << l;
             }
+            so = fma3(P.bias_w, nr, x);
             P.ray_n[k] = make_float4(nr.x, nr.y, nr.z, 0.f);
             P.ray_alb[k] = make_float4(albedo.x, albedo.y, albedo.z, __uint_as_float(owner));
             P.ray_base[k] = make_float4(emission.x + albedo.x * P.k_bounce * ind.x,
@@ -368,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant
         while (gate) {
             const int l = __ffs(gate) - 1;
             gate &= gate - 1;
-            P.tasks[pos++] = (k << 5) | (uint32_t)l;
+            P.tasks[pos++] = make_float4(so.x, so.y, so.z, __uint_as_float((k << 5) | (uint32_t)l));
         }
     }
 }
@@ -379,17 +411,12 @@ __global__ void __launch_bounds__(kThreads, 8) shadow_kernel(const __grid_consta
     const uint32_t n = min(P.counters[kTaskCount], P.task_capacity);
     trace_pool<T, Relax>(
         P.vol, n, &P.counters[kShadowPool], P.eps_w, P.max_steps, P.omega_shadow, pool_batch(P),
+        [](uint32_t) {},
         [&](uint32_t j, TraceState& st) {
-            const uint32_t tk = P.tasks[j];
-            const uint32_t k = tk >> 5;
+            const float4 task = P.tasks[j];
+            const uint32_t tk = __float_as_uint(task.w);
             const int l = (int)(tk & 31u);
-            const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
-            uint32_t flags;
-            const float3 o = probe_origin(P, p, &flags);
-            const float3 d = ray_dir(P, i);
-            const float3 x = fma3(P.ray_t[k], d, o);
-            const float4 n4 = P.ray_n[k];
-            st.o = fma3(P.bias_w, f3(n4.x, n4.y, n4.z), x);
+            st.o = f3(task.x, task.y, task.z);
             const LightDev& li = P.lights[l];
             if (li.type == SDFDDGI_LIGHT_DIRECTIONAL) {
                 st.d = f3(li.v[0], li.v[1], li.v[2]);
@@ -733,65 +760,152 @@ static cudaError_t launch_gather(const UpdateParams& p, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
+// Stage s (0 primary traces, 1 hit preparation, 2 shadow traces, 3 finalize + gather) of one
+// launch's probes (the volume, or one slab of it) on `stream`, followed by stage event s + 2
+// when ev is given. With pack, the tensor-core gather first packs the weight image (slab
+// branches find it packed before the fork).
 template <typename T>
-static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cudaEvent_t const* ev) {
+static cudaError_t launch_stage(const UpdateParams& p, const DeviceSetup& setup, int s, cudaStream_t stream,
+                                cudaEvent_t const* ev, bool pack) {
+    const int rp = p.omega_primary > 1.f ? 1 : 0, rs = p.omega_shadow > 1.f ? 1 : 0;
+    const uint32_t n = (uint32_t)p.P * (uint32_t)p.R;
+    cudaError_t e = cudaSuccess;
+    if (s == 0) {
+        const int g = persistent_blocks(setup, setup.occ_primary[rp][type_slot<T>()], p.sched.blocks_per_sm);
+        if (rp)
+            primary_kernel<T, true><<<g, kThreads, 0, stream>>>(p);
+        else
+            primary_kernel<T, false><<<g, kThreads, 0, stream>>>(p);
+    } else if (s == 1) {
+        prep_kernel<T><<<(n + kPrepRays - 1) / kPrepRays, kThreads, 0, stream>>>(p);
+    } else if (s == 2) {
+        const int g = persistent_blocks(setup, setup.occ_shadow[rs][type_slot<T>()], p.sched.blocks_per_sm);
+        if (rs)
+            shadow_kernel<T, true><<<g, kThreads, 0, stream>>>(p);
+        else
+            shadow_kernel<T, false><<<g, kThreads, 0, stream>>>(p);
+    } else {
+        finalize_kernel<<<(n + kFinalRays - 1) / kFinalRays, kThreads, 0, stream>>>(p);
+        if (gather_tc_supported(p) && p.sched.gather != 2)
+            e = launch_gather_tc(p, stream, pack);
+        else if (p.R <= 256)  // probes per gather CTA: as many as keep [R][G] values within 32 KiB
+            e = launch_gather<8>(p, stream);
+        else if (p.R <= 512)
+            e = launch_gather<4>(p, stream);
+        else
+            e = launch_gather<2>(p, stream);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[s + 2], stream);
+    return e;
+}
+
+constexpr bool kStageMajor = false;  // enqueue order of the slab branches' kernels
+
+// Slab c of K: the z-layers [c*gz/K, (c+1)*gz/K) of the probe grid, with every per-probe and
+// per-ray pointer moved to its first probe, its own counters and its own part of the task list.
+static UpdateParams slab_params(const UpdateParams& p, int c, int K) {
+    UpdateParams q = p;
+    const int layer = p.gdims[0] * p.gdims[1];
+    const int z0 = c * p.gdims[2] / K, z1 = (c + 1) * p.gdims[2] / K;
+    const size_t p0 = (size_t)layer * z0, k0 = p0 * (size_t)p.R;
+    const size_t lights = (size_t)(p.n_lights > 0 ? p.n_lights : 1);
+    q.P = layer * (z1 - z0);
+    q.p_begin = p.p_begin + (int)p0;
+    if (p.states) q.states = p.states + p0;
+    q.prev_irr = p.prev_irr + p0 * (kIrrT * kIrrT);
+    q.prev_depth = p.prev_depth + p0 * (kDepT * kDepT);
+    q.prev_valid = p.prev_valid + p0;
+    q.cur_irr = p.cur_irr + p0 * (kIrrT * kIrrT);
+    q.cur_depth = p.cur_depth + p0 * (kDepT * kDepT);
+    q.cur_valid = p.cur_valid + p0;
+    if (p.records) q.records = p.records + k0;
+    q.ray_t = p.ray_t + k0;
+    q.ray_es = p.ray_es + k0;
+    q.ray_n = p.ray_n + k0;
+    q.ray_alb = p.ray_alb + k0;
+    q.ray_base = p.ray_base + k0;
+    q.ray_lit = p.ray_lit + k0;
+    q.ray_ssteps = p.ray_ssteps + k0;
+    q.ray_val = p.ray_val + k0;
+    q.tasks = p.tasks + k0 * lights;
+    const size_t cap = (size_t)q.P * (size_t)p.R * lights;
+    q.task_capacity = (uint32_t)(cap < 0xffffffffu ? cap : 0xffffffffu);
+    q.counters = p.counters + (size_t)c * kSlabCounterStride;
+    return q;
+}
+
+template <typename T>
+static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cudaEvent_t const* ev,
+                                 const SlabLanes* lanes, int slabs) {
     const DeviceSetup* setup = nullptr;
     cudaError_t e = prepare_update_kernels(&setup);
     if (e != cudaSuccess) return e;
-    const int rp = p.omega_primary > 1.f ? 1 : 0, rs = p.omega_shadow > 1.f ? 1 : 0;
-    const int g_primary = persistent_blocks(*setup, setup->occ_primary[rp][type_slot<T>()], p.sched.blocks_per_sm);
-    const int g_shadow = persistent_blocks(*setup, setup->occ_shadow[rs][type_slot<T>()], p.sched.blocks_per_sm);
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], stream) : cudaSuccess; };
     e = mark(0);
-    // the pools and counts start at zero; the failure bits are sticky until read
-    if (e == cudaSuccess) e = cudaMemsetAsync(p.counters, 0, kFailWord * sizeof(uint32_t), stream);
+    // the pools and counts of every slab start at zero; the failure bits are sticky until read
+    for (int c = 0; c < slabs && e == cudaSuccess; ++c)
+        e = cudaMemsetAsync(p.counters + (size_t)c * kSlabCounterStride, 0, kFailWord * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return e;
-    const uint32_t n = (uint32_t)p.P * (uint32_t)p.R;
     if (p.depth_exp == 50)
         weights_kernel<50><<<p.R, kThreads, 0, stream>>>(p);
     else
         weights_kernel<0><<<p.R, kThreads, 0, stream>>>(p);
     weight_sums_kernel<<<1, kThreads, 0, stream>>>(p);
-    if ((e = mark(1)) != cudaSuccess) return e;
-    if (rp)
-        primary_kernel<T, true><<<g_primary, kThreads, 0, stream>>>(p);
-    else
-        primary_kernel<T, false><<<g_primary, kThreads, 0, stream>>>(p);
-    if ((e = mark(2)) != cudaSuccess) return e;
-    prep_kernel<T><<<(n + kPrepRays - 1) / kPrepRays, kThreads, 0, stream>>>(p);
-    if ((e = mark(3)) != cudaSuccess) return e;
-    if (rs)
-        shadow_kernel<T, true><<<g_shadow, kThreads, 0, stream>>>(p);
-    else
-        shadow_kernel<T, false><<<g_shadow, kThreads, 0, stream>>>(p);
-    if ((e = mark(4)) != cudaSuccess) return e;
-    finalize_kernel<<<(n + kFinalRays - 1) / kFinalRays, kThreads, 0, stream>>>(p);
-    if (gather_tc_supported(p) && p.sched.gather != 2) {
-        e = launch_gather_tc(p, stream);
-        if (e != cudaSuccess) return e;
-        return mark(5);
+    if (slabs == 1) {
+        if ((e = mark(1)) != cudaSuccess) return e;
+        for (int s = 0; s < 4 && e == cudaSuccess; ++s) e = launch_stage<T>(p, *setup, s, stream, ev, true);
+        return e;
     }
-    // probes per gather CTA: as many as keep the [R][G] values within 32 KiB of shared memory
-    if (p.R <= 256)
-        e = launch_gather<8>(p, stream);
-    else if (p.R <= 512)
-        e = launch_gather<4>(p, stream);
-    else
-        e = launch_gather<2>(p, stream);
+    // Slab branches: while one slab's pools drain (their last, longest rays keep few lanes
+    // busy), the other slabs' kernels fill the SMs. Slab c runs on its own stream (slab 0 on
+    // `stream`); the weights, shared by all, are ready before the fork.
+    const bool tc = gather_tc_supported(p) && p.sched.gather != 2;
+    if (tc && (e = launch_pack_weights(p, stream)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(lanes->fork, stream)) != cudaSuccess) return e;
+    for (int c = 1; c < slabs && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(lanes->side[c - 1], lanes->fork, 0);
     if (e != cudaSuccess) return e;
-    return mark(5);
+    UpdateParams q[kMaxSlabs];
+    for (int c = 0; c < slabs; ++c) q[c] = slab_params(p, c, slabs);
+    auto lane = [&](int c) { return c == 0 ? stream : lanes->side[c - 1]; };
+    if (kStageMajor) {
+        for (int s = 0; s < 4; ++s)
+            for (int c = 0; c < slabs && e == cudaSuccess; ++c) e = launch_stage<T>(q[c], *setup, s, lane(c), nullptr, false);
+    } else {
+        for (int c = 0; c < slabs; ++c)
+            for (int s = 0; s < 4 && e == cudaSuccess; ++s) e = launch_stage<T>(q[c], *setup, s, lane(c), nullptr, false);
+    }
+    // join even after a failed launch, so that no branch is left unjoined
+    cudaError_t j = cudaSuccess;
+    for (int c = 1; c < slabs && j == cudaSuccess; ++c) {
+        j = cudaEventRecord(lanes->join[c - 1], lanes->side[c - 1]);
+        if (j == cudaSuccess) j = cudaStreamWaitEvent(stream, lanes->join[c - 1], 0);
+    }
+    return e != cudaSuccess ? e : j;
 }
 
-cudaError_t launch_update(const UpdateParams& params, cudaStream_t stream, cudaEvent_t const* stage_events) {
+int slab_count(const UpdateParams& p, bool have_lanes, bool stage_events) {
+    if (!have_lanes || stage_events || p.P <= 0) return 1;
+    int k = p.sched.slabs;
+    // automatic: two slabs once an update is large enough for its pool tails to matter
+    if (k <= 0) k = (size_t)p.P * (size_t)p.R >= ((size_t)1 << 20) ? 2 : 1;
+    return max(1, min(min(k, kMaxSlabs), p.gdims[2]));
+}
+
+cudaError_t launch_update(const UpdateParams& params, cudaStream_t stream, cudaEvent_t const* stage_events,
+                          const SlabLanes* lanes) {
     if (params.P == 0) return cudaSuccess;
     UpdateParams p = params;
     if (!(p.omega_primary > 1.f)) p.omega_primary = 1.f;  // plain sphere tracing unless relaxation was asked for
     if (!(p.omega_shadow > 1.f)) p.omega_shadow = 1.f;
+    if (!p.look_irr) p.look_irr = p.prev_irr;
+    if (!p.look_valid) p.look_valid = p.prev_valid;
     p.dirs = reinterpret_cast<float4*>(p.weights + (size_t)(p.R + 1) * kTexels);  // after the weights
     p.ray_val = p.ray_n;  // the gather's values replace the normals, dead after the shadow stage
-    if (p.vol.dtype == kAnalytic) return launch_stages<Analytic>(p, stream, stage_events);
-    return p.vol.dtype == SDFDDGI_F16 ? launch_stages<__half>(p, stream, stage_events)
-                                      : launch_stages<float>(p, stream, stage_events);
+    const int slabs = slab_count(p, lanes != nullptr, stage_events != nullptr);
+    if (p.vol.dtype == kAnalytic) return launch_stages<Analytic>(p, stream, stage_events, lanes, slabs);
+    return p.vol.dtype == SDFDDGI_F16 ? launch_stages<__half>(p, stream, stage_events, lanes, slabs)
+                                      : launch_stages<float>(p, stream, stage_events, lanes, slabs);
 }
 
 }  // namespace sdfddgi

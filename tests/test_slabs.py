@@ -1,0 +1,111 @@
+"""Slab branches of one update (needs a B300).
+
+An update can run its probes as z-slabs of the probe grid, each slab's traces, shading and
+gather a chain of its own on one of two streams, so that one slab's kernels fill the SMs
+while another's pools drain to their last long rays. That is a schedule, not a change of
+arithmetic: the maps, the validity and every ray's record must equal the serial update's
+bit for bit. That includes the multi-bounce lookups near slab boundaries (they read the
+whole volume's last maps, Sec. 3.3), inactive probes, both gathers, uneven splits, the
+full open256 size the bench runs, and the fall-back to one slab while stage events are set.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2007_14394_b300 as S
+import workloads as W
+from harness import GpuVolume, make_workload
+
+pytestmark = pytest.mark.gpu
+
+
+class Pair:
+    """The same volume twice over one library scene: `serial` with one slab, `split` with
+    `slabs` slabs."""
+
+    def __init__(self, w, slabs):
+        self.w = w
+        self.scene = S.create_scene()
+        S.upload_sdf(self.scene, w.baked.sdf, w.baked.h, w.baked.origin, material=w.baked.material)
+        S.set_lights(self.scene, w.lights, w.sky)
+        self.serial = GpuVolume(w, seed=5, scene=self.scene)
+        self.split = GpuVolume(w, seed=5, scene=self.scene)
+        S.set_slabs(self.serial.vol, 1)
+        S.set_slabs(self.split.vol, slabs)
+
+    def step(self, frame, record=True):
+        rot = W.frame_rotation(9, frame)
+        self.serial.update(rot, record=record)
+        self.split.update(rot, record=record)
+
+    def assert_equal(self, label, records=True):
+        for x, y, name in zip(self.serial.state(), self.split.state(), ("irr", "depth", "valid")):
+            assert np.array_equal(x, y), (label, name)
+        if records:
+            torch.cuda.synchronize()
+            assert torch.equal(self.serial.records, self.split.records), (label, "records")
+        assert S.volume_status(self.serial.vol) == 0 and S.volume_status(self.split.vol) == 0, label
+
+    def close(self):
+        self.serial.close()
+        self.split.close()
+        S.destroy_scene(self.scene)
+
+
+@pytest.mark.parametrize("rays,dims,slabs", [
+    (64, (8, 8, 8), 2),     # tensor-core gather, even split
+    (64, (8, 8, 8), 3),     # uneven: 2, 3, 3 z-layers
+    (48, (6, 5, 7), 4),     # 1, 2, 2, 2 z-layers; slab sizes not multiples of the gather's 16 probes
+    (33, (5, 3, 6), 4),     # SIMT gather (R not a multiple of 16)
+])
+def test_slabs_equal_the_serial_update_bit_for_bit(cuda_device, rays, dims, slabs):
+    w = make_workload(W.PRESETS["room64"], rays=rays, probe_dims=dims, probe_origin=(0.7, 0.6, 0.5),
+                      probe_spacing=(0.9, 0.95, 0.9), k_bounce=0.9, hysteresis=0.5)
+    assert (w.states["flags"] & 1).sum() < len(w.states)  # some probes sit in geometry (inactive)
+    pr = Pair(w, slabs)
+    try:
+        assert S.volume_slabs(pr.split.vol) == slabs and S.volume_slabs(pr.serial.vol) == 1
+        for frame in range(3):  # frames 1 and 2 light hits from the last maps (multi-bounce)
+            pr.step(frame)
+            pr.assert_equal(f"frame {frame}")
+        assert np.abs(pr.split.state()[0][..., :3]).max() > 0
+    finally:
+        pr.close()
+
+
+def test_open256_auto_slabs_equal_serial(cuda_device):
+    """The bench's workload and launch configuration (automatic: two slabs) against one slab."""
+    w = make_workload(W.PRESETS["open256"])
+    pr = Pair(w, 0)
+    try:
+        assert S.volume_slabs(pr.split.vol) == 2
+        for frame in range(2):
+            pr.step(frame)
+            pr.assert_equal(f"open256 frame {frame}")
+    finally:
+        pr.close()
+
+
+def test_slab_arguments_and_stage_events(cuda_device):
+    w = make_workload(W.PRESETS["room64"])
+    gv = GpuVolume(w)
+    try:
+        assert S.volume_slabs(gv.vol) == 1  # 512 probes x 64 rays: below the automatic threshold
+        for bad in (-1, S.MAX_SLABS + 1):
+            with pytest.raises(S.SdfddgiError) as err:
+                S.set_slabs(gv.vol, bad)
+            assert err.value.code == S.ERR_INVALID_ARG
+        S.set_slabs(gv.vol, 4)
+        assert S.volume_slabs(gv.vol) == 4
+        events = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        for e in events:
+            e.record()
+        S.set_stage_events(gv.vol, events)
+        assert S.volume_slabs(gv.vol) == 1  # stage timing runs serially
+        gv.update(W.frame_rotation(1, 0), record=False)
+        torch.cuda.synchronize()
+        assert events[0].elapsed_time(events[5]) > 0
+        S.set_stage_events(gv.vol, [])
+        assert S.volume_slabs(gv.vol) == 4
+    finally:
+        gv.close()
