@@ -364,6 +364,21 @@ SDFDDGI_API int sdfddgi_get_maps(const sdfddgi_volume* v, const float** irr, con
  * written maps the history of the next update. Host copies are synchronous. */
 SDFDDGI_API int sdfddgi_read_state(const sdfddgi_volume* v, float* irr, float* depth, uint8_t* valid,
                                    int32_t on_device, void* stream);
+
+/* Asynchronous read of the current maps, for a pipeline that reads frame f's maps while
+ * frame f+1 updates: the copies run on a stream owned by the volume, ordered after
+ * everything enqueued on `stream` so far (the update that wrote the maps), and return at
+ * once. The maps are double-buffered: frame f+1 only reads the buffer being copied, and the
+ * library makes the first later call that overwrites it (update_probes two frames on,
+ * write_state, reset, a batch update or autotune) wait for the copy, on that call's stream.
+ *  irr, depth, valid -- as for read_state (any may be NULL), host or device memory; host
+ *                       memory must be page-locked for the copy to overlap device work.
+ *  stream            -- the stream the volume's updates are enqueued on.
+ *  done_event        -- NULL or a caller's cudaEvent_t (as void*), recorded after the
+ *                       copies: synchronize on it before using the arrays.
+ * Errors: INVALID_ARG for a NULL volume; CUDA when a copy or event call fails. */
+SDFDDGI_API int sdfddgi_read_state_async(sdfddgi_volume* v, float* irr, float* depth, uint8_t* valid, void* stream,
+                                         void* done_event);
 SDFDDGI_API int sdfddgi_write_state(sdfddgi_volume* v, const float* irr, const float* depth,
                                     const uint8_t* valid, int32_t on_device, void* stream);
 

@@ -94,6 +94,7 @@ def _load() -> C.CDLL:
         "sdfddgi_reset": ([vp, vp], C.c_int),
         "sdfddgi_set_stage_events": ([vp, C.POINTER(vp), i32], C.c_int),
         "sdfddgi_set_slabs": ([vp, i32], C.c_int),
+        "sdfddgi_read_state_async": ([vp, vp, vp, vp, vp, vp], C.c_int),
         "sdfddgi_volume_slabs": ([vp, C.POINTER(i32)], C.c_int),
         "sdfddgi_update_probes_noalloc": ([C.POINTER(VolumeDesc), vp, C.POINTER(i32), C.c_float, C.POINTER(C.c_float),
                                            i32, vp, C.POINTER(Light), i32, C.POINTER(C.c_float), u32, vp, vp,
@@ -134,7 +135,7 @@ EXPORTED = ("last_error", "create_scene", "destroy_scene", "upload_sdf", "set_li
             "create_denoiser", "destroy_denoiser", "denoiser_params", "denoise", "denoise_volume",
             "denoiser_gradients", "denoiser_adam", "denoiser_train_step", "volume_status", "denoiser_status",
             "relocate_probes", "sample_irradiance_visible", "upload_primitives", "sample_irradiance_cascade",
-            "set_slabs", "volume_slabs")
+            "set_slabs", "volume_slabs", "read_state_async")
 MAX_SLABS = 4
 DENOISER_PARAMS = 49219
 DENOISE_TENSOR, DENOISE_SIMT_BF16, DENOISE_SIMT_FP32 = 0, 1, 2
@@ -151,6 +152,19 @@ def set_stage_events(volume, events) -> None:
 def set_slabs(volume, slabs: int) -> None:
     """Slab branches per update of `volume`: 0 automatic, 1 serial, up to MAX_SLABS."""
     _check(lib.sdfddgi_set_slabs(volume, int(slabs)))
+
+
+def read_state_async(volume, irr, depth, valid, stream=None, done_event=None) -> None:
+    """Copies the current maps into irr/depth/valid (torch tensors, page-locked host or device
+    memory, or None) on the volume's copy stream, after the work enqueued on `stream`; records
+    `done_event` (a torch.cuda.Event, or None) after the copies. Returns at once."""
+    ptr = lambda t: None if t is None else t.data_ptr()
+    ev = None
+    if done_event is not None:
+        if not done_event.cuda_event:  # torch creates the CUDA event at its first record
+            done_event.record()
+        ev = done_event.cuda_event
+    _check(lib.sdfddgi_read_state_async(volume, ptr(irr), ptr(depth), ptr(valid), _stream(stream), ev))
 
 
 def volume_slabs(volume) -> int:

@@ -68,6 +68,12 @@ void free_volume_buffers(sdfddgi_volume* v) {
     }
     if (v->lanes.fork) cudaEventDestroy(v->lanes.fork);
     v->lanes = {};
+    if (v->copy) cudaStreamDestroy(v->copy);
+    if (v->read_order) cudaEventDestroy(v->read_order);
+    for (int b = 0; b < 2; ++b)
+        if (v->read_done[b]) cudaEventDestroy(v->read_done[b]);
+    v->copy = nullptr;
+    v->read_order = v->read_done[0] = v->read_done[1] = nullptr;
     v->weights = nullptr;
     v->wimage = nullptr;
     v->ray_t = nullptr;
@@ -333,6 +339,9 @@ SDFDDGI_API int sdfddgi_create_volume(const sdfddgi_volume_desc* d, sdfddgi_scen
             e = cudaStreamCreateWithFlags(&v->lanes.side[c], cudaStreamNonBlocking);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->lanes.join[c], cudaEventDisableTiming);
         }
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&v->copy, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->read_order, cudaEventDisableTiming);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaEventCreateWithFlags(&v->read_done[b], cudaEventDisableTiming);
         if (e != cudaSuccess) rc = fail(SDFDDGI_ERR_CUDA, "create_volume: %s", cudaGetErrorString(e));
     }
     if (rc) {
@@ -406,6 +415,13 @@ SDFDDGI_API int sdfddgi_frame_rotation(uint32_t seed, uint32_t frame, uint32_t v
 }
 
 }  // extern "C"
+
+cudaError_t sdfddgi::order_map_write(sdfddgi_volume* v, int buf, cudaStream_t stream) {
+    if (!v->pending_read[buf]) return cudaSuccess;
+    const cudaError_t e = cudaStreamWaitEvent(stream, v->read_done[buf], 0);
+    if (e == cudaSuccess) v->pending_read[buf] = false;
+    return e;
+}
 
 int sdfddgi::volume_params(sdfddgi_volume* v, UpdateParams* out) {
     sdfddgi_scene* s = v->scene;
@@ -491,7 +507,9 @@ SDFDDGI_API int sdfddgi_update_probes(sdfddgi_volume* v, uint32_t frame, const f
     }
     p.records = records;
     p.sched.slabs = v->slabs;
-    cudaError_t e = launch_update(p, st, v->has_stage_events ? v->stage_events : nullptr, &v->lanes);
+    cudaError_t e = order_map_write(v, v->cur ^ 1, st);  // the new maps replace a buffer being read?
+    if (e != cudaSuccess) return fail(SDFDDGI_ERR_CUDA, "update_probes: %s", cudaGetErrorString(e));
+    e = launch_update(p, st, v->has_stage_events ? v->stage_events : nullptr, &v->lanes);
     if (e != cudaSuccess) return fail(SDFDDGI_ERR_CUDA, "update_probes: launch failed: %s", cudaGetErrorString(e));
     v->cur ^= 1;
     return SDFDDGI_OK;
@@ -597,12 +615,29 @@ SDFDDGI_API int sdfddgi_read_state(const sdfddgi_volume* v, float* irr, float* d
     return SDFDDGI_OK;
 }
 
+SDFDDGI_API int sdfddgi_read_state_async(sdfddgi_volume* v, float* irr, float* depth, uint8_t* valid, void* stream,
+                                         void* done_event) {
+    if (!v) return fail(SDFDDGI_ERR_INVALID_ARG, "read_state_async: volume is NULL");
+    const int b = v->cur;
+    // after everything enqueued on `stream` so far (the update that wrote buffer b)
+    CUDA_TRY(cudaEventRecord(v->read_order, as_stream(stream)));
+    CUDA_TRY(cudaStreamWaitEvent(v->copy, v->read_order, 0));
+    if (irr) CUDA_TRY(cudaMemcpyAsync(irr, v->irr[b], v->P * kIrrBytes, cudaMemcpyDefault, v->copy));
+    if (depth) CUDA_TRY(cudaMemcpyAsync(depth, v->depth[b], v->P * kDepBytes, cudaMemcpyDefault, v->copy));
+    if (valid) CUDA_TRY(cudaMemcpyAsync(valid, v->valid[b], (size_t)v->P, cudaMemcpyDefault, v->copy));
+    CUDA_TRY(cudaEventRecord(v->read_done[b], v->copy));
+    v->pending_read[b] = true;
+    if (done_event) CUDA_TRY(cudaEventRecord(static_cast<cudaEvent_t>(done_event), v->copy));
+    return SDFDDGI_OK;
+}
+
 SDFDDGI_API int sdfddgi_write_state(sdfddgi_volume* v, const float* irr, const float* depth, const uint8_t* valid,
                                     int32_t on_device, void* stream) {
     if (!v) return fail(SDFDDGI_ERR_INVALID_ARG, "write_state: volume is NULL");
     if (!irr || !depth || !valid) return fail(SDFDDGI_ERR_INVALID_ARG, "write_state: NULL array");
     if (on_device != 0 && on_device != 1) return fail(SDFDDGI_ERR_INVALID_ARG, "write_state: on_device must be 0 or 1");
     cudaStream_t st = as_stream(stream);
+    CUDA_TRY(order_map_write(v, v->cur, st));
     CUDA_TRY(cudaMemcpyAsync(v->irr[v->cur], irr, v->P * kIrrBytes, cudaMemcpyDefault, st));
     CUDA_TRY(cudaMemcpyAsync(v->depth[v->cur], depth, v->P * kDepBytes, cudaMemcpyDefault, st));
     CUDA_TRY(cudaMemcpyAsync(v->valid[v->cur], valid, (size_t)v->P, cudaMemcpyDefault, st));
@@ -630,6 +665,7 @@ SDFDDGI_API int sdfddgi_reset(sdfddgi_volume* v, void* stream) {
     if (!v) return fail(SDFDDGI_ERR_INVALID_ARG, "reset: volume is NULL");
     cudaStream_t st = as_stream(stream);
     for (int k = 0; k < 2; ++k) {
+        CUDA_TRY(order_map_write(v, k, st));
         CUDA_TRY(cudaMemsetAsync(v->irr[k], 0, v->P * kIrrBytes, st));
         CUDA_TRY(cudaMemsetAsync(v->depth[k], 0, v->P * kDepBytes, st));
         CUDA_TRY(cudaMemsetAsync(v->valid[k], 0, (size_t)v->P, st));

@@ -178,6 +178,7 @@ SDFDDGI_API int sdfddgi_update_batch(sdfddgi_batch* b, uint32_t frame, const flo
         slot.exec = exec;
     }
     e = cudaMemcpyAsync(b->rot_dev, rot, sizeof(float) * 9 * b->n, cudaMemcpyHostToDevice, st);
+    for (int i = 0; i < b->n && e == cudaSuccess; ++i) e = order_map_write(b->vols[i], b->vols[i]->cur ^ 1, st);
     if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
     if (e != cudaSuccess) return bfail(SDFDDGI_ERR_CUDA, cudaGetErrorString(e));
     for (int i = 0; i < b->n; ++i) b->vols[i]->cur ^= 1;
@@ -195,6 +196,10 @@ SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* 
         sdfddgi_volume* v = b->vols[i];
         // every trial reads the current maps and writes the other buffer, which the next
         // real update overwrites: the volume's state is untouched
+        if (order_map_write(v, v->cur ^ 1, st) != cudaSuccess) {
+            rc = bfail(SDFDDGI_ERR_CUDA, "batch_autotune: cudaStreamWaitEvent failed");
+            break;
+        }
         UpdateParams probe;
         rc = volume_params(v, &probe);
         if (rc) break;

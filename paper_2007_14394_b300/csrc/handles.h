@@ -54,6 +54,13 @@ struct sdfddgi_volume {
     bool has_stage_events = false;
     int slabs = 0;                    // slab branches per update (0 automatic)
     sdfddgi::SlabLanes lanes = {};    // the second stream and fork/join events of slab branches
+    // asynchronous reads of the maps (read_state_async): they run on `copy`; read_done[b] is
+    // recorded after a read of buffer b, and pending_read[b] tells that work which writes
+    // buffer b must wait for it
+    cudaStream_t copy = nullptr;
+    cudaEvent_t read_order = nullptr;
+    cudaEvent_t read_done[2] = {nullptr, nullptr};
+    bool pending_read[2] = {false, false};
 };
 
 namespace sdfddgi {
@@ -63,4 +70,7 @@ void scene_view(const sdfddgi_scene* s, VolumeView* v);
 // ping-pong parity (rotation, probe states, records and schedule are left zero); ensures the
 // shadow-task capacity. Returns an sdfddgi_status.
 int volume_params(sdfddgi_volume* v, UpdateParams* p);
+// Makes `stream` wait for a pending asynchronous read of map buffer `buf` before work that
+// writes the buffer (a no-op when none is pending).
+cudaError_t order_map_write(sdfddgi_volume* v, int buf, cudaStream_t stream);
 }  // namespace sdfddgi
