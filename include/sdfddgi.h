@@ -527,7 +527,8 @@ SDFDDGI_API int sdfddgi_denoiser_train_step(sdfddgi_denoiser* d, const sdfddgi_p
  * layout, per-ray buffers, the shadow-task list, texel weights, counters) lives in one
  * fixed 32 MiB array in device memory that every GPU loading this library holds until
  * the process exits. An update needs, each part rounded up to 256 bytes: 16 bytes per
- * SDF voxel (8 at binary16), 64 + 16*max(n_lights,1) bytes per probe ray (P*R), and
+ * SDF voxel with nz rounded up to even (8 at binary16), 64 + 16*max(n_lights,1) bytes per
+ * probe ray (P*R), and
  * 944*R + 928 bytes -- e.g. a 64^3 float32 SDF with 512 probes x 64 rays and 1 light
  * takes about 6.6 MiB. An update that does not fit in 32 MiB is rejected with
  * SDFDDGI_ERR_INVALID_ARG before any device work, and sdfddgi_last_error() states the

@@ -182,7 +182,7 @@ SDFDDGI_API int sdfddgi_upload_sdf(sdfddgi_scene* s, const void* sdf, const int3
         s->sdf_bytes = sdf_bytes;
     }
     CUDA_TRY(cudaMemcpyAsync(s->sdf, sdf, sdf_bytes, cudaMemcpyDefault, st));
-    const size_t qb = quad_bytes(dtype, n);
+    const size_t qb = quad_bytes(dtype, dims);
     if (s->quads_bytes != qb) {
         cudaFree(s->quads);
         s->quads = nullptr;

@@ -23,6 +23,7 @@ __device__ __forceinline__ float3 fma3(float s, float3 d, float3 o) {
 // ------------------------------------------------------------------ volume sampling
 struct Cell {
     size_t base;  // linear index of corner (0,0,0)
+    int ix, iy, iz;
     float fx, fy, fz;
 };
 
@@ -39,6 +40,9 @@ __device__ __forceinline__ Cell cell_of(const VolumeView& v, float3 p) {
     int iy = clamp_index(fmaf(p.y - v.lo[1], v.inv_h, -0.5f), v.ny, &c.fy);
     int iz = clamp_index(fmaf(p.z - v.lo[2], v.inv_h, -0.5f), v.nz, &c.fz);
     c.base = ((size_t)iz * v.ny + iy) * v.nx + ix;
+    c.ix = ix;
+    c.iy = iy;
+    c.iz = iz;
     return c;
 }
 
@@ -63,8 +67,11 @@ __device__ __forceinline__ float4 ld_quad<__half>(const void* quads, size_t i) {
 template <typename T>
 __device__ __forceinline__ float sample_sdf(const VolumeView& v, float3 p) {
     const Cell c = cell_of(v, p);
-    const float4 q0 = ld_quad<T>(v.quads, c.base);                              // slice z
-    const float4 q1 = ld_quad<T>(v.quads, c.base + (size_t)v.nx * v.ny);        // slice z + 1
+    const size_t i0 = quad_index((size_t)c.ix, (size_t)c.iy, (size_t)c.iz, (size_t)v.nx, (size_t)v.ny);
+    // slice z + 1: the next entry for even z, else the first of the next pair
+    const size_t i1 = (c.iz & 1) ? i0 + (size_t)2 * v.nx * v.ny - 1 : i0 + 1;
+    const float4 q0 = ld_quad<T>(v.quads, i0);  // slice z
+    const float4 q1 = ld_quad<T>(v.quads, i1);  // slice z + 1
     const float x00 = lerp(q0.x, q0.y, c.fx), x10 = lerp(q0.z, q0.w, c.fx);
     const float x01 = lerp(q1.x, q1.y, c.fx), x11 = lerp(q1.z, q1.w, c.fx);
     return lerp(lerp(x00, x10, c.fy), lerp(x01, x11, c.fy), c.fz);

@@ -44,7 +44,7 @@ constexpr int kAnalytic = 2;  // VolumeView::dtype of a scene made of primitives
 // material volume) or, with dtype kAnalytic, a union of analytic primitives in clusters.
 struct VolumeView {
     const void* sdf;          // float or __half, [nz][ny][nx]
-    const void* quads;        // xy-quads of the same values: float4 or 4 x __half per voxel
+    const void* quads;        // xy-quads of the same values (float4 or 4 x __half), in z-pairs: quad_index
     const uint4* material;    // 8 x binary16 per voxel (albedo rgb, -, emission rgb, -), or null
     int nx, ny, nz;
     int dtype;                // SDFDDGI_F32 / SDFDDGI_F16 / kAnalytic
@@ -177,7 +177,12 @@ cudaError_t launch_update(const UpdateParams& p, cudaStream_t stream, cudaEvent_
 int slab_count(const UpdateParams& p, bool have_lanes, bool stage_events);
 cudaError_t launch_sample(const SampleParams& p, cudaStream_t stream);
 cudaError_t launch_sample_visible(const SampleParams& p, const VisParams& v, cudaStream_t stream);
-size_t quad_bytes(int dtype, size_t n_voxels);
+// Position of quad (x, y, z) in the xy-quad copy: z-pairs, [z/2][y][x][z%2].
+__host__ __device__ __forceinline__ size_t quad_index(size_t x, size_t y, size_t z, size_t nx, size_t ny) {
+    return (((z >> 1) * ny + y) * nx + x) * 2 + (z & 1);
+}
+// Bytes of the xy-quad copy of an SDF of `dims` voxels (nz rounded up to even).
+size_t quad_bytes(int dtype, const int dims[3]);
 inline size_t weights_bytes(int R) { return ((size_t)(R + 1) * kTexels + (size_t)R * 4) * sizeof(float); }
 int report_error(int code, const char* msg);  // sets the text of sdfddgi_last_error(), returns code
 // the gather of Eq. 3 on the tensor cores (R a multiple of 16 and a weight image present)

@@ -103,7 +103,7 @@ SDFDDGI_API int sdfddgi_update_probes_noalloc(
     // ---- scratch layout and its limit
     const size_t n_vox = (size_t)dims[0] * dims[1] * dims[2];
     const size_t n_rays = (size_t)P * R;
-    const size_t sizes[] = {quad_bytes(dtype, n_vox),
+    const size_t sizes[] = {quad_bytes(dtype, dims),
                             n_rays * 4,   // ray_t
                             n_rays * 4,   // ray_es
                             n_rays * 16,  // ray_n

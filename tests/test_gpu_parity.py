@@ -10,6 +10,8 @@ mismatch. The bar (float32 path):
   hit distance within 1e-3 voxel; irradiance and moments relative error <= 1e-4;
   borders bit-exact mirrors; history flags equal.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -90,6 +92,17 @@ def test_open256_full_size_sampled():
     for f, s in enumerate(stats):
         print("open256 frame", f, s)
         assert_bar(s, f"open256 frame {f}")
+
+
+def test_odd_depth_unequal_sides():
+    """An SDF of 64 x 56 x 61 voxels: unequal sides and an odd depth, so the last z-pair of
+    the quad store holds one slice; probes fill the cut room."""
+    pr = dataclasses.replace(W.PRESETS["room64"], sdf_dims=(64, 56, 61))
+    w = make_workload(pr, probe_dims=(6, 5, 6), probe_origin=(0.7, 0.6, 0.5), probe_spacing=(1.1, 1.2, 1.2))
+    (s,) = run_and_compare(w)
+    print("64x56x61", s)
+    assert s["rays"] > 5000
+    assert_bar(s, "64x56x61")
 
 
 @pytest.mark.parametrize("rays", [1, 7, 33, 1000, 1024])
