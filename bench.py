@@ -32,13 +32,13 @@ METRIC = "probe-rays/s & ms per probe-volume update; learned vs plain rays at eq
 UNIT = "probe-rays/s"
 WORKLOAD = "open256"
 L2_FLUSH_BYTES = 512 << 20
-KERNELS_PER_UPDATE = 8  # texel weights, weight sums, primary, hit preparation, shadow, finalize, weight image, gather
+KERNELS_PER_UPDATE = 7  # texel weights, primary, hit preparation, shadow, finalize, weight image, gather
 
 
 def kernels_per_update(slabs: int) -> int:
     """Kernel launches of one update run as `slabs` slab branches (tensor-core gather): the
-    weights, their sums and the weight image once, then five stage kernels per slab."""
-    return KERNELS_PER_UPDATE if slabs <= 1 else 3 + 5 * slabs
+    weights and the weight image once, then five stage kernels per slab."""
+    return KERNELS_PER_UPDATE if slabs <= 1 else 2 + 5 * slabs
 
 
 def peaks():

@@ -851,7 +851,9 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
         weights_kernel<50><<<p.R, kThreads, 0, stream>>>(p);
     else
         weights_kernel<0><<<p.R, kThreads, 0, stream>>>(p);
-    weight_sums_kernel<<<1, kThreads, 0, stream>>>(p);
+    const bool tc = gather_tc_supported(p) && p.sched.gather != 2;
+    // the column sums serve the SIMT gather; the tensor-core gather sums a ones channel
+    if (!tc) weight_sums_kernel<<<1, kThreads, 0, stream>>>(p);
     if (slabs == 1) {
         if ((e = mark(1)) != cudaSuccess) return e;
         for (int s = 0; s < 4 && e == cudaSuccess; ++s) e = launch_stage<T>(p, *setup, s, stream, ev, true);
@@ -860,7 +862,6 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
     // Slab branches: while one slab's pools drain (their last, longest rays keep few lanes
     // busy), the other slabs' kernels fill the SMs. Slab c runs on its own stream (slab 0 on
     // `stream`); the weights, shared by all, are ready before the fork.
-    const bool tc = gather_tc_supported(p) && p.sched.gather != 2;
     if (tc && (e = launch_pack_weights(p, stream)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(lanes->fork, stream)) != cudaSuccess) return e;
     for (int c = 1; c < slabs && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(lanes->side[c - 1], lanes->fork, 0);
