@@ -983,14 +983,26 @@ def cpu_baseline(pr, scene, baked, states, budget_s=10.0):
     prev, frames, t_total = None, 0, 0.0
     while t_total < budget_s and frames < 64:
         t0 = time.perf_counter()
-        out = O.update(osc, g, scene.lights, W.frame_rotation(pr.seed, frames), states, prev=prev, want_rays=False)
+        out = O.update(osc, g, scene.lights, W.frame_rotation(pr.seed, frames), states, prev=prev, want_rays=False,
+                       n_threads=cores)
         t_total += time.perf_counter() - t0
         prev = (out["irr"], out["depth"], out["valid"])
         frames += 1
+    # one core, on a seeded sample of the active probes sized for about a third of the budget
+    per_probe_1core = t_total / frames / n_active * cores
+    n1 = int(max(8, min(n_active, budget_s / 3 / max(per_probe_1core, 1e-9))))
+    sub = np.sort(np.random.default_rng(3).choice(np.flatnonzero(states["flags"] & 1), n1, replace=False))
+    t0 = time.perf_counter()
+    O.update(osc, g, scene.lights, W.frame_rotation(pr.seed, frames), states, prev=prev, subset=sub, want_rays=False,
+             n_threads=1)
+    t1 = time.perf_counter() - t0
     return {"value": frames * n_active * pr.rays / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{frames} consecutive full frames of {pr.name} ({n_active} active probes x {pr.rays} rays), "
                       f"{t_total:.1f} s on {cores} OpenMP threads",
-            "ms_per_step": 1e3 * t_total / frames}
+            "ms_per_step": 1e3 * t_total / frames,
+            "one_core": {"value": n1 * pr.rays / t1, "unit": UNIT, "cores": 1,
+                         "sample": f"{n1} seeded active probes of frame {frames} x {pr.rays} rays, {t1:.1f} s "
+                                   "on 1 thread"}}
 
 
 def run_reference(args):
