@@ -176,9 +176,10 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
     // and without a CTA-wide barrier:
     //  the copier (warp 4, lane 0) brings chunk c's weight image into stage c % kStages with one
     //    bulk copy as soon as the MMAs of chunk c - kStages are done (full_a counts the bytes);
-    //  producers (the first kProducers threads) then build chunk c's B operand from the rays'
-    //    values, split as the format asks, and arrive on full_b; each loads its values of the
-    //    next chunk into registers one chunk ahead;
+    //  producers (the first kProducers threads) build chunk c's B operand from the rays'
+    //    values at the same time (they too wait only for chunk c - kStages's MMAs), split as
+    //    the format asks, and arrive on full_b; each loads its values of the next chunk into
+    //    registers one chunk ahead;
     //  the issuer (warp 5, lane 0) issues chunk c's MMAs once both operands are in and commits
     //    them to empty[c % kStages], which frees the stage for both.
     // Copies thus run up to kStages - 1 chunks ahead of the MMAs.
@@ -208,10 +209,11 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
 #pragma unroll
                 for (int j = 0; j < kVec; ++j) nxt[j] = src[(size_t)(c + 1) * kChunk + j];
             }
-            {  // the stage is free once its weights are in (the copier waited for the MMAs of
-               // chunk c - kStages first); one lane of the warp waits, the others take its answer
+            if (c >= kStages) {  // the stage is free once chunk c - kStages's MMAs are done (its
+                                 // weights may still be arriving); one lane of the warp waits,
+                                 // the others take its answer
                 int ok = 1;
-                if (lane == 0) ok = mbar_wait(&bar_full_a[s], (c / kStages) & 1, fail_word);
+                if (lane == 0) ok = mbar_wait(&bar_empty[s], ((c / kStages) - 1) & 1, fail_word);
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) {
                     if (lane == 0) give_up();
