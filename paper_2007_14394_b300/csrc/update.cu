@@ -800,8 +800,6 @@ static cudaError_t launch_stage(const UpdateParams& p, const DeviceSetup& setup,
     return e;
 }
 
-constexpr bool kStageMajor = false;  // enqueue order of the slab branches' kernels
-
 // Slab c of K: the z-layers [c*gz/K, (c+1)*gz/K) of the probe grid, with every per-probe and
 // per-ray pointer moved to its first probe, its own counters and its own part of the task list.
 static UpdateParams slab_params(const UpdateParams& p, int c, int K) {
@@ -869,13 +867,8 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
     UpdateParams q[kMaxSlabs];
     for (int c = 0; c < slabs; ++c) q[c] = slab_params(p, c, slabs);
     auto lane = [&](int c) { return c == 0 ? stream : lanes->side[c - 1]; };
-    if (kStageMajor) {
-        for (int s = 0; s < 4; ++s)
-            for (int c = 0; c < slabs && e == cudaSuccess; ++c) e = launch_stage<T>(q[c], *setup, s, lane(c), nullptr, false);
-    } else {
-        for (int c = 0; c < slabs; ++c)
-            for (int s = 0; s < 4 && e == cudaSuccess; ++s) e = launch_stage<T>(q[c], *setup, s, lane(c), nullptr, false);
-    }
+    for (int c = 0; c < slabs; ++c)
+        for (int s = 0; s < 4 && e == cudaSuccess; ++s) e = launch_stage<T>(q[c], *setup, s, lane(c), nullptr, false);
     // join even after a failed launch, so that no branch is left unjoined
     cudaError_t j = cudaSuccess;
     for (int c = 1; c < slabs && j == cudaSuccess; ++c) {
