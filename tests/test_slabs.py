@@ -20,16 +20,21 @@ pytestmark = pytest.mark.gpu
 
 
 class Pair:
-    """The same volume twice over one library scene: `serial` with one slab, `split` with
-    `slabs` slabs."""
+    """The same volume twice: `serial` with one slab, `split` with `slabs` slabs; over one
+    library scene, or (analytic) each over its own identical scene of primitives."""
 
-    def __init__(self, w, slabs):
+    def __init__(self, w, slabs, flags=0, analytic=False):
         self.w = w
-        self.scene = S.create_scene()
-        S.upload_sdf(self.scene, w.baked.sdf, w.baked.h, w.baked.origin, material=w.baked.material)
-        S.set_lights(self.scene, w.lights, w.sky)
-        self.serial = GpuVolume(w, seed=5, scene=self.scene)
-        self.split = GpuVolume(w, seed=5, scene=self.scene)
+        self.scene = None
+        if analytic:
+            self.serial = GpuVolume(w, seed=5, flags=flags, analytic=True)
+            self.split = GpuVolume(w, seed=5, flags=flags, analytic=True)
+        else:
+            self.scene = S.create_scene()
+            S.upload_sdf(self.scene, w.baked.sdf, w.baked.h, w.baked.origin, material=w.baked.material)
+            S.set_lights(self.scene, w.lights, w.sky)
+            self.serial = GpuVolume(w, seed=5, flags=flags, scene=self.scene)
+            self.split = GpuVolume(w, seed=5, flags=flags, scene=self.scene)
         S.set_slabs(self.serial.vol, 1)
         S.set_slabs(self.split.vol, slabs)
 
@@ -49,7 +54,8 @@ class Pair:
     def close(self):
         self.serial.close()
         self.split.close()
-        S.destroy_scene(self.scene)
+        if self.scene is not None:
+            S.destroy_scene(self.scene)
 
 
 @pytest.mark.parametrize("rays,dims,slabs", [
@@ -69,6 +75,24 @@ def test_slabs_equal_the_serial_update_bit_for_bit(cuda_device, rays, dims, slab
             pr.step(frame)
             pr.assert_equal(f"frame {frame}")
         assert np.abs(pr.split.state()[0][..., :3]).max() > 0
+    finally:
+        pr.close()
+
+
+@pytest.mark.parametrize("form", ["binary16 SDF, bf16 gather", "relaxed traces", "analytic primitives"])
+def test_slabs_equal_serial_in_every_form(cuda_device, form):
+    """The other forms of the update run through the same slab branches."""
+    preset, flags, analytic = {
+        "binary16 SDF, bf16 gather": ("room64_fp16", S.FLAG_BLEND_BF16, False),
+        "relaxed traces": ("room64", S.FLAG_RELAXED_PRIMARY | S.FLAG_RELAXED_SHADOW, False),
+        "analytic primitives": ("room64", 0, True),
+    }[form]
+    w = make_workload(W.PRESETS[preset], k_bounce=0.9, hysteresis=0.5)
+    pr = Pair(w, 3, flags=flags, analytic=analytic)
+    try:
+        for frame in range(2):
+            pr.step(frame)
+            pr.assert_equal(f"{form}, frame {frame}")
     finally:
         pr.close()
 
