@@ -921,7 +921,7 @@ def run_learned(args, rank, world, local_rank):
                    "probes": P, "active_probes": n_active, "train_steps": args.train_steps, "batch_grids": 8,
                    "lr": 3e-4, "depth_scale": depth_scale,
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
-        "gpu_launches": (KERNELS_PER_UPDATE + 2) * args.steps,
+        "gpu_launches": (kernels_per_update(S.volume_slabs(v32)) + 2) * args.steps,
         "rmse_heldout": err, "rmse_train": err_train, "equal_error_rays": r_eq,
         "ms": {"learned32_frame": learned_ms, "denoise": denoise_ms, "update32": learned_ms - denoise_ms,
                **{f"plain{r}": t for r, t in plain_ms.items()}},

@@ -268,7 +268,7 @@ SDFDDGI_API int sdfddgi_set_stage_events(sdfddgi_volume* v, void* const* events,
  * lanes busy; the other slab's kernels fill the SMs meanwhile. The texel weights are
  * computed once, before the fork. Each slab has its own pool counters and part of the
  * shadow-task list; the multi-bounce lookup still reads the whole volume's last maps.
- *  slabs -- 0: automatic (2 when P*R >= 2^20 rays, else 1), 1: serial, up to
+ *  slabs -- 0: automatic (2 when P*R >= 2^19 rays, else 1), 1: serial, up to
  *           SDFDDGI_MAX_SLABS (at most nz slabs are used).
  * Returns SDFDDGI_ERR_INVALID_ARG outside [0, SDFDDGI_MAX_SLABS]. */
 SDFDDGI_API int sdfddgi_set_slabs(sdfddgi_volume* v, int32_t slabs);

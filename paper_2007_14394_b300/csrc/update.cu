@@ -882,7 +882,8 @@ int slab_count(const UpdateParams& p, bool have_lanes, bool stage_events) {
     if (!have_lanes || stage_events || p.P <= 0) return 1;
     int k = p.sched.slabs;
     // automatic: two slabs once an update is large enough for its pool tails to matter
-    if (k <= 0) k = (size_t)p.P * (size_t)p.R >= ((size_t)1 << 20) ? 2 : 1;
+    // (measured on open256: from 2^19 rays, 32 rays per probe, two slabs are ahead)
+    if (k <= 0) k = (size_t)p.P * (size_t)p.R >= ((size_t)1 << 19) ? 2 : 1;
     return max(1, min(min(k, kMaxSlabs), p.gdims[2]));
 }
 
