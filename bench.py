@@ -35,6 +35,26 @@ L2_FLUSH_BYTES = 512 << 20
 KERNELS_PER_UPDATE = 7  # texel weights, primary, hit preparation, shadow, finalize, weight image, gather
 
 
+def max_over_ranks(values, world: int, device=None):
+    """Each value's maximum over the ranks (the slowest rank's time); the values unchanged at
+    world size 1. NCCL reduces a tensor on `device`, gloo one in host memory."""
+    values = [float(v) for v in values]
+    if world <= 1:
+        return values
+    import torch
+    import torch.distributed as dist
+    on = device if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor(values, dtype=torch.float64, device=on)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_rate(world: int, units_per_rank_step: float, steps: int, ms_total: float) -> float:
+    """Units per second of the whole job: every rank processes units_per_rank_step per step
+    (weak scaling), over the slowest rank's total time in milliseconds."""
+    return world * units_per_rank_step * steps / (ms_total / 1e3)
+
+
 def kernels_per_update(slabs: int) -> int:
     """Kernel launches of one update run as `slabs` slab branches (tensor-core gather): the
     weights and the weight image once, then five stage kernels per slab."""
@@ -368,14 +388,11 @@ def run_ours(args, rank, world, local_rank):
                           "updates": n_r}
         S.destroy_volume(rvol)
 
-    if world > 1:
-        t = torch.tensor([dev_ms, e2e_ms, e2e_serial_ms, wall], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dev_ms, e2e_ms, e2e_serial_ms, wall = (float(x) for x in t.tolist())
+    dev_ms, e2e_ms, e2e_serial_ms, wall = max_over_ranks([dev_ms, e2e_ms, e2e_serial_ms, wall], world, dev)
 
     ms = dev_ms / args.steps
-    value = world * rays_per_step * args.steps / (dev_ms / 1e3)
-    e2e_value = world * rays_per_step * args.steps / (e2e_ms / 1e3)
+    value = whole_job_rate(world, rays_per_step, args.steps, dev_ms)
+    e2e_value = whole_job_rate(world, rays_per_step, args.steps, e2e_ms)
     hbm, peak_kind = peaks()
     sm_mhz = float((clk or {}).get("sm_max_mhz") or 2032.0)
     stages = {}
@@ -420,7 +437,7 @@ def run_ours(args, rank, world, local_rank):
                 "how": "update_probes with page-locked host probe states, then read_state_async of both maps and "
                        "validity into page-locked host memory; frame k's read overlaps frame k+1's update; one "
                        "CUDA-event interval over all steps, ending when the last read is done"},
-        "e2e_serial": {"value": world * rays_per_step * args.steps / (e2e_serial_ms / 1e3), "unit": UNIT,
+        "e2e_serial": {"value": whole_job_rate(world, rays_per_step, args.steps, e2e_serial_ms), "unit": UNIT,
                        "ms_per_step": e2e_serial_ms / args.steps,
                        "how": "the same calls with the synchronous read_state, each step timed alone, L2 flushed "
                               "between steps"},
@@ -533,12 +550,9 @@ def run_batch(args, rank, world, local_rank):
     e2e_step_ms = timed(e2e_step, 20_000)
 
     dev_ms, seq_ms, e2e_ms = float(sum(per_step)), float(sum(seq_step)), float(sum(e2e_step_ms))
-    if world > 1:
-        t = torch.tensor([dev_ms, seq_ms, e2e_ms, wall], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dev_ms, seq_ms, e2e_ms, wall = (float(x) for x in t.tolist())
+    dev_ms, seq_ms, e2e_ms, wall = max_over_ranks([dev_ms, seq_ms, e2e_ms, wall], world, dev)
     ms = dev_ms / args.steps
-    value = world * rays_per_step * args.steps / (dev_ms / 1e3)
+    value = whole_job_rate(world, rays_per_step, args.steps, dev_ms)
     hbm, peak_kind = peaks()
     frame_bytes = sum(w[k]["bytes"] for w in work for k in ("primary", "prep", "shadow"))
     ach = frame_bytes / (ms / 1e3) / 1e9
@@ -558,9 +572,9 @@ def run_batch(args, rank, world, local_rank):
             "active_rays_per_step": rays_per_step, "seed": base.seed,
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)", "autotune_s": t_tune},
         "gpu_launches": KERNELS_PER_UPDATE * len(vols) * args.steps,
-        "sequential": {"ms_per_step": seq_ms / args.steps, "value": world * rays_per_step * args.steps / (seq_ms / 1e3),
+        "sequential": {"ms_per_step": seq_ms / args.steps, "value": whole_job_rate(world, rays_per_step, args.steps, seq_ms),
                        "what": "one plain update_probes launch per volume, default schedules, same stream"},
-        "e2e": {"value": world * rays_per_step * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+        "e2e": {"value": whole_job_rate(world, rays_per_step, args.steps, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": P_all * 16,
                 "d2h_bytes_per_step": P_all * (8 * 8 * 4 * 4 + 16 * 16 * 2 * 4 + 1),
                 "ms_per_step": e2e_ms / args.steps},
@@ -666,15 +680,12 @@ def run_cascade_query(args, rank, world, local_rank):
         ho.copy_(out, non_blocking=True)
     e2e_ms = timed(e2e_step)
     ms, e2e = float(np.mean(per_step)), float(np.mean(e2e_ms))
-    if world > 1:
-        t = torch.tensor([ms, e2e], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e = (float(x) for x in t.tolist())
+    ms, e2e = max_over_ranks([ms, e2e], world, dev)
     hbm, peak_kind = peaks()
     alg = n * (24 + 12) + touched_map_bytes(c, pts, level, weight)
     ach = alg / (ms / 1e3) / 1e9
     line = {
-        "metric": "irradiance queries/s through a cascade of probe volumes", "value": world * n / (ms / 1e3),
+        "metric": "irradiance queries/s through a cascade of probe volumes", "value": whole_job_rate(world, n, 1, ms),
         "unit": "points/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (random maps, seeded points)",
@@ -684,7 +695,7 @@ def run_cascade_query(args, rank, world, local_rank):
                    "blending_points": int(blend.sum()),
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
         "gpu_launches": args.steps,
-        "e2e": {"value": world * n / (e2e / 1e3), "unit": "points/s", "h2d_bytes_per_step": n * 24,
+        "e2e": {"value": whole_job_rate(world, n, 1, e2e), "unit": "points/s", "h2d_bytes_per_step": n * 24,
                 "d2h_bytes_per_step": n * 12, "ms_per_step": e2e},
         "roofline": {"kernel": "cascade_kernel", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                      "frac": ach / hbm, "bytes_per_launch": alg, "peak_source": f"{peak_kind} hbm_gbs",
@@ -787,13 +798,10 @@ def run_analytic(args, rank, world, local_rank):
     ms_v, _, _ = measure(lambda sc: S.upload_sdf(sc, baked.sdf, baked.h, baked.origin, material=baked.material),
                          max(3, args.steps // 4))
     ms = float(np.mean(ms_c))
-    if world > 1:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    (ms,) = max_over_ranks([ms], world, dev)
     dominant = max(("primary", "prep", "shadow"), key=lambda n: stages[n])
     line = {
-        "metric": METRIC, "value": world * rays_per_step / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": whole_job_rate(world, rays_per_step, 1, ms), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scene of analytic primitives)",
         "config": dict(workload_config(pr, rays_per_step), workload=f"{args.workload}: the {pr.name} scene as "
@@ -905,12 +913,13 @@ def run_learned(args, rank, world, local_rank):
         plain_ms[rays] = statistics.median(timed(lambda f: S.update_probes(v, f, states=states_dev, stream=stream)))
         S.destroy_volume(v)
     learned_ms = statistics.median(learned_steps)
+    (learned_ms,) = max_over_ranks([learned_ms], world, dev)
     denoise_ms = statistics.median(dn_ms)
     P = pr.n_probes
     tc_peak, tc_kind = tensor_peak()
     ach = DENOISER_FLOPS_PER_PROBE * n_active / (denoise_ms / 1e3) / 1e12
     eq_rays = r_eq if r_eq else None
-    value = (n_active * eq_rays / (learned_ms / 1e3)) if eq_rays else None
+    value = whole_job_rate(world, n_active * eq_rays, 1, learned_ms) if eq_rays else None
     line = {
         "metric": METRIC, "value": value, "unit": "equal-error probe-rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": learned_ms, "higher_is_better": True, "scaling": "weak",
