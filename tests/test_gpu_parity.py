@@ -18,7 +18,7 @@ import pytest
 import oracle as O
 import workloads as W
 from harness import (T_TOL_VOX, T_COND_FACTOR, DELTA_VOX, DELTA_COS, GpuVolume, assert_bar, border_is_mirror,
-                     compare, force_from_records, make_workload, oracle_grid, oracle_scene)
+                     compare, f32, f32v, force_from_records, make_workload, oracle_grid, oracle_scene)
 
 pytestmark = pytest.mark.gpu
 
@@ -103,6 +103,34 @@ def test_odd_depth_unequal_sides():
     print("64x56x61", s)
     assert s["rays"] > 5000
     assert_bar(s, "64x56x61")
+
+
+@pytest.mark.parametrize("n_lights", [0, 32])
+def test_light_counts(n_lights):
+    """No light (no shadow task at all) and the most a scene holds, 32 (every value of the
+    tasks' 5-bit light index and every bit of the visibility mask)."""
+    w = make_workload(W.PRESETS["room64"], probe_dims=(4, 4, 4), probe_origin=(1.2, 1.2, 1.2),
+                      probe_spacing=(1.8, 1.8, 1.8))
+    rng = np.random.default_rng(n_lights)
+    points = [{"type": "point", "v": f32v(rng.uniform(1.0, 7.0, 3)), "rgb": f32v(rng.uniform(0.5, 4.0, 3)),
+               "range": f32(rng.uniform(2.0, 6.0))} for _ in range(max(n_lights - 1, 0))]
+    w = dataclasses.replace(w, lights=(w.lights[:1] + points) if n_lights else [])
+    (s,) = run_and_compare(w)
+    print(n_lights, "lights", s)
+    assert_bar(s, f"{n_lights} lights")
+
+
+def test_one_step_budget_and_probes_outside_the_box():
+    """A budget of one step (every ray that does not hit at once ends exhausted, shaded where
+    it stopped) and active probes outside the volume box (x = -1 and 8.6 m for an 8 m box:
+    their rays leave before their first sample)."""
+    w = make_workload(W.PRESETS["room64"], max_steps=1, probe_dims=(4, 3, 3), probe_origin=(-1.0, 2.0, 2.0),
+                      probe_spacing=(3.2, 2.0, 2.0))
+    outside = (w.states["pos"][:, 0] < 0) | (w.states["pos"][:, 0] > 8)
+    assert (w.states["flags"][outside] & 1).all() and outside.sum() == 18
+    (s,) = run_and_compare(w)
+    print("one step", s)
+    assert_bar(s, "one step, probes outside")
 
 
 @pytest.mark.parametrize("rays", [1, 7, 33, 1000, 1024])
