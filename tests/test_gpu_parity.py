@@ -81,14 +81,16 @@ def test_room64_multiframe_multibounce():
 
 
 def test_open256_full_size_sampled():
-    """The 256^3 open scene at full size and in the bench's launch configuration; the
-    oracle checks a seeded sample of probes (active and inactive), two frames."""
+    """The 256^3 open scene at full size and in the bench's launch configuration (two slab
+    branches); the oracle checks a seeded sample of probes (active and inactive) in each of
+    8 consecutive frames, every frame after the first lit through the previous frame's
+    probes (multi-bounce)."""
     w = make_workload(W.PRESETS["open256"])
     rng = np.random.default_rng(5)
     act = np.flatnonzero(w.states["flags"] & 1)
     ina = np.flatnonzero((w.states["flags"] & 1) == 0)
     sub = np.sort(np.concatenate([rng.choice(act, 48, replace=False), ina[:4]]))
-    stats = run_and_compare(w, frames=2, subset=sub, seed_rot=11)
+    stats = run_and_compare(w, frames=8, subset=sub, seed_rot=11)
     for f, s in enumerate(stats):
         print("open256 frame", f, s)
         assert_bar(s, f"open256 frame {f}")
