@@ -133,3 +133,35 @@ def test_slab_arguments_and_stage_events(cuda_device):
         assert S.volume_slabs(gv.vol) == 4
     finally:
         gv.close()
+
+
+def test_slab_updates_captured_in_a_graph(cuda_device):
+    """Two slab-branched updates captured into a CUDA graph (their fork and join become graph
+    edges) and replayed twice equal a twin volume updated directly, bit for bit."""
+    w = make_workload(W.PRESETS["room64"], k_bounce=0.9, hysteresis=0.5)
+    a = GpuVolume(w, seed=5)
+    b = GpuVolume(w, seed=5)
+    try:
+        for gv in (a, b):
+            S.set_slabs(gv.vol, 2)
+        rots = [W.frame_rotation(3, f) for f in range(2)]
+        for gv in (a, b):  # buffers and one-time set-up before any capture
+            gv.update(rots[1], record=False)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for r in rots:  # two updates: the ping-pong parity is back where it was
+                S.update_probes(a.vol, 0, rotation=r, states=a.states_dev, stream=s)
+        for rep in range(2):
+            g.replay()
+            for r in rots:
+                b.update(r, record=False)
+            torch.cuda.synchronize()
+            for x, y, name in zip(a.state(), b.state(), ("irr", "depth", "valid")):
+                assert np.array_equal(x, y), (rep, name)
+        assert np.abs(b.state()[0][..., :3]).max() > 0
+        assert S.volume_status(a.vol) == 0
+    finally:
+        a.close()
+        b.close()
