@@ -937,7 +937,7 @@ def run_learned(args, rank, world, local_rank):
         "training": {"pairs_s": t_pairs, "train_s": t_train, "loss": hist},
         "roofline": {"kernel": "denoise_tc_kernel", "bound": "tensor", "achieved": ach, "peak": tc_peak,
                      "unit": "TFLOP/s", "frac": ach / tc_peak, "flops_per_launch": DENOISER_FLOPS_PER_PROBE * n_active,
-                     "peak_source": f"{tc_kind} bf16 burst", "traffic": None},
+                     "peak_source": f"{tc_kind} bf16 burst", "traffic": measured_traffic("denoise", LEARNED)},
         "clocks": clk,
     }
     S.destroy_volume(v32)
