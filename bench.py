@@ -729,6 +729,188 @@ def cascade_query_cpu_baseline(c, host_maps, pts, nrm, budget_s):
             "sample": f"the first {k} of the step's points, one oracle call each ({dt:.1f} s)"}
 
 
+VISIBILITY_QUERY = "visibility256_query"
+RELOCATE = "relocate256"
+
+
+def surface_points(baked, lo, hi, n, seed):
+    """n seeded shading-like points: uniform in the box [lo, hi] where the nearest voxel's SDF lies
+    between half a voxel and two voxels (a shell over the surfaces), each with the unit gradient
+    of the baked SDF there as its normal (central differences of the neighbouring voxels)."""
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = baked.sdf.shape
+    sdf = baked.sdf.astype(np.float32)
+    pts, nrm = np.empty((0, 3)), np.empty((0, 3))
+    while len(pts) < n:
+        c = rng.uniform(lo, hi, (8 * n, 3))
+        g = np.clip(np.floor((c - np.asarray(baked.origin)) / baked.h).astype(np.int64), 1, [nx - 2, ny - 2, nz - 2])
+        v = sdf[g[:, 2], g[:, 1], g[:, 0]]
+        keep = (v > 0.5 * baked.h) & (v <= 2.0 * baked.h)
+        g, c = g[keep], c[keep]
+        grad = np.stack([sdf[g[:, 2], g[:, 1], g[:, 0] + 1] - sdf[g[:, 2], g[:, 1], g[:, 0] - 1],
+                         sdf[g[:, 2], g[:, 1] + 1, g[:, 0]] - sdf[g[:, 2], g[:, 1] - 1, g[:, 0]],
+                         sdf[g[:, 2] + 1, g[:, 1], g[:, 0]] - sdf[g[:, 2] - 1, g[:, 1], g[:, 0]]], axis=1)
+        ln = np.linalg.norm(grad, axis=1)
+        ok = ln > 0
+        pts = np.concatenate([pts, c[ok]])
+        nrm = np.concatenate([nrm, grad[ok] / ln[ok, None]])
+    return pts[:n].astype(np.float32), nrm[:n].astype(np.float32)
+
+
+def run_point_query(args, rank, world, local_rank):
+    """Interpolation with SDF probe visibility (Sec. 3.4) at 1920x1080 points of open256: each
+    point weighs its 8 probes by a soft SDF shadow march toward each; the maps are those of 4
+    updates of the open256 volume. Or (relocate256) probe relocation (Sec. 3.2) of the open256
+    grid: a descent on the SDF per probe."""
+    import torch
+    import paper_2007_14394_b300 as S
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pr = W.PRESETS["open256"]
+    scene, baked, states = build_inputs(pr)
+    sc = S.create_scene()
+    S.upload_sdf(sc, baked.sdf, baked.h, baked.origin, material=baked.material)
+    S.set_lights(sc, scene.lights, scene.sky)
+    desc = S.make_desc(pr.probe_dims, pr.rays, pr.probe_origin, pr.probe_spacing, pr.max_steps, pr.depth_exponent,
+                       pr.eps_vox, pr.tmax_vox, pr.hysteresis, pr.k_bounce, pr.bias_vox, seed=pr.seed)
+    vol = S.create_volume(desc, sc)
+    states_dev = torch.from_numpy(states.view(np.uint8).copy()).to(dev)
+    for f in range(4):
+        S.update_probes(vol, f, states=states_dev)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(step_fn):
+        for _ in range(args.warmup):
+            step_fn()
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            step_fn()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+    hbm, peak_kind = peaks()
+    lo = np.asarray(pr.probe_origin, np.float64)
+    hi = lo + (np.asarray(pr.probe_dims) - 1) * np.asarray(pr.probe_spacing)
+    if args.workload == VISIBILITY_QUERY:
+        softness = 8.0
+        n = W.QUERY_POINTS
+        pts, nrm = surface_points(baked, lo, hi, n, seed=13)
+        p_d, n_d = torch.from_numpy(pts).to(dev), torch.from_numpy(nrm).to(dev)
+        out = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        clocks = Clocks(local_rank)
+        per_step = timed(lambda: S.sample_irradiance_visible(vol, p_d, n_d, out, softness, states_dev, stream=stream))
+        clk = clocks.stop()
+        hp, hn = torch.from_numpy(pts).pin_memory(), torch.from_numpy(nrm).pin_memory()
+        ho = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            p_d.copy_(hp, non_blocking=True)
+            n_d.copy_(hn, non_blocking=True)
+            S.sample_irradiance_visible(vol, p_d, n_d, out, softness, states_dev, stream=stream)
+            ho.copy_(out, non_blocking=True)
+        e2e_ms = timed(e2e_step)
+        units, unit, kernel = n, "points/s", "sample_visible_kernel"
+        fixed = n * (24 + 12 + 8 * (16 + 4 * 16 + 1))  # point, normal, result; per probe its state, 4 texels, flag
+        h2d, d2h = n * 24, n * 12
+        what = (f"{VISIBILITY_QUERY}: {n} seeded shading points (1920x1080) in the probe box of open256, 0.5 to 2 "
+                f"voxels off the surfaces, normals from the SDF's gradient, softness {softness}; maps of 4 updates")
+        cpu = visibility_cpu_baseline(pr, baked, states, vol, pts, nrm, softness, args.cpu_budget) \
+            if rank == 0 and world == 1 and not args.no_cpu_baseline else None
+    else:
+        n = pr.n_probes
+        out = torch.empty(n * 16, dtype=torch.uint8, device=dev)
+        clocks = Clocks(local_rank)
+        per_step = timed(lambda: S.relocate_probes(vol, out, stream=stream))
+        clk = clocks.stop()
+        ho = torch.empty(n * 16, dtype=torch.uint8).pin_memory()
+
+        def e2e_step():
+            S.relocate_probes(vol, out, stream=stream)
+            ho.copy_(out, non_blocking=True)
+        e2e_ms = timed(e2e_step)
+        units, unit, kernel = n, "probes/s", "relocate_kernel"
+        fixed = n * 16  # each probe's new state
+        h2d, d2h = 0, n * 16
+        what = f"{RELOCATE}: relocation of the {n} probes of open256 (clearance 2 voxels, at most 16 descent steps)"
+        cpu = relocate_cpu_baseline(pr, baked, args.cpu_budget) \
+            if rank == 0 and world == 1 and not args.no_cpu_baseline else None
+    ms, e2e = float(np.mean(per_step)), float(np.mean(e2e_ms))
+    ms, e2e = max_over_ranks([ms, e2e], world, dev)
+    ach = fixed / (ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": whole_job_rate(world, units, 1, ms), "unit": unit, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scene and points, baked on the host)",
+        "config": {"workload": what, "units": units,
+                   "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
+        "gpu_launches": args.steps,
+        "e2e": {"value": whole_job_rate(world, units, 1, e2e), "unit": unit, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
+        "roofline": {"kernel": kernel, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                     "frac": ach / hbm, "bytes_per_launch": fixed, "peak_source": f"{peak_kind} hbm_gbs",
+                     "traffic": None,
+                     "note": "a lower bound: the bytes counted are the fixed ones per unit; the SDF samples of the "
+                             "marches or descent steps (their counts are not exposed) come on top"},
+        "step_ms": {"min": min(per_step), "median": statistics.median(per_step), "max": max(per_step)},
+        "clocks": clk,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    S.destroy_volume(vol)
+    S.destroy_scene(sc)
+    return line
+
+
+def visibility_cpu_baseline(pr, baked, states, vol, pts, nrm, softness, budget_s):
+    """The oracle's visibility-weighted interpolation, one point per call, on the same maps."""
+    import oracle as O
+    import paper_2007_14394_b300 as S
+    osc = O.OracleScene(baked.sdf, baked.h, baked.origin, baked.material)
+    g = O.make_grid(pr.probe_dims, pr.probe_origin, pr.probe_spacing, pr.rays, pr.max_steps, pr.eps_vox,
+                    pr.tmax_vox, pr.hysteresis, pr.depth_exponent, pr.k_bounce, pr.bias_vox)
+    P = pr.n_probes
+    irr = np.empty((P, 8, 8, 4), np.float32)
+    dep = np.empty((P, 16, 16, 2), np.float32)
+    val = np.empty(P, np.uint8)
+    S.read_state(vol, irr, dep, val)
+    irr64 = irr.astype(np.float64)
+    pos = states["pos"].astype(np.float32)
+    t0, k = time.perf_counter(), 0
+    while time.perf_counter() - t0 < budget_s and k < len(pts):
+        O.sample_irradiance_visible(osc, g, irr64, val, pts[k].astype(np.float64), nrm[k].astype(np.float64),
+                                    softness, probe_pos=pos)
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": f"the first {k} of the step's points, one oracle call each ({dt:.1f} s)"}
+
+
+def relocate_cpu_baseline(pr, baked, budget_s):
+    """The oracle's relocation of the whole grid, repeated for about budget_s seconds."""
+    import oracle as O
+    osc = O.OracleScene(baked.sdf, baked.h, baked.origin, baked.material)
+    g = O.make_grid(pr.probe_dims, pr.probe_origin, pr.probe_spacing, pr.rays, pr.max_steps, pr.eps_vox,
+                    pr.tmax_vox, pr.hysteresis, pr.depth_exponent, pr.k_bounce, pr.bias_vox)
+    t0, k = time.perf_counter(), 0
+    while time.perf_counter() - t0 < budget_s and k < 64:
+        O.relocate(osc, g, 2.0, 0.0)
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": k * pr.n_probes / dt, "unit": "probes/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"{k} relocations of the whole grid ({pr.n_probes} probes), {dt:.1f} s"}
+
+
 ANALYTIC = {"open256_analytic": "open256", "room64_analytic": "room64"}
 
 
@@ -1048,7 +1230,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=sorted(W.PRESETS) + sorted(W.CASCADES) + [LEARNED] + sorted(ANALYTIC) + [CASCADE_QUERY])
+                    choices=sorted(W.PRESETS) + sorted(W.CASCADES) + [LEARNED] + sorted(ANALYTIC) + [CASCADE_QUERY]
+                    + [VISIBILITY_QUERY, RELOCATE])
     ap.add_argument("--train-steps", type=int, default=6000, help="training steps of the learned32 workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--slabs", type=int, default=0,
@@ -1062,7 +1245,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
-        if args.workload in W.CASCADES or args.workload in (LEARNED, CASCADE_QUERY) or args.workload in ANALYTIC:
+        if args.workload in W.CASCADES or args.workload in (LEARNED, CASCADE_QUERY, VISIBILITY_QUERY, RELOCATE) \
+                or args.workload in ANALYTIC:
             ap.error("the reference arm times single-volume workloads")
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
@@ -1074,7 +1258,7 @@ def main():
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     run = (run_batch if args.workload in W.CASCADES else run_learned if args.workload == LEARNED
            else run_analytic if args.workload in ANALYTIC else run_cascade_query if args.workload == CASCADE_QUERY
-           else run_ours)
+           else run_point_query if args.workload in (VISIBILITY_QUERY, RELOCATE) else run_ours)
     line = run(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(line), flush=True)
