@@ -57,8 +57,8 @@ def whole_job_rate(world: int, units_per_rank_step: float, steps: int, ms_total:
 
 def kernels_per_update(slabs: int) -> int:
     """Kernel launches of one update run as `slabs` slab branches (tensor-core gather): the
-    weights and the weight image once, then five stage kernels per slab."""
-    return KERNELS_PER_UPDATE if slabs <= 1 else 2 + 5 * slabs
+    directions, the weights and the weight image once, then five stage kernels per slab."""
+    return KERNELS_PER_UPDATE if slabs <= 1 else 3 + 5 * slabs
 
 
 def peaks():

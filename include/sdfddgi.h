@@ -265,8 +265,9 @@ SDFDDGI_API int sdfddgi_set_stage_events(sdfddgi_volume* v, void* const* events,
  * 2 on the caller's stream, slab 1, 3 on a second stream owned by the volume, forked from
  * and joined back into the caller's stream (so the update stays one stream-ordered unit,
  * also under graph capture). The pools of a stage end with a few long rays that keep few
- * lanes busy; the other slab's kernels fill the SMs meanwhile. The texel weights are
- * computed once, before the fork. Each slab has its own pool counters and part of the
+ * lanes busy; the other slab's kernels fill the SMs meanwhile. The ray directions are
+ * computed once, before the fork; the texel weights, which only the gathers read, on a
+ * stream of their own beside the traces. Each slab has its own pool counters and part of the
  * shadow-task list; the multi-bounce lookup still reads the whole volume's last maps.
  *  slabs -- 0: automatic (2 when P*R >= 2^19 rays, else 1), 1: serial, up to
  *           SDFDDGI_MAX_SLABS (at most nz slabs are used).

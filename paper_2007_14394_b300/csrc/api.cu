@@ -67,6 +67,7 @@ void free_volume_buffers(sdfddgi_volume* v) {
         if (v->lanes.join[c]) cudaEventDestroy(v->lanes.join[c]);
     }
     if (v->lanes.fork) cudaEventDestroy(v->lanes.fork);
+    if (v->lanes.weights_ready) cudaEventDestroy(v->lanes.weights_ready);
     v->lanes = {};
     if (v->copy) cudaStreamDestroy(v->copy);
     if (v->read_order) cudaEventDestroy(v->read_order);
@@ -335,6 +336,7 @@ SDFDDGI_API int sdfddgi_create_volume(const sdfddgi_volume_desc* d, sdfddgi_scen
     if (!rc) rc = alloc_scratch(v);
     if (!rc) {
         cudaError_t e = cudaEventCreateWithFlags(&v->lanes.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->lanes.weights_ready, cudaEventDisableTiming);
         for (int c = 0; c < kMaxSlabs - 1 && e == cudaSuccess; ++c) {
             e = cudaStreamCreateWithFlags(&v->lanes.side[c], cudaStreamNonBlocking);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->lanes.join[c], cudaEventDisableTiming);

@@ -167,6 +167,7 @@ struct SlabLanes {
     cudaStream_t side[SDFDDGI_MAX_SLABS - 1];
     cudaEvent_t fork;
     cudaEvent_t join[SDFDDGI_MAX_SLABS - 1];
+    cudaEvent_t weights_ready;  // the texel weights and their image, made on slab 1's stream
 };
 
 // stage_events: null, or SDFDDGI_STAGE_EVENTS events recorded on `stream` at the stage boundaries

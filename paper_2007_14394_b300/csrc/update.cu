@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, 8) shadow_kernel(const __grid_consta
 // The texel weights max(0, u_j . d_i)^e depend on the frame's ray set only, so they are
 // computed once per update: row i (ray) x column j (texel, irradiance first), plus each
 // column's sum, in ray order.
-template <int PEXP>
+template <int PEXP, bool Dirs>
 __global__ void __launch_bounds__(kThreads) weights_kernel(const __grid_constant__ UpdateParams P) {
     const int i = blockIdx.x;  // one ray per block, one texel per thread
     const int j = threadIdx.x;
@@ -450,11 +450,20 @@ __global__ void __launch_bounds__(kThreads) weights_kernel(const __grid_constant
     const int jj = irr ? j : j - kIrrTexels, n = irr ? kIrrN : kDepN;
     const float3 u = texel_dir(jj % n, jj / n, n);
     const float3 d = ray_direction(i, P.R, P.rot_dev ? P.rot_dev : P.rot);
-    if (j == 0) P.dirs[i] = make_float4(d.x, d.y, d.z, 0.f);
+    if (Dirs && j == 0) P.dirs[i] = make_float4(d.x, d.y, d.z, 0.f);
     const float c = fmaf(u.x, d.x, fmaf(u.y, d.y, u.z * d.z));
     float w = 0.f;
     if (c > 0.f) w = irr ? c : (PEXP == 50 ? pow50(c) : pow_runtime(c, P.depth_exp));
     P.weights[(size_t)i * kTexels + j] = w;
+}
+
+// The frame's R ray directions alone (what the traces need of stage 0), for updates whose
+// texel weights are computed beside the traces.
+__global__ void __launch_bounds__(kThreads) ray_dirs_kernel(const __grid_constant__ UpdateParams P) {
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    if (i >= P.R) return;
+    const float3 d = ray_direction(i, P.R, P.rot_dev ? P.rot_dev : P.rot);
+    P.dirs[i] = make_float4(d.x, d.y, d.z, 0.f);
 }
 
 // Column sums of the texel weights, in ray order.
@@ -845,35 +854,57 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
     for (int c = 0; c < slabs && e == cudaSuccess; ++c)
         e = cudaMemsetAsync(p.counters + (size_t)c * kSlabCounterStride, 0, kFailWord * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return e;
-    if (p.depth_exp == 50)
-        weights_kernel<50><<<p.R, kThreads, 0, stream>>>(p);
-    else
-        weights_kernel<0><<<p.R, kThreads, 0, stream>>>(p);
     const bool tc = gather_tc_supported(p) && p.sched.gather != 2;
-    // the column sums serve the SIMT gather; the tensor-core gather sums a ones channel
-    if (!tc) weight_sums_kernel<<<1, kThreads, 0, stream>>>(p);
+    // the texel weights (with the frame's directions when dirs is set); the column sums serve
+    // the SIMT gather, the tensor-core gather sums a ones channel
+    auto weights = [&](cudaStream_t s, bool dirs) {
+        if (p.depth_exp == 50) {
+            if (dirs)
+                weights_kernel<50, true><<<p.R, kThreads, 0, s>>>(p);
+            else
+                weights_kernel<50, false><<<p.R, kThreads, 0, s>>>(p);
+        } else {
+            if (dirs)
+                weights_kernel<0, true><<<p.R, kThreads, 0, s>>>(p);
+            else
+                weights_kernel<0, false><<<p.R, kThreads, 0, s>>>(p);
+        }
+        if (!tc) weight_sums_kernel<<<1, kThreads, 0, s>>>(p);
+    };
     if (slabs == 1) {
+        weights(stream, true);
         if ((e = mark(1)) != cudaSuccess) return e;
         for (int s = 0; s < 4 && e == cudaSuccess; ++s) e = launch_stage<T>(p, *setup, s, stream, ev, true);
         return e;
     }
     // Slab branches: while one slab's pools drain (their last, longest rays keep few lanes
     // busy), the other slabs' kernels fill the SMs. Slab c runs on its own stream (slab 0 on
-    // `stream`); the weights, shared by all, are ready before the fork.
-    if (tc && (e = launch_pack_weights(p, stream)) != cudaSuccess) return e;
+    // `stream`). Only the directions come before the fork: the texel weights and their image,
+    // which only the gathers read, run on a stream of their own (a spare side stream, else
+    // the last slab's), and every other slab's gather waits for them.
+    ray_dirs_kernel<<<(p.R + kThreads - 1) / kThreads, kThreads, 0, stream>>>(p);
     if ((e = cudaEventRecord(lanes->fork, stream)) != cudaSuccess) return e;
-    for (int c = 1; c < slabs && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(lanes->side[c - 1], lanes->fork, 0);
+    const int n_side = slabs < kMaxSlabs ? slabs : slabs - 1;  // side streams in use
+    for (int c = 0; c < n_side && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(lanes->side[c], lanes->fork, 0);
     if (e != cudaSuccess) return e;
     UpdateParams q[kMaxSlabs];
     for (int c = 0; c < slabs; ++c) q[c] = slab_params(p, c, slabs);
     auto lane = [&](int c) { return c == 0 ? stream : lanes->side[c - 1]; };
+    const cudaStream_t ws = lanes->side[n_side - 1];
+    const int w_slab = slabs < kMaxSlabs ? -1 : slabs - 1;  // the slab sharing that stream, if any
+    weights(ws, false);
+    if (tc) e = launch_pack_weights(p, ws);
+    if (e == cudaSuccess) e = cudaEventRecord(lanes->weights_ready, ws);
     for (int c = 0; c < slabs; ++c)
-        for (int s = 0; s < 4 && e == cudaSuccess; ++s) e = launch_stage<T>(q[c], *setup, s, lane(c), nullptr, false);
+        for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
+            if (s == 3 && c != w_slab) e = cudaStreamWaitEvent(lane(c), lanes->weights_ready, 0);
+            if (e == cudaSuccess) e = launch_stage<T>(q[c], *setup, s, lane(c), nullptr, false);
+        }
     // join even after a failed launch, so that no branch is left unjoined
     cudaError_t j = cudaSuccess;
-    for (int c = 1; c < slabs && j == cudaSuccess; ++c) {
-        j = cudaEventRecord(lanes->join[c - 1], lanes->side[c - 1]);
-        if (j == cudaSuccess) j = cudaStreamWaitEvent(stream, lanes->join[c - 1], 0);
+    for (int c = 0; c < n_side && j == cudaSuccess; ++c) {  // the slabs' streams and the weights' stream
+        j = cudaEventRecord(lanes->join[c], lanes->side[c]);
+        if (j == cudaSuccess) j = cudaStreamWaitEvent(stream, lanes->join[c], 0);
     }
     return e != cudaSuccess ? e : j;
 }
