@@ -34,6 +34,11 @@ constexpr int kThreads = 256;
 // measured 3 % faster, while 128 slowed the primary traces and 256 the shadow ones.
 constexpr int kBatch = 64;
 constexpr int kShadowBatch = 128;
+// Threads per CTA of the persistent trace kernels: two warps, 32 CTAs resident per SM for the
+// same 64 warps. As a pool drains, its CTAs leave a warp pair at a time, so the next kernel
+// (the other slab's traces, the next stage) takes over freed slots sooner than from CTAs of
+// eight warps that wait for their slowest ray.
+constexpr int kTraceThreads = 64;
 
 // c^p for the depth weights; p = 50 (the usual sharpness) as a fixed product chain.
 __device__ __forceinline__ float pow50(float c) {
@@ -258,9 +263,9 @@ __device__ __forceinline__ float light_scale(const LightDev& li, float3 x, float
 // size, so the probe's origin and flags are decoded once per batch, by lane 0 into its
 // warp's slot; a task outside the slot's probe decodes its own.
 template <typename T, bool Relax>
-__global__ void __launch_bounds__(kThreads, 8) primary_kernel(const __grid_constant__ UpdateParams P) {
-    __shared__ float4 s_origin[kThreads / 32];  // probe origin, its first task index (bits)
-    __shared__ uint32_t s_flags[kThreads / 32];
+__global__ void __launch_bounds__(kTraceThreads, 32) primary_kernel(const __grid_constant__ UpdateParams P) {
+    __shared__ float4 s_origin[kTraceThreads / 32];  // probe origin, its first task index (bits)
+    __shared__ uint32_t s_flags[kTraceThreads / 32];
     const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
     const int warp = threadIdx.x >> 5;
     trace_pool<T, Relax>(
@@ -409,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant
 
 // ------------------------------------------------------------------ 3. shadow traces
 template <typename T, bool Relax>
-__global__ void __launch_bounds__(kThreads, 8) shadow_kernel(const __grid_constant__ UpdateParams P) {
+__global__ void __launch_bounds__(kTraceThreads, 32) shadow_kernel(const __grid_constant__ UpdateParams P) {
     const uint32_t n = min(P.counters[kTaskCount], P.task_capacity);
     trace_pool<T, Relax>(
         P.vol, n, &P.counters[kShadowPool], P.eps_w, P.max_steps, P.omega_shadow, pool_batch(P, kShadowBatch),
@@ -718,9 +723,9 @@ DeviceSetup g_setup[kMaxDevices];
 template <typename T>
 constexpr int type_slot() { return std::is_same<T, float>::value ? 0 : (std::is_same<T, __half>::value ? 1 : 2); }
 
-int occupancy(const void* kernel) {
+int occupancy(const void* kernel, int threads = kThreads) {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, 0) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess) return 1;
     return max(1, occ);
 }
 
@@ -735,18 +740,18 @@ cudaError_t prepare_update_kernels(const DeviceSetup** out) {
     DeviceSetup& s = g_setup[dev];
     if (!s.done) {
         s.err = cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev);
-        s.occ_primary[0][0] = occupancy((const void*)primary_kernel<float, false>);
-        s.occ_primary[0][1] = occupancy((const void*)primary_kernel<__half, false>);
-        s.occ_primary[0][2] = occupancy((const void*)primary_kernel<Analytic, false>);
-        s.occ_shadow[0][0] = occupancy((const void*)shadow_kernel<float, false>);
-        s.occ_shadow[0][1] = occupancy((const void*)shadow_kernel<__half, false>);
-        s.occ_shadow[0][2] = occupancy((const void*)shadow_kernel<Analytic, false>);
-        s.occ_primary[1][0] = occupancy((const void*)primary_kernel<float, true>);
-        s.occ_primary[1][1] = occupancy((const void*)primary_kernel<__half, true>);
-        s.occ_primary[1][2] = occupancy((const void*)primary_kernel<Analytic, true>);
-        s.occ_shadow[1][0] = occupancy((const void*)shadow_kernel<float, true>);
-        s.occ_shadow[1][1] = occupancy((const void*)shadow_kernel<__half, true>);
-        s.occ_shadow[1][2] = occupancy((const void*)shadow_kernel<Analytic, true>);
+        s.occ_primary[0][0] = occupancy((const void*)primary_kernel<float, false>, kTraceThreads);
+        s.occ_primary[0][1] = occupancy((const void*)primary_kernel<__half, false>, kTraceThreads);
+        s.occ_primary[0][2] = occupancy((const void*)primary_kernel<Analytic, false>, kTraceThreads);
+        s.occ_shadow[0][0] = occupancy((const void*)shadow_kernel<float, false>, kTraceThreads);
+        s.occ_shadow[0][1] = occupancy((const void*)shadow_kernel<__half, false>, kTraceThreads);
+        s.occ_shadow[0][2] = occupancy((const void*)shadow_kernel<Analytic, false>, kTraceThreads);
+        s.occ_primary[1][0] = occupancy((const void*)primary_kernel<float, true>, kTraceThreads);
+        s.occ_primary[1][1] = occupancy((const void*)primary_kernel<__half, true>, kTraceThreads);
+        s.occ_primary[1][2] = occupancy((const void*)primary_kernel<Analytic, true>, kTraceThreads);
+        s.occ_shadow[1][0] = occupancy((const void*)shadow_kernel<float, true>, kTraceThreads);
+        s.occ_shadow[1][1] = occupancy((const void*)shadow_kernel<__half, true>, kTraceThreads);
+        s.occ_shadow[1][2] = occupancy((const void*)shadow_kernel<Analytic, true>, kTraceThreads);
         // the SIMT gathers stage [R][G] values: at most 32 KiB for the G chosen per R
         for (const void* k : {(const void*)gather_kernel<8>, (const void*)gather_kernel<4>, (const void*)gather_kernel<2>})
             if (s.err == cudaSuccess) s.err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 << 10);
@@ -784,17 +789,17 @@ static cudaError_t launch_stage(const UpdateParams& p, const DeviceSetup& setup,
     if (s == 0) {
         const int g = persistent_blocks(setup, setup.occ_primary[rp][type_slot<T>()], p.sched.blocks_per_sm);
         if (rp)
-            primary_kernel<T, true><<<g, kThreads, 0, stream>>>(p);
+            primary_kernel<T, true><<<g, kTraceThreads, 0, stream>>>(p);
         else
-            primary_kernel<T, false><<<g, kThreads, 0, stream>>>(p);
+            primary_kernel<T, false><<<g, kTraceThreads, 0, stream>>>(p);
     } else if (s == 1) {
         prep_kernel<T><<<(n + kPrepRays - 1) / kPrepRays, kThreads, 0, stream>>>(p);
     } else if (s == 2) {
         const int g = persistent_blocks(setup, setup.occ_shadow[rs][type_slot<T>()], p.sched.blocks_per_sm);
         if (rs)
-            shadow_kernel<T, true><<<g, kThreads, 0, stream>>>(p);
+            shadow_kernel<T, true><<<g, kTraceThreads, 0, stream>>>(p);
         else
-            shadow_kernel<T, false><<<g, kThreads, 0, stream>>>(p);
+            shadow_kernel<T, false><<<g, kTraceThreads, 0, stream>>>(p);
     } else {
         finalize_kernel<<<(n + kFinalRays - 1) / kFinalRays, kThreads, 0, stream>>>(p);
         if (gather_tc_supported(p) && p.sched.gather != 2)
