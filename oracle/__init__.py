@@ -68,10 +68,10 @@ RAY_DTYPE = np.dtype([("t", "f8"), ("L", "f8", (3,)), ("margin_primary", "f8"),
                       ("margin_shadow", "f8"), ("margin_decision", "f8"), ("event", "i4"),
                       ("steps", "i4"), ("natural_event", "i4"), ("natural_steps", "i4"),
                       ("lit_mask", "u4"), ("natural_lit_mask", "u4"), ("traced_mask", "u4"),
-                      ("shadow_steps", "i4"), ("forced", "i4"), ("hard", "i4"), ("t_own", "f8"),
-                      ("t_cond", "f8"), ("t_forced", "i4"), ("pad", "i4"), ("dLdt", "f8", (3,)),
+                      ("shadow_steps", "i4"), ("forced", "i4"), ("hard", "i4"),
+                      ("t_cond", "f8"), ("dLdt", "f8", (3,)),
                       ("dLdcos", "f8", (3,)), ("owner", "i4"), ("natural_owner", "i4"), ("margin_owner", "f8")])
-FORCE_DTYPE = np.dtype([("event", "i4"), ("steps", "i4"), ("lit_mask", "u4"), ("t", "f4"), ("owner", "i4")])
+FORCE_DTYPE = np.dtype([("event", "i4"), ("steps", "i4"), ("lit_mask", "u4"), ("owner", "i4")])
 
 
 def is_miss(event):
@@ -105,7 +105,6 @@ def _load():
             lib.oracle_shade.argtypes = [C.POINTER(Volume), C.POINTER(Grid), C.POINTER(Light), C.c_int32,
                                          dp, C.c_void_p, dp, dp, C.c_void_p, C.c_void_p]
             lib.oracle_set_delta.argtypes = [C.c_double, C.c_double]
-            lib.oracle_set_t_tolerance.argtypes = [C.c_double, C.c_double]
             lib.oracle_update.argtypes = [C.POINTER(Volume), C.POINTER(Grid), C.POINTER(Light), C.c_int32,
                                           C.POINTER(C.c_float), C.c_void_p, dp, dp, C.c_void_p,
                                           dp, dp, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
@@ -126,6 +125,10 @@ def _load():
                 C.POINTER(C.c_double), C.POINTER(C.c_int32), dp]
             lib.oracle_relocate.argtypes = [C.POINTER(Volume), C.POINTER(Grid), C.POINTER(Relocation), C.c_void_p,
                                             dp, C.c_void_p, C.c_void_p, C.c_void_p]
+            lib.oracle_record_sizes.argtypes = [C.c_int32]
+            lib.oracle_record_sizes.restype = C.c_int32
+            assert lib.oracle_record_sizes(0) == RAY_DTYPE.itemsize, "or_ray layout differs from RAY_DTYPE"
+            assert lib.oracle_record_sizes(1) == FORCE_DTYPE.itemsize, "or_force layout differs from FORCE_DTYPE"
             _lib = lib
     return _lib
 
@@ -230,11 +233,6 @@ def sample_sdf(scene: OracleScene, p) -> float:
 def set_delta(delta_vox: float = 2e-4, delta_cos: float = 1e-4) -> None:
     """Widths of the rounding-sensitive band used when following another side's decisions."""
     _load().oracle_set_delta(float(delta_vox), float(delta_cos))
-
-
-def set_t_tolerance(tol_vox: float = 1e-3, factor: float = 8.0) -> None:
-    """Hit-distance tolerance and the multiple of a ray's rounding bound that explains more."""
-    _load().oracle_set_t_tolerance(float(tol_vox), float(factor))
 
 
 def trace(scene: OracleScene, o, d, eps_vox: float, tlimit: float, max_steps: int, omega: float = 1.0):

@@ -10,10 +10,17 @@
  * then let every octahedral texel gather its cosine-weighted irradiance from
  * all of the probe's samples (Eq. 3) and mix it temporally with the last frame.
  *
- * Where the paper is silent the readings are the numbered choices O1..O13 of
- * the design notes; each function names the one it follows. Parity pins:
- * every function here is checked in tests/test_oracle_pins.py against closed
- * forms, invariants or brute force (no pin retypes a formula from this file).
+ * Where the paper is silent, each function states the reading it takes (ray
+ * set, trace termination, octahedral map and border, shading terms, temporal
+ * mixing). Parity pins: every function here is checked in
+ * tests/test_oracle_pins.py against closed forms, invariants or brute force
+ * (no pin retypes a formula from this file).
+ *
+ * Independence from the implementation under test: the oracle may be told the
+ * other side's DISCRETE outcomes of a ray (exit event, step count, light
+ * visibility, owning primitive) and follows one only where its own FP64
+ * decision lies within a stated rounding band of the threshold. It never takes
+ * a continuous value (a distance, a radiance) from the other side.
  */
 #include "oracle.h"
 
@@ -212,17 +219,9 @@ static void sample_material(const or_volume* vol, const double p[3], double albe
 static double g_delta_vox = 2e-4; /* rounding band of distance decisions, voxels */
 static double g_delta_cos = 1e-4; /* rounding band of light-gating decisions */
 
-static double g_t_tol_vox = 1e-3; /* hit-distance tolerance, voxels */
-static double g_t_factor = 8.0;   /* multiple of t_cond that explains a larger difference */
-
 void oracle_set_delta(double delta_vox, double delta_cos) {
     g_delta_vox = delta_vox;
     g_delta_cos = delta_cos;
-}
-
-void oracle_set_t_tolerance(double tol_vox, double factor) {
-    g_t_tol_vox = tol_vox;
-    g_t_factor = factor;
 }
 
 /* Derivative of the trilinear field along d at p (world units); zero across clamped axes. */
@@ -259,7 +258,7 @@ static double sdf_slope(const or_volume* vol, const double p[3], const double d[
  * outcome. With fe >= 0 the path follows the given event (fe) and step count (fs)
  * instead of its own tests; every test so overridden increments *forced, and
  * *hard as well when its margin was at least delta. *cond receives the first-order
- * float32 rounding bound of the returned t (voxels), see oracle_set_t_tolerance.
+ * float32 rounding bound of the returned t (voxels): see or_ray.t_cond.
  *
  * With omega > 1 the steps are over-relaxed (the accelerated sphere tracing of Sec. 3.3,
  * after enhanced sphere tracing): a step is omega times the sampled distance, and a sample
@@ -435,6 +434,8 @@ int32_t oracle_trace_relaxed(const or_volume* vol, const double o[3], const doub
     return trace_relaxed(vol, o, d, eps_vox, tlimit, max_steps, omega, -1, 0, 0u, NULL, t_out, steps_out, margin_vox,
                          &forced, &hard, &cond);
 }
+
+int32_t oracle_record_sizes(int32_t which) { return which == 0 ? (int32_t)sizeof(or_ray) : (int32_t)sizeof(or_force); }
 
 static int is_miss(int32_t event) { return event == OR_LEFT_VOLUME || event == OR_PAST_LIMIT; }
 
@@ -839,18 +840,6 @@ static void update_one_probe(const or_volume* vol, const or_grid* g, const or_li
             double m_unused;
             rec.event = trace_follow(vol, o, d, g->eps_vox, tmax, g->max_steps, g->omega_primary, fi->event, fi->steps,
                                      n_inband, &t, &rec.steps, &m_unused, &rec.forced, &rec.hard, &rec.t_cond);
-        }
-        rec.t_own = t;
-        if (fi && !is_miss(rec.event)) {
-            double diff = fabs(t - (double)fi->t) / h;
-            if (diff > g_t_tol_vox) {
-                if (diff <= g_t_factor * rec.t_cond) {
-                    t = (double)fi->t; /* ill-conditioned ray: continue from the other side's hit point */
-                    rec.t_forced = 1;
-                } else {
-                    rec.hard++;
-                }
-            }
         }
         rec.t = t;
         if (is_miss(rec.event)) {

@@ -101,7 +101,6 @@ typedef struct {
     int32_t event;
     int32_t steps;
     uint32_t lit_mask;
-    float t;                 /* the other side's hit distance (world) */
     int32_t owner;           /* analytic scenes: index + 1 of the primitive whose material the hit
                                 took (0: not given) */
 } or_force;
@@ -123,10 +122,8 @@ typedef struct {
     int32_t shadow_steps;    /* SDF samples over all natural shadow traces */
     int32_t forced;          /* decisions taken from the force record */
     int32_t hard;            /* of those, decisions whose margin exceeded delta */
-    double t_own;            /* this side's hit distance along the path taken (world) */
-    double t_cond;           /* voxels: first-order bound of the float32 rounding error of t */
-    int32_t t_forced;        /* 1 if t was taken from the force record (see oracle_set_t_tolerance) */
-    int32_t pad;
+    double t_cond;           /* voxels: first-order bound of the float32 rounding error of t, see
+                                oracle_update */
     double dLdt[3];          /* derivative of L with respect to the hit distance, visibility held fixed */
     double dLdcos[3];        /* derivative of L with respect to each visible light's cosine n.l, summed
                                 over those lights (sensitivity to the rounding of the shading normal) */
@@ -134,6 +131,9 @@ typedef struct {
     int32_t natural_owner;   /* the oracle's own choice */
     double margin_owner;     /* voxels: second-smallest minus smallest primitive distance at the hit */
 } or_ray;
+
+/* sizeof(or_ray) (which = 0) or sizeof(or_force) (which = 1), for bindings to check their layouts. */
+int32_t oracle_record_sizes(int32_t which);
 
 /* Spherical-Fibonacci direction i of n (unrotated). */
 void oracle_sf_dir(int32_t i, int32_t n, double out[3]);
@@ -169,15 +169,12 @@ void oracle_shade(const or_volume* vol, const or_grid* g, const or_light* lights
 /* Widths of the rounding-sensitive band: distances in voxels, cosines unitless. */
 void oracle_set_delta(double delta_vox, double delta_cos);
 
-/* Hit distances. Sphere tracing can amplify rounding: a perturbation of t grows by
- * (1 + dsdf/dt) per step, which exceeds 1 while a ray moves away from a surface it
- * grazed. t_cond propagates that first-order bound with a float32 rounding of the
- * step's coordinates, distance and t as the per-step perturbation. With a force
- * record, t is taken from the record when the two differ by more than tol_vox and
- * by at most factor * t_cond (an ill-conditioned ray); a larger difference is hard. */
-void oracle_set_t_tolerance(double tol_vox, double factor);
-
 /* One probe update over the probes listed in `subset` (all probes if subset is NULL).
+ * Hit distances are always this side's own. Sphere tracing can amplify rounding: a
+ * perturbation of t grows by (1 + dsdf/dt) per step, which exceeds 1 while a ray moves
+ * away from a surface it grazed. Each record's t_cond propagates that first-order bound,
+ * with a float32 rounding of the step's coordinates, distance and t as the per-step
+ * perturbation, so that a test can tell an ill-conditioned ray from a wrong one.
  * prev_irr [P][8][8][4], prev_depth [P][16][16][2], prev_valid [P]: the previous maps.
  * cur_*: written for the listed probes only. rays: NULL or [n_subset][R] records.
  * force: NULL or [n_subset][R] outcomes to follow within the rounding band.

@@ -98,51 +98,36 @@ def force_from_records(rec: np.ndarray) -> np.ndarray:
     f["event"] = rec["event"].astype(np.int32)
     f["steps"] = rec["steps"].astype(np.int32)
     f["lit_mask"] = rec["lit_mask"]
-    f["t"] = rec["t"]
     f["owner"] = rec["material_owner"].astype(np.int32)
     return f
 
 
-EPS_COS = 5e-7           # bound of the float32 error of a texel-direction . ray-direction cosine
-WEIGHT_ERR_FACTOR = 4.0  # safety factor on the first-order weight-error term
-TRACE_ERR_FACTOR = 2.0   # safety factor on the first-order effect of the measured hit-distance differences
-# The shading normal is normalised from differences of two trilinear samples h apart; each
-# sample carries a few float32 ulps of the local distances (~1e-7 m below 1 m), so a normal
-# component is good to ~1e-6 and a light's cosine n.l to ~2e-6. Where a light grazes the
-# surface that absolute error is a large relative one; the oracle records dL/d(n.l).
-EPS_SHADE_COS = 2e-6
-
-
 def texel_geometry(rays: int, rot, exponent: int):
-    """Per map (irradiance [6,6], depth [14,14]): the oracle-side cosines c [n,n,R] of every interior
-    texel with every ray, the derivative of the weight w(c) (1 or p c^(p-1), 0 below the cutoff band)
-    and the weight sums [n,n]. A texel whose sum lies inside the rounding band of the cosine cutoff
-    (irradiance) or of float32 underflow of cos^p (depth) makes 'no ray reached it' rounding-sensitive."""
+    """Per map (irradiance [6,6], depth [14,14]): the oracle-side weights w [n,n,R] of every interior
+    texel for every ray (max(0, u.d) and max(0, u.d)^p, Eq. 3 and the moment weight) and their
+    sums [n,n]. A texel whose sum lies inside the rounding band of the cosine cutoff (irradiance)
+    or of float32 underflow of cos^p (depth) makes 'no ray reached it' rounding-sensitive."""
     d = np.array([O.sf_dir(i, rays) for i in range(rays)]) @ np.asarray(rot, np.float64).T
     out = []
     for n, e in ((O.IRR_N, 1), (O.DEP_N, exponent)):
         u = np.array([[O.oct_decode([(a + 0.5) / n, (b + 0.5) / n]) for a in range(n)] for b in range(n)])
-        c = u @ d.T
-        cp = np.maximum(c, 0.0)
-        dw = np.where(c > -EPS_COS, e * cp ** (e - 1) if e > 1 else 1.0, 0.0)
-        w_ = cp ** e
-        out.append((w_, dw, w_.sum(axis=-1)))
+        w_ = np.maximum(u @ d.T, 0.0) ** e
+        out.append((w_, w_.sum(axis=-1)))
     return out
 
 
-def conditioning(geo, vals, dvals, o_map, active):
-    """First-order sensitivities of each texel mean m_j = sum w_ij v_i / sum w_ij:
-    to an absolute error of 1 in every cosine, sum_i |dw/dc|_ij |v_i - m_j| / sum_i w_ij, and to the
-    measured per-ray value differences dvals, sum_i w_ij dv_i / sum_i w_ij.
-    vals, dvals [P,R,C]; o_map [P,n,n,C]."""
-    w_, dw, sw = geo
-    cw, ct = np.zeros_like(o_map), np.zeros_like(o_map)
+def illcond_effect(geo, dvals, active):
+    """First-order effect on each texel mean m_j = sum_i w_ij v_i / sum_i w_ij of per-ray value
+    differences dvals [P,R,C] (nonzero only on the counted ill-conditioned rays):
+    sum_i w_ij |dv_i| / sum_i w_ij, shape [P,n,n,C]."""
+    w_, sw = geo
+    P = dvals.shape[0]
+    out = np.zeros((P,) + sw.shape + (dvals.shape[-1],))
     safe = np.where(sw > 0, sw, 1.0)
     for p in np.flatnonzero(active):
-        diff = np.abs(vals[p][None, None, :, :] - o_map[p][:, :, None, :])     # [n,n,R,C]
-        cw[p] = (dw[..., None] * diff).sum(axis=2) / safe[..., None]
-        ct[p] = np.einsum("abr,rc->abc", w_, dvals[p]) / safe[..., None]
-    return cw, ct
+        if dvals[p].any():
+            out[p] = np.einsum("abr,rc->abc", w_, dvals[p]) / safe[..., None]
+    return out
 
 
 # ------------------------------------------------------------------------- GPU side
@@ -208,19 +193,40 @@ def rel_err(g, o):
 
 IRR_SW_BAND = 1e-5     # irradiance texels whose cosine sum is below this are rounding-sensitive
 DEP_SW_BAND = 1e-30    # depth texels whose cos^p sum is below this underflow in float32
+ILLCOND_FACTOR = 2.0   # safety factor on the first-order effect of an ill-conditioned ray's hit distance
+FORCED_FRAC_MAX = 1e-3      # rays whose discrete decisions the oracle followed inside the rounding band
+T_ILLCOND_RATE = 1e-4       # hits whose distance may differ by more than T_TOL_VOX (at least one per sample)
+# The shading normal is normalised from differences of float32 trilinear samples one voxel
+# apart. Each sample carries a few roundings of corner values up to ~2 voxels, so a normal
+# component is good to ~1e-6 and a light's cosine n.l to EPS_NL. Where a light grazes the
+# surface that absolute error is a large relative one. The oracle reports dL/d(n.l) per ray
+# (summed over its visible lights); tests/test_oracle_pins.py pins EPS_NL against a float32
+# restatement of the normal on seeded surface points.
+EPS_NL = 2e-6
 
 
 def compare(w: Workload, gpu_state, gpu_rec, orc, subset, h_vox: float, rot=None):
     """Statistics of one update over `subset` probes. gpu_rec: [P,R] records; orc: oracle output
-    (forced by the GPU's records) for `subset`; rot: the frame rotation (for the texel bands)."""
+    (told the GPU's discrete decisions) for `subset`; rot: the frame rotation.
+
+    Hit distances: the oracle keeps its own. A hit whose distances differ by more than
+    T_TOL_VOX is ill-conditioned when the difference is within T_COND_FACTOR times the
+    oracle's first-order float32 rounding bound of that trace (t_cond), and a hard mismatch
+    otherwise. Texels: relative error <= REL_TOL on every texel, except where a texel's value
+    is sensitive beyond a tenth of that to (a) the distance difference of an ill-conditioned
+    hit (the oracle's own dL/dt times the difference for the radiance, the difference itself
+    for the moments) or (b) the float32 rounding EPS_NL of the cosine of a light that grazes
+    the surface (the oracle's own dL/d(n.l)). Those texels are counted, and held to REL_TOL
+    plus that first-order effect."""
     irr_g, dep_g, val_g = gpu_state
     rays_o = orc["rays"]
     rec = gpu_rec[subset]
     act = rays_o["event"] >= 0
     n_rays = int(act.sum())
     st = {"rays": n_rays}
-    st["hard"] = int((rays_o["hard"][act] > 0).sum())
+    st["hard_decisions"] = int((rays_o["hard"][act] > 0).sum())
     st["forced"] = int((rays_o["forced"][act] > 0).sum())
+    st["forced_frac"] = st["forced"] / n_rays if n_rays else 0.0
     miss_g = np.isin(rec["event"], (0, 2))
     miss_o = O.is_miss(rays_o["natural_event"])
     grazing = rays_o["margin_primary"] < DELTA_VOX
@@ -228,19 +234,26 @@ def compare(w: Workload, gpu_state, gpu_rec, orc, subset, h_vox: float, rot=None
     ok = act & ~grazing
     st["class_agree_nongrazing"] = float((miss_g == miss_o)[ok].mean()) if ok.any() else 1.0
     st["grazing_frac"] = float(grazing[act].mean()) if n_rays else 0.0
-    same_path = act & (rays_o["hard"] == 0)
-    dt_own = np.abs(rec["t"].astype(np.float64) - rays_o["t_own"]) / h_vox
-    st["t_within_tol_frac"] = float((dt_own[act] <= T_TOL_VOX).mean()) if n_rays else 1.0
-    st["t_forced_frac"] = float((rays_o["t_forced"][act] > 0).mean()) if n_rays else 0.0
-    ratio = dt_own / np.maximum(rays_o["t_cond"], 1e-300)
-    forced_t = act & (rays_o["t_forced"] > 0)
-    st["t_forced_max_ratio"] = float(ratio[forced_t].max()) if forced_t.any() else 0.0
-    st["t_err_vox_max"] = float(dt_own[act & (rays_o["t_forced"] == 0) & same_path].max()) if n_rays else 0.0
+    hit = act & ~O.is_miss(rays_o["event"]) & (rays_o["hard"] == 0)
+    dt = np.where(hit, np.abs(rec["t"].astype(np.float64) - rays_o["t"]) / h_vox, 0.0)
+    illcond = hit & (dt > T_TOL_VOX)
+    t_hard = illcond & (dt > T_COND_FACTOR * rays_o["t_cond"])
+    st["hits"] = int(hit.sum())
+    st["t_within_tol_frac"] = float((dt[hit] <= T_TOL_VOX).mean()) if hit.any() else 1.0
+    st["t_illcond"] = int(illcond.sum())
+    st["t_hard"] = int(t_hard.sum())
+    st["t_err_vox_max"] = float(dt[hit].max()) if hit.any() else 0.0
+    st["t_err_vox_max_wellcond"] = float(dt[hit & ~illcond].max()) if (hit & ~illcond).any() else 0.0
+    st["t_illcond_max_ratio"] = (float((dt / np.maximum(rays_o["t_cond"], 1e-300))[illcond].max())
+                                 if illcond.any() else 0.0)
+    st["t_illcond_allowed"] = max(1, int(T_ILLCOND_RATE * st["hits"]))
+    st["hard"] = st["hard_decisions"] + st["t_hard"]
+    same = act & (rays_o["hard"] == 0)
     st["event_equal"] = bool(np.array_equal(rec["event"][act].astype(np.int32), rays_o["event"][act]))
     st["steps_equal"] = bool(np.array_equal(rec["steps"][act].astype(np.int32), rays_o["steps"][act]))
     st["lit_equal"] = bool(np.array_equal(rec["lit_mask"][act], rays_o["lit_mask"][act]))
-    Lerr = rel_err(rec["L"][same_path], rays_o["L"][same_path]) if same_path.any() else np.zeros(1)
-    st["ray_L_rel_max"] = float(Lerr.max())
+    wc = same & ~illcond
+    st["ray_L_rel_max"] = float(rel_err(rec["L"][wc], rays_o["L"][wc]).max()) if wc.any() else 0.0
     ig, io = irr_g[subset][:, 1:-1, 1:-1, :3], orc["irr"][subset][:, 1:-1, 1:-1, :3]
     dg, do = dep_g[subset][:, 1:-1, 1:-1], orc["depth"][subset][:, 1:-1, 1:-1]
     keep_i = np.ones(ig.shape[1:3], bool)
@@ -248,30 +261,37 @@ def compare(w: Workload, gpu_state, gpu_rec, orc, subset, h_vox: float, rot=None
     geo = None
     if rot is not None:
         geo = texel_geometry(w.params["rays"], rot, w.params["depth_exponent"])
-        keep_i, keep_d = geo[0][2] >= IRR_SW_BAND, geo[1][2] >= DEP_SW_BAND
+        keep_i, keep_d = geo[0][1] >= IRR_SW_BAND, geo[1][1] >= DEP_SW_BAND
     st["texels_banded"] = int((~keep_i).sum() + (~keep_d).sum())
-    # values the texels average: radiance, and (distance, distance^2) with misses at t_max
+    # first-order effect of the ill-conditioned rays' distance differences on their values
     tmax = w.params["tmax_vox"] * h_vox
-    ev = rays_o["event"]
-    that = np.where(O.is_miss(ev), tmax, np.minimum(rays_o["t"], tmax))
-    vals = (rays_o["L"], np.stack([that, that * that], axis=-1))
-    # first-order effect on each ray's values of the measured hit-distance difference (t within tolerance)
-    dt_w = np.where(O.is_miss(ev), 0.0, np.abs(rec["t"].astype(np.float64) - rays_o["t"]))
-    dvals = (np.abs(rays_o["dLdt"]) * dt_w[..., None] + EPS_SHADE_COS * np.abs(rays_o["dLdcos"]),
-             np.stack([dt_w, 2.0 * that * dt_w], axis=-1))
+    that = np.minimum(rays_o["t"], tmax)
+    dt_w = np.where(illcond, dt * h_vox, 0.0)
+    dvals = (np.abs(rays_o["dLdt"]) * dt_w[..., None], np.stack([dt_w, 2.0 * that * dt_w], axis=-1))
+    dshade = np.where(act[..., None], EPS_NL * np.abs(rays_o["dLdcos"]), 0.0)
     for name, g_map, o_map, keep, k in (("irr", ig, io, keep_i, 0), ("depth", dg, do, keep_d, 1)):
-        cw = ct = np.zeros_like(o_map)
-        if geo is not None:
-            cw, ct = conditioning(geo[k], vals[k], dvals[k], o_map, act.any(axis=1))
+        eff_t, eff_s = np.zeros_like(o_map), np.zeros_like(o_map)
+        if geo is not None and illcond.any():
+            eff_t = ILLCOND_FACTOR * illcond_effect(geo[k], dvals[k], act.any(axis=1))
+        if geo is not None and k == 0 and dshade.any():
+            eff_s = illcond_effect(geo[k], dshade, act.any(axis=1))
         g_k, o_k = g_map[:, keep], o_map[:, keep]
-        prop = WEIGHT_ERR_FACTOR * EPS_COS * cw[:, keep] + TRACE_ERR_FACTOR * ct[:, keep]
-        tol = REL_TOL * np.abs(o_k) + prop
-        err = np.abs(g_k.astype(np.float64) - o_k)
-        well = prop <= 0.1 * REL_TOL * np.abs(o_k)
-        st[f"{name}_tol_ratio_max"] = float((err / np.maximum(tol, 1e-300)).max()) if err.size else 0.0
-        st[f"{name}_rel_max"] = float(rel_err(g_k, o_k)[well].max()) if well.any() else 0.0
-        st[f"{name}_rel_max_all"] = float(rel_err(g_k, o_k).max()) if err.size else 0.0
-        st[f"{name}_illcond_texels"] = int((~well).sum())
+        et, es = eff_t[:, keep], eff_s[:, keep]
+        re = rel_err(g_k, o_k)
+        touched = et > 0.1 * REL_TOL * np.abs(o_k)
+        grazing_l = (es > 0.1 * REL_TOL * np.abs(o_k)) & ~touched
+        plain = ~touched & ~grazing_l
+        floor = 1e-6 * max(float(np.abs(o_k).max()), 1e-30) if o_k.size else 1.0
+        tol_rel = REL_TOL + (et + es) / np.maximum(np.abs(o_k), floor)
+        st[f"{name}_rel_max_all"] = float(re.max()) if re.size else 0.0
+        st[f"{name}_rel_max"] = float(re[plain].max()) if plain.any() else 0.0
+        st[f"{name}_touched_texels"] = int(touched.sum())
+        st[f"{name}_touched_rel_max"] = float(re[touched].max()) if touched.any() else 0.0
+        st[f"{name}_grazing_light_texels"] = int(grazing_l.sum())
+        st[f"{name}_grazing_light_rel_max"] = float(re[grazing_l].max()) if grazing_l.any() else 0.0
+        st[f"{name}_tol_ratio_max"] = float((re / tol_rel).max()) if re.size else 0.0
+        st[f"{name}_over_1e4"] = int((re > REL_TOL).sum())
+        st[f"{name}_over_1e4_frac"] = float((re > REL_TOL).mean()) if re.size else 0.0
     ag, ao = irr_g[subset][:, 1:-1, 1:-1, 3], orc["irr"][subset][:, 1:-1, 1:-1, 3]
     st["alpha_equal"] = bool(np.array_equal(ag[:, keep_i], ao[:, keep_i]))
     st["valid_equal"] = bool(np.array_equal(val_g[subset], orc["valid"][subset]))
@@ -289,11 +309,11 @@ def border_is_mirror(maps: np.ndarray) -> bool:
 
 def assert_bar(s, label=""):
     assert s["hard"] == 0, (label, s)
+    assert s["forced_frac"] <= FORCED_FRAC_MAX, (label, s)
     assert s["class_agree_nongrazing"] >= 0.999, (label, s)
-    assert s["t_err_vox_max"] <= T_TOL_VOX, (label, s)
-    assert s["t_within_tol_frac"] >= 0.99, (label, s)      # ill-conditioned rays are the exception
-    # relative 1e-4 on every well-conditioned texel; on all texels, 1e-4 relative plus the
-    # first-order error of the float32 cosine weights
+    assert s["t_illcond"] <= s["t_illcond_allowed"], (label, s)
+    # relative 1e-4 on every texel; the counted texels that an ill-conditioned hit distance or a
+    # grazing light reaches within 1e-4 plus the oracle's own first-order effect of it
     assert s["irr_rel_max"] <= REL_TOL and s["irr_tol_ratio_max"] <= 1.0, (label, s)
     assert s["depth_rel_max"] <= REL_TOL and s["depth_tol_ratio_max"] <= 1.0, (label, s)
     assert s["alpha_equal"] and s["valid_equal"], (label, s)

@@ -14,7 +14,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from harness import (DELTA_COS, DELTA_VOX, T_COND_FACTOR, T_TOL_VOX, GpuVolume, assert_bar, border_is_mirror,
+from harness import (DELTA_COS, DELTA_VOX, GpuVolume, assert_bar, border_is_mirror,
                      compare, force_from_records, make_workload, oracle_grid, oracle_scene)
 
 pytestmark = pytest.mark.gpu
@@ -23,7 +23,6 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(autouse=True)
 def _band(cuda_device):
     O.set_delta(DELTA_VOX, DELTA_COS)
-    O.set_t_tolerance(T_TOL_VOX, T_COND_FACTOR)
 
 
 def run_analytic(w, frames=1, subset=None, seed_rot=7, cluster_size=8):

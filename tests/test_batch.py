@@ -14,7 +14,7 @@ import pytest
 import oracle as O
 import paper_2007_14394_b300 as S
 import workloads as W
-from harness import (DELTA_COS, DELTA_VOX, REL_TOL, T_COND_FACTOR, T_TOL_VOX, GpuVolume, assert_bar,
+from harness import (DELTA_COS, DELTA_VOX, REL_TOL, GpuVolume, assert_bar,
                      border_is_mirror, compare, force_from_records, make_cascade, make_workload, oracle_grid,
                      oracle_scene, rel_err)
 
@@ -173,7 +173,6 @@ def test_cascade512_full_size_sampled(cuda_device):
     oracle checks a seeded sample of every volume's probes (active and inactive) against
     the plain updates' records."""
     O.set_delta(DELTA_VOX, DELTA_COS)
-    O.set_t_tolerance(T_TOL_VOX, T_COND_FACTOR)
     c = W.CASCADES["cascade512"]
     ws = make_cascade(c)
     t = Twins(ws, with_states=(True, True, True, True))

@@ -17,7 +17,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from harness import (T_TOL_VOX, T_COND_FACTOR, DELTA_VOX, DELTA_COS, GpuVolume, assert_bar, border_is_mirror,
+from harness import (DELTA_VOX, DELTA_COS, GpuVolume, assert_bar, border_is_mirror,
                      compare, f32, f32v, force_from_records, make_workload, oracle_grid, oracle_scene)
 
 pytestmark = pytest.mark.gpu
@@ -26,7 +26,6 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(autouse=True)
 def _band(cuda_device):
     O.set_delta(DELTA_VOX, DELTA_COS)
-    O.set_t_tolerance(T_TOL_VOX, T_COND_FACTOR)
 
 
 def run_and_compare(w, frames=1, subset=None, seed_rot=7, prev_gpu=None, record_check=False):

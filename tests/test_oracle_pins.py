@@ -582,3 +582,193 @@ def test_sample_rule_at_probe_and_validity():
     alt = O.sample_irradiance(g, m2, v2, x, n)
     assert np.all(alt < 10.0) and not np.allclose(alt, base)
     assert np.all(O.sample_irradiance(g, maps, np.zeros(27, np.uint8), x, n) == 0.0)
+
+
+# --------------------------------------------------------------------------- gather weights (Eq. 3)
+def _texel_dir(a, b, n):
+    return np.asarray(O.oct_decode([(a + 0.5) / n, (b + 0.5) / n]))
+
+
+def test_irradiance_weight_emissive_cap_closed_form():
+    """Eq. 3 with direction-dependent radiance: an emissive sphere (albedo 0, radiance Le) seen
+    from a probe in an otherwise empty box subtends a cap of half-angle alpha. For a texel whose
+    hemisphere holds the whole cap (theta + alpha <= 90 deg, theta = angle between the texel and
+    the cap centre) the cosine-weighted mean is Le sin^2(alpha) cos(theta) (the cap's irradiance
+    pi Le sin^2 alpha cos theta over the hemisphere's pi); a texel whose hemisphere misses the cap
+    is exactly 0. A cos^2 weight would give Le (1 - cos^3 alpha) at theta = 0 (here 0.90 against
+    0.66), a flipped lobe non-zero far texels."""
+    h, dims = 0.25, (64, 64, 64)
+    c0 = np.array([8.0, 8.0, 8.0])
+    u0 = _texel_dir(2, 3, O.IRR_N)
+    D, alpha, Le = 5.0, math.radians(35.0), 2.0
+    sc = O.OracleScene.analytic([W.SPHERE], [[*(c0 + D * u0), D * math.sin(alpha), 0, 0, 0]], [[0, 0, 0]],
+                                [[Le, Le, Le]], (0, 0, 0), dims, h)
+    g = grid_for((1, 1, 1), tuple(c0), (1, 1, 1), 16384, max_steps=4000, tmax_vox=200.0, eps_vox=1e-4)
+    maps = [O.update(sc, g, [], W.frame_rotation(11, f), probes_at([c0]), want_rays=False)["irr"][0]
+            for f in range(16)]
+    mean = np.mean(maps, axis=0)
+    n_full = n_zero = 0
+    for b in range(O.IRR_N):
+        for a in range(O.IRR_N):
+            th = math.acos(float(np.clip(_texel_dir(a, b, O.IRR_N) @ u0, -1.0, 1.0)))
+            if th + alpha <= math.pi / 2:
+                expect = Le * math.sin(alpha) ** 2 * math.cos(th)
+                assert np.allclose(mean[b + 1, a + 1, :3], expect, rtol=2e-3), (a, b, mean[b + 1, a + 1], expect)
+                n_full += 1
+            elif th - alpha >= math.pi / 2:
+                assert all(np.all(m[b + 1, a + 1, :3] == 0.0) for m in maps), (a, b)
+                n_zero += 1
+    assert n_full >= 6 and n_zero >= 6
+
+
+def _moment_quadrature(u, p, t_of):
+    """int max(0,u.d)^p t(d)^k dd / int max(0,u.d)^p dd for k = 1, 2 by Gauss-Legendre in the
+    angle psi from u and the trapezoid rule (spectrally accurate, periodic) in its azimuth."""
+    xg, wg = np.polynomial.legendre.leggauss(200)
+    psi, wpsi = (xg + 1) * (math.pi / 4), wg * (math.pi / 4)
+    phi = np.arange(128) * (2 * math.pi / 128)
+    a = np.array([1.0, 0.0, 0.0]) if abs(u[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    e1 = np.cross(u, a)
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(u, e1)
+    P, F = np.meshgrid(psi, phi, indexing="ij")
+    d = (np.cos(P)[..., None] * u + (np.sin(P) * np.cos(F))[..., None] * e1
+         + (np.sin(P) * np.sin(F))[..., None] * e2)
+    w = np.cos(P) ** p * np.sin(P) * wpsi[:, None]
+    t = t_of(d.reshape(-1, 3)).reshape(P.shape)
+    return (w * t).sum() / w.sum(), (w * t * t).sum() / w.sum()
+
+
+def test_depth_moment_weight_exponent_off_centre_ball():
+    """The depth moments' weight max(0, u.d)^p: an off-centre probe in a hollow ball sees the
+    wall at t(d) = -(c.d) + sqrt((c.d)^2 - |c|^2 + r^2) (c = probe - centre). Every texel's
+    moments equal the quadrature of their defining integrals; with p = 40 or 64 instead of 50
+    the quadrature moves by ~3e-3, thirty times the tolerance, and a transposed texel index
+    reads another direction of this asymmetric field."""
+    h, dims = 0.25, (64, 64, 64)
+    C, rb = np.array([8.0, 8.0, 8.0]), 6.0
+    off = np.array([3.0, -1.5, 2.0])
+    sc = O.OracleScene.analytic([W.INV_SPHERE], [[*C, rb, 0, 0, 0]], [[0.5, 0.5, 0.5]], [[0, 0, 0]], (0, 0, 0),
+                                dims, h)
+
+    def t_of(d):
+        cd = d @ off
+        return -cd + np.sqrt(cd * cd - off @ off + rb * rb)
+
+    g = grid_for((1, 1, 1), tuple(C + off), (1, 1, 1), 4096, max_steps=4000, tmax_vox=200.0, eps_vox=1e-4,
+                 depth_exponent=50)
+    K = 4
+    dep = sum(O.update(sc, g, [], W.frame_rotation(13, f), probes_at([C + off]), want_rays=False)["depth"][0]
+              for f in range(K)) / K
+    rng = np.random.default_rng(8)
+    moved = 0.0
+    for j in rng.choice(O.DEP_N * O.DEP_N, 24, replace=False):
+        a, b = int(j % O.DEP_N), int(j // O.DEP_N)
+        u = _texel_dir(a, b, O.DEP_N)
+        m1, m2 = _moment_quadrature(u, 50, t_of)
+        assert abs(dep[b + 1, a + 1, 0] - m1) <= 1e-4 * m1, (a, b, dep[b + 1, a + 1], m1)
+        assert abs(dep[b + 1, a + 1, 1] - m2) <= 2e-4 * m2, (a, b, dep[b + 1, a + 1], m2)
+        for p_wrong in (40, 64):
+            moved = max(moved, abs(_moment_quadrature(u, p_wrong, t_of)[0] - m1) / m1)
+    assert moved > 30 * 1e-4  # the pin tells a wrong exponent apart
+
+
+# --------------------------------------------------------------------------- float32 rounding bounds
+def _trilinear_np(sdf, h, origin, p, ft):
+    """The trilinear sampling rule restated in numpy in dtype ft (no fused multiply-add)."""
+    nz, ny, nx = sdf.shape
+    v = sdf.astype(ft)
+    inv_h = ft(1.0) / ft(h)
+    idx, fr = [], []
+    for a, n in ((0, nx), (1, ny), (2, nz)):
+        g = (p[:, a] - ft(origin[a])) * inv_h - ft(0.5)
+        i = np.clip(np.floor(g).astype(np.int64), 0, n - 2)
+        idx.append(i)
+        fr.append(np.clip(g - i.astype(ft), ft(0), ft(1)).astype(ft))
+    (ix, iy, iz), (fx, fy, fz) = idx, fr
+
+    def V(dx, dy, dz):
+        return v[iz + dz, iy + dy, ix + dx]
+
+    def lerp(a, b, t):
+        return a + t * (b - a)
+
+    x00, x10 = lerp(V(0, 0, 0), V(1, 0, 0), fx), lerp(V(0, 1, 0), V(1, 1, 0), fx)
+    x01, x11 = lerp(V(0, 0, 1), V(1, 0, 1), fx), lerp(V(0, 1, 1), V(1, 1, 1), fx)
+    return lerp(lerp(x00, x10, fy), lerp(x01, x11, fy), fz)
+
+
+def _room_rays(seed_rot=7, stride=2):
+    import harness as H
+    w = H.make_workload(W.PRESETS["room64"])
+    sub = np.flatnonzero(w.states["flags"] & 1)[::stride]
+    rot = W.frame_rotation(seed_rot, 0)
+    out = O.update(H.oracle_scene(w), H.oracle_grid(w), w.lights, rot, w.states, subset=sub)
+    R = w.params["rays"]
+    dirs = np.array([O.sf_dir(i, R) for i in range(R)]) @ rot.astype(np.float64).T
+    o = np.repeat(w.states["pos"][sub].astype(np.float64), R, axis=0)
+    return w, out["rays"].reshape(-1), o, np.tile(dirs, (len(sub), 1))
+
+
+def test_t_cond_bounds_a_float32_trace():
+    """The oracle's per-ray t_cond (first-order float32 rounding bound of the hit distance,
+    propagated through every step) against an actual float32 sphere trace of the same rays on
+    the same baked field: wherever the float32 trace takes the oracle's path (event and step
+    count), |t_f32 - t_f64| <= t_cond."""
+    w, rays, o, d = _room_rays()
+    f32, h = np.float32, w.baked.h
+    o32, d32 = o.astype(f32), d.astype(f32)
+    eps, tl = f32(w.params["eps_vox"] * h), f32(w.params["tmax_vox"] * h)
+    lo = np.array(w.baked.origin, f32)
+    hi = lo + np.array(w.baked.sdf.shape[::-1], f32) * f32(h)
+    n = len(o)
+    t, ev, st = np.zeros(n, f32), np.full(n, O.EXHAUSTED), np.full(n, w.params["max_steps"])
+    alive = np.ones(n, bool)
+    for s in range(w.params["max_steps"]):
+        idx = np.flatnonzero(alive)
+        if not len(idx):
+            break
+        p = o32[idx] + t[idx, None] * d32[idx]
+        out = np.any((p < lo) | (p > hi), axis=1)
+        ev[idx[out]], st[idx[out]], alive[idx[out]] = O.LEFT_VOLUME, s, False
+        idx, p = idx[~out], p[~out]
+        sd = _trilinear_np(w.baked.sdf, h, w.baked.origin, p, f32)
+        hit = sd < eps
+        ev[idx[hit]], st[idx[hit]], alive[idx[hit]] = O.HIT, s + 1, False
+        idx, sd = idx[~hit], sd[~hit]
+        t[idx] = t[idx] + sd
+        past = t[idx] > tl
+        ev[idx[past]], st[idx[past]], alive[idx[past]] = O.PAST_LIMIT, s + 1, False
+    same = (ev == rays["natural_event"]) & (st == rays["natural_steps"]) & ~O.is_miss(ev)
+    assert same.sum() > 0.95 * (~O.is_miss(rays["natural_event"])).sum()
+    dt = np.abs(t.astype(np.float64) - rays["t"])[same] / h
+    assert np.all(dt <= rays["t_cond"][same]), float((dt / rays["t_cond"][same]).max())
+
+
+def test_float32_shading_normal_cosine_within_eps_nl():
+    """The parity bar's EPS_NL: the light cosine n.l of a shading normal normalised from float32
+    central differences (six trilinear samples half a voxel off the hit) stays within EPS_NL of
+    the same rule in FP64, at the oracle's hit points of a room for 64 seeded light directions."""
+    import harness as H
+    w, rays, o, d = _room_rays(stride=3)
+    h = w.baked.h
+    hit = rays["natural_event"] == O.HIT
+    x = (o[hit] + rays["t"][hit, None] * d[hit]).astype(np.float32)
+
+    def normal(x, ft):
+        g = []
+        for a in range(3):
+            e = np.zeros(3, ft)
+            e[a] = ft(0.5 * h)
+            g.append(_trilinear_np(w.baked.sdf, h, w.baked.origin, (x + e).astype(ft), ft)
+                     - _trilinear_np(w.baked.sdf, h, w.baked.origin, (x - e).astype(ft), ft))
+        g = np.stack(g, 1)
+        return g / np.sqrt((g * g).sum(1))[:, None]
+
+    n32 = normal(x, np.float32).astype(np.float64)
+    n64 = normal(x.astype(np.float64), np.float64)
+    rng = np.random.default_rng(0)
+    L = rng.normal(size=(64, 3))
+    L /= np.linalg.norm(L, axis=1)[:, None]
+    err = np.abs(n32 @ L.T - n64 @ L.T)
+    assert err.max() <= H.EPS_NL, float(err.max())

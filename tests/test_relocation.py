@@ -20,7 +20,7 @@ import pytest
 import oracle as O
 import paper_2007_14394_b300 as S
 import workloads as W
-from harness import (DELTA_COS, DELTA_VOX, T_COND_FACTOR, T_TOL_VOX, GpuVolume, assert_bar, border_is_mirror,
+from harness import (DELTA_COS, DELTA_VOX, GpuVolume, assert_bar, border_is_mirror,
                      compare, force_from_records, make_workload, oracle_grid, oracle_scene)
 
 pytestmark = pytest.mark.gpu
@@ -99,7 +99,6 @@ def test_relocation_from_last_positions_in_place(room):
 def test_update_with_relocated_probes_matches_oracle(room):
     import torch
     O.set_delta(DELTA_VOX, DELTA_COS)
-    O.set_t_tolerance(T_TOL_VOX, T_COND_FACTOR)
     w, gv = room
     out = torch.empty(w.P * 16, dtype=torch.uint8, device="cuda")
     states = _relocate(gv, out, clearance=3.0, max_offset=0.45)
