@@ -313,21 +313,6 @@ __device__ __forceinline__ float3 interpolate_irradiance(const int gd[3], const 
     return f3(r * inv, g * inv, bl * inv);
 }
 
-// ------------------------------------------------------------------ ray set
-// Ray i of R: spherical Fibonacci (z = 1 - (2i+1)/R, azimuth = 2 pi frac(i phi^-1) with the
-// golden fraction in 32-bit fixed point) rotated by the frame rotation.
-__device__ __forceinline__ float3 ray_direction(int i, int R, const float rot[9]) {
-    const uint32_t phase = (uint32_t)i * 2654435769u;
-    float s, c;
-    sincospif((float)phase * 0x1p-31f, &s, &c);  // angle 2 pi phase / 2^32
-    const float a = (float)(2 * i + 1) / (float)R;
-    const float z = 1.f - a;
-    const float r = sqrtf(fmaxf(0.f, a * (2.f - a)));  // sqrt(1 - z^2) without cancellation
-    const float3 d = f3(r * c, r * s, z);
-    return f3(fmaf(rot[0], d.x, fmaf(rot[1], d.y, rot[2] * d.z)), fmaf(rot[3], d.x, fmaf(rot[4], d.y, rot[5] * d.z)),
-              fmaf(rot[6], d.x, fmaf(rot[7], d.y, rot[8] * d.z)));
-}
-
 // ------------------------------------------------------------------ probe visibility
 // Visibility of probe position q from x (normal n), the paper's per-pixel visibility test
 // (Sec. 3.4) as a soft SDF shadow trace: from x + bias * n toward q, vis = min over the

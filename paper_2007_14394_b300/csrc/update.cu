@@ -23,6 +23,7 @@
 #include <type_traits>
 
 #include "device.cuh"
+#include "dfloat.cuh"
 
 namespace sdfddgi {
 
@@ -40,21 +41,6 @@ constexpr int kShadowBatch = 128;
 // eight warps that wait for their slowest ray.
 constexpr int kTraceThreads = 64;
 
-// c^p for the depth weights; p = 50 (the usual sharpness) as a fixed product chain.
-__device__ __forceinline__ float pow50(float c) {
-    const float c2 = c * c, c4 = c2 * c2, c8 = c4 * c4, c16 = c8 * c8, c32 = c16 * c16;
-    return c32 * c16 * c2;
-}
-
-__device__ __forceinline__ float pow_runtime(float c, int p) {
-    float r = 1.f, b = c;
-    while (p) {
-        if (p & 1) r *= b;
-        b *= b;
-        p >>= 1;
-    }
-    return r;
-}
 
 struct TraceState {
     float3 o, d;
@@ -447,39 +433,53 @@ __global__ void __launch_bounds__(kTraceThreads, 32) shadow_kernel(const __grid_
 // ------------------------------------------------------------------ 4. gather (Eq. 3)
 // The texel weights max(0, u_j . d_i)^e depend on the frame's ray set only, so they are
 // computed once per update: row i (ray) x column j (texel, irradiance first), plus each
-// column's sum, in ray order.
+// column's sum, in ray order. Directions and cosines are taken in double-float arithmetic
+// (csrc/dfloat.cuh) and each weight rounded to float once, so that a weight keeps its
+// relative accuracy down to the cosine cutoff; the traces read the directions rounded to
+// float from the same computation.
 template <int PEXP, bool Dirs>
 __global__ void __launch_bounds__(kThreads) weights_kernel(const __grid_constant__ UpdateParams P) {
+    __shared__ dfloat s_d[3];
     const int i = blockIdx.x;  // one ray per block, one texel per thread
     const int j = threadIdx.x;
+    if (j == 0) {
+        dfloat d[3];
+        df_ray_direction(i, P.R, P.rot_dev ? P.rot_dev : P.rot, d);
+        s_d[0] = d[0];
+        s_d[1] = d[1];
+        s_d[2] = d[2];
+        if (Dirs) P.dirs[i] = make_float4(d[0].hi, d[1].hi, d[2].hi, 0.f);
+    }
+    __syncthreads();
     if (j >= kTexels) return;
     const bool irr = j < kIrrTexels;
     const int jj = irr ? j : j - kIrrTexels, n = irr ? kIrrN : kDepN;
-    const float3 u = texel_dir(jj % n, jj / n, n);
-    const float3 d = ray_direction(i, P.R, P.rot_dev ? P.rot_dev : P.rot);
-    if (Dirs && j == 0) P.dirs[i] = make_float4(d.x, d.y, d.z, 0.f);
-    const float c = fmaf(u.x, d.x, fmaf(u.y, d.y, u.z * d.z));
+    dfloat u[3];
+    df_texel_direction(jj % n, jj / n, n, u);
+    const dfloat d[3] = {s_d[0], s_d[1], s_d[2]};
+    const dfloat c = df_dot(u, d);
     float w = 0.f;
-    if (c > 0.f) w = irr ? c : (PEXP == 50 ? pow50(c) : pow_runtime(c, P.depth_exp));
+    if (c.hi > 0.f) w = irr ? c.hi : df_pow(c, PEXP == 50 ? 50 : P.depth_exp).hi;
     P.weights[(size_t)i * kTexels + j] = w;
 }
 
 // The frame's R ray directions alone (what the traces need of stage 0), for updates whose
-// texel weights are computed beside the traces.
+// texel weights are computed beside the traces; the same rounding as weights_kernel's.
 __global__ void __launch_bounds__(kThreads) ray_dirs_kernel(const __grid_constant__ UpdateParams P) {
     const int i = blockIdx.x * kThreads + threadIdx.x;
     if (i >= P.R) return;
-    const float3 d = ray_direction(i, P.R, P.rot_dev ? P.rot_dev : P.rot);
-    P.dirs[i] = make_float4(d.x, d.y, d.z, 0.f);
+    dfloat d[3];
+    df_ray_direction(i, P.R, P.rot_dev ? P.rot_dev : P.rot, d);
+    P.dirs[i] = make_float4(d[0].hi, d[1].hi, d[2].hi, 0.f);
 }
 
-// Column sums of the texel weights, in ray order.
+// Column sums of the texel weights, accumulated in double-float in ray order.
 __global__ void __launch_bounds__(kThreads) weight_sums_kernel(const __grid_constant__ UpdateParams P) {
     const int j = threadIdx.x;
     if (j >= kTexels) return;
-    float sw = 0.f;
-    for (int i = 0; i < P.R; ++i) sw += P.weights[(size_t)i * kTexels + j];
-    P.weights[(size_t)P.R * kTexels + j] = sw;
+    dfloat sw = df(0.f);
+    for (int i = 0; i < P.R; ++i) sw = sw + df(P.weights[(size_t)i * kTexels + j]);
+    P.weights[(size_t)P.R * kTexels + j] = sw.hi;
 }
 
 // Radiance (visible lights summed in light order) and clamped distance of ray k.
