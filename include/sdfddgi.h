@@ -521,17 +521,19 @@ SDFDDGI_API int sdfddgi_denoiser_train_step(sdfddgi_denoiser* d, const sdfddgi_p
 /* The paper has no counterpart to this entry point; it exists for callers that may not
  * allocate device memory while they run -- an engine that reserves all GPU memory at
  * start-up and sub-allocates its own pools, a plug-in inside another framework's memory
- * manager, or a real-time loop where a cudaMalloc could stall the frame. It computes
- * exactly what sdfddgi_update_probes computes, with the same kernels, but takes every
- * input and output from the caller and allocates nothing: no cudaMalloc, no cudaFree, no
- * allocating library call. The update's scratch (a copy of the SDF in the kernels'
- * layout, per-ray buffers, the shadow-task list, texel weights, counters) lives in one
+ * manager, or a real-time loop where a cudaMalloc could stall the frame. It runs the same
+ * kernels as sdfddgi_update_probes (including the tensor-core gather when R is a multiple
+ * of 16) with the stages one after another on `stream`, never as slab branches; the maps
+ * equal those of sdfddgi_update_probes bit for bit. It takes every input and output from
+ * the caller and allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
+ * The update's scratch (a copy of the SDF in the kernels' layout, per-ray buffers, the
+ * shadow-task list, texel weights and their tensor-core image, counters) lives in one
  * fixed 32 MiB array in device memory that every GPU loading this library holds until
  * the process exits. An update needs, each part rounded up to 256 bytes: 16 bytes per
  * SDF voxel with nz rounded up to even (8 at binary16), 64 + 16*max(n_lights,1) bytes per
- * probe ray (P*R), and
- * 944*R + 928 bytes -- e.g. a 64^3 float32 SDF with 512 probes x 64 rays and 1 light
- * takes about 6.6 MiB. An update that does not fit in 32 MiB is rejected with
+ * probe ray (P*R), 944*R + 928 bytes of texel weights and 32768*ceil(R/16) bytes of their
+ * tensor-core image -- e.g. a 64^3 float32 SDF with 512 probes x 64 rays and 1 light
+ * takes about 6.7 MiB. An update that does not fit in 32 MiB is rejected with
  * SDFDDGI_ERR_INVALID_ARG before any device work, and sdfddgi_last_error() states the
  * bytes needed and available.
  *  - The first call on a device looks up the array's device address
@@ -541,16 +543,24 @@ SDFDDGI_API int sdfddgi_denoiser_train_step(sdfddgi_denoiser* d, const sdfddgi_p
  *    parts that must start at zero are cleared by each call): calls whose work overlaps
  *    on the GPU (different streams, or different host threads) race; serialise them.
  * Arguments:
- *  desc                        -- the probe volume, as for sdfddgi_create_volume.
+ *  desc                        -- the probe volume, as for sdfddgi_create_volume; of the
+ *                                 flags only SDFDDGI_FLAG_BLEND_BF16 and the two RELAXED
+ *                                 flags are accepted (others: SDFDDGI_ERR_INVALID_ARG).
  *  sdf, dims, voxel_size, origin, dtype, material
  *                              -- the scene, as for sdfddgi_upload_sdf, in DEVICE memory.
  *  lights, n_lights, sky_rgb   -- as for sdfddgi_set_lights (host memory; sky may be NULL).
- *  frame, rotation             -- as for sdfddgi_update_probes (rotation: host, nullable).
+ *  frame, rotation             -- as for sdfddgi_update_probes (rotation: host, nullable,
+ *                                 finite).
  *  states                      -- NULL (grid positions, all active) or P device states.
  *  prev_irr/prev_depth/prev_valid -- the previous maps (device; zeros for no history).
- *  cur_irr/cur_depth/cur_valid -- receive the new maps (device; must not alias prev_*).
+ *  cur_irr/cur_depth/cur_valid -- receive the new maps (device). A cur_* range that shares
+ *                                 a byte with a prev_* range or with another cur_* range is
+ *                                 rejected with SDFDDGI_ERR_INVALID_ARG.
  *  records                     -- NULL or P*R device records, as for sdfddgi_update_probes.
- * Map layouts are those of sdfddgi_get_maps. Work is enqueued on `stream`. */
+ * The library cannot see the sizes of the caller's buffers: each must hold what the layouts
+ * of sdfddgi_get_maps give for P = prod(desc->dims) probes (and P*R records), and the SDF
+ * and material prod(dims) voxels; a smaller buffer is read or written out of bounds.
+ * Work is enqueued on `stream`. */
 SDFDDGI_API int sdfddgi_update_probes_noalloc(
     const sdfddgi_volume_desc* desc, const void* sdf, const int32_t dims[3], float voxel_size,
     const float origin[3], int32_t dtype, const void* material, const sdfddgi_light* lights, int32_t n_lights,

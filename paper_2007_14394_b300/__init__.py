@@ -350,6 +350,28 @@ def update_probes_noalloc(desc: VolumeDesc, sdf, voxel_size: float, origin, ligh
     dtype = F32 if name.endswith("float32") else F16 if name.endswith("float16") else None
     if dtype is None or len(shape) != 3:
         raise ValueError("sdf must be a 3-D float32 or float16 device tensor")
+    # the library cannot see buffer sizes: check every one against desc before the call
+    P = int(desc.dims[0]) * int(desc.dims[1]) * int(desc.dims[2])
+    R = int(desc.rays_per_probe)
+    if len(prev) != 3 or len(cur) != 3:
+        raise ValueError("prev and cur are (irr, depth, valid)")
+    for label, (irr, dep, val) in (("prev", prev), ("cur", cur)):
+        for t, n, kind in ((irr, P * IRR_SIDE * IRR_SIDE * 4, "float32"), (dep, P * DEPTH_SIDE * DEPTH_SIDE * 2, "float32"),
+                           (val, P, "uint8")):
+            if t is None or not _is_torch(t) or not str(t.dtype).endswith(kind) or t.numel() != n:
+                raise ValueError(f"update_probes_noalloc: {label} maps must be {kind} tensors of "
+                                 f"{P}x(8*8*4, 16*16*2, 1) elements for {P} probes")
+    if material is not None and (tuple(material.shape) != (*shape, 8) or not str(material.dtype).endswith("float16")):
+        raise ValueError(f"update_probes_noalloc: material must be float16 of shape {(*shape, 8)}")
+    for t, n, label in ((states, P * 16, "states"), (records, P * R * 32, "records")):
+        if t is not None and (not _is_torch(t) or t.numel() * t.element_size() != n):
+            raise ValueError(f"update_probes_noalloc: {label} must hold {n} bytes")
+    spans = [(t.data_ptr(), t.numel() * t.element_size()) for t in (*cur, *prev)]
+    for i in range(3):
+        for j in range(i + 1, 6):
+            (a, na), (b, nb) = spans[i], spans[j]
+            if a < b + nb and b < a + na:
+                raise ValueError("update_probes_noalloc: the cur maps share memory with prev or with each other")
     for t in (sdf, material, states, records, *prev, *cur):
         if t is not None and not (_is_torch(t) and t.is_cuda):
             raise ValueError("update_probes_noalloc: every buffer must be a CUDA tensor")

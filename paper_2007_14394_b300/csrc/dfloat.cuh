@@ -20,7 +20,7 @@ struct dfloat {
     float hi, lo;
 };
 
-__device__ __forceinline__ dfloat df(float a) { return {a, 0.f}; }
+__host__ __device__ constexpr dfloat df(float a) { return {a, 0.f}; }
 
 // s + e == a + b exactly (Knuth).
 __device__ __forceinline__ dfloat two_sum(float a, float b) {
@@ -83,11 +83,15 @@ __device__ __forceinline__ dfloat df_sqrt(float m) {
     return quick_two_sum(s, e / (2.f * s));
 }
 
+// A real constant as a double-float: the nearest float and the float nearest the remainder,
+// evaluated by the compiler (constexpr) in double precision; nothing of it runs on the GPU.
+__host__ __device__ constexpr dfloat df_const(double x) { return {(float)x, (float)(x - (double)(float)x)}; }
+
 // cos and sin of 2 pi k / 2^32 for a 32-bit fixed-point turn k (the spherical-Fibonacci
 // azimuth). The reduction is exact integer arithmetic: q = the nearest quarter turn, and
 // the remainder r = k - q 2^30 (|r| <= 2^29) gives an angle a = 2 pi r / 2^32 in
 // [-pi/4, pi/4]. sin a and cos a come from their Taylor series in Horner form (terms up to
-// a^13 and a^14: truncation below 1e-11 on that interval), then the quarter turns rotate them.
+// a^13 and a^14: truncation below 1e-12 on that interval), then the quarter turns rotate them.
 __device__ __forceinline__ void df_sincos_turn(uint32_t k, dfloat* s_out, dfloat* c_out) {
     const uint32_t q = (k + (1u << 29)) >> 30;  // 0..4, taken mod 4 below
     const int32_t r = (int32_t)(k - (q << 30));
@@ -98,16 +102,26 @@ __device__ __forceinline__ void df_sincos_turn(uint32_t k, dfloat* s_out, dfloat
     const dfloat turn = {6.28318548202514648438f * 0x1p-32f, -1.7484555314695172e-07f * 0x1p-32f};
     const dfloat a = rr * turn;
     const dfloat a2 = a * a;
-    dfloat sn = df(1.f), cs = df(1.f);
-    for (int j = 6; j >= 1; --j) {  // sin a / a = 1 - a^2/(2*3) (1 - a^2/(4*5) (1 - ...))
-        const float den = (float)((2 * j) * (2 * j + 1));
-        sn = df(1.f) - (a2 * sn) / df(den);
-    }
-    for (int j = 7; j >= 1; --j) {  // cos a = 1 - a^2/(1*2) (1 - a^2/(3*4) (1 - ...))
-        const float den = (float)((2 * j - 1) * (2 * j));
-        cs = df(1.f) - (a2 * cs) / df(den);
-    }
-    sn = sn * a;
+    // Taylor coefficients (-1)^j / (2j+1)! of sin a / a and (-1)^j / (2j)! of cos a
+    constexpr dfloat s1 = df_const(-1.0 / 6.0), s2 = df_const(1.0 / 120.0), s3 = df_const(-1.0 / 5040.0),
+                     s4 = df_const(1.0 / 362880.0), s5 = df_const(-1.0 / 39916800.0),
+                     s6 = df_const(1.0 / 6227020800.0);
+    constexpr dfloat c1 = df_const(-1.0 / 2.0), c2 = df_const(1.0 / 24.0), c3 = df_const(-1.0 / 720.0),
+                     c4 = df_const(1.0 / 40320.0), c5 = df_const(-1.0 / 3628800.0),
+                     c6 = df_const(1.0 / 479001600.0), c7 = df_const(-1.0 / 87178291200.0);
+    dfloat sn = s5 + a2 * s6;
+    sn = s4 + a2 * sn;
+    sn = s3 + a2 * sn;
+    sn = s2 + a2 * sn;
+    sn = s1 + a2 * sn;
+    sn = (df(1.f) + a2 * sn) * a;
+    dfloat cs = c6 + a2 * c7;
+    cs = c5 + a2 * cs;
+    cs = c4 + a2 * cs;
+    cs = c3 + a2 * cs;
+    cs = c2 + a2 * cs;
+    cs = c1 + a2 * cs;
+    cs = df(1.f) + a2 * cs;
     switch (q & 3u) {
         case 0: *s_out = sn; *c_out = cs; break;
         case 1: *s_out = cs; *c_out = -sn; break;
@@ -142,10 +156,10 @@ __device__ __forceinline__ void df_texel_direction(int a, int b, int n, dfloat u
         x = fx;
         y = fy;
     }
-    const dfloat len = df_sqrt((float)(x * x + y * y + z * z));
-    u[0] = df((float)x) / len;
-    u[1] = df((float)y) / len;
-    u[2] = df((float)z) / len;
+    const dfloat inv = df(1.f) / df_sqrt((float)(x * x + y * y + z * z));
+    u[0] = inv * (float)x;
+    u[1] = inv * (float)y;
+    u[2] = inv * (float)z;
 }
 
 __device__ __forceinline__ dfloat df_dot(const dfloat a[3], const dfloat b[3]) {

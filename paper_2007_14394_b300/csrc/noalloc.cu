@@ -4,13 +4,15 @@
 // that reserves all device memory up front and hands out sub-ranges of its own pools, a
 // plug-in living inside another framework's memory manager, or a real-time loop where an
 // allocation (which may synchronise the device) would break the frame budget. For them,
-// sdfddgi_update_probes_noalloc runs the same four-stage update as sdfddgi_update_probes,
-// taking every input and output buffer from the caller; the stages' scratch (the SDF's
-// xy-quad copy, per-ray buffers, shadow-task list, texel weights, pool counters) lives in
-// one file-scope __device__ array of kScratchBytes that every GPU loading this library
-// holds until the process exits.
+// sdfddgi_update_probes_noalloc runs the same kernels as sdfddgi_update_probes (the stages
+// serially on the caller's stream, which gives the same maps bit for bit as the slab
+// branches), taking every input and output buffer from the caller; the stages' scratch (the
+// SDF's xy-quad copy, per-ray buffers, shadow-task list, texel weights and their tensor-core
+// image, pool counters) lives in one file-scope __device__ array of kScratchBytes that
+// every GPU loading this library holds until the process exits.
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -66,6 +68,14 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool pos_finite(float x) { return std::isfinite(x) && x > 0.f; }
 
+// Do the byte ranges [a, a + na) and [b, b + nb) share a byte?
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
+constexpr uint32_t kAcceptedFlags = SDFDDGI_FLAG_BLEND_BF16 | SDFDDGI_FLAG_RELAXED_SHADOW | SDFDDGI_FLAG_RELAXED_PRIMARY;
+
 }  // namespace
 
 extern "C" {
@@ -89,16 +99,39 @@ SDFDDGI_API int sdfddgi_update_probes_noalloc(
             return nofail(SDFDDGI_ERR_INVALID_ARG, "update_probes_noalloc: SDF dims must be in [2, 16384]");
         if (d->dims[a] < 1 || !pos_finite(d->spacing[a]) || !std::isfinite(d->origin[a]))
             return nofail(SDFDDGI_ERR_INVALID_ARG, "update_probes_noalloc: invalid probe grid");
-        P *= d->dims[a];
+        P *= d->dims[a];  // each factor < 2^31 and P <= 2^31 - 1 so far: no overflow
+        if (P > INT32_MAX)
+            return nofail(SDFDDGI_ERR_INVALID_ARG, "update_probes_noalloc: more than 2^31-1 probes");
     }
     const int R = d->rays_per_probe;
     if (R < 1 || R > SDFDDGI_MAX_RAYS || d->max_steps < 1 || d->max_steps > SDFDDGI_MAX_STEPS ||
         d->depth_exponent < 1 || d->depth_exponent > 1024 || !pos_finite(d->eps) || !std::isfinite(d->t_max) ||
         !(d->hysteresis >= 0.f && d->hysteresis <= 1.f) || !(d->multibounce_k >= 0.f && d->multibounce_k <= 1.f) ||
-        !(d->normal_bias >= 0.f) || !std::isfinite(d->normal_bias) || d->flags != 0)
+        !(d->normal_bias >= 0.f) || !std::isfinite(d->normal_bias))
         return nofail(SDFDDGI_ERR_INVALID_ARG, "update_probes_noalloc: invalid volume description");
+    if (d->flags & ~kAcceptedFlags)
+        return nofail(SDFDDGI_ERR_INVALID_ARG,
+                      "update_probes_noalloc: flags 0x%x: only BLEND_BF16 and the RELAXED_* flags are accepted",
+                      (unsigned)d->flags);
+    if (P * R > ((int64_t)1 << 27))
+        return nofail(SDFDDGI_ERR_INVALID_ARG, "update_probes_noalloc: more than 2^27 probe rays");
     if (n_lights < 0 || n_lights > SDFDDGI_MAX_LIGHTS || (n_lights > 0 && !lights))
         return nofail(SDFDDGI_ERR_INVALID_ARG, "update_probes_noalloc: n_lights must be in [0, 32]");
+    if (rotation)
+        for (int k = 0; k < 9; ++k)
+            if (!std::isfinite(rotation[k]))
+                return nofail(SDFDDGI_ERR_INVALID_ARG, "update_probes_noalloc: rotation not finite");
+    {  // the new maps must not share memory with the previous ones, nor with each other
+        const size_t irr_b = (size_t)P * kIrrT * kIrrT * 16, dep_b = (size_t)P * kDepT * kDepT * 8, val_b = (size_t)P;
+        const void* in[3] = {prev_irr, prev_depth, prev_valid};
+        const void* out[3] = {cur_irr, cur_depth, cur_valid};
+        const size_t nb[3] = {irr_b, dep_b, val_b};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                if (overlap(out[i], nb[i], in[j], nb[j]) || (j > i && overlap(out[i], nb[i], out[j], nb[j])))
+                    return nofail(SDFDDGI_ERR_INVALID_ARG,
+                                  "update_probes_noalloc: the cur_* maps overlap the prev_* maps or each other");
+    }
 
     // ---- scratch layout and its limit
     const size_t n_vox = (size_t)dims[0] * dims[1] * dims[2];
@@ -113,13 +146,14 @@ SDFDDGI_API int sdfddgi_update_probes_noalloc(
                             n_rays * 4,   // ray_ssteps
                             n_rays * 16 * (size_t)(n_lights > 0 ? n_lights : 1),  // tasks
                             kCounterWords * 4,  // counters
-                            weights_bytes(R)};  // texel weights, their sums, ray directions
+                            weights_bytes(R),   // texel weights, their sums, ray directions
+                            wimage_bytes(R)};   // the weights as the tensor-core gather's operand
     size_t off[sizeof sizes / sizeof sizes[0]], total = 0;
     for (size_t k = 0; k < sizeof sizes / sizeof sizes[0]; ++k) {
         off[k] = total;
         total += align256(sizes[k]);
     }
-    if (n_rays > ((size_t)1 << 27) || total > kScratchBytes)
+    if (total > kScratchBytes)
         return nofail(SDFDDGI_ERR_INVALID_ARG,
                       "update_probes_noalloc: this update needs %zu bytes of scratch; the fixed scratch holds %zu "
                       "(%zu voxels, %zu probe rays, %d lights)",
@@ -203,6 +237,10 @@ SDFDDGI_API int sdfddgi_update_probes_noalloc(
     p.task_capacity = (uint32_t)(n_rays * (size_t)(n_lights > 0 ? n_lights : 1));
     p.counters = reinterpret_cast<uint32_t*>(s + off[9]);
     p.weights = reinterpret_cast<float*>(s + off[10]);
+    p.wimage = s + off[11];
+    p.blend_bf16 = (d->flags & SDFDDGI_FLAG_BLEND_BF16) ? 1 : 0;
+    p.omega_primary = (d->flags & SDFDDGI_FLAG_RELAXED_PRIMARY) ? SDFDDGI_RELAX_OMEGA : 1.f;
+    p.omega_shadow = (d->flags & SDFDDGI_FLAG_RELAXED_SHADOW) ? SDFDDGI_RELAX_OMEGA : 1.f;
     e = cudaMemsetAsync(p.counters, 0, kCounterWords * sizeof(uint32_t), st);  // the scratch is shared: no sticky bits
     if (e == cudaSuccess) e = launch_update(p, st);
     if (e != cudaSuccess) return nofail(SDFDDGI_ERR_CUDA, "update_probes_noalloc: launch failed: %s", cudaGetErrorString(e));

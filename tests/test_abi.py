@@ -94,3 +94,63 @@ def test_batch_argument_errors_before_device_work(S):
     assert S.lib.sdfddgi_batch_autotune(None, 3, None) == S.ERR_INVALID_ARG
     assert S.lib.sdfddgi_batch_schedule(None, 0, (C.c_int32 * 3)(), None) == S.ERR_INVALID_ARG
     S.lib.sdfddgi_destroy_batch(None)
+
+
+def test_noalloc_argument_errors_before_device_work(S):
+    """The allocation-free update checks everything it can see before touching the device:
+    flags it does not run, probe counts past int32, non-finite rotations, output maps that
+    share memory with the inputs, and updates beyond its fixed scratch. The pointers below
+    are never dereferenced: each call returns at its argument check."""
+    import ctypes as C
+    fake = [C.c_void_p(0x100000 * (k + 1)) for k in range(8)]  # distinct, far-apart stand-in addresses
+    dims = (C.c_int32 * 3)(64, 64, 64)
+    org = (C.c_float * 3)(0.0, 0.0, 0.0)
+
+    def call(desc, rotation=None, cur=None, dims_=dims):
+        cur = cur or (fake[4], fake[5], fake[6])
+        rot = (C.c_float * 9)(*rotation) if rotation is not None else None
+        return S.lib.sdfddgi_update_probes_noalloc(C.byref(desc), fake[0], dims_, 0.125, org, S.F32, None, None, 0,
+                                                   None, 0, rot, None, fake[1], fake[2], fake[3], *cur, None, None)
+
+    ok = S.make_desc((4, 4, 4), 64, (1.0, 1.0, 1.0), (2.0, 2.0, 2.0), 64)
+    bad_flags = S.make_desc((4, 4, 4), 64, (1.0, 1.0, 1.0), (2.0, 2.0, 2.0), 64, flags=S.FLAG_TEST_GATHER_STALL)
+    assert call(bad_flags) == S.ERR_INVALID_ARG and "flags" in S.last_error()
+    huge = S.make_desc((65536, 65536, 2), 1, (1.0, 1.0, 1.0), (2.0, 2.0, 2.0), 64)
+    assert call(huge) == S.ERR_INVALID_ARG and "2^31" in S.last_error()
+    many_rays = S.make_desc((512, 512, 2), 1024, (1.0, 1.0, 1.0), (2.0, 2.0, 2.0), 64)
+    assert call(many_rays) == S.ERR_INVALID_ARG and "2^27" in S.last_error()
+    assert call(ok, rotation=[1, 0, 0, 0, float("nan"), 0, 0, 0, 1]) == S.ERR_INVALID_ARG
+    assert "rotation" in S.last_error()
+    assert call(ok, cur=(fake[1], fake[5], fake[6])) == S.ERR_INVALID_ARG  # cur_irr is prev_irr
+    assert "overlap" in S.last_error()
+    assert call(ok, cur=(fake[4], fake[4], fake[6])) == S.ERR_INVALID_ARG  # cur_depth is cur_irr
+    big = (C.c_int32 * 3)(512, 512, 512)
+    assert call(ok, dims_=big) == S.ERR_INVALID_ARG and "scratch" in S.last_error()
+
+
+def test_noalloc_binding_checks_buffer_sizes(S):
+    """The binding checks every caller buffer against the volume description, since the C ABI
+    cannot see their sizes; this needs no device (the checks come first)."""
+    import torch
+    desc = S.make_desc((2, 2, 2), 16, (1.0, 1.0, 1.0), (2.0, 2.0, 2.0), 32)
+    sdf = torch.zeros((8, 8, 8))
+
+    def maps(P=8):
+        return (torch.zeros((P, 8, 8, 4)), torch.zeros((P, 16, 16, 2)), torch.zeros(P, dtype=torch.uint8))
+
+    with pytest.raises(ValueError, match="cur maps"):
+        S.update_probes_noalloc(desc, sdf, 0.25, (0, 0, 0), [], (0, 0, 0), maps(), maps(7))
+    with pytest.raises(ValueError, match="prev maps"):
+        bad = maps()
+        S.update_probes_noalloc(desc, sdf, 0.25, (0, 0, 0), [], (0, 0, 0), (bad[0].double(), bad[1], bad[2]), maps())
+    with pytest.raises(ValueError, match="records"):
+        S.update_probes_noalloc(desc, sdf, 0.25, (0, 0, 0), [], (0, 0, 0), maps(), maps(),
+                                records=torch.zeros(8 * 16 * 32 - 1, dtype=torch.uint8))
+    with pytest.raises(ValueError, match="material"):
+        S.update_probes_noalloc(desc, sdf, 0.25, (0, 0, 0), [], (0, 0, 0), maps(), maps(),
+                                material=torch.zeros((8, 8, 8, 4), dtype=torch.float16))
+    same = maps()
+    with pytest.raises(ValueError, match="share memory"):
+        S.update_probes_noalloc(desc, sdf, 0.25, (0, 0, 0), [], (0, 0, 0), same, same)
+    with pytest.raises(ValueError, match="CUDA"):  # right sizes, host tensors
+        S.update_probes_noalloc(desc, sdf, 0.25, (0, 0, 0), [], (0, 0, 0), maps(), maps())
