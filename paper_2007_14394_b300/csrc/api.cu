@@ -232,6 +232,7 @@ void sdfddgi::scene_view(const sdfddgi_scene* s, VolumeView* v) {
         v->lo[a] = s->origin[a];
         v->hi[a] = s->origin[a] + (float)s->dims[a] * s->h;
     }
+    set_trace_constants(v);
     if (s->dtype == kAnalytic) {
         v->prims = s->prims;
         v->clusters = s->clusters;

@@ -64,17 +64,38 @@ __device__ __forceinline__ float4 ld_quad<__half>(const void* quads, size_t i) {
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
+// Trilinear interpolation of a cell from its two quads (slices z and z + 1).
+__device__ __forceinline__ float trilinear_quads(float4 q0, float4 q1, float fx, float fy, float fz) {
+    const float x00 = lerp(q0.x, q0.y, fx), x10 = lerp(q0.z, q0.w, fx);
+    const float x01 = lerp(q1.x, q1.y, fx), x11 = lerp(q1.z, q1.w, fx);
+    return lerp(lerp(x00, x10, fy), lerp(x01, x11, fy), fz);
+}
+
+// The SDF at world point p by the sampling rule (cell and fractions clamped).
 template <typename T>
 __device__ __forceinline__ float sample_sdf(const VolumeView& v, float3 p) {
     const Cell c = cell_of(v, p);
-    const size_t i0 = quad_index((size_t)c.ix, (size_t)c.iy, (size_t)c.iz, (size_t)v.nx, (size_t)v.ny);
+    const int z = c.iz + 1;  // padded slice of the cell's lower corner
+    const size_t i0 = quad_index((size_t)c.ix + 1, (size_t)c.iy + 1, (size_t)z, (size_t)v.qx, (size_t)v.qy);
     // slice z + 1: the next entry for even z, else the first of the next pair
-    const size_t i1 = (c.iz & 1) ? i0 + (size_t)2 * v.nx * v.ny - 1 : i0 + 1;
-    const float4 q0 = ld_quad<T>(v.quads, i0);  // slice z
-    const float4 q1 = ld_quad<T>(v.quads, i1);  // slice z + 1
-    const float x00 = lerp(q0.x, q0.y, c.fx), x10 = lerp(q0.z, q0.w, c.fx);
-    const float x01 = lerp(q1.x, q1.y, c.fx), x11 = lerp(q1.z, q1.w, c.fx);
-    return lerp(lerp(x00, x10, c.fy), lerp(x01, x11, c.fy), c.fz);
+    const size_t i1 = (z & 1) ? i0 + (size_t)2 * v.qx * v.qy - 1 : i0 + 1;
+    return trilinear_quads(ld_quad<T>(v.quads, i0), ld_quad<T>(v.quads, i1), c.fx, c.fy, c.fz);
+}
+
+// The SDF at voxel coordinate g (voxel centres at integers, g = (p - lo)/h - 1/2) for a point
+// inside the volume box, g in [-1/2, n - 1/2] on every axis: the cell floor(g) lies in
+// [-1, n - 1], which the apron of the quad store covers, so neither the cell nor the
+// fractions need clamping; where the clamped rule would clamp, the apron's copies of the
+// edge values give the same value.
+template <typename T>
+__device__ __forceinline__ float sample_sdf_vox(const VolumeView& v, float3 g) {
+    const int ix = __float2int_rd(g.x), iy = __float2int_rd(g.y), iz = __float2int_rd(g.z);
+    const float fx = g.x - (float)ix, fy = g.y - (float)iy, fz = g.z - (float)iz;
+    const int z = iz + 1;  // padded slice of the cell's lower corner
+    const uint32_t row = (uint32_t)(z >> 1) * (uint32_t)v.qy + (uint32_t)(iy + 1);
+    const size_t i0 = ((size_t)row * (uint32_t)v.qx + (uint32_t)(ix + 1)) * 2 + (uint32_t)(z & 1);
+    const size_t i1 = (z & 1) ? i0 + (size_t)2 * v.qx * v.qy - 1 : i0 + 1;
+    return trilinear_quads(ld_quad<T>(v.quads, i0), ld_quad<T>(v.quads, i1), fx, fy, fz);
 }
 
 // ------------------------------------------------------------------ analytic scene (Sec. 3.1)

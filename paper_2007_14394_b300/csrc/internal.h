@@ -44,13 +44,16 @@ constexpr int kAnalytic = 2;  // VolumeView::dtype of a scene made of primitives
 // material volume) or, with dtype kAnalytic, a union of analytic primitives in clusters.
 struct VolumeView {
     const void* sdf;          // float or __half, [nz][ny][nx]
-    const void* quads;        // xy-quads of the same values (float4 or 4 x __half), in z-pairs: quad_index
+    const void* quads;        // xy-quads of the same values (float4 or 4 x __half), in z-pairs with a
+                              // one-voxel apron on every side: quad_index of the padded coordinates
     const uint4* material;    // 8 x binary16 per voxel (albedo rgb, -, emission rgb, -), or null
     int nx, ny, nz;
     int dtype;                // SDFDDGI_F32 / SDFDDGI_F16 / kAnalytic
     float h, inv_h;           // voxel size (analytic: the unit of voxel parameters)
     float lo[3];              // world box of the volume (bounds every trace)
     float hi[3];
+    int qx, qy;               // padded x and y extents of the quad store (nx + 2, ny + 2)
+    float gmax[3];            // n - 1/2 per axis: the box in voxel coordinates is [-1/2, n - 1/2]
     const PrimDev* prims;     // analytic: unbounded primitives first, then each cluster's run
     const ClusterDev* clusters;
     int n_unbounded;
@@ -178,12 +181,22 @@ cudaError_t launch_update(const UpdateParams& p, cudaStream_t stream, cudaEvent_
 int slab_count(const UpdateParams& p, bool have_lanes, bool stage_events);
 cudaError_t launch_sample(const SampleParams& p, cudaStream_t stream);
 cudaError_t launch_sample_visible(const SampleParams& p, const VisParams& v, cudaStream_t stream);
-// Position of quad (x, y, z) in the xy-quad copy: z-pairs, [z/2][y][x][z%2].
-__host__ __device__ __forceinline__ size_t quad_index(size_t x, size_t y, size_t z, size_t nx, size_t ny) {
-    return (((z >> 1) * ny + y) * nx + x) * 2 + (z & 1);
+// Position of quad (x, y, z) in an xy-quad store of padded extents qx, qy: z-pairs,
+// [z/2][y][x][z%2]. Padded coordinates: voxel (i, j, k) is quad (i + 1, j + 1, k + 1).
+__host__ __device__ __forceinline__ size_t quad_index(size_t x, size_t y, size_t z, size_t qx, size_t qy) {
+    return (((z >> 1) * qy + y) * qx + x) * 2 + (z & 1);
 }
-// Bytes of the xy-quad copy of an SDF of `dims` voxels (nz rounded up to even).
+// Bytes of the xy-quad copy of an SDF of `dims` voxels: a one-voxel apron on every side,
+// nz + 2 rounded up to even.
 size_t quad_bytes(int dtype, const int dims[3]);
+// The view's derived constants of the voxel-space traces (qx, qy, gmax), from nx, ny, nz.
+inline void set_trace_constants(VolumeView* v) {
+    v->qx = v->nx + 2;
+    v->qy = v->ny + 2;
+    v->gmax[0] = (float)v->nx - 0.5f;
+    v->gmax[1] = (float)v->ny - 0.5f;
+    v->gmax[2] = (float)v->nz - 0.5f;
+}
 inline size_t weights_bytes(int R) { return ((size_t)(R + 1) * kTexels + (size_t)R * 4) * sizeof(float); }
 int report_error(int code, const char* msg);  // sets the text of sdfddgi_last_error(), returns code
 // the gather of Eq. 3 on the tensor cores (R a multiple of 16 and a weight image present)

@@ -200,6 +200,7 @@ SDFDDGI_API int sdfddgi_update_probes_noalloc(
     vol.dtype = dtype;
     vol.h = voxel_size;
     vol.inv_h = 1.0f / voxel_size;
+    set_trace_constants(&vol);
     for (int a = 0; a < 3; ++a) {
         vol.lo[a] = origin[a];
         vol.hi[a] = origin[a] + (float)dims[a] * voxel_size;

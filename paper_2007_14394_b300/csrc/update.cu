@@ -42,6 +42,9 @@ constexpr int kShadowBatch = 128;
 constexpr int kTraceThreads = 64;
 
 
+// A voxel-volume trace runs in voxel coordinates: o is the origin's voxel coordinate
+// ((p - lo)/h - 1/2, voxel centres at integers), t and tlimit are in voxels (d is the same
+// unit direction). A trace of primitives runs in world units.
 struct TraceState {
     float3 o, d;
     float t, tlimit;
@@ -84,18 +87,30 @@ __device__ __forceinline__ float trace_sample(const VolumeView& v, TraceState& s
 template <typename T, bool Relax>
 __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, float eps, int max_steps,
                                           int* steps, float* t_end) {
-    const float3 p = fma3(st.t, st.d, st.o);
+    constexpr bool kVox = !std::is_same<T, Analytic>::value;
+    const float3 p = fma3(st.t, st.d, st.o);  // voxel coordinate (volumes) or world point (primitives)
+    // outside the box, or not a number (the negated test sends NaN out of the volume too)
     const bool outside =
-        p.x < v.lo[0] || p.x > v.hi[0] || p.y < v.lo[1] || p.y > v.hi[1] || p.z < v.lo[2] || p.z > v.hi[2];
+        kVox ? !(p.x >= -0.5f && p.x <= v.gmax[0] && p.y >= -0.5f && p.y <= v.gmax[1] && p.z >= -0.5f &&
+                 p.z <= v.gmax[2])
+             : (p.x < v.lo[0] || p.x > v.hi[0] || p.y < v.lo[1] || p.y > v.hi[1] || p.z < v.lo[2] || p.z > v.hi[2]);
     if (outside && !(Relax && st.omega > 1.f)) {
         *steps = st.s;
         *t_end = st.tlimit;
         return kLeftVolume;
     }
     // a relaxed step that left the box failed like one whose spheres do not overlap
-    const float sd = outside ? 0.f : trace_sample<T>(v, st, p);
+    float sd = 0.f;
+    if (!outside) {
+        if constexpr (kVox)
+            sd = sample_sdf_vox<T>(v, p);
+        else
+            sd = trace_sample<T>(v, st, p);
+    }
+    // the step in the trace's units (the SDF holds world distances)
+    const float sdu = kVox ? sd * v.inv_h : sd;
     if constexpr (Relax) {
-        if (st.omega > 1.f && (outside || sd + st.prev_r < st.step)) {
+        if (st.omega > 1.f && (outside || sdu + st.prev_r < st.step)) {
             const float back = st.prev_r - st.step;
             st.t += back;
             st.moved = -back;
@@ -115,10 +130,12 @@ __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, f
         return kHit;
     }
     if constexpr (Relax) {
-        st.prev_r = sd;
-        st.step = st.omega * sd;
+        st.prev_r = sdu;
+        st.step = st.omega * sdu;
         st.moved = st.step;
         st.t += st.step;
+    } else if constexpr (kVox) {
+        st.t = fmaf(sd, v.inv_h, st.t);
     } else {
         st.moved = sd;
         st.t += sd;
@@ -139,9 +156,11 @@ __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, f
 // Device-wide pool of sphere traces. Tasks 0..n-1 are claimed from *counter by whole
 // warps in batches of kBatch and handed to lanes as they finish their current trace;
 // claim(b) runs on every lane of the warp when it has claimed tasks b..b+batch-1 (work
-// shared by the whole batch is done there once), init(k, st) returns false for a task
-// that needs no trace (it is then complete), done(st, event, steps, t) consumes a
-// finished trace. Every lane of the warp must take part (full-warp votes).
+// shared by the whole batch is done there once), init(k, st) sets the origin, direction and
+// limit in world units or returns false for a task that needs no trace (it is then
+// complete), done(st, event, steps, t) consumes a finished trace (t in world units). A
+// voxel-volume trace runs in voxel coordinates between the two. Every lane of the warp must
+// take part (full-warp votes).
 template <typename T, bool Relax, typename Claim, typename Init, typename Done>
 __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint32_t* counter, float eps,
                                            int max_steps, float omega, uint32_t batch, Claim claim, Init init,
@@ -170,6 +189,11 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
                 if (k >= n) {
                     dry = true;  // the pool is exhausted for this lane
                 } else if (init(k, st)) {
+                    if constexpr (!std::is_same<T, Analytic>::value) {  // into voxel coordinates
+                        st.o = f3(fmaf(st.o.x - v.lo[0], v.inv_h, -0.5f), fmaf(st.o.y - v.lo[1], v.inv_h, -0.5f),
+                                  fmaf(st.o.z - v.lo[2], v.inv_h, -0.5f));
+                        st.tlimit *= v.inv_h;
+                    }
                     st.t = 0.f;
                     st.s = 0;
                     st.last = INFINITY;
@@ -190,6 +214,7 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
             float t_end;
             const int ev = trace_step<T, Relax>(v, st, eps, max_steps, &steps, &t_end);
             if (ev >= 0) {
+                if constexpr (!std::is_same<T, Analytic>::value) t_end *= v.h;  // back to world units
                 done(st, ev, steps, t_end);
                 busy = false;
                 need = true;

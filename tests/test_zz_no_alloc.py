@@ -26,7 +26,7 @@ def scratch_needed(sdf_dims, sdf_elem, P, R, n_lights):
     nx, ny, nz = sdf_dims
     up = lambda x: (x + 255) // 256 * 256  # noqa: E731
     rays = P * R
-    parts = [nx * ny * (nz + nz % 2) * 4 * sdf_elem, rays * 4, rays * 4, rays * 16, rays * 16, rays * 16, rays * 4,
+    parts = [(nx + 2) * (ny + 2) * (nz + 2 + nz % 2) * 4 * sdf_elem, rays * 4, rays * 4, rays * 16, rays * 16, rays * 16, rays * 4,
              rays * 4, rays * 16 * max(n_lights, 1), 32, 944 * R + 928, 32768 * ((R + 15) // 16)]
     return sum(up(x) for x in parts)
 
