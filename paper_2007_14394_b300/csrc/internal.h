@@ -66,6 +66,7 @@ struct Schedule {
     int blocks_per_sm;   // resident CTAs per SM of the persistent trace kernels (default: occupancy limit)
     int gather;          // 0 automatic (tensor cores when R % 16 == 0), 1 tensor cores, 2 SIMT
     int slabs;           // z-slabs of probes run as concurrent branches: 0 automatic, 1 (serial) .. kMaxSlabs
+    int refill;          // idle lanes of a trace warp before it hands out new tasks: 0 default, 1..32
 };
 
 constexpr int kMaxSlabs = SDFDDGI_MAX_SLABS;

@@ -161,18 +161,22 @@ __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, f
 // complete), done(st, event, steps, t) consumes a finished trace (t in world units). A
 // voxel-volume trace runs in voxel coordinates between the two. Every lane of the warp must
 // take part (full-warp votes).
+// A warp hands out new tasks only once at least `refill` of its lanes wait for one (or no
+// lane is tracing): a ray lasts a few steps, so refilling lanes one by one would run the
+// hand-out on nearly every step for one or two lanes at a time.
 template <typename T, bool Relax, typename Claim, typename Init, typename Done>
 __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint32_t* counter, float eps,
-                                           int max_steps, float omega, uint32_t batch, Claim claim, Init init,
-                                           Done done) {
+                                           int max_steps, float omega, uint32_t batch, int refill, Claim claim,
+                                           Init init, Done done) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     uint32_t batch_next = 0, batch_end = 0;  // warp-uniform
     bool need = true, busy = false, dry = false;
+    unsigned tracing = 0;  // lanes with a trace in progress, as of the last vote
     TraceState st;
     for (;;) {
         const unsigned want = __ballot_sync(full, need && !dry);
-        if (want) {
+        if (want && (__popc(want) >= refill || !tracing)) {
             if (batch_next >= batch_end) {
                 uint32_t b = 0;
                 if (lane == 0) b = atomicAdd(counter, batch);
@@ -208,7 +212,11 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
             }
             batch_next += min((uint32_t)__popc(want), avail);
         }
-        if (!__any_sync(full, busy || (need && !dry))) break;
+        tracing = __ballot_sync(full, busy);
+        if (!tracing) {
+            if (!__any_sync(full, need && !dry)) break;
+            continue;  // every lane waits for a task (its last ones needed no trace): hand out more
+        }
         if (busy) {
             int steps;
             float t_end;
@@ -225,6 +233,13 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
 
 __device__ __forceinline__ uint32_t pool_batch(const UpdateParams& P, int fallback = kBatch) {
     return P.sched.pool_batch > 0 ? (uint32_t)P.sched.pool_batch : (uint32_t)fallback;
+}
+
+#ifndef SDFDDGI_REFILL_DEFAULT
+#define SDFDDGI_REFILL_DEFAULT 12  // measured on open256 (256 and 32 rays): 1, 4, 8, 12, 16, 24 idle lanes
+#endif
+__device__ __forceinline__ int pool_refill(const UpdateParams& P) {
+    return P.sched.refill > 0 ? min(P.sched.refill, 32) : SDFDDGI_REFILL_DEFAULT;
 }
 
 // Direction of ray i of the frame (shared by every probe), stored by the weights stage.
@@ -280,7 +295,7 @@ __global__ void __launch_bounds__(kTraceThreads, 32) primary_kernel(const __grid
     const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
     const int warp = threadIdx.x >> 5;
     trace_pool<T, Relax>(
-        P.vol, n, &P.counters[kPrimaryPool], P.eps_w, P.max_steps, P.omega_primary, pool_batch(P),
+        P.vol, n, &P.counters[kPrimaryPool], P.eps_w, P.max_steps, P.omega_primary, pool_batch(P), pool_refill(P),
         [&](uint32_t b) {
             __syncwarp();  // every lane has read the previous batch's slot
             if ((threadIdx.x & 31) == 0 && b < n) {
@@ -429,6 +444,7 @@ __global__ void __launch_bounds__(kTraceThreads, 32) shadow_kernel(const __grid_
     const uint32_t n = min(P.counters[kTaskCount], P.task_capacity);
     trace_pool<T, Relax>(
         P.vol, n, &P.counters[kShadowPool], P.eps_w, P.max_steps, P.omega_shadow, pool_batch(P, kShadowBatch),
+        pool_refill(P),
         [](uint32_t) {},
         [&](uint32_t j, TraceState& st) {
             const float4 task = P.tasks[j];
