@@ -52,7 +52,8 @@ typedef enum {
     SDFDDGI_ERR_OOM = -2,         /* a device or host allocation failed          */
     SDFDDGI_ERR_CUDA = -3,        /* a CUDA runtime call or launch failed        */
     SDFDDGI_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up          */
-    SDFDDGI_ERR_STATE = -5        /* the handle is not ready for this call       */
+    SDFDDGI_ERR_STATE = -5,       /* the handle is not ready for this call       */
+    SDFDDGI_ERR_BOUNDS = -6       /* the bounds-checked build found an index outside its buffer */
 } sdfddgi_status;
 
 typedef struct sdfddgi_scene sdfddgi_scene;   /* SDF + material volume + lights */
@@ -387,8 +388,13 @@ SDFDDGI_API int sdfddgi_write_state(sdfddgi_volume* v, const float* irr, const f
  * (may be NULL): bit 0 -- the shadow-task list overflowed and shadow rays were dropped (the
  * library sizes the list so that this cannot happen); bit 1 -- a bounded wait of the
  * tensor-core gather gave up: that update's maps are not valid, and later updates skip
- * the tensor-core gather (leaving their maps invalid too) until this call clears the bit.
- * Waits for the device, clears the bits, returns SDFDDGI_ERR_TIMEOUT if bit 1 was set. */
+ * the tensor-core gather (leaving their maps invalid too) until this call clears the bit;
+ * bit 2 -- only in the bounds-checked build of the library (compiled with SDFDDGI_CHECKED,
+ * libsdfddgi_checked.so): an update's kernel met an index outside its buffer (an SDF or
+ * material sample, the multi-bounce map lookup, a per-ray array reached through a task) and
+ * used element 0 instead; the maps are not valid.
+ * Waits for the device, clears the bits, returns SDFDDGI_ERR_TIMEOUT if bit 1 was set, else
+ * SDFDDGI_ERR_BOUNDS if bit 2 was set. */
 SDFDDGI_API int sdfddgi_volume_status(sdfddgi_volume* v, uint32_t* flags);
 
 /* Clears every map and the history (as at creation). */

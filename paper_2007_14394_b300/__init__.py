@@ -14,9 +14,10 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libsdfddgi.so")
+# SDFDDGI_CHECKED=1 in the environment loads the bounds-checked build instead (libsdfddgi_checked.so)
+LIB_PATH = os.path.join(_PKG, "libsdfddgi_checked.so" if os.environ.get("SDFDDGI_CHECKED") == "1" else "libsdfddgi.so")
 
-OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_BOUNDS = 0, -1, -2, -3, -4, -5, -6
 F32, F16 = 0, 1
 LIGHT_DIRECTIONAL, LIGHT_POINT = 0, 1
 PROBE_ACTIVE, PROBE_REJECT_HISTORY = 1, 2
@@ -505,7 +506,8 @@ def denoiser_train_step(d, maps: ProbeMaps, target, lr: float, loss=None, mode=D
 
 def volume_status(volume) -> int:
     """Failure bits recorded by the volume's updates since the last call (cleared);
-    raises SdfddgiError (SDFDDGI_ERR_TIMEOUT) if a tensor-core wait gave up."""
+    raises SdfddgiError: SDFDDGI_ERR_TIMEOUT if a tensor-core wait gave up, SDFDDGI_ERR_BOUNDS if
+    the bounds-checked build met an index outside its buffer."""
     f = C.c_uint32()
     _check(lib.sdfddgi_volume_status(volume, C.byref(f)))
     return f.value

@@ -239,7 +239,6 @@ void sdfddgi::scene_view(const sdfddgi_scene* s, VolumeView* v) {
         v->n_unbounded = s->n_unbounded;
         v->n_clusters = s->n_clusters;
     } else {
-        v->sdf = s->sdf;
         v->quads = s->quads;
         v->material = s->has_material ? static_cast<const uint4*>(s->material) : nullptr;
     }
@@ -660,7 +659,9 @@ SDFDDGI_API int sdfddgi_volume_status(sdfddgi_volume* v, uint32_t* flags) {
         CUDA_TRY(cudaMemset(v->counters + c * kSlabCounterStride + kFailWord, 0, sizeof(uint32_t)));
     }
     if (flags) *flags = f;
-    if (f & 2u) return fail(SDFDDGI_ERR_TIMEOUT, "volume_status: a bounded wait of the tensor-core gather gave up");
+    if (f & kFailWait) return fail(SDFDDGI_ERR_TIMEOUT, "volume_status: a bounded wait of the tensor-core gather gave up");
+    if (f & kFailBounds)
+        return fail(SDFDDGI_ERR_BOUNDS, "volume_status: the bounds-checked build found an index outside its buffer");
     return SDFDDGI_OK;
 }
 

@@ -39,8 +39,6 @@ struct CascadeVol {
     VisParams vis;
 };
 
-static_assert(sizeof(VisParams) < 160, "cascade parameters must stay within 4 KiB");
-
 struct CascadeArgs {
     CascadeVol v[kMaxCascade];
     int n;
@@ -51,6 +49,7 @@ struct CascadeArgs {
     float* weight;
     int64_t n_pts;
 };
+static_assert(sizeof(CascadeArgs) <= 4096, "cascade parameters must stay within 4 KiB");
 
 __device__ __forceinline__ float sgnf(float v) { return (float)((v > 0.f) - (v < 0.f)); }
 

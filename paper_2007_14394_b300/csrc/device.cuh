@@ -20,6 +20,19 @@ __device__ __forceinline__ float3 fma3(float s, float3 d, float3 o) {
     return f3(fmaf(s, d.x, o.x), fmaf(s, d.y, o.y), fmaf(s, d.z, o.z));
 }
 
+// The index i of a buffer of n elements; in the bounds-checked build an index outside
+// [0, n) sets kFailBounds in *fail (when given) and becomes 0.
+template <typename I>
+__device__ __forceinline__ I checked(I i, size_t n, uint32_t* fail) {
+    if constexpr (kChecked) {
+        if (!((size_t)i < n)) {
+            if (fail) atomicOr(fail, kFailBounds);
+            return (I)0;
+        }
+    }
+    return i;
+}
+
 // ------------------------------------------------------------------ volume sampling
 struct Cell {
     size_t base;  // linear index of corner (0,0,0)
@@ -79,7 +92,8 @@ __device__ __forceinline__ float sample_sdf(const VolumeView& v, float3 p) {
     const size_t i0 = quad_index((size_t)c.ix + 1, (size_t)c.iy + 1, (size_t)z, (size_t)v.qx, (size_t)v.qy);
     // slice z + 1: the next entry for even z, else the first of the next pair
     const size_t i1 = (z & 1) ? i0 + (size_t)2 * v.qx * v.qy - 1 : i0 + 1;
-    return trilinear_quads(ld_quad<T>(v.quads, i0), ld_quad<T>(v.quads, i1), c.fx, c.fy, c.fz);
+    return trilinear_quads(ld_quad<T>(v.quads, checked(i0, v.n_quads, v.fail)),
+                           ld_quad<T>(v.quads, checked(i1, v.n_quads, v.fail)), c.fx, c.fy, c.fz);
 }
 
 // The SDF at voxel coordinate g (voxel centres at integers, g = (p - lo)/h - 1/2) for a point
@@ -95,7 +109,8 @@ __device__ __forceinline__ float sample_sdf_vox(const VolumeView& v, float3 g) {
     const uint32_t row = (uint32_t)(z >> 1) * (uint32_t)v.qy + (uint32_t)(iy + 1);
     const size_t i0 = ((size_t)row * (uint32_t)v.qx + (uint32_t)(ix + 1)) * 2 + (uint32_t)(z & 1);
     const size_t i1 = (z & 1) ? i0 + (size_t)2 * v.qx * v.qy - 1 : i0 + 1;
-    return trilinear_quads(ld_quad<T>(v.quads, i0), ld_quad<T>(v.quads, i1), fx, fy, fz);
+    return trilinear_quads(ld_quad<T>(v.quads, checked(i0, v.n_quads, v.fail)),
+                           ld_quad<T>(v.quads, checked(i1, v.n_quads, v.fail)), fx, fy, fz);
 }
 
 // ------------------------------------------------------------------ analytic scene (Sec. 3.1)
@@ -193,7 +208,7 @@ __device__ __forceinline__ void sample_material(const VolumeView& v, float3 p, f
     for (int k = 0; k < 8; ++k) {
         const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
         const float w = (dx ? c.fx : 1.f - c.fx) * (dy ? c.fy : 1.f - c.fy) * (dz ? c.fz : 1.f - c.fz);
-        const uint4 raw = __ldg(v.material + c.base + dz * sz + dy * sy + dx);
+        const uint4 raw = __ldg(v.material + checked(c.base + dz * sz + dy * sy + dx, sz * v.nz, v.fail));
         const __half2 h01 = *reinterpret_cast<const __half2*>(&raw.x);
         const __half2 h23 = *reinterpret_cast<const __half2*>(&raw.y);
         const __half2 h45 = *reinterpret_cast<const __half2*>(&raw.z);
@@ -295,7 +310,7 @@ __device__ __forceinline__ int2 border_source(int y, int x, int n) {
 // oct(nrm); weights renormalised, 0 when they all vanish.
 __device__ __forceinline__ float3 interpolate_irradiance(const int gd[3], const float go[3], const float gs[3],
                                                          const float4* irr, const uint8_t* valid, float3 x,
-                                                         float3 nrm) {
+                                                         float3 nrm, uint32_t* fail = nullptr) {
     const float xs[3] = {x.x, x.y, x.z};
     int base[3];
     float f[3];
@@ -316,13 +331,14 @@ __device__ __forceinline__ float3 interpolate_irradiance(const int gd[3], const 
     for (int k = 0; k < 8; ++k) {
         const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
         const int ix = min(base[0] + dx, gd[0] - 1), iy = min(base[1] + dy, gd[1] - 1), iz = min(base[2] + dz, gd[2] - 1);
-        const size_t p = ((size_t)iz * gd[1] + iy) * gd[0] + ix;
+        const size_t p = checked(((size_t)iz * gd[1] + iy) * gd[0] + ix, (size_t)gd[0] * gd[1] * gd[2], fail);
         float w = (dx ? f[0] : 1.f - f[0]) * (dy ? f[1] : 1.f - f[1]) * (dz ? f[2] : 1.f - f[2]);
         if (!__ldg(valid + p)) w = 0.f;
         if (!(w > 0.f)) continue;
         const float4* m = irr + p * (kIrrT * kIrrT);
-        const float4 t00 = __ldg(m + y0 * kIrrT + x0), t01 = __ldg(m + y0 * kIrrT + x0 + 1);
-        const float4 t10 = __ldg(m + (y0 + 1) * kIrrT + x0), t11 = __ldg(m + (y0 + 1) * kIrrT + x0 + 1);
+        const int t0 = checked(y0 * kIrrT + x0, kIrrT * kIrrT - kIrrT - 1, fail);  // the 2x2 texels stay in the map
+        const float4 t00 = __ldg(m + t0), t01 = __ldg(m + t0 + 1);
+        const float4 t10 = __ldg(m + t0 + kIrrT), t11 = __ldg(m + t0 + kIrrT + 1);
         const float w00 = (1.f - fx) * (1.f - fy), w01 = fx * (1.f - fy), w10 = (1.f - fx) * fy, w11 = fx * fy;
         r = fmaf(w, w00 * t00.x + w01 * t01.x + w10 * t10.x + w11 * t11.x, r);
         g = fmaf(w, w00 * t00.y + w01 * t01.y + w10 * t10.y + w11 * t11.y, g);

@@ -196,7 +196,10 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
         const int g = tid % kG, kq = (tid / kG) % kQuads, part = tid / (kG * kQuads);
         const bool live = g < ng;
         const float one = live ? 1.f : 0.f;
-        const float4* src = P.ray_val + (size_t)(p0 + (live ? g : 0)) * P.R + kq * kVec;
+        const float4* src =
+            P.ray_val + checked((size_t)(p0 + (live ? g : 0)) * P.R + kq * kVec,
+                                (size_t)P.P * P.R - P.R + kChunk - kVec + 1,  // the reads below stay inside
+                                P.vol.fail);
         float4 nxt[kVec];  // the next chunk's values, loaded one chunk ahead
 #pragma unroll
         for (int j = 0; j < kVec; ++j) nxt[j] = live ? src[j] : make_float4(0.f, 0.f, 0.f, 0.f);

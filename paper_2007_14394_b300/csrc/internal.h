@@ -43,7 +43,6 @@ constexpr int kAnalytic = 2;  // VolumeView::dtype of a scene made of primitives
 // The scene's SDF as the kernels read it: a voxel volume (float or binary16, with its
 // material volume) or, with dtype kAnalytic, a union of analytic primitives in clusters.
 struct VolumeView {
-    const void* sdf;          // float or __half, [nz][ny][nx]
     const void* quads;        // xy-quads of the same values (float4 or 4 x __half), in z-pairs with a
                               // one-voxel apron on every side: quad_index of the padded coordinates
     const uint4* material;    // 8 x binary16 per voxel (albedo rgb, -, emission rgb, -), or null
@@ -52,6 +51,8 @@ struct VolumeView {
     float h, inv_h;           // voxel size (analytic: the unit of voxel parameters)
     float lo[3];              // world box of the volume (bounds every trace)
     float hi[3];
+    size_t n_quads;           // quads in the store (bounds of the checked build)
+    uint32_t* fail;           // null, or the launch's failure word (the checked build reports there)
     int qx, qy;               // padded x and y extents of the quad store (nx + 2, ny + 2)
     float gmax[3];            // n - 1/2 per axis: the box in voxel coordinates is [-1/2, n - 1/2]
     const PrimDev* prims;     // analytic: unbounded primitives first, then each cluster's run
@@ -138,6 +139,18 @@ constexpr int kTexels = kIrrTexels + kDepTexels;  // 232 gather rows: irradiance
 // words 0..kFailWord-1 are zeroed by every launch.
 constexpr int kPrimaryPool = 0, kTaskCount = 1, kShadowPool = 2;
 constexpr int kFailWord = 7;
+// Bits of the failure word: 1 the shadow-task list overflowed, 2 a tensor-core wait gave up,
+// 4 (checked build) an index lay outside its buffer.
+constexpr uint32_t kFailTasks = 1u, kFailWait = 2u, kFailBounds = 4u;
+// The bounds-checked build (compiled with SDFDDGI_CHECKED): the update's data-dependent
+// accesses -- SDF and material samples, the multi-bounce map lookup, per-ray arrays reached
+// through task payloads -- check their index and, outside the buffer, set kFailBounds and use
+// element 0 instead, so that a bad index is reported rather than read or written.
+#ifdef SDFDDGI_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
 constexpr int kCounterWords = 8;
 // The slabs of one update keep their counters 256 bytes apart, so that concurrent slab
 // branches' atomics do not meet in one L2 line.
@@ -194,6 +207,7 @@ size_t quad_bytes(int dtype, const int dims[3]);
 inline void set_trace_constants(VolumeView* v) {
     v->qx = v->nx + 2;
     v->qy = v->ny + 2;
+    v->n_quads = (size_t)v->qx * v->qy * (((size_t)v->nz + 3) / 2 * 2);
     v->gmax[0] = (float)v->nx - 0.5f;
     v->gmax[1] = (float)v->ny - 0.5f;
     v->gmax[2] = (float)v->nz - 0.5f;

@@ -191,7 +191,6 @@ SDFDDGI_API int sdfddgi_update_probes_noalloc(
     if (e != cudaSuccess) return nofail(SDFDDGI_ERR_CUDA, "update_probes_noalloc: %s", cudaGetErrorString(e));
 
     VolumeView& vol = p.vol;
-    vol.sdf = sdf;
     vol.quads = s + off[0];
     vol.material = static_cast<const uint4*>(material);
     vol.nx = dims[0];

@@ -330,8 +330,9 @@ __global__ void __launch_bounds__(kTraceThreads, 32) primary_kernel(const __grid
             return true;
         },
         [&](const TraceState& st, int ev, int steps, float t_end) {
-            P.ray_t[st.aux] = t_end;
-            P.ray_es[st.aux] = (uint32_t)ev | ((uint32_t)steps << 8);
+            const uint32_t k = checked(st.aux, n, P.vol.fail);
+            P.ray_t[k] = t_end;
+            P.ray_es[k] = (uint32_t)ev | ((uint32_t)steps << 8);
         });
 }
 
@@ -399,7 +400,8 @@ __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant
             }
             float3 ind = f3(0.f, 0.f, 0.f);
             if (P.k_bounce != 0.f)
-                ind = interpolate_irradiance(P.gdims, P.gorigin, P.gspacing, P.look_irr, P.look_valid, x, nr);
+                ind = interpolate_irradiance(P.gdims, P.gorigin, P.gspacing, P.look_irr, P.look_valid, x, nr,
+                                             P.vol.fail);
             for (int l = 0; l < P.n_lights; ++l) {
                 bool g;
                 light_scale(P.lights[l], x, nr, &g);
@@ -426,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant
         if (lane == 31) base = atomicAdd(&P.counters[kTaskCount], (uint32_t)total);
         base = __shfl_sync(0xffffffffu, base, 31);
         if (base + (uint32_t)total > P.task_capacity) {  // cannot happen with capacity P*R*lights
-            if (lane == 31) atomicOr(&P.counters[kFailWord], 1u);
+            if (lane == 31) atomicOr(&P.counters[kFailWord], kFailTasks);
             continue;
         }
         uint32_t pos = base + (uint32_t)(incl - cnt);
@@ -465,7 +467,7 @@ __global__ void __launch_bounds__(kTraceThreads, 32) shadow_kernel(const __grid_
             return true;
         },
         [&](const TraceState& st, int ev, int steps, float) {
-            const uint32_t k = st.aux >> 5;
+            const uint32_t k = checked(st.aux >> 5, (size_t)P.P * P.R, P.vol.fail);
             atomicAdd(&P.ray_ssteps[k], (uint32_t)steps);
             if (is_miss(ev)) atomicOr(&P.ray_lit[k], 1u << (st.aux & 31u));  // hit or exhausted: occluded
         });
@@ -887,6 +889,7 @@ static UpdateParams slab_params(const UpdateParams& p, int c, int K) {
     const size_t cap = (size_t)q.P * (size_t)p.R * lights;
     q.task_capacity = (uint32_t)(cap < 0xffffffffu ? cap : 0xffffffffu);
     q.counters = p.counters + (size_t)c * kSlabCounterStride;
+    q.vol.fail = q.counters + kFailWord;
     return q;
 }
 
@@ -976,6 +979,7 @@ cudaError_t launch_update(const UpdateParams& params, cudaStream_t stream, cudaE
     if (!p.look_valid) p.look_valid = p.prev_valid;
     p.dirs = reinterpret_cast<float4*>(p.weights + (size_t)(p.R + 1) * kTexels);  // after the weights
     p.ray_val = p.ray_n;  // the gather's values replace the normals, dead after the shadow stage
+    p.vol.fail = p.counters + kFailWord;
     const int slabs = slab_count(p, lanes != nullptr, stage_events != nullptr);
     if (p.vol.dtype == kAnalytic) return launch_stages<Analytic>(p, stream, stage_events, lanes, slabs);
     return p.vol.dtype == SDFDDGI_F16 ? launch_stages<__half>(p, stream, stage_events, lanes, slabs)

@@ -154,3 +154,12 @@ def test_noalloc_binding_checks_buffer_sizes(S):
         S.update_probes_noalloc(desc, sdf, 0.25, (0, 0, 0), [], (0, 0, 0), same, same)
     with pytest.raises(ValueError, match="CUDA"):  # right sizes, host tensors
         S.update_probes_noalloc(desc, sdf, 0.25, (0, 0, 0), [], (0, 0, 0), maps(), maps())
+
+
+def test_checked_build_exports_the_same_symbols(S):
+    """The bounds-checked variant (built by build() beside the plain library) exports exactly the
+    declared entry points, so that either loads under the same binding."""
+    lib = os.path.join(ROOT, "paper_2007_14394_b300", "libsdfddgi_checked.so")
+    out = subprocess.check_output(["nm", "-D", "--defined-only", lib], text=True)
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line and "sdfddgi_" in line}
+    assert exported == set(declared_symbols())
