@@ -388,6 +388,54 @@ def run_ours(args, rank, world, local_rank):
                           "updates": n_r}
         S.destroy_volume(rvol)
 
+    # the precision form on the same workload: a binary16 SDF (rounded toward zero when baked) and
+    # the bf16 x bf16 tensor-core gather; same schedule, same timing rules (its per-output errors
+    # against the FP64 oracle are measured by tests/test_precision_form.py)
+    precision = None
+    if pr.sdf_dtype == "f32" and pr.blend == "f32":
+        baked16 = W.bake(scene, pr.sdf_dims, pr.h, (0.0, 0.0, 0.0), dtype="f16")
+        sc16 = S.create_scene()
+        S.upload_sdf(sc16, baked16.sdf, baked16.h, baked16.origin, material=baked16.material)
+        S.set_lights(sc16, scene.lights, scene.sky)
+        pdesc = S.make_desc(pr.probe_dims, R, pr.probe_origin, pr.probe_spacing, pr.max_steps, pr.depth_exponent,
+                            pr.eps_vox, pr.tmax_vox, pr.hysteresis, pr.k_bounce, pr.bias_vox, seed=pr.seed,
+                            flags=S.FLAG_BLEND_BF16)
+        pvol = S.create_volume(pdesc, sc16)
+        S.set_slabs(pvol, args.slabs)
+        for k in range(args.warmup):
+            S.update_probes(pvol, k, states=states_dev, stream=stream)
+        n_p = max(10, min(args.steps, 200))
+        pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_p)]
+        torch.cuda.synchronize()
+        for k in range(n_p):
+            flush.fill_(float(k))
+            pe[k][0].record(stream)
+            S.update_probes(pvol, args.warmup + k, states=states_dev, stream=stream)
+            pe[k][1].record(stream)
+        torch.cuda.synchronize()
+        p_ms = statistics.median(a.elapsed_time(b) for a, b in pe)
+        p_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(n_p)]
+        for evs in p_ev:
+            for e in evs:
+                e.record(stream)
+        torch.cuda.synchronize()
+        for k in range(n_p):
+            flush.fill_(float(k))
+            S.set_stage_events(pvol, p_ev[k])
+            S.update_probes(pvol, args.warmup + n_p + k, states=states_dev, stream=stream)
+        torch.cuda.synchronize()
+        S.set_stage_events(pvol, [])
+        assert S.volume_status(pvol) == 0
+        p_stage = {name: sum(evs[i].elapsed_time(evs[i + 1]) for evs in p_ev) / n_p for i, name in enumerate(S.STAGES)}
+        precision = {"form": "binary16 SDF (rounded toward zero), float32 stepping, bf16 x bf16 tensor-core gather "
+                             "with float32 accumulation",
+                     "ms_per_update": p_ms, "value": rays_per_step / (p_ms / 1e3), "unit": UNIT,
+                     "float32_ms_per_update": statistics.median(per_step),
+                     "serial_stage_ms": p_stage, "updates": n_p,
+                     "errors": "per-output errors against the FP64 oracle: tests/test_precision_form.py"}
+        S.destroy_volume(pvol)
+        S.destroy_scene(sc16)
+
     dev_ms, e2e_ms, e2e_serial_ms, wall = max_over_ranks([dev_ms, e2e_ms, e2e_serial_ms, wall], world, dev)
 
     ms = dev_ms / args.steps
@@ -443,6 +491,7 @@ def run_ours(args, rank, world, local_rank):
                               "between steps"},
         "roofline": roof,
         "stages": stages,
+        "precision_form": precision,
         "relaxed_trace_variants": dict(relaxed, omega=S.RELAX_OMEGA,
                                        note="SDFDDGI_FLAG_RELAXED_* volumes, same workload, stage events (serial); "
                                             "plain serial path: " + f"{serial_ms:.4f} ms"),

@@ -64,6 +64,41 @@ def test_precision_form_error_table(cuda_device):
     assert prec["irr_rmse_rel"] > f32["irr_rmse_rel"]  # the form is really in use
 
 
+def test_precision_form_error_table_open256(cuda_device):
+    """The same table on the open256 workload (the bench's), one frame from no history, for a
+    seeded sample of 64 active probes, in the bench's launch configuration (two slab branches)."""
+    O.set_delta(DELTA_VOX, DELTA_COS)
+    w32 = make_workload(W.PRESETS["open256"])
+    w16 = make_workload(W.PRESETS["open256"], sdf_dtype="f16")
+    rng = np.random.default_rng(21)
+    sub = np.sort(rng.choice(np.flatnonzero(w32.states["flags"] & 1), 64, replace=False))
+    rot = W.frame_rotation(11, 0)
+    ref = O.update(oracle_scene(w32), oracle_grid(w32), w32.lights, rot, w32.states, subset=sub)
+    keep = np.zeros(w32.P, bool)
+    keep[sub] = True
+    ref = dict(ref, valid=ref["valid"] * keep)  # compare the sampled probes only
+    rays = np.zeros((w32.P, w32.params["rays"]), dtype=O.RAY_DTYPE)
+    rays["event"] = -1
+    rays[sub] = ref["rays"]
+    ref["rays"] = rays
+    h = w32.baked.h
+    table = {}
+    for name, w, flags in (("float32 path", w32, 0), ("precision form", w16, S.FLAG_BLEND_BF16)):
+        gv = GpuVolume(w, flags=flags)
+        try:
+            gv.update(rot)
+            table[name] = errors(gv.state(), gv.records_np(), ref, h)
+        finally:
+            gv.close()
+    print("\nper-output error vs the FP64 oracle (open256, 64 sampled probes, one frame):")
+    for name, e in table.items():
+        print(f"  {name:15s} " + "  ".join(f"{k}={v:.3g}" for k, v in e.items()))
+    f32, prec = table["float32 path"], table["precision form"]
+    assert f32["irr_rmse_rel"] < 1e-4 and f32["hit_agreement"] >= 0.999
+    assert prec["irr_rmse_rel"] < 5e-2 and prec["hit_agreement"] >= 0.98
+    assert prec["irr_rmse_rel"] > f32["irr_rmse_rel"]
+
+
 def test_bf16_gather_close_to_float32_gather(cuda_device):
     """Same inputs, same traces: the bf16 gather differs from the float32 one only by the
     rounding of weights and values to 8 significant bits."""
