@@ -1284,7 +1284,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=sorted(W.PRESETS) + sorted(W.CASCADES) + [LEARNED] + sorted(ANALYTIC) + [CASCADE_QUERY]
                     + [VISIBILITY_QUERY, RELOCATE])
-    ap.add_argument("--train-steps", type=int, default=6000, help="training steps of the learned32 workload")
+    ap.add_argument("--train-steps", type=int, default=24000, help="training steps of the learned32 workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--slabs", type=int, default=0,
                     help="slab branches per update of the open256 volume (0: the library's automatic choice)")
