@@ -537,10 +537,10 @@ SDFDDGI_API int sdfddgi_denoiser_train_step(sdfddgi_denoiser* d, const sdfddgi_p
  * fixed 32 MiB array in device memory that every GPU loading this library holds until
  * the process exits. An update needs, each part rounded up to 256 bytes: 16 bytes (8 at
  * binary16) per voxel of the SDF grown by one voxel on every side, (nx+2)(ny+2)(nz+2) with
- * nz+2 rounded up to even, 64 + 16*max(n_lights,1) bytes per
+ * nz+2 rounded up to even, 68 + 20*max(n_lights,1) bytes per
  * probe ray (P*R), 944*R + 928 bytes of texel weights and 32768*ceil(R/16) bytes of their
  * tensor-core image -- e.g. a 64^3 float32 SDF with 512 probes x 64 rays and 1 light
- * takes about 6.9 MiB. An update that does not fit in 32 MiB is rejected with
+ * takes about 7.3 MiB. An update that does not fit in 32 MiB is rejected with
  * SDFDDGI_ERR_INVALID_ARG before any device work, and sdfddgi_last_error() states the
  * bytes needed and available.
  *  - The first call on a device looks up the array's device address

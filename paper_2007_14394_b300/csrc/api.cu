@@ -60,7 +60,7 @@ void free_volume_buffers(sdfddgi_volume* v) {
     cudaFree(v->states);
     v->states = nullptr;
     void* scratch[] = {v->ray_t, v->ray_es, v->ray_n, v->ray_alb, v->ray_base, v->ray_lit, v->ray_ssteps,
-                       v->counters, v->tasks, v->weights, v->wimage};
+                       v->counters, v->tasks, v->task_scale, v->fin_list, v->weights, v->wimage};
     for (void* q : scratch) cudaFree(q);
     for (int c = 0; c < kMaxSlabs - 1; ++c) {
         if (v->lanes.side[c]) cudaStreamDestroy(v->lanes.side[c]);
@@ -82,6 +82,8 @@ void free_volume_buffers(sdfddgi_volume* v) {
     v->ray_n = v->ray_alb = v->ray_base = nullptr;
     v->ray_lit = v->ray_ssteps = v->counters = nullptr;
     v->tasks = nullptr;
+    v->task_scale = nullptr;
+    v->fin_list = nullptr;
     v->task_capacity = 0;
 }
 
@@ -94,6 +96,7 @@ int alloc_scratch(sdfddgi_volume* v) {
     if (!rc) rc = alloc((void**)&v->ray_base, n * sizeof(float4));
     if (!rc) rc = alloc((void**)&v->ray_lit, n * sizeof(uint32_t));
     if (!rc) rc = alloc((void**)&v->ray_ssteps, n * sizeof(uint32_t));
+    if (!rc) rc = alloc((void**)&v->fin_list, n * sizeof(uint32_t));
     if (!rc) rc = alloc((void**)&v->counters, kMaxSlabs * kSlabCounterStride * sizeof(uint32_t));
     if (!rc) rc = alloc((void**)&v->weights, weights_bytes(v->desc.rays_per_probe));
     if (!rc) rc = alloc(&v->wimage, wimage_bytes(v->desc.rays_per_probe));
@@ -105,9 +108,12 @@ int ensure_task_capacity(sdfddgi_volume* v, int n_lights) {
     const size_t need = (size_t)v->P * v->desc.rays_per_probe * (size_t)(n_lights > 0 ? n_lights : 1);
     if (need <= v->task_capacity) return SDFDDGI_OK;
     cudaFree(v->tasks);
+    cudaFree(v->task_scale);
     v->tasks = nullptr;
+    v->task_scale = nullptr;
     v->task_capacity = 0;
     int rc = alloc((void**)&v->tasks, need * sizeof(float4));
+    if (!rc) rc = alloc((void**)&v->task_scale, need * sizeof(float));
     if (!rc) v->task_capacity = need;
     return rc;
 }
@@ -468,6 +474,8 @@ int sdfddgi::volume_params(sdfddgi_volume* v, UpdateParams* out) {
     p.ray_lit = v->ray_lit;
     p.ray_ssteps = v->ray_ssteps;
     p.tasks = v->tasks;
+    p.task_scale = v->task_scale;
+    p.fin_list = v->fin_list;
     p.task_capacity = (uint32_t)(v->task_capacity < 0xffffffffu ? v->task_capacity : 0xffffffffu);
     p.counters = v->counters;
     p.weights = v->weights;

@@ -47,7 +47,9 @@ struct sdfddgi_volume {
     uint32_t* ray_ssteps = nullptr;
     uint32_t* counters = nullptr;  // kMaxSlabs slabs' kCounterWords words, kSlabCounterStride apart
     float4* tasks = nullptr;
+    float* task_scale = nullptr;  // one light factor per task slot
     size_t task_capacity = 0;
+    uint32_t* fin_list = nullptr;  // P * R: the hits the finalize stage completes
     float* weights = nullptr;  // texel weights of the frame's ray set and their column sums
     void* wimage = nullptr;    // the weights as the tensor-core gather's operand image
     cudaEvent_t stage_events[SDFDDGI_STAGE_EVENTS] = {};  // caller's, recorded at stage boundaries

@@ -111,13 +111,15 @@ struct UpdateParams {
     // per-ray scratch of the staged update, index k = probe * R + ray
     float* ray_t;             // hit distance (t_max for misses)
     uint32_t* ray_es;         // event | steps << 8
-    float4* ray_n;            // normal at the hit
+    float4* ray_n;            // a hit with shadow tasks: its gated-light mask and first task (bits of x, y)
     float4* ray_alb;          // albedo
     float4* ray_base;         // emission + k * albedo * last-frame irradiance
     uint32_t* ray_lit;        // visible-light mask
     uint32_t* ray_ssteps;     // shadow steps
     float4* tasks;            // shadow tasks: origin xyz, bits of (k << 5 | light)
+    float* task_scale;        // [task_capacity] each task's light factor at its hit (light_scale)
     uint32_t task_capacity;
+    uint32_t* fin_list;       // [P*R] the hits with shadow tasks, for the finalize stage
     uint32_t* counters;       // kCounterWords words: pools and counts (zeroed by each launch), then at
                               // kFailWord the failure bits, sticky: 1 task overflow, 2 a tensor-core wait gave up
     float* weights;           // [R][kTexels] texel weights of the frame's ray set, [kTexels] column sums,
@@ -135,9 +137,10 @@ struct UpdateParams {
 
 constexpr int kTexels = kIrrTexels + kDepTexels;  // 232 gather rows: irradiance texels first
 
-// Words of UpdateParams::counters: 0 primary pool, 1 shadow-task count, 2 shadow pool;
+// Words of UpdateParams::counters: 0 primary pool, 1 shadow-task count, 2 shadow pool, 3 the
+// finalize list's length;
 // words 0..kFailWord-1 are zeroed by every launch.
-constexpr int kPrimaryPool = 0, kTaskCount = 1, kShadowPool = 2;
+constexpr int kPrimaryPool = 0, kTaskCount = 1, kShadowPool = 2, kFinCount = 3;
 constexpr int kFailWord = 7;
 // Bits of the failure word: 1 the shadow-task list overflowed, 2 a tensor-core wait gave up,
 // 4 (checked build) an index lay outside its buffer.

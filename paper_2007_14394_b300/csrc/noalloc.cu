@@ -147,7 +147,9 @@ SDFDDGI_API int sdfddgi_update_probes_noalloc(
                             n_rays * 16 * (size_t)(n_lights > 0 ? n_lights : 1),  // tasks
                             kCounterWords * 4,  // counters
                             weights_bytes(R),   // texel weights, their sums, ray directions
-                            wimage_bytes(R)};   // the weights as the tensor-core gather's operand
+                            wimage_bytes(R),    // the weights as the tensor-core gather's operand
+                            n_rays * 4 * (size_t)(n_lights > 0 ? n_lights : 1),  // task light factors
+                            n_rays * 4};        // finalize list
     size_t off[sizeof sizes / sizeof sizes[0]], total = 0;
     for (size_t k = 0; k < sizeof sizes / sizeof sizes[0]; ++k) {
         off[k] = total;
@@ -238,6 +240,8 @@ SDFDDGI_API int sdfddgi_update_probes_noalloc(
     p.counters = reinterpret_cast<uint32_t*>(s + off[9]);
     p.weights = reinterpret_cast<float*>(s + off[10]);
     p.wimage = s + off[11];
+    p.task_scale = reinterpret_cast<float*>(s + off[12]);
+    p.fin_list = reinterpret_cast<uint32_t*>(s + off[13]);
     p.blend_bf16 = (d->flags & SDFDDGI_FLAG_BLEND_BF16) ? 1 : 0;
     p.omega_primary = (d->flags & SDFDDGI_FLAG_RELAXED_PRIMARY) ? SDFDDGI_RELAX_OMEGA : 1.f;
     p.omega_shadow = (d->flags & SDFDDGI_FLAG_RELAXED_SHADOW) ? SDFDDGI_RELAX_OMEGA : 1.f;

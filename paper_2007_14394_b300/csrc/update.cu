@@ -336,11 +336,32 @@ __global__ void __launch_bounds__(kTraceThreads, 32) primary_kernel(const __grid
         });
 }
 
+// The ray's record, when records were asked for.
+__device__ __forceinline__ void write_record(const UpdateParams& P, uint32_t k, uint32_t es, float4 v, uint32_t lit) {
+    const int ev = (int)(es & 0xffu);
+    sdfddgi_ray_record rec = {};
+    rec.event = (uint8_t)ev;
+    if (ev != kNoRay) {
+        rec.t = P.ray_t[k];
+        rec.L[0] = v.x;
+        rec.L[1] = v.y;
+        rec.L[2] = v.z;
+        rec.lit_mask = lit;
+        rec.shadow_steps = is_miss(ev) ? 0u : P.ray_ssteps[k];
+        rec.steps = (uint16_t)(es >> 8);
+        rec.material_owner = is_miss(ev) ? 0u : __float_as_uint(P.ray_alb[k].w);
+    }
+    P.records[k] = rec;
+}
+
 // ------------------------------------------------------------------ 2. hit preparation
 constexpr int kPrepRays = 2048;  // rays per hit-preparation CTA
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant__ UpdateParams P) {
+#ifndef SDFDDGI_PREP_CTAS
+#define SDFDDGI_PREP_CTAS 4
+#endif
+__global__ void __launch_bounds__(kThreads, SDFDDGI_PREP_CTAS) prep_kernel(const __grid_constant__ UpdateParams P) {
     // The CTA's rays to shade (hit, or step budget spent) are first gathered into shared
     // memory, so that the shading below runs in full warps instead of one thread per ray
     // with the misses idle.
@@ -355,8 +376,15 @@ __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant
         const uint32_t k = first + (uint32_t)r;
         bool shade = false;
         if (k < n) {
-            const int ev = (int)(P.ray_es[k] & 0xffu);
+            const uint32_t es = P.ray_es[k];
+            const int ev = (int)(es & 0xffu);
             shade = ev != kNoRay && !is_miss(ev);
+            if (!shade) {  // a miss, or a ray of an inactive probe: its value for the gather is final
+                const float4 v = ev == kNoRay ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                              : make_float4(P.sky[0], P.sky[1], P.sky[2], P.tmax_w);
+                P.ray_val[k] = v;
+                if (P.records) write_record(P, k, es, v, 0u);
+            }
         }
         const unsigned want = __ballot_sync(0xffffffffu, shade);
         int base = 0;
@@ -366,10 +394,11 @@ __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant
     }
     __syncthreads();
     const int n_shade = s_count;
+    const float inv_pi = 0.318309886183790671538f;
     for (int j0 = 0; j0 < n_shade; j0 += kThreads) {
         const int j = j0 + threadIdx.x;
         uint32_t gate = 0, k = 0;
-        float3 so = f3(0.f, 0.f, 0.f);  // the shadow rays' origin: the hit lifted off the surface
+        float3 x = f3(0.f, 0.f, 0.f), nr = f3(0.f, 0.f, 0.f);  // the hit and its normal
         if (j < n_shade) {
             k = s_rays[j];
             P.ray_lit[k] = 0;
@@ -379,13 +408,14 @@ __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant
             uint32_t flags;
             const float3 o = probe_origin(P, p, &flags);
             const float3 d = ray_dir(P, i);
-            const float3 x = fma3(P.ray_t[k], d, o);
+            const float t = P.ray_t[k];
+            x = fma3(t, d, o);
             const float hh = 0.5f * V.h;
             const float gx = sample_sdf<T>(V, f3(x.x + hh, x.y, x.z)) - sample_sdf<T>(V, f3(x.x - hh, x.y, x.z));
             const float gy = sample_sdf<T>(V, f3(x.x, x.y + hh, x.z)) - sample_sdf<T>(V, f3(x.x, x.y - hh, x.z));
             const float gz = sample_sdf<T>(V, f3(x.x, x.y, x.z + hh)) - sample_sdf<T>(V, f3(x.x, x.y, x.z - hh));
             const float glen = sqrtf(gx * gx + gy * gy + gz * gz);
-            const float3 nr = glen > 0.f ? f3(gx / glen, gy / glen, gz / glen) : f3(-d.x, -d.y, -d.z);
+            nr = glen > 0.f ? f3(gx / glen, gy / glen, gz / glen) : f3(-d.x, -d.y, -d.z);
             float3 albedo, emission;
             uint32_t owner = 0;  // scenes of primitives: the caller's index + 1 of the material's primitive
             if constexpr (std::is_same<T, Analytic>::value) {
@@ -407,14 +437,21 @@ __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant
                 light_scale(P.lights[l], x, nr, &g);
                 if (g) gate |= 1u << l;
             }
-            so = fma3(P.bias_w, nr, x);
-            P.ray_n[k] = make_float4(nr.x, nr.y, nr.z, 0.f);
-            P.ray_alb[k] = make_float4(albedo.x, albedo.y, albedo.z, __uint_as_float(owner));
-            P.ray_base[k] = make_float4(emission.x + albedo.x * P.k_bounce * ind.x,
-                                        emission.y + albedo.y * P.k_bounce * ind.y,
-                                        emission.z + albedo.z * P.k_bounce * ind.z, 0.f);
+            const float4 alb = make_float4(albedo.x, albedo.y, albedo.z, __uint_as_float(owner));
+            const float4 b = make_float4(emission.x + albedo.x * P.k_bounce * ind.x,
+                                         emission.y + albedo.y * P.k_bounce * ind.y,
+                                         emission.z + albedo.z * P.k_bounce * ind.z, 0.f);
+            P.ray_alb[k] = alb;
+            P.ray_base[k] = b;
+            if (!gate) {  // no light can reach the hit: its value (the finalize rule's with no light) is final
+                const float4 v = make_float4(fmaf(alb.x * inv_pi, 0.f, b.x), fmaf(alb.y * inv_pi, 0.f, b.y),
+                                             fmaf(alb.z * inv_pi, 0.f, b.z), fminf(t, P.tmax_w));
+                P.ray_val[k] = v;
+                if (P.records) write_record(P, k, P.ray_es[k], v, 0u);
+            }
         }
-        // append this warp's (ray, light) pairs to the task list with one atomic
+        // append this warp's (ray, light) pairs to the task list with one atomic, and its rays
+        // with tasks to the finalize list with another
         const int cnt = __popc(gate);
         int incl = cnt;
 #pragma unroll
@@ -424,17 +461,30 @@ __global__ void __launch_bounds__(kThreads, 4) prep_kernel(const __grid_constant
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
         if (total == 0) continue;
-        uint32_t base = 0;
-        if (lane == 31) base = atomicAdd(&P.counters[kTaskCount], (uint32_t)total);
+        const unsigned fin = __ballot_sync(0xffffffffu, gate != 0u);
+        uint32_t base = 0, fbase = 0;
+        if (lane == 31) {
+            base = atomicAdd(&P.counters[kTaskCount], (uint32_t)total);
+            fbase = atomicAdd(&P.counters[kFinCount], (uint32_t)__popc(fin));
+        }
         base = __shfl_sync(0xffffffffu, base, 31);
+        fbase = __shfl_sync(0xffffffffu, fbase, 31);
+        uint32_t pos = base + (uint32_t)(incl - cnt);
         if (base + (uint32_t)total > P.task_capacity) {  // cannot happen with capacity P*R*lights
             if (lane == 31) atomicOr(&P.counters[kFailWord], kFailTasks);
-            continue;
+            gate = 0;  // no task: the ray is finalized with no light (the update is flagged invalid)
+            pos = 0;
         }
-        uint32_t pos = base + (uint32_t)(incl - cnt);
+        if (fin & (1u << lane)) {
+            P.fin_list[checked(fbase + (uint32_t)__popc(fin & ((1u << lane) - 1u)), n, P.vol.fail)] = k;
+            P.ray_n[k] = make_float4(__uint_as_float(gate), __uint_as_float(pos), 0.f, 0.f);  // for finalize
+        }
+        const float3 so = fma3(P.bias_w, nr, x);  // the shadow rays' origin: the hit lifted off the surface
         while (gate) {
             const int l = __ffs(gate) - 1;
             gate &= gate - 1;
+            bool g;
+            P.task_scale[pos] = light_scale(P.lights[l], x, nr, &g);  // the factor the gating saw
             P.tasks[pos++] = make_float4(so.x, so.y, so.z, __uint_as_float((k << 5) | (uint32_t)l));
         }
     }
@@ -525,94 +575,33 @@ __global__ void __launch_bounds__(kThreads) weight_sums_kernel(const __grid_cons
     P.weights[(size_t)P.R * kTexels + j] = sw.hi;
 }
 
-// Radiance (visible lights summed in light order) and clamped distance of ray k.
-__device__ __forceinline__ float4 ray_value(const UpdateParams& P, size_t k, int i, float3 o, float3 d,
-                                            uint32_t* lit_out) {
-    const uint32_t es = P.ray_es[k];
-    const int ev = (int)(es & 0xffu);
-    const float t = P.ray_t[k];
-    *lit_out = 0;
-    if (is_miss(ev)) return make_float4(P.sky[0], P.sky[1], P.sky[2], P.tmax_w);
-    const float3 x = fma3(t, d, o);
-    const float4 n4 = P.ray_n[k];
-    const float3 n = f3(n4.x, n4.y, n4.z);
-    const uint32_t lit = P.ray_lit[k];
-    float3 direct = f3(0.f, 0.f, 0.f);
-    for (int l = 0; l < P.n_lights; ++l) {
-        if (!((lit >> l) & 1u)) continue;
-        bool g;
-        const float sc = light_scale(P.lights[l], x, n, &g);
-        direct = fma3(sc, f3(P.lights[l].rgb[0], P.lights[l].rgb[1], P.lights[l].rgb[2]), direct);
-    }
-    const float inv_pi = 0.318309886183790671538f;
-    const float4 a = P.ray_alb[k], b = P.ray_base[k];
-    *lit_out = lit;
-    return make_float4(fmaf(a.x * inv_pi, direct.x, b.x), fmaf(a.y * inv_pi, direct.y, b.y),
-                       fmaf(a.z * inv_pi, direct.z, b.z), fminf(t, P.tmax_w));
-}
-
-// The ray's record, when records were asked for.
-__device__ __forceinline__ void write_record(const UpdateParams& P, uint32_t k, uint32_t es, float4 v, uint32_t lit) {
-    const int ev = (int)(es & 0xffu);
-    sdfddgi_ray_record rec = {};
-    rec.event = (uint8_t)ev;
-    if (ev != kNoRay) {
-        rec.t = P.ray_t[k];
-        rec.L[0] = v.x;
-        rec.L[1] = v.y;
-        rec.L[2] = v.z;
-        rec.lit_mask = lit;
-        rec.shadow_steps = is_miss(ev) ? 0u : P.ray_ssteps[k];
-        rec.steps = (uint16_t)(es >> 8);
-        rec.material_owner = is_miss(ev) ? 0u : __float_as_uint(P.ray_alb[k].w);
-    }
-    P.records[k] = rec;
-}
-
-constexpr int kFinalRays = 2048;  // rays per finalize CTA
-
-// The rays' values for the gather -- radiance and clamped distance, zero for rays of
-// inactive probes -- written over the rays' normals, which no later stage reads; and the
-// rays' records when records were asked for. A CTA takes 2048 rays: misses and rays of
-// inactive probes are written directly, the rays to shade are gathered in shared memory
-// and shaded in full warps (the light loop would otherwise leave the misses' lanes idle).
+// The hits with shadow tasks (the finalize list, written by the hit preparation, which
+// completes every other ray): radiance = base + albedo / pi * the sum over visible lights, in
+// light order, of the light's factor at the hit (stored with its task) times its rgb, and the
+// clamped distance; written over the ray's slot of the gather's values, and the ray's record
+// when records were asked for. Grid-stride over the list.
 __global__ void __launch_bounds__(kThreads) finalize_kernel(const __grid_constant__ UpdateParams P) {
-    __shared__ uint32_t s_rays[kFinalRays];
-    __shared__ int s_count;
     const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
-    const uint32_t first = blockIdx.x * (uint32_t)kFinalRays;
-    const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) s_count = 0;
-    __syncthreads();
-    for (int r = threadIdx.x; r < kFinalRays; r += kThreads) {
-        const uint32_t k = first + (uint32_t)r;
-        bool shade = false;
-        if (k < n) {
-            const uint32_t es = P.ray_es[k];
-            const int ev = (int)(es & 0xffu);
-            if (ev == kNoRay || is_miss(ev)) {
-                const float4 v = ev == kNoRay ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                              : make_float4(P.sky[0], P.sky[1], P.sky[2], P.tmax_w);
-                P.ray_val[k] = v;
-                if (P.records) write_record(P, k, es, v, 0u);
-            } else {
-                shade = true;
+    const uint32_t count = min(P.counters[kFinCount], n);
+    const float inv_pi = 0.318309886183790671538f;
+    for (uint32_t j = blockIdx.x * kThreads + threadIdx.x; j < count; j += gridDim.x * kThreads) {
+        const uint32_t k = checked(P.fin_list[j], n, P.vol.fail);
+        const float4 gp = P.ray_n[k];
+        uint32_t gate = __float_as_uint(gp.x), pos = __float_as_uint(gp.y);
+        const uint32_t lit = P.ray_lit[k];
+        float3 direct = f3(0.f, 0.f, 0.f);
+        while (gate) {
+            const int l = __ffs(gate) - 1;
+            gate &= gate - 1;
+            if ((lit >> l) & 1u) {
+                const float sc = P.task_scale[checked(pos, P.task_capacity, P.vol.fail)];
+                direct = fma3(sc, f3(P.lights[l].rgb[0], P.lights[l].rgb[1], P.lights[l].rgb[2]), direct);
             }
+            ++pos;
         }
-        const unsigned want = __ballot_sync(0xffffffffu, shade);
-        int base = 0;
-        if (lane == 0 && want) base = atomicAdd(&s_count, __popc(want));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (shade) s_rays[base + __popc(want & ((1u << lane) - 1u))] = k;
-    }
-    __syncthreads();
-    const int n_shade = s_count;
-    for (int j = threadIdx.x; j < n_shade; j += kThreads) {
-        const uint32_t k = s_rays[j];
-        const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
-        uint32_t flags, lit;
-        const float3 o = probe_origin(P, p, &flags);
-        const float4 v = ray_value(P, k, i, o, ray_dir(P, i), &lit);
+        const float4 a = P.ray_alb[k], b = P.ray_base[k];
+        const float4 v = make_float4(fmaf(a.x * inv_pi, direct.x, b.x), fmaf(a.y * inv_pi, direct.y, b.y),
+                                     fmaf(a.z * inv_pi, direct.z, b.z), fminf(P.ray_t[k], P.tmax_w));
         P.ray_val[k] = v;
         if (P.records) write_record(P, k, P.ray_es[k], v, lit);
     }
@@ -844,7 +833,7 @@ static cudaError_t launch_stage(const UpdateParams& p, const DeviceSetup& setup,
         else
             shadow_kernel<T, false><<<g, kTraceThreads, 0, stream>>>(p);
     } else {
-        finalize_kernel<<<(n + kFinalRays - 1) / kFinalRays, kThreads, 0, stream>>>(p);
+        finalize_kernel<<<max(1, min((int)((n + kThreads - 1) / kThreads), 8 * setup.sms)), kThreads, 0, stream>>>(p);
         if (gather_tc_supported(p) && p.sched.gather != 2)
             e = launch_gather_tc(p, stream, pack);
         else if (p.R <= 256)  // probes per gather CTA: as many as keep [R][G] values within 32 KiB
@@ -886,6 +875,8 @@ static UpdateParams slab_params(const UpdateParams& p, int c, int K) {
     q.ray_ssteps = p.ray_ssteps + k0;
     q.ray_val = p.ray_val + k0;
     q.tasks = p.tasks + k0 * lights;
+    q.task_scale = p.task_scale + k0 * lights;
+    q.fin_list = p.fin_list + k0;
     const size_t cap = (size_t)q.P * (size_t)p.R * lights;
     q.task_capacity = (uint32_t)(cap < 0xffffffffu ? cap : 0xffffffffu);
     q.counters = p.counters + (size_t)c * kSlabCounterStride;

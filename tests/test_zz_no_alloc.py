@@ -27,7 +27,8 @@ def scratch_needed(sdf_dims, sdf_elem, P, R, n_lights):
     up = lambda x: (x + 255) // 256 * 256  # noqa: E731
     rays = P * R
     parts = [(nx + 2) * (ny + 2) * (nz + 2 + nz % 2) * 4 * sdf_elem, rays * 4, rays * 4, rays * 16, rays * 16, rays * 16, rays * 4,
-             rays * 4, rays * 16 * max(n_lights, 1), 32, 944 * R + 928, 32768 * ((R + 15) // 16)]
+             rays * 4, rays * 16 * max(n_lights, 1), 32, 944 * R + 928, 32768 * ((R + 15) // 16),
+             rays * 4 * max(n_lights, 1), rays * 4]
     return sum(up(x) for x in parts)
 
 
@@ -96,14 +97,14 @@ def test_noalloc_precision_form_and_relaxed_traces(cuda_device):
 
 
 def test_noalloc_just_under_its_scratch_limit(cuda_device):
-    """7x7x6 probes at 1024 rays over the 64^3 room need 29.9 MiB of the 32 MiB; one more probe
-    layer (7x7x7) does not fit and is rejected before any device work."""
+    """7x6x6 probes at 1024 rays over the 64^3 room need 29.0 MiB of the 32 MiB; one more probe
+    row (7x7x6) does not fit and is rejected before any device work."""
     pr = W.PRESETS["room64"]
-    w = make_workload(pr, rays=1024, probe_dims=(7, 7, 6), probe_origin=(0.6, 0.6, 0.7), probe_spacing=(1.1, 1.1, 1.3))
+    w = make_workload(pr, rays=1024, probe_dims=(7, 6, 6), probe_origin=(0.6, 0.6, 0.7), probe_spacing=(1.1, 1.3, 1.3))
     need = scratch_needed(pr.sdf_dims, 4, w.P, 1024, len(w.lights))
     assert 28 << 20 < need <= SCRATCH_BYTES
     assert_equal_to_update_probes(w, frames=1)
-    w7 = make_workload(pr, rays=1024, probe_dims=(7, 7, 7), probe_origin=(0.6, 0.6, 0.7), probe_spacing=(1.1, 1.1, 1.1))
+    w7 = make_workload(pr, rays=1024, probe_dims=(7, 7, 6), probe_origin=(0.6, 0.6, 0.7), probe_spacing=(1.1, 1.1, 1.3))
     assert scratch_needed(pr.sdf_dims, 4, w7.P, 1024, len(w7.lights)) > SCRATCH_BYTES
     gv = GpuVolume(w7)
     try:
