@@ -305,6 +305,11 @@ PRESETS = {
         "point lights, 256 rays/probe, <=128 steps, 8 frames with multi-bounce",
         world=64.0, sdf_dims=(256, 256, 256), h=0.25, probe_dims=(32, 16, 32), probe_origin=(1.0, 2.0, 1.0),
         probe_spacing=(2.0, 2.0, 2.0), rays=256, max_steps=128, frames=8, seed=11, scene_kind="open"),
+    "open256_quarter": Preset(
+        "open256_quarter", "the open256 scene and SDF with the first 8 of its 32 probe layers (32x16x8 probes): "
+        "the same kernels on a quarter of the probes, for profiler captures (the SDF copies still exceed L2)",
+        world=64.0, sdf_dims=(256, 256, 256), h=0.25, probe_dims=(32, 16, 8), probe_origin=(1.0, 2.0, 1.0),
+        probe_spacing=(2.0, 2.0, 2.0), rays=256, max_steps=128, frames=8, seed=11, scene_kind="open"),
     "room64_fp16": Preset(
         "room64_fp16", "room64 with a float16 SDF (rounded toward zero), float32 stepping, bf16 blend",
         world=8.0, sdf_dims=(64, 64, 64), h=0.125, probe_dims=(8, 8, 8), probe_origin=(0.5, 0.5, 0.5),
