@@ -433,11 +433,11 @@ def batch_autotune(batch, repeats: int = 3, stream=None) -> None:
 
 
 def batch_schedule(batch, i: int):
-    """(pool_batch, blocks_per_sm, gather, tuned_ms) of volume i."""
-    out = (C.c_int32 * 3)()
+    """(pool_batch, blocks_per_sm, gather, index, tuned_ms) of volume i."""
+    out = (C.c_int32 * 4)()
     ms = C.c_float()
     _check(lib.sdfddgi_batch_schedule(batch, int(i), out, C.byref(ms)))
-    return out[0], out[1], out[2], ms.value
+    return out[0], out[1], out[2], out[3], ms.value
 
 
 # ------------------------------------------------------------------ the learned form

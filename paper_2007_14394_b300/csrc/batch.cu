@@ -207,10 +207,16 @@ SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* 
         std::vector<Schedule> cand;
         for (int pb : {16, 32, 64})
             for (int bps : {0, 4})
-                for (int g : {1, 2}) {
-                    if (g == 1 && !tc_ok) continue;
-                    cand.push_back(Schedule{pb, bps, g});
-                }
+                for (int g : {1, 2})
+                    for (int ix : {1, 2}) {  // the traces' quad-index arithmetic (same addresses)
+                        if (g == 1 && !tc_ok) continue;
+                        Schedule c = {};
+                        c.pool_batch = pb;
+                        c.blocks_per_sm = bps;
+                        c.gather = g;
+                        c.index = ix;
+                        cand.push_back(c);
+                    }
         float best = 1e30f;
         Schedule best_s = {};
         for (const Schedule& sc : cand) {
@@ -250,11 +256,12 @@ SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* 
     return rc;
 }
 
-SDFDDGI_API int sdfddgi_batch_schedule(const sdfddgi_batch* b, int32_t i, int32_t out[3], float* tuned_ms) {
+SDFDDGI_API int sdfddgi_batch_schedule(const sdfddgi_batch* b, int32_t i, int32_t out[4], float* tuned_ms) {
     if (!b || !out || i < 0 || i >= b->n) return bfail(SDFDDGI_ERR_INVALID_ARG, "batch_schedule: invalid arguments");
     out[0] = b->sched[i].pool_batch;
     out[1] = b->sched[i].blocks_per_sm;
     out[2] = b->sched[i].gather;
+    out[3] = b->sched[i].index;
     if (tuned_ms) *tuned_ms = b->tuned_ms[i];
     return SDFDDGI_OK;
 }

@@ -100,14 +100,22 @@ __device__ __forceinline__ float sample_sdf(const VolumeView& v, float3 p) {
 // inside the volume box, g in [-1/2, n - 1/2] on every axis: the cell floor(g) lies in
 // [-1, n - 1], which the apron of the quad store covers, so neither the cell nor the
 // fractions need clamping; where the clamped rule would clamp, the apron's copies of the
-// edge values give the same value.
-template <typename T>
+// edge values give the same value. The two forms of the quad index (Idx64: all in 64 bits,
+// else the z-pair row in 32 bits) give the same addresses; which one runs faster depends on
+// the store (measured: the 32-bit form on a 275 MB float32 store, the 64-bit form on a 1 GB
+// binary16 one).
+template <typename T, bool Idx64>
 __device__ __forceinline__ float sample_sdf_vox(const VolumeView& v, float3 g) {
     const int ix = __float2int_rd(g.x), iy = __float2int_rd(g.y), iz = __float2int_rd(g.z);
     const float fx = g.x - (float)ix, fy = g.y - (float)iy, fz = g.z - (float)iz;
     const int z = iz + 1;  // padded slice of the cell's lower corner
-    const uint32_t row = (uint32_t)(z >> 1) * (uint32_t)v.qy + (uint32_t)(iy + 1);
-    const size_t i0 = ((size_t)row * (uint32_t)v.qx + (uint32_t)(ix + 1)) * 2 + (uint32_t)(z & 1);
+    size_t i0;
+    if constexpr (Idx64) {
+        i0 = quad_index((size_t)ix + 1, (size_t)iy + 1, (size_t)z, (size_t)v.qx, (size_t)v.qy);
+    } else {
+        const uint32_t row = (uint32_t)(z >> 1) * (uint32_t)v.qy + (uint32_t)(iy + 1);
+        i0 = ((size_t)row * (uint32_t)v.qx + (uint32_t)(ix + 1)) * 2 + (uint32_t)(z & 1);
+    }
     const size_t i1 = (z & 1) ? i0 + (size_t)2 * v.qx * v.qy - 1 : i0 + 1;
     return trilinear_quads(ld_quad<T>(v.quads, checked(i0, v.n_quads, v.fail)),
                            ld_quad<T>(v.quads, checked(i1, v.n_quads, v.fail)), fx, fy, fz);

@@ -67,6 +67,8 @@ struct Schedule {
     int blocks_per_sm;   // resident CTAs per SM of the persistent trace kernels (default: occupancy limit)
     int gather;          // 0 automatic (tensor cores when R % 16 == 0), 1 tensor cores, 2 SIMT
     int slabs;           // z-slabs of probes run as concurrent branches: 0 automatic, 1 (serial) .. kMaxSlabs
+    int index;           // the traces' quad-index arithmetic: 0 automatic (64-bit above a 512 MiB store),
+                         // 1 a 32-bit z-pair row, 2 all in 64 bits (the same addresses either way)
     int refill;          // idle lanes of a trace warp before it hands out new tasks: 0 default, 1..32
 };
 
@@ -207,8 +209,10 @@ __host__ __device__ __forceinline__ size_t quad_index(size_t x, size_t y, size_t
 // nz + 2 rounded up to even.
 size_t quad_bytes(int dtype, const int dims[3]);
 // The view's derived constants of the voxel-space traces (qx, qy, gmax), from nx, ny, nz.
+// Padded x extent of the quad store.
+inline int padded_qx(int nx) { return nx + 2; }
 inline void set_trace_constants(VolumeView* v) {
-    v->qx = v->nx + 2;
+    v->qx = padded_qx(v->nx);
     v->qy = v->ny + 2;
     v->n_quads = (size_t)v->qx * v->qy * (((size_t)v->nz + 3) / 2 * 2);
     v->gmax[0] = (float)v->nx - 0.5f;

@@ -84,7 +84,7 @@ __device__ __forceinline__ float trace_sample(const VolumeView& v, TraceState& s
 // step left the volume box, the step may have passed a surface, so the trace goes back to the
 // previous point's plain step and stays plain (omega = 1) for the rest of the ray; the
 // discarded sample counts as a step.
-template <typename T, bool Relax>
+template <typename T, bool Relax, bool Idx64>
 __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, float eps, int max_steps,
                                           int* steps, float* t_end) {
     constexpr bool kVox = !std::is_same<T, Analytic>::value;
@@ -103,7 +103,7 @@ __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, f
     float sd = 0.f;
     if (!outside) {
         if constexpr (kVox)
-            sd = sample_sdf_vox<T>(v, p);
+            sd = sample_sdf_vox<T, Idx64>(v, p);
         else
             sd = trace_sample<T>(v, st, p);
     }
@@ -164,7 +164,7 @@ __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, f
 // A warp hands out new tasks only once at least `refill` of its lanes wait for one (or no
 // lane is tracing): a ray lasts a few steps, so refilling lanes one by one would run the
 // hand-out on nearly every step for one or two lanes at a time.
-template <typename T, bool Relax, typename Claim, typename Init, typename Done>
+template <typename T, bool Relax, bool Idx64, typename Claim, typename Init, typename Done>
 __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint32_t* counter, float eps,
                                            int max_steps, float omega, uint32_t batch, int refill, Claim claim,
                                            Init init, Done done) {
@@ -220,7 +220,7 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
         if (busy) {
             int steps;
             float t_end;
-            const int ev = trace_step<T, Relax>(v, st, eps, max_steps, &steps, &t_end);
+            const int ev = trace_step<T, Relax, Idx64>(v, st, eps, max_steps, &steps, &t_end);
             if (ev >= 0) {
                 if constexpr (!std::is_same<T, Analytic>::value) t_end *= v.h;  // back to world units
                 done(st, ev, steps, t_end);
@@ -288,13 +288,13 @@ __device__ __forceinline__ float light_scale(const LightDev& li, float3 x, float
 // A claimed batch of tasks lies within one probe whenever R is a multiple of the batch
 // size, so the probe's origin and flags are decoded once per batch, by lane 0 into its
 // warp's slot; a task outside the slot's probe decodes its own.
-template <typename T, bool Relax>
+template <typename T, bool Relax, bool Idx64>
 __global__ void __launch_bounds__(kTraceThreads, 32) primary_kernel(const __grid_constant__ UpdateParams P) {
     __shared__ float4 s_origin[kTraceThreads / 32];  // probe origin, its first task index (bits)
     __shared__ uint32_t s_flags[kTraceThreads / 32];
     const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
     const int warp = threadIdx.x >> 5;
-    trace_pool<T, Relax>(
+    trace_pool<T, Relax, Idx64>(
         P.vol, n, &P.counters[kPrimaryPool], P.eps_w, P.max_steps, P.omega_primary, pool_batch(P), pool_refill(P),
         [&](uint32_t b) {
             __syncwarp();  // every lane has read the previous batch's slot
@@ -491,10 +491,10 @@ __global__ void __launch_bounds__(kThreads, SDFDDGI_PREP_CTAS) prep_kernel(const
 }
 
 // ------------------------------------------------------------------ 3. shadow traces
-template <typename T, bool Relax>
+template <typename T, bool Relax, bool Idx64>
 __global__ void __launch_bounds__(kTraceThreads, 32) shadow_kernel(const __grid_constant__ UpdateParams P) {
     const uint32_t n = min(P.counters[kTaskCount], P.task_capacity);
-    trace_pool<T, Relax>(
+    trace_pool<T, Relax, Idx64>(
         P.vol, n, &P.counters[kShadowPool], P.eps_w, P.max_steps, P.omega_shadow, pool_batch(P, kShadowBatch),
         pool_refill(P),
         [](uint32_t) {},
@@ -772,18 +772,18 @@ cudaError_t prepare_update_kernels(const DeviceSetup** out) {
     DeviceSetup& s = g_setup[dev];
     if (!s.done) {
         s.err = cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev);
-        s.occ_primary[0][0] = occupancy((const void*)primary_kernel<float, false>, kTraceThreads);
-        s.occ_primary[0][1] = occupancy((const void*)primary_kernel<__half, false>, kTraceThreads);
-        s.occ_primary[0][2] = occupancy((const void*)primary_kernel<Analytic, false>, kTraceThreads);
-        s.occ_shadow[0][0] = occupancy((const void*)shadow_kernel<float, false>, kTraceThreads);
-        s.occ_shadow[0][1] = occupancy((const void*)shadow_kernel<__half, false>, kTraceThreads);
-        s.occ_shadow[0][2] = occupancy((const void*)shadow_kernel<Analytic, false>, kTraceThreads);
-        s.occ_primary[1][0] = occupancy((const void*)primary_kernel<float, true>, kTraceThreads);
-        s.occ_primary[1][1] = occupancy((const void*)primary_kernel<__half, true>, kTraceThreads);
-        s.occ_primary[1][2] = occupancy((const void*)primary_kernel<Analytic, true>, kTraceThreads);
-        s.occ_shadow[1][0] = occupancy((const void*)shadow_kernel<float, true>, kTraceThreads);
-        s.occ_shadow[1][1] = occupancy((const void*)shadow_kernel<__half, true>, kTraceThreads);
-        s.occ_shadow[1][2] = occupancy((const void*)shadow_kernel<Analytic, true>, kTraceThreads);
+        s.occ_primary[0][0] = occupancy((const void*)primary_kernel<float, false, false>, kTraceThreads);
+        s.occ_primary[0][1] = occupancy((const void*)primary_kernel<__half, false, false>, kTraceThreads);
+        s.occ_primary[0][2] = occupancy((const void*)primary_kernel<Analytic, false, false>, kTraceThreads);
+        s.occ_shadow[0][0] = occupancy((const void*)shadow_kernel<float, false, false>, kTraceThreads);
+        s.occ_shadow[0][1] = occupancy((const void*)shadow_kernel<__half, false, false>, kTraceThreads);
+        s.occ_shadow[0][2] = occupancy((const void*)shadow_kernel<Analytic, false, false>, kTraceThreads);
+        s.occ_primary[1][0] = occupancy((const void*)primary_kernel<float, true, false>, kTraceThreads);
+        s.occ_primary[1][1] = occupancy((const void*)primary_kernel<__half, true, false>, kTraceThreads);
+        s.occ_primary[1][2] = occupancy((const void*)primary_kernel<Analytic, true, false>, kTraceThreads);
+        s.occ_shadow[1][0] = occupancy((const void*)shadow_kernel<float, true, false>, kTraceThreads);
+        s.occ_shadow[1][1] = occupancy((const void*)shadow_kernel<__half, true, false>, kTraceThreads);
+        s.occ_shadow[1][2] = occupancy((const void*)shadow_kernel<Analytic, true, false>, kTraceThreads);
         // the SIMT gathers stage [R][G] values: at most 32 KiB for the G chosen per R
         for (const void* k : {(const void*)gather_kernel<8>, (const void*)gather_kernel<4>, (const void*)gather_kernel<2>})
             if (s.err == cudaSuccess) s.err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 << 10);
@@ -818,20 +818,27 @@ static cudaError_t launch_stage(const UpdateParams& p, const DeviceSetup& setup,
     const int rp = p.omega_primary > 1.f ? 1 : 0, rs = p.omega_shadow > 1.f ? 1 : 0;
     const uint32_t n = (uint32_t)p.P * (uint32_t)p.R;
     cudaError_t e = cudaSuccess;
+    // the quad-index arithmetic of the traces (same addresses): the 64-bit form above a 512 MiB store
+    const size_t store = p.vol.n_quads * (p.vol.dtype == SDFDDGI_F16 ? 8 : 16);
+    const bool i64 = p.sched.index == 2 || (p.sched.index == 0 && store > ((size_t)512 << 20));
     if (s == 0) {
         const int g = persistent_blocks(setup, setup.occ_primary[rp][type_slot<T>()], p.sched.blocks_per_sm);
         if (rp)
-            primary_kernel<T, true><<<g, kTraceThreads, 0, stream>>>(p);
+            i64 ? primary_kernel<T, true, true><<<g, kTraceThreads, 0, stream>>>(p)
+                : primary_kernel<T, true, false><<<g, kTraceThreads, 0, stream>>>(p);
         else
-            primary_kernel<T, false><<<g, kTraceThreads, 0, stream>>>(p);
+            i64 ? primary_kernel<T, false, true><<<g, kTraceThreads, 0, stream>>>(p)
+                : primary_kernel<T, false, false><<<g, kTraceThreads, 0, stream>>>(p);
     } else if (s == 1) {
         prep_kernel<T><<<(n + kPrepRays - 1) / kPrepRays, kThreads, 0, stream>>>(p);
     } else if (s == 2) {
         const int g = persistent_blocks(setup, setup.occ_shadow[rs][type_slot<T>()], p.sched.blocks_per_sm);
         if (rs)
-            shadow_kernel<T, true><<<g, kTraceThreads, 0, stream>>>(p);
+            i64 ? shadow_kernel<T, true, true><<<g, kTraceThreads, 0, stream>>>(p)
+                : shadow_kernel<T, true, false><<<g, kTraceThreads, 0, stream>>>(p);
         else
-            shadow_kernel<T, false><<<g, kTraceThreads, 0, stream>>>(p);
+            i64 ? shadow_kernel<T, false, true><<<g, kTraceThreads, 0, stream>>>(p)
+                : shadow_kernel<T, false, false><<<g, kTraceThreads, 0, stream>>>(p);
     } else {
         finalize_kernel<<<max(1, min((int)((n + kThreads - 1) / kThreads), 8 * setup.sms)), kThreads, 0, stream>>>(p);
         if (gather_tc_supported(p) && p.sched.gather != 2)

@@ -18,8 +18,8 @@
 namespace sdfddgi {
 
 template <typename T, typename Q>
-__global__ void build_quads_kernel(const T* __restrict__ sdf, Q* __restrict__ quads, int nx, int ny, int nz) {
-    const int qx = nx + 2, qy = ny + 2, qz = nz + 2;  // padded extents
+__global__ void build_quads_kernel(const T* __restrict__ sdf, Q* __restrict__ quads, int nx, int ny, int nz, int qx) {
+    const int qy = ny + 2, qz = nz + 2;  // padded extents
     const size_t n = (size_t)qx * qy * qz;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const int X = (int)(i % qx), Y = (int)((i / qx) % qy), Z = (int)(i / ((size_t)qx * qy));
@@ -40,19 +40,19 @@ __global__ void build_quads_kernel(const T* __restrict__ sdf, Q* __restrict__ qu
 
 size_t quad_bytes(int dtype, const int dims[3]) {
     const size_t pairs = ((size_t)dims[2] + 3) / 2;
-    return 2 * pairs * ((size_t)dims[0] + 2) * ((size_t)dims[1] + 2) * (dtype == SDFDDGI_F16 ? 8 : 16);
+    return 2 * pairs * (size_t)padded_qx(dims[0]) * ((size_t)dims[1] + 2) * (dtype == SDFDDGI_F16 ? 8 : 16);
 }
 
 cudaError_t build_quads(const void* sdf, void* quads, int dtype, const int dims[3], cudaStream_t stream) {
-    const size_t n = ((size_t)dims[0] + 2) * ((size_t)dims[1] + 2) * ((size_t)dims[2] + 2);
+    const size_t n = (size_t)padded_qx(dims[0]) * ((size_t)dims[1] + 2) * ((size_t)dims[2] + 2);
     const int threads = 256;
     const int blocks = (int)std::min<size_t>((n + threads - 1) / threads, 148 * 64);
     if (dtype == SDFDDGI_F16)
         build_quads_kernel<__half, uint2><<<blocks, threads, 0, stream>>>(
-            static_cast<const __half*>(sdf), static_cast<uint2*>(quads), dims[0], dims[1], dims[2]);
+            static_cast<const __half*>(sdf), static_cast<uint2*>(quads), dims[0], dims[1], dims[2], padded_qx(dims[0]));
     else
         build_quads_kernel<float, float4><<<blocks, threads, 0, stream>>>(
-            static_cast<const float*>(sdf), static_cast<float4*>(quads), dims[0], dims[1], dims[2]);
+            static_cast<const float*>(sdf), static_cast<float4*>(quads), dims[0], dims[1], dims[2], padded_qx(dims[0]));
     return cudaGetLastError();
 }
 

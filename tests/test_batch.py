@@ -79,8 +79,8 @@ def test_batch_equals_plain_updates_bit_for_bit(cuda_device):
             t.assert_equal(f"frame {frame}")
         assert np.abs(t.batched[0].state()[0][..., :3]).max() > 0
         for i, w in enumerate(t.ws):
-            pb, bps, g, ms = S.batch_schedule(t.batch, i)
-            assert (pb, bps, g, ms) == (0, 0, 0, 0.0)
+            pb, bps, g, ix, ms = S.batch_schedule(t.batch, i)
+            assert (pb, bps, g, ix, ms) == (0, 0, 0, 0, 0.0)
     finally:
         t.close()
 
@@ -132,8 +132,8 @@ def test_autotune_keeps_state_and_results(cuda_device):
         for b, a in zip(before, after):
             assert all(np.array_equal(x, y) for x, y in zip(b, a))
         for i, w in enumerate(t.ws):
-            pb, bps, g, ms = S.batch_schedule(t.batch, i)
-            assert pb in (16, 32, 64) and bps in (0, 4) and g in (1, 2) and ms > 0, (i, pb, bps, g, ms)
+            pb, bps, g, ix, ms = S.batch_schedule(t.batch, i)
+            assert pb in (16, 32, 64) and bps in (0, 4) and g in (1, 2) and ix in (1, 2) and ms > 0, (i, pb, bps, g, ms)
             assert g == 2 or w.params["rays"] % 16 == 0
         # the tuned schedule differs from the default one at most in the gather's rounding
         for frame in (1, 2):
