@@ -33,6 +33,7 @@ UNIT = "probe-rays/s"
 WORKLOAD = "open256"
 L2_FLUSH_BYTES = 512 << 20
 KERNELS_PER_UPDATE = 7  # texel weights, primary, hit preparation, shadow, finalize, weight image, gather
+MERGED_KERNELS = 7  # a merged batch frame: the same seven stages, each one launch over every volume
 
 
 def max_over_ranks(values, world: int, device=None):
@@ -551,6 +552,7 @@ def run_batch(args, rank, world, local_rank):
     t_tune = time.perf_counter() - t_tune
     schedules = [dict(zip(("pool_batch", "blocks_per_sm", "gather", "index", "tuned_ms"), S.batch_schedule(batch, i)))
                  for i in range(len(vols))]
+    form, tuned_branches, tuned_merged = S.batch_form(batch)
 
     def barrier():
         if world > 1:
@@ -583,6 +585,21 @@ def run_batch(args, rank, world, local_rank):
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     seq_step = timed(plain, 10_000)
+    # both forms of the frame, each timed the same way (the headline runs the autotuner's)
+    forms = {}
+    for name, f in (("branches", S.BATCH_FORM_BRANCHES), ("merged", S.BATCH_FORM_MERGED)):
+        try:
+            S.batch_set_form(batch, f)
+        except S.SdfddgiError as err:
+            forms[name] = {"unavailable": str(err)}
+            continue
+        forms[name] = {"ms_per_step": statistics.median(timed(lambda fr: S.update_batch(batch, fr, stream=stream),
+                                                              30_000 + 1000 * f))}
+    S.batch_set_form(batch, S.BATCH_FORM_AUTO)
+    forms.update({"chosen": "merged" if form == S.BATCH_FORM_MERGED else "branches",
+                  "autotune_ms": {"branches": tuned_branches, "merged": tuned_merged},
+                  "what": "median step of each form; branches: one graph branch of stage kernels per volume; "
+                          "merged: one launch per stage over all volumes, the trace pools spanning every volume"})
 
     # end to end: probe states in from pinned host memory, every volume's maps out
     host_states = [torch.from_numpy(st.view(np.uint8).copy()).pin_memory() for st in states]
@@ -605,7 +622,7 @@ def run_batch(args, rank, world, local_rank):
     hbm, peak_kind = peaks()
     frame_bytes = sum(w[k]["bytes"] for w in work for k in ("primary", "prep", "shadow"))
     ach = frame_bytes / (ms / 1e3) / 1e9
-    roof = {"kernel": "frame (all stages of all volumes in one graph)", "bound": "hbm", "achieved": ach,
+    roof = {"kernel": "frame (all stages of all volumes in one graph launch)", "bound": "hbm", "achieved": ach,
             "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "bytes_per_launch": frame_bytes,
             "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
             "note": "trace/prep/shadow gathered bytes of every volume over the whole frame's time"}
@@ -620,7 +637,8 @@ def run_batch(args, rank, world, local_rank):
             "sdf": "x".join(map(str, base.sdf_dims)) + f" {base.sdf_dtype}", "max_steps": base.max_steps,
             "active_rays_per_step": rays_per_step, "seed": base.seed,
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)", "autotune_s": t_tune},
-        "gpu_launches": KERNELS_PER_UPDATE * len(vols) * args.steps,
+        "gpu_launches": (MERGED_KERNELS if form == S.BATCH_FORM_MERGED else KERNELS_PER_UPDATE * len(vols)) * args.steps,
+        "forms": forms,
         "sequential": {"ms_per_step": seq_ms / args.steps, "value": whole_job_rate(world, rays_per_step, args.steps, seq_ms),
                        "what": "one plain update_probes launch per volume, default schedules, same stream"},
         "e2e": {"value": whole_job_rate(world, rays_per_step, args.steps, e2e_ms), "unit": UNIT,

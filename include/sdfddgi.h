@@ -405,10 +405,15 @@ SDFDDGI_API int sdfddgi_reset(sdfddgi_volume* v, void* stream);
 /* Sec. 3.5 (cascade volume) covers a large scene with several probe volumes of
  * different density -- dense near the camera, sparse far away -- all updated every
  * frame. A batch updates up to 8 volumes of one scene together: each frame is one
- * CUDA graph, with one branch per volume, so the volumes' stages overlap on the GPU and
- * the frame costs one launch. Each volume computes exactly what sdfddgi_update_probes
- * would compute for it with the same launch shapes (schedule); the results do not
- * depend on the schedule beyond the rounding order of the gather.
+ * CUDA graph launch, in one of two forms (sdfddgi_batch_set_form):
+ *  branches -- one branch of stage kernels per volume, so the volumes' stages overlap on
+ *              the GPU;
+ *  merged   -- one launch per stage covering every volume: the persistent trace kernels
+ *              take (volume, task) work items from one pool over all the volumes' rays,
+ *              the other stages lay the volumes' thread blocks one after another.
+ * Each volume computes exactly what sdfddgi_update_probes would compute for it with the
+ * same launch shapes (schedule), in either form; the results do not depend on the
+ * schedule beyond the rounding order of the gather.
  *  volumes -- n distinct volumes of the same scene (not owned; they must outlive the
  *             batch and must not be updated by other calls while the batch is in use).
  *  states  -- NULL, or n pointers each NULL (grid positions) or P_i DEVICE states that
@@ -434,8 +439,10 @@ SDFDDGI_API int sdfddgi_update_batch(sdfddgi_batch* b, uint32_t frame, const flo
  * CTAs per SM of the trace kernels (4 or the occupancy limit), gather (tensor cores when
  * rays_per_probe is a multiple of 16, or SIMT), and the traces' SDF-index arithmetic (a
  * 32-bit row or 64-bit; the same addresses). The trials write only each volume's
- * spare ping-pong buffer, so the maps and history are unchanged. Synchronises `stream`.
- * repeats: 1..64. */
+ * spare ping-pong buffer, so the maps and history are unchanged. Then, when the volumes
+ * allow the merged form, it times `repeats` whole frames in each form and keeps the faster
+ * one for SDFDDGI_BATCH_FORM_AUTO (sdfddgi_batch_form reports both times). Synchronises
+ * `stream`. repeats: 1..64. */
 SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* stream);
 
 /* Volume i's schedule: out[0] pool batch, out[1] CTAs per SM (0 = occupancy limit),
@@ -444,6 +451,23 @@ SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* 
  * same addresses, a speed choice); tuned_ms (nullable) receives the autotuner's mean update
  * time of that schedule (0 before tuning). */
 SDFDDGI_API int sdfddgi_batch_schedule(const sdfddgi_batch* b, int32_t i, int32_t out[4], float* tuned_ms);
+
+/* The form of a batch's frames. AUTO (the default): the autotuner's choice (it times whole
+ * frames in both forms after choosing the volumes' schedules), branches before tuning.
+ * MERGED needs volumes that share the hit threshold, the step budget, the relaxation of
+ * their traces, the depth exponent and the gather precision, a voxel SDF, and the
+ * tensor-core gather for every volume (rays per probe a multiple of 16); its pools take the
+ * first volume's pool batch, CTAs per SM and index arithmetic, and a bounds failure in a
+ * merged trace is reported by the first volume's status. */
+#define SDFDDGI_BATCH_FORM_AUTO 0
+#define SDFDDGI_BATCH_FORM_BRANCHES 1
+#define SDFDDGI_BATCH_FORM_MERGED 2
+/* Errors: SDFDDGI_ERR_INVALID_ARG (NULL, form out of range, MERGED for volumes that do not
+ * allow it -- sdfddgi_last_error says why). */
+SDFDDGI_API int sdfddgi_batch_set_form(sdfddgi_batch* b, int32_t form);
+/* The form the next frame runs in (BRANCHES or MERGED), and (ms, nullable) the autotuner's
+ * mean frame times of the two forms (0 where not timed). */
+SDFDDGI_API int sdfddgi_batch_form(const sdfddgi_batch* b, int32_t* form, float ms[2]);
 
 /* ---- the learned form: a denoiser of low-ray-count updates -------------- */
 

@@ -25,6 +25,7 @@ FLAG_BLEND_BF16 = 1  # volume flag: the precision form of the gather (bf16 tenso
 FLAG_RELAXED_SHADOW = 2   # volume flag: over-relaxed shadow traces (RELAX_OMEGA)
 FLAG_RELAXED_PRIMARY = 4  # volume flag: over-relaxed primary traces
 RELAX_OMEGA = float(np.float32(1.6))  # the relaxation factor of FLAG_RELAXED_TRACE (float32 1.6)
+BATCH_FORM_AUTO, BATCH_FORM_BRANCHES, BATCH_FORM_MERGED = 0, 1, 2  # sdfddgi_batch_set_form
 FLAG_TEST_GATHER_STALL = 1 << 30  # volume flag for failure tests: the gather's bounded waits run out
 MAX_LIGHTS, MAX_RAYS, MAX_STEPS = 32, 1024, 65535
 IRR_SIDE, DEPTH_SIDE = 8, 16
@@ -120,6 +121,8 @@ def _load() -> C.CDLL:
         "sdfddgi_update_batch": ([vp, u32, vp, vp], C.c_int),
         "sdfddgi_batch_autotune": ([vp, i32, vp], C.c_int),
         "sdfddgi_batch_schedule": ([vp, i32, C.POINTER(i32), C.POINTER(C.c_float)], C.c_int),
+        "sdfddgi_batch_set_form": ([vp, i32], C.c_int),
+        "sdfddgi_batch_form": ([vp, C.POINTER(i32), C.POINTER(C.c_float)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -133,6 +136,7 @@ EXPORTED = ("last_error", "create_scene", "destroy_scene", "upload_sdf", "set_li
             "destroy_volume", "volume_probe_count", "frame_rotation", "update_probes", "update_probes_noalloc",
             "sample_irradiance", "set_stage_events", "get_maps", "read_state", "write_state", "reset",
             "create_batch", "destroy_batch", "update_batch", "batch_autotune", "batch_schedule",
+            "batch_set_form", "batch_form",
             "create_denoiser", "destroy_denoiser", "denoiser_params", "denoise", "denoise_volume",
             "denoiser_gradients", "denoiser_adam", "denoiser_train_step", "volume_status", "denoiser_status",
             "relocate_probes", "sample_irradiance_visible", "upload_primitives", "sample_irradiance_cascade",
@@ -438,6 +442,19 @@ def batch_schedule(batch, i: int):
     ms = C.c_float()
     _check(lib.sdfddgi_batch_schedule(batch, int(i), out, C.byref(ms)))
     return out[0], out[1], out[2], out[3], ms.value
+
+
+def batch_set_form(batch, form: int) -> None:
+    """BATCH_FORM_AUTO (the autotuner's choice), BATCH_FORM_BRANCHES or BATCH_FORM_MERGED."""
+    _check(lib.sdfddgi_batch_set_form(batch, int(form)))
+
+
+def batch_form(batch):
+    """(form of the next frame, autotuned ms per frame of the branches form, of the merged form)."""
+    f = C.c_int32()
+    ms = (C.c_float * 2)()
+    _check(lib.sdfddgi_batch_form(batch, C.byref(f), ms))
+    return f.value, ms[0], ms[1]
 
 
 # ------------------------------------------------------------------ the learned form

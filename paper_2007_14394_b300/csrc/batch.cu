@@ -1,13 +1,17 @@
 // batch.cu -- several probe volumes (e.g. the nested cascades of the paper's Sec. 3.5)
-// updated together: one CUDA graph per frame, with one branch per volume, so that the
-// volumes' stages overlap on the GPU (a small volume's pool tails fill with the large
-// volumes' work) and the whole frame is a single launch from the host. The graph is
-// captured once per ping-pong parity and scene version and replayed; the frame's
-// rotations reach it through a small device buffer written before each replay.
+// updated together, each frame one CUDA graph launch from the host, in one of two forms:
+//  branches -- one branch of stage kernels per volume, so that the volumes' stages overlap
+//              on the GPU (a small volume's pool tails fill with the large volumes' work);
+//  merged   -- one launch per stage covering every volume: the persistent trace kernels
+//              take (volume, task) work items from one pool over all the volumes' rays, and
+//              the other stages lay the volumes' CTAs one after another (MergedParams).
+// The graph is captured once per ping-pong parity, form and scene version and replayed; the
+// frame's rotations reach it through a small device buffer written before each replay.
 //
 // The autotuner picks each volume's launch shapes (trace-pool batch, resident CTAs per
-// SM of the trace kernels, tensor-core or SIMT gather) by timing real updates of that
-// volume; the trials write only the volume's spare ping-pong buffer.
+// SM of the trace kernels, tensor-core or SIMT gather, index arithmetic) by timing real
+// updates of that volume, then the faster form by timing whole frames; the trials write
+// only the volumes' spare ping-pong buffers.
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -45,6 +49,10 @@ struct sdfddgi_batch {
     float* rot_dev = nullptr;  // [n][9]
     CachedGraph cache[kGraphCache];
     int next_slot = 0;
+    int form_asked = SDFDDGI_BATCH_FORM_AUTO;  // SDFDDGI_BATCH_FORM_*
+    int form_tuned = 0;                        // the autotuner's choice (0 before tuning)
+    float form_ms[2] = {0.f, 0.f};             // the autotuner's frame times: branches, merged
+    MergedParams merged;                       // the merged launches' parameters (host copy)
 };
 
 namespace {
@@ -56,16 +64,55 @@ void drop_graphs(sdfddgi_batch* b) {
     }
 }
 
+// The launch parameters of volume i's next frame (reads the current maps, writes the other).
+int batch_params(sdfddgi_batch* b, int i, UpdateParams* p) {
+    int rc = volume_params(b->vols[i], p);
+    if (rc) return rc;
+    p->rot_dev = b->rot_dev + 9 * i;
+    p->states = b->states[i];
+    p->sched = b->sched[i];
+    return SDFDDGI_OK;
+}
+
+// Whether the volumes can run merged (and, when not, why).
+bool merged_ok(sdfddgi_batch* b, const char** why) {
+    UpdateParams p[kMaxBatch];
+    for (int i = 0; i < b->n; ++i)
+        if (batch_params(b, i, &p[i])) {
+            if (why) *why = "a volume's parameters could not be prepared";
+            return false;
+        }
+    return merged_supported(p, b->n, why);
+}
+
+// The form a frame runs in: the caller's, else the autotuner's, else branches.
+int frame_form(const sdfddgi_batch* b) {
+    if (b->form_asked != SDFDDGI_BATCH_FORM_AUTO) return b->form_asked;
+    return b->form_tuned ? b->form_tuned : SDFDDGI_BATCH_FORM_BRANCHES;
+}
+
+// Records every volume's stages with one launch per stage on the capturing stream.
+int record_frame_merged(sdfddgi_batch* b, cudaStream_t st) {
+    UpdateParams p[kMaxBatch];
+    for (int i = 0; i < b->n; ++i) {
+        int rc = batch_params(b, i, &p[i]);
+        if (rc) return rc;
+    }
+    const char* why = nullptr;
+    if (!merged_supported(p, b->n, &why)) return bfail(SDFDDGI_ERR_INVALID_ARG, why);
+    cudaError_t e = launch_merged(p, b->n, &b->merged, st);
+    if (e != cudaSuccess) return bfail(SDFDDGI_ERR_CUDA, cudaGetErrorString(e));
+    return SDFDDGI_OK;
+}
+
 // Records the stages of every volume, one forked stream each, on the capturing stream.
 int record_frame(sdfddgi_batch* b, cudaStream_t st) {
+    if (frame_form(b) == SDFDDGI_BATCH_FORM_MERGED) return record_frame_merged(b, st);
     cudaError_t e = cudaEventRecord(b->fork, st);
     for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
         UpdateParams p;
-        int rc = volume_params(b->vols[i], &p);
+        int rc = batch_params(b, i, &p);
         if (rc) return rc;
-        p.rot_dev = b->rot_dev + 9 * i;
-        p.states = b->states[i];
-        p.sched = b->sched[i];
         e = cudaStreamWaitEvent(b->side[i], b->fork, 0);
         if (e == cudaSuccess) e = launch_update(p, b->side[i]);
         if (e == cudaSuccess) e = cudaEventRecord(b->join[i], b->side[i]);
@@ -78,7 +125,15 @@ int record_frame(sdfddgi_batch* b, cudaStream_t st) {
 uint64_t parity_key(const sdfddgi_batch* b) {
     uint64_t k = 0;
     for (int i = 0; i < b->n; ++i) k |= (uint64_t)(b->vols[i]->cur & 1) << i;
-    return k;
+    return k | (uint64_t)frame_form(b) << 32;
+}
+
+// Every volume's frame rotations for `frame` into rot (host, [n][9]).
+void frame_rotations(const sdfddgi_batch* b, uint32_t frame, float* rot) {
+    for (int i = 0; i < b->n; ++i) {
+        const sdfddgi_volume_desc& d = b->vols[i]->desc;
+        sdfddgi_frame_rotation(d.seed, frame, d.volume_id, rot + 9 * i);
+    }
 }
 
 }  // namespace
@@ -109,6 +164,11 @@ SDFDDGI_API int sdfddgi_create_batch(sdfddgi_volume* const* volumes, const sdfdd
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaMalloc(&b->rot_dev, sizeof(float) * 9 * n);
+    if (e == cudaSuccess) {  // frame 0's rotations until the first update writes its own
+        float rot[kMaxBatch * 9];
+        frame_rotations(b, 0, rot);
+        e = cudaMemcpy(b->rot_dev, rot, sizeof(float) * 9 * n, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         sdfddgi_destroy_batch(b);
         return bfail(e == cudaErrorMemoryAllocation ? SDFDDGI_ERR_OOM : SDFDDGI_ERR_CUDA, cudaGetErrorString(e));
@@ -134,16 +194,13 @@ SDFDDGI_API int sdfddgi_update_batch(sdfddgi_batch* b, uint32_t frame, const flo
     if (!b) return bfail(SDFDDGI_ERR_INVALID_ARG, "update_batch: batch is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     float rot[kMaxBatch * 9];
-    for (int i = 0; i < b->n; ++i) {
-        if (rotations) {
-            for (int k = 0; k < 9; ++k) {
-                if (!std::isfinite(rotations[9 * i + k])) return bfail(SDFDDGI_ERR_INVALID_ARG, "update_batch: rotation not finite");
-                rot[9 * i + k] = rotations[9 * i + k];
-            }
-        } else {
-            const sdfddgi_volume_desc& d = b->vols[i]->desc;
-            sdfddgi_frame_rotation(d.seed, frame, d.volume_id, rot + 9 * i);
+    if (rotations) {
+        for (int k = 0; k < 9 * b->n; ++k) {
+            if (!std::isfinite(rotations[k])) return bfail(SDFDDGI_ERR_INVALID_ARG, "update_batch: rotation not finite");
+            rot[k] = rotations[k];
         }
+    } else {
+        frame_rotations(b, frame, rot);
     }
     // everything the captured work reads from the host side must be current
     UpdateParams probe;
@@ -250,10 +307,68 @@ SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* 
             b->tuned_ms[i] = best;
         }
     }
+    // then the form: whole frames in each form the volumes allow, launched directly on `stream`
+    // (each writes the volumes' spare buffers, as the trials above)
+    if (rc == SDFDDGI_OK) {
+        b->form_ms[0] = b->form_ms[1] = 0.f;
+        const bool can_merge = merged_ok(b, nullptr);
+        const int saved = b->form_asked;
+        for (int f = SDFDDGI_BATCH_FORM_BRANCHES; f <= SDFDDGI_BATCH_FORM_MERGED && rc == SDFDDGI_OK; ++f) {
+            if (f == SDFDDGI_BATCH_FORM_MERGED && !can_merge) break;
+            b->form_asked = f;
+            float total = 0.f;
+            for (int r = 0; r <= repeats && rc == SDFDDGI_OK; ++r) {  // the first frame warms up
+                float rot[kMaxBatch * 9];
+                frame_rotations(b, (uint32_t)r, rot);
+                cudaError_t e = cudaMemcpyAsync(b->rot_dev, rot, sizeof(float) * 9 * b->n, cudaMemcpyHostToDevice, st);
+                for (int i = 0; i < b->n && e == cudaSuccess; ++i) e = order_map_write(b->vols[i], b->vols[i]->cur ^ 1, st);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+                if (e != cudaSuccess) {
+                    rc = bfail(SDFDDGI_ERR_CUDA, "batch_autotune: frame trial failed");
+                    break;
+                }
+                rc = record_frame(b, st);
+                if (rc) break;
+                if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = bfail(SDFDDGI_ERR_CUDA, "batch_autotune: frame trial failed");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r > 0) total += ms;
+            }
+            b->form_ms[f - 1] = total / repeats;
+        }
+        b->form_asked = saved;
+        if (rc == SDFDDGI_OK)
+            b->form_tuned = can_merge && b->form_ms[1] < b->form_ms[0] ? SDFDDGI_BATCH_FORM_MERGED
+                                                                       : SDFDDGI_BATCH_FORM_BRANCHES;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     drop_graphs(b);
     return rc;
+}
+
+SDFDDGI_API int sdfddgi_batch_set_form(sdfddgi_batch* b, int32_t form) {
+    if (!b || form < SDFDDGI_BATCH_FORM_AUTO || form > SDFDDGI_BATCH_FORM_MERGED)
+        return bfail(SDFDDGI_ERR_INVALID_ARG, "batch_set_form: invalid arguments");
+    if (form == SDFDDGI_BATCH_FORM_MERGED) {
+        const char* why = nullptr;
+        if (!merged_ok(b, &why)) return bfail(SDFDDGI_ERR_INVALID_ARG, why ? why : "batch_set_form: not mergeable");
+    }
+    b->form_asked = form;  // the graph cache is keyed by the form
+    return SDFDDGI_OK;
+}
+
+SDFDDGI_API int sdfddgi_batch_form(const sdfddgi_batch* b, int32_t* form, float ms[2]) {
+    if (!b || !form) return bfail(SDFDDGI_ERR_INVALID_ARG, "batch_form: NULL argument");
+    *form = frame_form(b);
+    if (ms) {
+        ms[0] = b->form_ms[0];
+        ms[1] = b->form_ms[1];
+    }
+    return SDFDDGI_OK;
 }
 
 SDFDDGI_API int sdfddgi_batch_schedule(const sdfddgi_batch* b, int32_t i, int32_t out[4], float* tuned_ms) {

@@ -105,10 +105,9 @@ __device__ __forceinline__ void put(unsigned char* part, uint32_t off, float v) 
 // its parts (tf32: hi then lo; bf16: one), element (row, k) at Fmt::offset(row, k).
 // Thread per (texel row, ray).
 template <bool BF16>
-__global__ void __launch_bounds__(256) pack_weights_kernel(const __grid_constant__ UpdateParams P) {
+__device__ __forceinline__ void pack_weights_body(const UpdateParams& P, int i) {  // ray i
     using F = tc::Fmt<BF16>;
     const int m = threadIdx.x;         // texel row 0..255
-    const int i = blockIdx.x;          // ray
     const float w = m < kTexels ? P.weights[(size_t)i * kTexels + m] : 0.f;
     const int c = i / tc::kChunk, k = i % tc::kChunk, t = m >> 7, r = m & 127;
     unsigned char* base = reinterpret_cast<unsigned char*>(P.wimage) + (size_t)c * F::kABytes + t * F::kParts * F::kTilePart;
@@ -122,7 +121,13 @@ __global__ void __launch_bounds__(256) pack_weights_kernel(const __grid_constant
 }
 
 template <bool BF16>
-__global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid_constant__ UpdateParams P) {
+__global__ void __launch_bounds__(256) pack_weights_kernel(const __grid_constant__ UpdateParams P) {
+    pack_weights_body<BF16>(P, blockIdx.x);  // one ray per block
+}
+
+// The CTA of probes block * kG .. + kG - 1 of one launch's probes.
+template <bool BF16>
+__device__ __forceinline__ void gather_tc_body(const UpdateParams& P, int block) {
     using namespace tc;
     using F = Fmt<BF16>;
     constexpr int kABytes = F::kABytes, kBBytes = F::kBBytes, kBPart = F::kBPart, kTilePart = F::kTilePart;
@@ -137,7 +142,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
     __shared__ uint32_t s_flags[kG];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int p0 = blockIdx.x * kG;
+    const int p0 = block * kG;
     const int ng = min(kG, P.P - p0);
     const int n_chunks = P.R / kChunk;
 
@@ -408,6 +413,32 @@ __global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid
     if (tid < ng) P.cur_valid[p0 + tid] = (s_flags[tid] & SDFDDGI_PROBE_ACTIVE) ? 1 : P.prev_valid[p0 + tid];
 }
 
+template <bool BF16>
+__global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_kernel(const __grid_constant__ UpdateParams P) {
+    gather_tc_body<BF16>(P, blockIdx.x);
+}
+
+// The merged launches of the batched form: one block per ray of every volume for the weight
+// images, and each volume's gather CTAs after the earlier volumes'.
+__device__ __forceinline__ int merged_part_tc(const uint32_t* begin, int n, uint32_t x) {
+    int v = 0;
+#pragma unroll
+    for (int i = 1; i < kMaxMerged; ++i) v += (i < n && x >= begin[i]) ? 1 : 0;
+    return v;
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(256) pack_weights_merged_kernel(const __grid_constant__ MergedParams M) {
+    const int v = merged_part_tc(M.dir_begin, M.n, blockIdx.x);
+    pack_weights_body<BF16>(M.p[v], (int)(blockIdx.x - M.dir_begin[v]));
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(tc::kThreads, 2) gather_tc_merged_kernel(const __grid_constant__ MergedParams M) {
+    const int v = merged_part_tc(M.gather_begin, M.n, blockIdx.x);
+    gather_tc_body<BF16>(M.p[v], (int)(blockIdx.x - M.gather_begin[v]));
+}
+
 bool gather_tc_supported(const UpdateParams& p) { return p.R % tc::kChunk == 0 && p.wimage != nullptr; }
 
 size_t wimage_bytes(int R) { return (size_t)((R + tc::kChunk - 1) / tc::kChunk) * tc::Fmt<false>::kABytes; }
@@ -427,6 +458,12 @@ cudaError_t prepare_gather_tc() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(gather_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tc_smem<true>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gather_tc_merged_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc_smem<false>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gather_tc_merged_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc_smem<true>());
     return e;
 }
 
@@ -443,6 +480,17 @@ cudaError_t launch_gather_tc(const UpdateParams& p, cudaStream_t stream, bool pa
 
 cudaError_t launch_pack_weights(const UpdateParams& p, cudaStream_t stream) {
     return p.blend_bf16 ? launch_tc<true>(p, stream, true, false) : launch_tc<false>(p, stream, true, false);
+}
+
+template <bool BF16>
+static cudaError_t launch_tc_merged(const MergedParams& m, cudaStream_t stream, bool pack) {
+    if (pack) pack_weights_merged_kernel<BF16><<<m.dir_begin[m.n], 256, 0, stream>>>(m);
+    gather_tc_merged_kernel<BF16><<<m.gather_begin[m.n], tc::kThreads, tc_smem<BF16>(), stream>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_tc_merged(const MergedParams& m, cudaStream_t stream, bool pack) {
+    return m.p[0].blend_bf16 ? launch_tc_merged<true>(m, stream, pack) : launch_tc_merged<false>(m, stream, pack);
 }
 
 }  // namespace sdfddgi

@@ -198,6 +198,38 @@ cudaError_t launch_update(const UpdateParams& p, cudaStream_t stream, cudaEvent_
                           const SlabLanes* lanes = nullptr);
 // The number of slab branches launch_update runs p as (1 = serial).
 int slab_count(const UpdateParams& p, bool have_lanes, bool stage_events);
+// The parameters launch_update actually runs: plain traces unless relaxation was asked for,
+// the multi-bounce lookup maps, the directions and value slots inside the scratch, the
+// failure word.
+UpdateParams prepared_params(const UpdateParams& p);
+
+// Several volumes of one scene updated with one launch per stage, each launch covering every
+// volume (the batched form's merged schedule). Per stage, the volumes' parts follow one
+// another: volume v owns tasks ray_begin[v] .. ray_begin[v + 1] - 1 of the merged primary
+// pool (its P*R rays, padded to a multiple of the pool batch, so that a claimed batch lies
+// within one volume), CTAs prep_begin[v] .. of the hit preparation, gather_begin[v] .. of the
+// gather, and blocks dir_begin[v] .. (one per ray) of the texel weights and their image. The
+// shadow pool is laid out the same way from the task counts on the device. The merged pools'
+// counters are volume 0's pool words, which the launch zeroes with every volume's counters.
+constexpr int kMaxMerged = 8;
+struct MergedParams {
+    int n;
+    uint32_t primary_batch, shadow_batch;  // tasks per claim of the two merged pools
+    uint32_t ray_begin[kMaxMerged + 1];
+    uint32_t prep_begin[kMaxMerged + 1];
+    uint32_t gather_begin[kMaxMerged + 1];
+    uint32_t dir_begin[kMaxMerged + 1];
+    UpdateParams p[kMaxMerged];  // prepared_params of each volume
+};
+// Whether n volumes (their launch parameters) can run as one launch per stage: one scene, the
+// same hit threshold, step budget, relaxation, depth exponent and gather precision, the
+// tensor-core gather for every volume, and at most kMaxMerged of them. The message says why not.
+bool merged_supported(const UpdateParams* p, int n, const char** why);
+// Builds m from the volumes' parameters (prepared here) and enqueues the frame on `stream`:
+// the counters, the texel weights and their image, then one launch per stage.
+cudaError_t launch_merged(const UpdateParams* p, int n, MergedParams* m, cudaStream_t stream);
+// The merged tensor-core gather (with pack: first the volumes' weight images).
+cudaError_t launch_gather_tc_merged(const MergedParams& m, cudaStream_t stream, bool pack);
 cudaError_t launch_sample(const SampleParams& p, cudaStream_t stream);
 cudaError_t launch_sample_visible(const SampleParams& p, const VisParams& v, cudaStream_t stream);
 // Position of quad (x, y, z) in an xy-quad store of padded extents qx, qy: z-pairs,

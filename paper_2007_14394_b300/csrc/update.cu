@@ -19,6 +19,7 @@
 //                         contiguous 16-byte stores.
 // Device-wide pools pay the latency of the longest ray once per launch instead of once
 // per probe.
+#include <cstring>
 #include <mutex>
 #include <type_traits>
 
@@ -231,8 +232,9 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
     }
 }
 
+__host__ __device__ __forceinline__ int pool_batch_host(int asked, int fallback) { return asked > 0 ? asked : fallback; }
 __device__ __forceinline__ uint32_t pool_batch(const UpdateParams& P, int fallback = kBatch) {
-    return P.sched.pool_batch > 0 ? (uint32_t)P.sched.pool_batch : (uint32_t)fallback;
+    return (uint32_t)pool_batch_host(P.sched.pool_batch, fallback);
 }
 
 #ifndef SDFDDGI_REFILL_DEFAULT
@@ -357,18 +359,19 @@ __device__ __forceinline__ void write_record(const UpdateParams& P, uint32_t k, 
 // ------------------------------------------------------------------ 2. hit preparation
 constexpr int kPrepRays = 2048;  // rays per hit-preparation CTA
 
-template <typename T>
 #ifndef SDFDDGI_PREP_CTAS
 #define SDFDDGI_PREP_CTAS 4
 #endif
-__global__ void __launch_bounds__(kThreads, SDFDDGI_PREP_CTAS) prep_kernel(const __grid_constant__ UpdateParams P) {
+// Rays block * kPrepRays .. + kPrepRays - 1 of one launch's probes.
+template <typename T>
+__device__ __forceinline__ void prep_body(const UpdateParams& P, uint32_t block) {
     // The CTA's rays to shade (hit, or step budget spent) are first gathered into shared
     // memory, so that the shading below runs in full warps instead of one thread per ray
     // with the misses idle.
     __shared__ uint32_t s_rays[kPrepRays];
     __shared__ int s_count;
     const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
-    const uint32_t first = blockIdx.x * (uint32_t)kPrepRays;
+    const uint32_t first = block * (uint32_t)kPrepRays;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) s_count = 0;
     __syncthreads();
@@ -490,6 +493,11 @@ __global__ void __launch_bounds__(kThreads, SDFDDGI_PREP_CTAS) prep_kernel(const
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreads, SDFDDGI_PREP_CTAS) prep_kernel(const __grid_constant__ UpdateParams P) {
+    prep_body<T>(P, blockIdx.x);
+}
+
 // ------------------------------------------------------------------ 3. shadow traces
 template <typename T, bool Relax, bool Idx64>
 __global__ void __launch_bounds__(kTraceThreads, 32) shadow_kernel(const __grid_constant__ UpdateParams P) {
@@ -523,6 +531,145 @@ __global__ void __launch_bounds__(kTraceThreads, 32) shadow_kernel(const __grid_
         });
 }
 
+// ------------------------------------------------------------------ merged launches (batched form)
+// The part of a merged launch that x (a task, CTA or block index) falls in: the last volume
+// whose part begins at or before x (an empty part is skipped, as the next one begins where it
+// ends).
+__device__ __forceinline__ int merged_part(const uint32_t* begin, int n, uint32_t x) {
+    int v = 0;
+#pragma unroll
+    for (int i = 1; i < kMaxMerged; ++i) v += (i < n && x >= begin[i]) ? 1 : 0;
+    return v;
+}
+
+// Primary traces of every volume from one pool. A claimed batch lies within one volume (the
+// parts are padded to the batch); its volume and, as in primary_kernel, its probe are decoded
+// once per claim. A ray's payload is its merged task index, from which the completion finds
+// the volume again.
+template <typename T, bool Relax, bool Idx64>
+__global__ void __launch_bounds__(kTraceThreads, 32) primary_merged_kernel(const __grid_constant__ MergedParams M) {
+    __shared__ float4 s_origin[kTraceThreads / 32];  // probe origin, its first merged task index (bits)
+    __shared__ uint32_t s_flags[kTraceThreads / 32];
+    __shared__ int s_vol[kTraceThreads / 32];
+    const UpdateParams& P0 = M.p[0];
+    const uint32_t n = M.ray_begin[M.n];
+    const int warp = threadIdx.x >> 5;
+    trace_pool<T, Relax, Idx64>(
+        P0.vol, n, &P0.counters[kPrimaryPool], P0.eps_w, P0.max_steps, P0.omega_primary, M.primary_batch,
+        pool_refill(P0),
+        [&](uint32_t b) {
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0 && b < n) {
+                const int v = merged_part(M.ray_begin, M.n, b);
+                const UpdateParams& P = M.p[v];
+                const uint32_t k = b - M.ray_begin[v];
+                uint32_t flags = 0;
+                float3 o = f3(0.f, 0.f, 0.f);
+                const uint32_t p = k / (uint32_t)P.R;
+                if (k < (uint32_t)P.P * (uint32_t)P.R) o = probe_origin(P, (int)p, &flags);
+                s_origin[warp] = make_float4(o.x, o.y, o.z, __uint_as_float(M.ray_begin[v] + p * (uint32_t)P.R));
+                s_flags[warp] = flags;
+                s_vol[warp] = v;
+            }
+            __syncwarp();
+        },
+        [&](uint32_t kg, TraceState& st) {
+            const int v = s_vol[warp];
+            const UpdateParams& P = M.p[v];
+            const uint32_t k = kg - M.ray_begin[v];
+            if (k >= (uint32_t)P.P * (uint32_t)P.R) return false;  // padding of the volume's part
+            const float4 so = s_origin[warp];
+            const uint32_t rel = kg - __float_as_uint(so.w);
+            int i;
+            uint32_t flags;
+            if (rel < (uint32_t)P.R) {
+                i = (int)rel;
+                flags = s_flags[warp];
+                st.o = f3(so.x, so.y, so.z);
+            } else {
+                i = (int)(k % (uint32_t)P.R);
+                st.o = probe_origin(P, (int)(k / (uint32_t)P.R), &flags);
+            }
+            if (!(flags & SDFDDGI_PROBE_ACTIVE)) {
+                P.ray_es[k] = kNoRay;
+                return false;
+            }
+            st.d = ray_dir(P, i);
+            st.tlimit = P.tmax_w;
+            st.aux = kg;
+            return true;
+        },
+        [&](const TraceState& st, int ev, int steps, float t_end) {
+            const int v = merged_part(M.ray_begin, M.n, st.aux);
+            const UpdateParams& P = M.p[v];
+            const uint32_t k = checked(st.aux - M.ray_begin[v], (size_t)P.P * P.R, P.vol.fail);
+            P.ray_t[k] = t_end;
+            P.ray_es[k] = (uint32_t)ev | ((uint32_t)steps << 8);
+        });
+}
+
+// Shadow traces of every volume from one pool: volume v's tasks follow the earlier volumes'
+// (each part padded to the batch), laid out by every CTA from the task counts the hit
+// preparation left. A task's payload is its merged index; the completion reads the task's
+// ray and light from the volume's list again.
+template <typename T, bool Relax, bool Idx64>
+__global__ void __launch_bounds__(kTraceThreads, 32) shadow_merged_kernel(const __grid_constant__ MergedParams M) {
+    __shared__ uint32_t s_begin[kMaxMerged + 1], s_count[kMaxMerged];
+    if (threadIdx.x == 0) {
+        uint32_t b = 0;
+        for (int v = 0; v < M.n; ++v) {
+            const uint32_t c = min(M.p[v].counters[kTaskCount], M.p[v].task_capacity);
+            s_begin[v] = b;
+            s_count[v] = c;
+            b += (c + M.shadow_batch - 1) / M.shadow_batch * M.shadow_batch;
+        }
+        s_begin[M.n] = b;
+    }
+    __syncthreads();
+    const UpdateParams& P0 = M.p[0];
+    const uint32_t n = s_begin[M.n];
+    trace_pool<T, Relax, Idx64>(
+        P0.vol, n, &P0.counters[kShadowPool], P0.eps_w, P0.max_steps, P0.omega_shadow, M.shadow_batch,
+        pool_refill(P0),
+        [](uint32_t) {},
+        [&](uint32_t jg, TraceState& st) {
+            const int v = merged_part(s_begin, M.n, jg);
+            const uint32_t j = jg - s_begin[v];
+            if (j >= s_count[v]) return false;  // padding of the volume's part
+            const UpdateParams& P = M.p[v];
+            const float4 task = P.tasks[j];
+            const int l = (int)(__float_as_uint(task.w) & 31u);
+            st.o = f3(task.x, task.y, task.z);
+            const LightDev& li = P.lights[l];
+            if (li.type == SDFDDGI_LIGHT_DIRECTIONAL) {
+                st.d = f3(li.v[0], li.v[1], li.v[2]);
+                st.tlimit = P.tmax_w;
+            } else {
+                const float3 Ls = f3(li.v[0], li.v[1], li.v[2]) - st.o;
+                const float ds = sqrtf(dot(Ls, Ls));
+                st.d = (1.f / ds) * Ls;
+                st.tlimit = ds;
+            }
+            st.aux = jg;
+            return true;
+        },
+        [&](const TraceState& st, int ev, int steps, float) {
+            const int v = merged_part(s_begin, M.n, st.aux);
+            const UpdateParams& P = M.p[v];
+            const uint32_t j = checked(st.aux - s_begin[v], P.task_capacity, P.vol.fail);
+            const uint32_t tk = __float_as_uint(P.tasks[j].w);
+            const uint32_t k = checked(tk >> 5, (size_t)P.P * P.R, P.vol.fail);
+            atomicAdd(&P.ray_ssteps[k], (uint32_t)steps);
+            if (is_miss(ev)) atomicOr(&P.ray_lit[k], 1u << (tk & 31u));  // hit or exhausted: occluded
+        });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, SDFDDGI_PREP_CTAS) prep_merged_kernel(const __grid_constant__ MergedParams M) {
+    const int v = merged_part(M.prep_begin, M.n, blockIdx.x);
+    prep_body<T>(M.p[v], blockIdx.x - M.prep_begin[v]);
+}
+
 // ------------------------------------------------------------------ 4. gather (Eq. 3)
 // The texel weights max(0, u_j . d_i)^e depend on the frame's ray set only, so they are
 // computed once per update: row i (ray) x column j (texel, irradiance first), plus each
@@ -531,9 +678,8 @@ __global__ void __launch_bounds__(kTraceThreads, 32) shadow_kernel(const __grid_
 // relative accuracy down to the cosine cutoff; the traces read the directions rounded to
 // float from the same computation.
 template <int PEXP, bool Dirs>
-__global__ void __launch_bounds__(kThreads) weights_kernel(const __grid_constant__ UpdateParams P) {
+__device__ __forceinline__ void weights_body(const UpdateParams& P, int i) {  // ray i, one texel per thread
     __shared__ dfloat s_d[3];
-    const int i = blockIdx.x;  // one ray per block, one texel per thread
     const int j = threadIdx.x;
     if (j == 0) {
         dfloat d[3];
@@ -554,6 +700,11 @@ __global__ void __launch_bounds__(kThreads) weights_kernel(const __grid_constant
     float w = 0.f;
     if (c.hi > 0.f) w = irr ? c.hi : df_pow(c, PEXP == 50 ? 50 : P.depth_exp).hi;
     P.weights[(size_t)i * kTexels + j] = w;
+}
+
+template <int PEXP, bool Dirs>
+__global__ void __launch_bounds__(kThreads) weights_kernel(const __grid_constant__ UpdateParams P) {
+    weights_body<PEXP, Dirs>(P, blockIdx.x);  // one ray per block
 }
 
 // The frame's R ray directions alone (what the traces need of stage 0), for updates whose
@@ -580,7 +731,7 @@ __global__ void __launch_bounds__(kThreads) weight_sums_kernel(const __grid_cons
 // light order, of the light's factor at the hit (stored with its task) times its rgb, and the
 // clamped distance; written over the ray's slot of the gather's values, and the ray's record
 // when records were asked for. Grid-stride over the list.
-__global__ void __launch_bounds__(kThreads) finalize_kernel(const __grid_constant__ UpdateParams P) {
+__device__ __forceinline__ void finalize_body(const UpdateParams& P) {
     const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
     const uint32_t count = min(P.counters[kFinCount], n);
     const float inv_pi = 0.318309886183790671538f;
@@ -605,6 +756,20 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(const __grid_constan
         P.ray_val[k] = v;
         if (P.records) write_record(P, k, P.ray_es[k], v, lit);
     }
+}
+
+__global__ void __launch_bounds__(kThreads) finalize_kernel(const __grid_constant__ UpdateParams P) { finalize_body(P); }
+
+// The merged launches of the texel weights (one block per ray of every volume, all with the
+// same depth exponent) and of the finalize stage (each volume's list in turn, grid-stride).
+template <int PEXP>
+__global__ void __launch_bounds__(kThreads) weights_merged_kernel(const __grid_constant__ MergedParams M) {
+    const int v = merged_part(M.dir_begin, M.n, blockIdx.x);
+    weights_body<PEXP, true>(M.p[v], (int)(blockIdx.x - M.dir_begin[v]));
+}
+
+__global__ void __launch_bounds__(kThreads) finalize_merged_kernel(const __grid_constant__ MergedParams M) {
+    for (int v = 0; v < M.n; ++v) finalize_body(M.p[v]);
 }
 
 // G probes per CTA. Stage a: the rays' values of the G probes go to shared memory (one
@@ -744,6 +909,8 @@ struct DeviceSetup {
     int sms = 0;
     int occ_primary[2][3] = {};  // [plain, relaxed][float, __half, Analytic]
     int occ_shadow[2][3] = {};
+    int occ_primary_merged[2][2] = {};  // [plain, relaxed][float, __half]
+    int occ_shadow_merged[2][2] = {};
 };
 
 namespace {
@@ -784,6 +951,14 @@ cudaError_t prepare_update_kernels(const DeviceSetup** out) {
         s.occ_shadow[1][0] = occupancy((const void*)shadow_kernel<float, true, false>, kTraceThreads);
         s.occ_shadow[1][1] = occupancy((const void*)shadow_kernel<__half, true, false>, kTraceThreads);
         s.occ_shadow[1][2] = occupancy((const void*)shadow_kernel<Analytic, true, false>, kTraceThreads);
+        s.occ_primary_merged[0][0] = occupancy((const void*)primary_merged_kernel<float, false, false>, kTraceThreads);
+        s.occ_primary_merged[0][1] = occupancy((const void*)primary_merged_kernel<__half, false, false>, kTraceThreads);
+        s.occ_primary_merged[1][0] = occupancy((const void*)primary_merged_kernel<float, true, false>, kTraceThreads);
+        s.occ_primary_merged[1][1] = occupancy((const void*)primary_merged_kernel<__half, true, false>, kTraceThreads);
+        s.occ_shadow_merged[0][0] = occupancy((const void*)shadow_merged_kernel<float, false, false>, kTraceThreads);
+        s.occ_shadow_merged[0][1] = occupancy((const void*)shadow_merged_kernel<__half, false, false>, kTraceThreads);
+        s.occ_shadow_merged[1][0] = occupancy((const void*)shadow_merged_kernel<float, true, false>, kTraceThreads);
+        s.occ_shadow_merged[1][1] = occupancy((const void*)shadow_merged_kernel<__half, true, false>, kTraceThreads);
         // the SIMT gathers stage [R][G] values: at most 32 KiB for the G chosen per R
         for (const void* k : {(const void*)gather_kernel<8>, (const void*)gather_kernel<4>, (const void*)gather_kernel<2>})
             if (s.err == cudaSuccess) s.err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 << 10);
@@ -958,6 +1133,75 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
     return e != cudaSuccess ? e : j;
 }
 
+template <typename T>
+static cudaError_t launch_merged_stages(const MergedParams& m, const DeviceSetup& setup, cudaStream_t stream) {
+    const UpdateParams& p0 = m.p[0];
+    const int rp = p0.omega_primary > 1.f ? 1 : 0, rs = p0.omega_shadow > 1.f ? 1 : 0;
+    size_t store = p0.vol.n_quads * (p0.vol.dtype == SDFDDGI_F16 ? 8 : 16);
+    const bool i64 = p0.sched.index == 2 || (p0.sched.index == 0 && store > ((size_t)512 << 20));
+    cudaError_t e = cudaSuccess;
+    if (p0.depth_exp == 50)
+        weights_merged_kernel<50><<<m.dir_begin[m.n], kThreads, 0, stream>>>(m);
+    else
+        weights_merged_kernel<0><<<m.dir_begin[m.n], kThreads, 0, stream>>>(m);
+    const int gp = persistent_blocks(setup, setup.occ_primary_merged[rp][type_slot<T>()], p0.sched.blocks_per_sm);
+    if (rp)
+        i64 ? primary_merged_kernel<T, true, true><<<gp, kTraceThreads, 0, stream>>>(m)
+            : primary_merged_kernel<T, true, false><<<gp, kTraceThreads, 0, stream>>>(m);
+    else
+        i64 ? primary_merged_kernel<T, false, true><<<gp, kTraceThreads, 0, stream>>>(m)
+            : primary_merged_kernel<T, false, false><<<gp, kTraceThreads, 0, stream>>>(m);
+    prep_merged_kernel<T><<<m.prep_begin[m.n], kThreads, 0, stream>>>(m);
+    const int gs = persistent_blocks(setup, setup.occ_shadow_merged[rs][type_slot<T>()], p0.sched.blocks_per_sm);
+    if (rs)
+        i64 ? shadow_merged_kernel<T, true, true><<<gs, kTraceThreads, 0, stream>>>(m)
+            : shadow_merged_kernel<T, true, false><<<gs, kTraceThreads, 0, stream>>>(m);
+    else
+        i64 ? shadow_merged_kernel<T, false, true><<<gs, kTraceThreads, 0, stream>>>(m)
+            : shadow_merged_kernel<T, false, false><<<gs, kTraceThreads, 0, stream>>>(m);
+    uint32_t rays = 0;
+    for (int v = 0; v < m.n; ++v) rays += (uint32_t)m.p[v].P * (uint32_t)m.p[v].R;
+    finalize_merged_kernel<<<max(1, min((int)((rays + kThreads - 1) / kThreads), 8 * setup.sms)), kThreads, 0, stream>>>(m);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_gather_tc_merged(m, stream, true);
+    return e;
+}
+
+cudaError_t launch_merged(const UpdateParams* p, int n, MergedParams* m, cudaStream_t stream) {
+    if (!merged_supported(p, n, nullptr)) return cudaErrorInvalidValue;
+    const DeviceSetup* setup = nullptr;
+    cudaError_t e = prepare_update_kernels(&setup);
+    if (e != cudaSuccess) return e;
+    std::memset(m, 0, sizeof *m);
+    m->n = n;
+    m->primary_batch = (uint32_t)pool_batch_host(p[0].sched.pool_batch, kBatch);
+    m->shadow_batch = (uint32_t)pool_batch_host(p[0].sched.pool_batch, kShadowBatch);
+    uint64_t rb = 0, pb = 0, gb = 0, db = 0;
+    for (int v = 0; v < n; ++v) {
+        m->p[v] = prepared_params(p[v]);
+        const uint64_t rays = (uint64_t)p[v].P * (uint64_t)p[v].R;
+        m->ray_begin[v] = (uint32_t)rb;
+        m->prep_begin[v] = (uint32_t)pb;
+        m->gather_begin[v] = (uint32_t)gb;
+        m->dir_begin[v] = (uint32_t)db;
+        rb += (rays + m->primary_batch - 1) / m->primary_batch * m->primary_batch;
+        pb += (rays + kPrepRays - 1) / kPrepRays;
+        gb += ((uint64_t)p[v].P + 15) / 16;
+        db += (uint64_t)(p[v].P > 0 ? p[v].R : 0);
+    }
+    if (rb >= 0xffffffffull - 2 * kShadowBatch) return cudaErrorInvalidValue;  // merged task indices are 32-bit
+    m->ray_begin[n] = (uint32_t)rb;
+    m->prep_begin[n] = (uint32_t)pb;
+    m->gather_begin[n] = (uint32_t)gb;
+    m->dir_begin[n] = (uint32_t)db;
+    // every volume's pools and counts start at zero (the merged pools are volume 0's words)
+    for (int v = 0; v < n && e == cudaSuccess; ++v)
+        e = cudaMemsetAsync(m->p[v].counters, 0, kFailWord * sizeof(uint32_t), stream);
+    if (e != cudaSuccess || rb == 0) return e;
+    return p[0].vol.dtype == SDFDDGI_F16 ? launch_merged_stages<__half>(*m, *setup, stream)
+                                         : launch_merged_stages<float>(*m, *setup, stream);
+}
+
 int slab_count(const UpdateParams& p, bool have_lanes, bool stage_events) {
     if (!have_lanes || stage_events || p.P <= 0) return 1;
     int k = p.sched.slabs;
@@ -967,9 +1211,34 @@ int slab_count(const UpdateParams& p, bool have_lanes, bool stage_events) {
     return max(1, min(min(k, kMaxSlabs), p.gdims[2]));
 }
 
-cudaError_t launch_update(const UpdateParams& params, cudaStream_t stream, cudaEvent_t const* stage_events,
-                          const SlabLanes* lanes) {
-    if (params.P == 0) return cudaSuccess;
+bool merged_supported(const UpdateParams* p, int n, const char** why) {
+    auto no = [&](const char* m) {
+        if (why) *why = m;
+        return false;
+    };
+    if (n < 1 || n > kMaxMerged) return no("the merged form takes 1 to 8 volumes");
+    for (int i = 0; i < n; ++i) {
+        const UpdateParams& a = p[i];
+        const UpdateParams& b = p[0];
+        if (a.vol.dtype != SDFDDGI_F32 && a.vol.dtype != SDFDDGI_F16) return no("the merged form needs a voxel SDF");
+        if (a.vol.quads != b.vol.quads) return no("the volumes must share one scene");
+        if (a.eps_w != b.eps_w || a.max_steps != b.max_steps)
+            return no("the volumes must share the hit threshold and the step budget");
+        if ((a.omega_primary > 1.f) != (b.omega_primary > 1.f) || (a.omega_shadow > 1.f) != (b.omega_shadow > 1.f) ||
+            (a.omega_primary > 1.f && a.omega_primary != b.omega_primary) ||
+            (a.omega_shadow > 1.f && a.omega_shadow != b.omega_shadow))
+            return no("the volumes must share the relaxation of their traces");
+        if (a.depth_exp != b.depth_exp || a.blend_bf16 != b.blend_bf16)
+            return no("the volumes must share the depth exponent and the gather precision");
+        if (!gather_tc_supported(a) || a.sched.gather == 2)
+            return no("the merged form needs the tensor-core gather (rays per probe a multiple of 16)");
+        if (a.records || a.test_stall) return no("the merged form records no rays");
+    }
+    if (why) *why = nullptr;
+    return true;
+}
+
+UpdateParams prepared_params(const UpdateParams& params) {
     UpdateParams p = params;
     if (!(p.omega_primary > 1.f)) p.omega_primary = 1.f;  // plain sphere tracing unless relaxation was asked for
     if (!(p.omega_shadow > 1.f)) p.omega_shadow = 1.f;
@@ -978,6 +1247,13 @@ cudaError_t launch_update(const UpdateParams& params, cudaStream_t stream, cudaE
     p.dirs = reinterpret_cast<float4*>(p.weights + (size_t)(p.R + 1) * kTexels);  // after the weights
     p.ray_val = p.ray_n;  // the gather's values replace the normals, dead after the shadow stage
     p.vol.fail = p.counters + kFailWord;
+    return p;
+}
+
+cudaError_t launch_update(const UpdateParams& params, cudaStream_t stream, cudaEvent_t const* stage_events,
+                          const SlabLanes* lanes) {
+    if (params.P == 0) return cudaSuccess;
+    const UpdateParams p = prepared_params(params);
     const int slabs = slab_count(p, lanes != nullptr, stage_events != nullptr);
     if (p.vol.dtype == kAnalytic) return launch_stages<Analytic>(p, stream, stage_events, lanes, slabs);
     return p.vol.dtype == SDFDDGI_F16 ? launch_stages<__half>(p, stream, stage_events, lanes, slabs)

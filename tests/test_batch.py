@@ -1,12 +1,13 @@
 """The batched update of several probe volumes in one graph launch (needs a B300).
 
 Sec. 3.5 covers a large scene with cascaded probe volumes of different density, all
-updated every frame. A batch records the stages of all its volumes as parallel branches
-of one CUDA graph. Each volume must come out exactly as a plain update of that volume
-with the same launch shapes would leave it. These tests check that bit for bit over
-several frames: with both gathers, after scene changes, after the autotuner has
-chosen schedules, and at the full 4-volume cascade size. At that size the oracle also
-checks a sample of every volume's probes.
+updated every frame. A batch records the stages of all its volumes either as parallel
+branches of one CUDA graph or, merged, as one launch per stage over every volume. Each
+volume must come out exactly as a plain update of that volume with the same launch shapes
+would leave it. These tests check that bit for bit over several frames: in both forms, with
+both gathers, after scene changes, after the autotuner has chosen schedules and form, and at
+the full 4-volume cascade size. At that size the oracle also checks a sample of every
+volume's probes.
 """
 import numpy as np
 import pytest
@@ -148,6 +149,80 @@ def test_autotune_keeps_state_and_results(cuda_device):
         t.close()
 
 
+def merged_members():
+    """Volumes the merged form takes (rays per probe multiples of 16: the tensor-core gather
+    for all), of uneven sizes and ray counts: the preset grid at 64 rays, an offset grid of 45
+    probes at 48 rays (2160 rays: the merged pool pads its part to the next whole batch) and a
+    coarse grid at 512 rays."""
+    pr = W.PRESETS["room64"]
+    return [make_workload(pr),
+            make_workload(pr, rays=48, probe_dims=(5, 3, 3), probe_origin=(1.1, 1.3, 0.9),
+                          probe_spacing=(1.3, 2.1, 1.7)),
+            make_workload(pr, rays=512, probe_dims=(3, 3, 3), probe_origin=(1.5, 1.5, 1.5),
+                          probe_spacing=(2.5, 2.5, 2.5))]
+
+
+def test_merged_batch_equals_plain_updates_bit_for_bit(cuda_device):
+    """One launch per stage over all volumes: every volume equals its plain update."""
+    t = Twins(merged_members())
+    try:
+        assert S.batch_form(t.batch) == (S.BATCH_FORM_BRANCHES, 0.0, 0.0)  # untuned automatic form
+        S.batch_set_form(t.batch, S.BATCH_FORM_MERGED)
+        assert S.batch_form(t.batch)[0] == S.BATCH_FORM_MERGED
+        for frame in range(4):
+            t.update_batch(frame)
+            t.update_plain(frame)
+            t.assert_equal(f"merged frame {frame}")
+        assert np.abs(t.batched[1].state()[0][..., :3]).max() > 0
+        # back to branches mid-stream: the same results
+        S.batch_set_form(t.batch, S.BATCH_FORM_BRANCHES)
+        t.update_batch(4)
+        t.update_plain(4)
+        t.assert_equal("branches after merged")
+    finally:
+        t.close()
+
+
+def test_merged_form_needs_tensor_core_gathers(cuda_device):
+    """A 33-ray volume gathers on the SIMT path, so the batch cannot run merged."""
+    t = Twins(room_members())
+    try:
+        with pytest.raises(S.SdfddgiError, match="tensor-core gather"):
+            S.batch_set_form(t.batch, S.BATCH_FORM_MERGED)
+        with pytest.raises(S.SdfddgiError):
+            S.batch_set_form(t.batch, 7)
+        S.batch_autotune(t.batch, repeats=1)
+        form, ms_b, ms_m = S.batch_form(t.batch)
+        assert form == S.BATCH_FORM_BRANCHES and ms_b > 0 and ms_m == 0.0
+    finally:
+        t.close()
+
+
+def test_autotune_times_both_forms(cuda_device):
+    t = Twins(merged_members())
+    try:
+        t.update_batch(0)
+        t.update_plain(0)
+        before = [gv.state() for gv in t.batched]
+        S.batch_autotune(t.batch, repeats=2)
+        for b, a in zip(before, [gv.state() for gv in t.batched]):
+            assert all(np.array_equal(x, y) for x, y in zip(b, a))
+        form, ms_b, ms_m = S.batch_form(t.batch)
+        print("frame ms: branches", ms_b, "merged", ms_m, "chosen", form)
+        assert ms_b > 0 and ms_m > 0
+        assert form == (S.BATCH_FORM_MERGED if ms_m < ms_b else S.BATCH_FORM_BRANCHES)
+        for frame in (1, 2):
+            t.update_batch(frame)
+            t.update_plain(frame)
+            for i, (a, b) in enumerate(zip(t.batched, t.plain)):
+                x, y = a.state(), b.state()
+                assert np.array_equal(x[2], y[2]), (frame, i)
+                assert rel_err(x[0], y[0]).max() <= REL_TOL, (frame, i)
+                assert rel_err(x[1], y[1]).max() <= REL_TOL, (frame, i)
+    finally:
+        t.close()
+
+
 def test_batch_argument_errors(cuda_device):
     w = make_workload(W.PRESETS["room64"], probe_dims=(2, 2, 2))
     a, b = GpuVolume(w), GpuVolume(w)
@@ -199,5 +274,11 @@ def test_cascade512_full_size_sampled(cuda_device):
                 s["border_depth"] = border_is_mirror(cur[1][sub])
                 print("cascade volume", i, "frame", frame, s)
                 assert_bar(s, f"cascade volume {i} frame {frame}")
+        # the merged form at full size: one launch per stage over the four volumes
+        S.batch_set_form(t.batch, S.BATCH_FORM_MERGED)
+        for frame in (2, 3):
+            t.update_batch(frame)
+            t.update_plain(frame)
+            t.assert_equal(f"cascade merged frame {frame}")
     finally:
         t.close()
