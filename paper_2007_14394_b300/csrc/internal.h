@@ -217,6 +217,7 @@ struct MergedParams {
     uint32_t primary_batch, shadow_batch;  // tasks per claim of the two merged pools
     uint32_t ray_begin[kMaxMerged + 1];
     uint32_t prep_begin[kMaxMerged + 1];
+    uint32_t prep_rays[kMaxMerged];  // rays per hit-preparation CTA of each volume
     uint32_t gather_begin[kMaxMerged + 1];
     uint32_t dir_begin[kMaxMerged + 1];
     UpdateParams p[kMaxMerged];  // prepared_params of each volume
