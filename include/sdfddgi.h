@@ -435,7 +435,8 @@ SDFDDGI_API void sdfddgi_destroy_batch(sdfddgi_batch* b);
 SDFDDGI_API int sdfddgi_update_batch(sdfddgi_batch* b, uint32_t frame, const float* rotation, void* stream);
 
 /* Chooses each volume's schedule by timing `repeats` real updates (plus one warm-up) of
- * each candidate on `stream`: trace-pool batch (16, 32, 64 tasks per warp claim), resident
+ * each candidate on `stream`: trace-pool batch (16, 32, 64 tasks per warp claim, or, for
+ * more than 64 rays per probe, a warp per probe: all of a probe's rays per claim), resident
  * CTAs per SM of the trace kernels (4 or the occupancy limit), gather (tensor cores when
  * rays_per_probe is a multiple of 16, or SIMT), and the traces' SDF-index arithmetic (a
  * 32-bit row or 64-bit; the same addresses). The trials write only each volume's
@@ -445,7 +446,8 @@ SDFDDGI_API int sdfddgi_update_batch(sdfddgi_batch* b, uint32_t frame, const flo
  * `stream`. repeats: 1..64. */
 SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* stream);
 
-/* Volume i's schedule: out[0] pool batch, out[1] CTAs per SM (0 = occupancy limit),
+/* Volume i's schedule: out[0] pool batch (tasks per warp claim; 0 = the default), out[1] CTAs
+ * per SM (0 = occupancy limit),
  * out[2] gather (0 automatic, 1 tensor cores, 2 SIMT), out[3] the traces' SDF-index
  * arithmetic (0 automatic: 64-bit above a 512 MiB SDF copy; 1 a 32-bit row, 2 64-bit; the
  * same addresses, a speed choice); tuned_ms (nullable) receives the autotuner's mean update

@@ -262,7 +262,12 @@ SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* 
         if (rc) break;
         const bool tc_ok = gather_tc_supported(probe);
         std::vector<Schedule> cand;
-        for (int pb : {16, 32, 64})
+        // trace tasks per warp claim: 16, 32 or 64 rays, or a warp per probe (all R rays of one
+        // probe per claim, where R is larger)
+        const int R = probe.R;
+        std::vector<int> batches = {16, 32, 64};
+        if (R > 64) batches.push_back(R);
+        for (int pb : batches)
             for (int bps : {0, 4})
                 for (int g : {1, 2})
                     for (int ix : {1, 2}) {  // the traces' quad-index arithmetic (same addresses)

@@ -63,7 +63,8 @@ struct VolumeView {
 
 // Launch shapes of one update; zero fields select the defaults.
 struct Schedule {
-    int pool_batch;      // trace tasks a warp claims per atomic: 8, 16, 32 or 64 (default: 64 primary, 128 shadow)
+    int pool_batch;      // trace tasks a warp claims per atomic, e.g. 16, 32, 64, or R (a warp per probe);
+                         // 0: 64 primary, 128 shadow
     int blocks_per_sm;   // resident CTAs per SM of the persistent trace kernels (default: occupancy limit)
     int gather;          // 0 automatic (tensor cores when R % 16 == 0), 1 tensor cores, 2 SIMT
     int slabs;           // z-slabs of probes run as concurrent branches: 0 automatic, 1 (serial) .. kMaxSlabs

@@ -134,7 +134,9 @@ def test_autotune_keeps_state_and_results(cuda_device):
             assert all(np.array_equal(x, y) for x, y in zip(b, a))
         for i, w in enumerate(t.ws):
             pb, bps, g, ix, ms = S.batch_schedule(t.batch, i)
-            assert pb in (16, 32, 64) and bps in (0, 4) and g in (1, 2) and ix in (1, 2) and ms > 0, (i, pb, bps, g, ms)
+            R = w.params["rays"]
+            assert pb in (16, 32, 64) + ((R,) if R > 64 else ()), (i, pb, R)  # or a warp per probe
+            assert bps in (0, 4) and g in (1, 2) and ix in (1, 2) and ms > 0, (i, pb, bps, g, ms)
             assert g == 2 or w.params["rays"] % 16 == 0
         # the tuned schedule differs from the default one at most in the gather's rounding
         for frame in (1, 2):
