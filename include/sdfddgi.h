@@ -458,9 +458,9 @@ SDFDDGI_API int sdfddgi_batch_schedule(const sdfddgi_batch* b, int32_t i, int32_
  * frames in both forms after choosing the volumes' schedules), branches before tuning.
  * MERGED needs volumes that share the hit threshold, the step budget, the relaxation of
  * their traces, the depth exponent and the gather precision, a voxel SDF, and the
- * tensor-core gather for every volume (rays per probe a multiple of 16); its pools take the
- * first volume's pool batch, CTAs per SM and index arithmetic, and a bounds failure in a
- * merged trace is reported by the first volume's status. */
+ * tensor-core gather for every volume (rays per probe a multiple of 16); its pools span every
+ * volume and take the default launch shapes (not the volumes' tuned schedules), and a bounds
+ * failure in a merged trace is reported by the first volume's status. */
 #define SDFDDGI_BATCH_FORM_AUTO 0
 #define SDFDDGI_BATCH_FORM_BRANCHES 1
 #define SDFDDGI_BATCH_FORM_MERGED 2

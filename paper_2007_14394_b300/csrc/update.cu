@@ -232,9 +232,8 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
     }
 }
 
-__host__ __device__ __forceinline__ int pool_batch_host(int asked, int fallback) { return asked > 0 ? asked : fallback; }
 __device__ __forceinline__ uint32_t pool_batch(const UpdateParams& P, int fallback = kBatch) {
-    return (uint32_t)pool_batch_host(P.sched.pool_batch, fallback);
+    return P.sched.pool_batch > 0 ? (uint32_t)P.sched.pool_batch : (uint32_t)fallback;
 }
 
 #ifndef SDFDDGI_REFILL_DEFAULT
@@ -1162,16 +1161,18 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
 
 template <typename T>
 static cudaError_t launch_merged_stages(const MergedParams& m, const DeviceSetup& setup, cudaStream_t stream) {
+    // the merged pools span every volume, so they take the default shapes rather than one
+    // volume's tuned schedule: the occupancy limit of CTAs and the index form by the store's size
     const UpdateParams& p0 = m.p[0];
     const int rp = p0.omega_primary > 1.f ? 1 : 0, rs = p0.omega_shadow > 1.f ? 1 : 0;
-    size_t store = p0.vol.n_quads * (p0.vol.dtype == SDFDDGI_F16 ? 8 : 16);
-    const bool i64 = p0.sched.index == 2 || (p0.sched.index == 0 && store > ((size_t)512 << 20));
+    const size_t store = p0.vol.n_quads * (p0.vol.dtype == SDFDDGI_F16 ? 8 : 16);
+    const bool i64 = store > ((size_t)512 << 20);
     cudaError_t e = cudaSuccess;
     if (p0.depth_exp == 50)
         weights_merged_kernel<50><<<m.dir_begin[m.n], kThreads, 0, stream>>>(m);
     else
         weights_merged_kernel<0><<<m.dir_begin[m.n], kThreads, 0, stream>>>(m);
-    const int gp = persistent_blocks(setup, setup.occ_primary_merged[rp][type_slot<T>()], p0.sched.blocks_per_sm);
+    const int gp = persistent_blocks(setup, setup.occ_primary_merged[rp][type_slot<T>()], 0);
     if (rp)
         i64 ? primary_merged_kernel<T, true, true><<<gp, kTraceThreads, 0, stream>>>(m)
             : primary_merged_kernel<T, true, false><<<gp, kTraceThreads, 0, stream>>>(m);
@@ -1179,7 +1180,7 @@ static cudaError_t launch_merged_stages(const MergedParams& m, const DeviceSetup
         i64 ? primary_merged_kernel<T, false, true><<<gp, kTraceThreads, 0, stream>>>(m)
             : primary_merged_kernel<T, false, false><<<gp, kTraceThreads, 0, stream>>>(m);
     prep_merged_kernel<T><<<m.prep_begin[m.n], kThreads, 0, stream>>>(m);
-    const int gs = persistent_blocks(setup, setup.occ_shadow_merged[rs][type_slot<T>()], p0.sched.blocks_per_sm);
+    const int gs = persistent_blocks(setup, setup.occ_shadow_merged[rs][type_slot<T>()], 0);
     if (rs)
         i64 ? shadow_merged_kernel<T, true, true><<<gs, kTraceThreads, 0, stream>>>(m)
             : shadow_merged_kernel<T, true, false><<<gs, kTraceThreads, 0, stream>>>(m);
@@ -1201,8 +1202,8 @@ cudaError_t launch_merged(const UpdateParams* p, int n, MergedParams* m, cudaStr
     if (e != cudaSuccess) return e;
     std::memset(m, 0, sizeof *m);
     m->n = n;
-    m->primary_batch = (uint32_t)pool_batch_host(p[0].sched.pool_batch, kBatch);
-    m->shadow_batch = (uint32_t)pool_batch_host(p[0].sched.pool_batch, kShadowBatch);
+    m->primary_batch = (uint32_t)kBatch;
+    m->shadow_batch = (uint32_t)kShadowBatch;
     uint64_t rb = 0, pb = 0, gb = 0, db = 0;
     for (int v = 0; v < n; ++v) {
         m->p[v] = prepared_params(p[v]);
