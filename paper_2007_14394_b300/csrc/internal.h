@@ -114,9 +114,9 @@ struct UpdateParams {
     // per-ray scratch of the staged update, index k = probe * R + ray
     float* ray_t;             // hit distance (t_max for misses)
     uint32_t* ray_es;         // event | steps << 8
-    float4* ray_n;            // a hit with shadow tasks: its gated-light mask and first task (bits of x, y)
-    float4* ray_alb;          // albedo
-    float4* ray_base;         // emission + k * albedo * last-frame irradiance
+    float4* ray_n;            // (records only) a hit with shadow tasks: its material owner (bits of x)
+    float4* ray_alb;          // per finalize-list entry: albedo rgb, gated-light mask (bits of w)
+    float4* ray_base;         // per finalize-list entry: emission + k * albedo * last-frame irradiance, first task (bits of w)
     uint32_t* ray_lit;        // visible-light mask
     uint32_t* ray_ssteps;     // shadow steps
     float4* tasks;            // shadow tasks: origin xyz, bits of (k << 5 | light)

@@ -350,7 +350,8 @@ __global__ void __launch_bounds__(kTraceThreads, 32) primary_kernel(const __grid
 }
 
 // The ray's record, when records were asked for.
-__device__ __forceinline__ void write_record(const UpdateParams& P, uint32_t k, uint32_t es, float4 v, uint32_t lit) {
+__device__ __forceinline__ void write_record(const UpdateParams& P, uint32_t k, uint32_t es, float4 v, uint32_t lit,
+                                             uint32_t owner) {
     const int ev = (int)(es & 0xffu);
     sdfddgi_ray_record rec = {};
     rec.event = (uint8_t)ev;
@@ -362,7 +363,7 @@ __device__ __forceinline__ void write_record(const UpdateParams& P, uint32_t k, 
         rec.lit_mask = lit;
         rec.shadow_steps = is_miss(ev) ? 0u : P.ray_ssteps[k];
         rec.steps = (uint16_t)(es >> 8);
-        rec.material_owner = is_miss(ev) ? 0u : __float_as_uint(P.ray_alb[k].w);
+        rec.material_owner = is_miss(ev) ? 0u : owner;
     }
     P.records[k] = rec;
 }
@@ -409,7 +410,7 @@ __device__ __forceinline__ void prep_body(const UpdateParams& P, uint32_t block,
                 const float4 v = ev == kNoRay ? make_float4(0.f, 0.f, 0.f, 0.f)
                                               : make_float4(P.sky[0], P.sky[1], P.sky[2], P.tmax_w);
                 P.ray_val[k] = v;
-                if (P.records) write_record(P, k, es, v, 0u);
+                if (P.records) write_record(P, k, es, v, 0u, 0u);
             }
         }
         const unsigned want = __ballot_sync(0xffffffffu, shade);
@@ -425,6 +426,7 @@ __device__ __forceinline__ void prep_body(const UpdateParams& P, uint32_t block,
         const int j = j0 + threadIdx.x;
         uint32_t gate = 0, k = 0;
         float3 x = f3(0.f, 0.f, 0.f), nr = f3(0.f, 0.f, 0.f);  // the hit and its normal
+        float4 alb = make_float4(0.f, 0.f, 0.f, 0.f), b = alb;    // albedo + owner bits, base
         if (j < n_shade) {
             k = s_rays[j];
             P.ray_lit[k] = 0;
@@ -464,17 +466,14 @@ __device__ __forceinline__ void prep_body(const UpdateParams& P, uint32_t block,
                 light_scale(P.lights[l], x, nr, &g);
                 if (g) gate |= 1u << l;
             }
-            const float4 alb = make_float4(albedo.x, albedo.y, albedo.z, __uint_as_float(owner));
-            const float4 b = make_float4(emission.x + albedo.x * P.k_bounce * ind.x,
-                                         emission.y + albedo.y * P.k_bounce * ind.y,
-                                         emission.z + albedo.z * P.k_bounce * ind.z, 0.f);
-            P.ray_alb[k] = alb;
-            P.ray_base[k] = b;
+            alb = make_float4(albedo.x, albedo.y, albedo.z, __uint_as_float(owner));
+            b = make_float4(emission.x + albedo.x * P.k_bounce * ind.x, emission.y + albedo.y * P.k_bounce * ind.y,
+                            emission.z + albedo.z * P.k_bounce * ind.z, 0.f);
             if (!gate) {  // no light can reach the hit: its value (the finalize rule's with no light) is final
                 const float4 v = make_float4(fmaf(alb.x * inv_pi, 0.f, b.x), fmaf(alb.y * inv_pi, 0.f, b.y),
                                              fmaf(alb.z * inv_pi, 0.f, b.z), fminf(t, P.tmax_w));
                 P.ray_val[k] = v;
-                if (P.records) write_record(P, k, P.ray_es[k], v, 0u);
+                if (P.records) write_record(P, k, P.ray_es[k], v, 0u, owner);
             }
         }
         // append this warp's (ray, light) pairs to the task list with one atomic, and its rays
@@ -502,9 +501,12 @@ __device__ __forceinline__ void prep_body(const UpdateParams& P, uint32_t block,
             gate = 0;  // no task: the ray is finalized with no light (the update is flagged invalid)
             pos = 0;
         }
-        if (fin & (1u << lane)) {
-            P.fin_list[checked(fbase + (uint32_t)__popc(fin & ((1u << lane) - 1u)), n, P.vol.fail)] = k;
-            P.ray_n[k] = make_float4(__uint_as_float(gate), __uint_as_float(pos), 0.f, 0.f);  // for finalize
+        if (fin & (1u << lane)) {  // the finalize list's entry: the ray, and its shading in list order
+            const uint32_t f = checked(fbase + (uint32_t)__popc(fin & ((1u << lane) - 1u)), n, P.vol.fail);
+            P.fin_list[f] = k;
+            P.ray_alb[f] = make_float4(alb.x, alb.y, alb.z, __uint_as_float(gate));
+            P.ray_base[f] = make_float4(b.x, b.y, b.z, __uint_as_float(pos));
+            if (P.records) P.ray_n[k] = make_float4(alb.w, 0.f, 0.f, 0.f);  // the owner, for the record
         }
         const float3 so = fma3(P.bias_w, nr, x);  // the shadow rays' origin: the hit lifted off the surface
         while (gate) {
@@ -762,8 +764,8 @@ __device__ __forceinline__ void finalize_body(const UpdateParams& P) {
     const float inv_pi = 0.318309886183790671538f;
     for (uint32_t j = blockIdx.x * kThreads + threadIdx.x; j < count; j += gridDim.x * kThreads) {
         const uint32_t k = checked(P.fin_list[j], n, P.vol.fail);
-        const float4 gp = P.ray_n[k];
-        uint32_t gate = __float_as_uint(gp.x), pos = __float_as_uint(gp.y);
+        const float4 a = P.ray_alb[j], b = P.ray_base[j];  // in list order: albedo + gate mask, base + first task
+        uint32_t gate = __float_as_uint(a.w), pos = __float_as_uint(b.w);
         const uint32_t lit = P.ray_lit[k];
         float3 direct = f3(0.f, 0.f, 0.f);
         while (gate) {
@@ -775,11 +777,11 @@ __device__ __forceinline__ void finalize_body(const UpdateParams& P) {
             }
             ++pos;
         }
-        const float4 a = P.ray_alb[k], b = P.ray_base[k];
+        const uint32_t owner = P.records ? __float_as_uint(P.ray_n[k].x) : 0u;  // read before ray_val overwrites it
         const float4 v = make_float4(fmaf(a.x * inv_pi, direct.x, b.x), fmaf(a.y * inv_pi, direct.y, b.y),
                                      fmaf(a.z * inv_pi, direct.z, b.z), fminf(P.ray_t[k], P.tmax_w));
         P.ray_val[k] = v;
-        if (P.records) write_record(P, k, P.ray_es[k], v, lit);
+        if (P.records) write_record(P, k, P.ray_es[k], v, lit, owner);
     }
 }
 
