@@ -117,9 +117,9 @@ struct UpdateParams {
     float4* ray_n;            // (records only) a hit with shadow tasks: its material owner (bits of x)
     float4* ray_alb;          // per finalize-list entry: albedo rgb, gated-light mask (bits of w)
     float4* ray_base;         // per finalize-list entry: emission + k * albedo * last-frame irradiance, first task (bits of w)
-    uint32_t* ray_lit;        // visible-light mask
-    uint32_t* ray_ssteps;     // shadow steps
-    float4* tasks;            // shadow tasks: origin xyz, bits of (k << 5 | light)
+    uint32_t* ray_lit;        // per finalize-list entry: visible-light mask
+    uint32_t* ray_ssteps;     // per finalize-list entry: shadow steps (kept only when records are asked for)
+    float4* tasks;            // shadow tasks: origin xyz, bits of (finalize-list entry << 5 | light)
     float* task_scale;        // [task_capacity] each task's light factor at its hit (light_scale)
     uint32_t task_capacity;
     uint32_t* fin_list;       // [P*R] the hits with shadow tasks, for the finalize stage

@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kTraceThreads, 32) primary_kernel(const __grid
 
 // The ray's record, when records were asked for.
 __device__ __forceinline__ void write_record(const UpdateParams& P, uint32_t k, uint32_t es, float4 v, uint32_t lit,
-                                             uint32_t owner) {
+                                             uint32_t owner, uint32_t shadow_steps) {
     const int ev = (int)(es & 0xffu);
     sdfddgi_ray_record rec = {};
     rec.event = (uint8_t)ev;
@@ -361,7 +361,7 @@ __device__ __forceinline__ void write_record(const UpdateParams& P, uint32_t k, 
         rec.L[1] = v.y;
         rec.L[2] = v.z;
         rec.lit_mask = lit;
-        rec.shadow_steps = is_miss(ev) ? 0u : P.ray_ssteps[k];
+        rec.shadow_steps = is_miss(ev) ? 0u : shadow_steps;
         rec.steps = (uint16_t)(es >> 8);
         rec.material_owner = is_miss(ev) ? 0u : owner;
     }
@@ -410,7 +410,7 @@ __device__ __forceinline__ void prep_body(const UpdateParams& P, uint32_t block,
                 const float4 v = ev == kNoRay ? make_float4(0.f, 0.f, 0.f, 0.f)
                                               : make_float4(P.sky[0], P.sky[1], P.sky[2], P.tmax_w);
                 P.ray_val[k] = v;
-                if (P.records) write_record(P, k, es, v, 0u, 0u);
+                if (P.records) write_record(P, k, es, v, 0u, 0u, 0u);
             }
         }
         const unsigned want = __ballot_sync(0xffffffffu, shade);
@@ -429,8 +429,6 @@ __device__ __forceinline__ void prep_body(const UpdateParams& P, uint32_t block,
         float4 alb = make_float4(0.f, 0.f, 0.f, 0.f), b = alb;    // albedo + owner bits, base
         if (j < n_shade) {
             k = s_rays[j];
-            P.ray_lit[k] = 0;
-            P.ray_ssteps[k] = 0;
             const VolumeView& V = P.vol;
             const int p = (int)(k / (uint32_t)P.R), i = (int)(k % (uint32_t)P.R);
             uint32_t flags;
@@ -473,7 +471,7 @@ __device__ __forceinline__ void prep_body(const UpdateParams& P, uint32_t block,
                 const float4 v = make_float4(fmaf(alb.x * inv_pi, 0.f, b.x), fmaf(alb.y * inv_pi, 0.f, b.y),
                                              fmaf(alb.z * inv_pi, 0.f, b.z), fminf(t, P.tmax_w));
                 P.ray_val[k] = v;
-                if (P.records) write_record(P, k, P.ray_es[k], v, 0u, owner);
+                if (P.records) write_record(P, k, P.ray_es[k], v, 0u, owner, 0u);
             }
         }
         // append this warp's (ray, light) pairs to the task list with one atomic, and its rays
@@ -501,12 +499,18 @@ __device__ __forceinline__ void prep_body(const UpdateParams& P, uint32_t block,
             gate = 0;  // no task: the ray is finalized with no light (the update is flagged invalid)
             pos = 0;
         }
+        uint32_t entry = 0;  // the ray's finalize-list position, which its shadow tasks carry
         if (fin & (1u << lane)) {  // the finalize list's entry: the ray, and its shading in list order
             const uint32_t f = checked(fbase + (uint32_t)__popc(fin & ((1u << lane) - 1u)), n, P.vol.fail);
             P.fin_list[f] = k;
             P.ray_alb[f] = make_float4(alb.x, alb.y, alb.z, __uint_as_float(gate));
             P.ray_base[f] = make_float4(b.x, b.y, b.z, __uint_as_float(pos));
-            if (P.records) P.ray_n[k] = make_float4(alb.w, 0.f, 0.f, 0.f);  // the owner, for the record
+            P.ray_lit[f] = 0;  // the shadow traces set the visible lights' bits
+            if (P.records) {
+                P.ray_ssteps[f] = 0;
+                P.ray_n[k] = make_float4(alb.w, 0.f, 0.f, 0.f);  // the owner, for the record
+            }
+            entry = f;
         }
         const float3 so = fma3(P.bias_w, nr, x);  // the shadow rays' origin: the hit lifted off the surface
         while (gate) {
@@ -514,7 +518,7 @@ __device__ __forceinline__ void prep_body(const UpdateParams& P, uint32_t block,
             gate &= gate - 1;
             bool g;
             P.task_scale[pos] = light_scale(P.lights[l], x, nr, &g);  // the factor the gating saw
-            P.tasks[pos++] = make_float4(so.x, so.y, so.z, __uint_as_float((k << 5) | (uint32_t)l));
+            P.tasks[pos++] = make_float4(so.x, so.y, so.z, __uint_as_float((entry << 5) | (uint32_t)l));
         }
     }
 }
@@ -552,9 +556,9 @@ __global__ void __launch_bounds__(kTraceThreads, 32) shadow_kernel(const __grid_
             return true;
         },
         [&](const TraceState& st, int ev, int steps, float) {
-            const uint32_t k = checked(st.aux >> 5, (size_t)P.P * P.R, P.vol.fail);
-            atomicAdd(&P.ray_ssteps[k], (uint32_t)steps);
-            if (is_miss(ev)) atomicOr(&P.ray_lit[k], 1u << (st.aux & 31u));  // hit or exhausted: occluded
+            const uint32_t f = checked(st.aux >> 5, (size_t)P.P * P.R, P.vol.fail);  // the hit's finalize entry
+            if (P.records) atomicAdd(&P.ray_ssteps[f], (uint32_t)steps);
+            if (is_miss(ev)) atomicOr(&P.ray_lit[f], 1u << (st.aux & 31u));  // hit or exhausted: occluded
         });
 }
 
@@ -685,9 +689,9 @@ __global__ void __launch_bounds__(kTraceThreads, 32) shadow_merged_kernel(const 
             const UpdateParams& P = M.p[v];
             const uint32_t j = checked(st.aux - s_begin[v], P.task_capacity, P.vol.fail);
             const uint32_t tk = __float_as_uint(P.tasks[j].w);
-            const uint32_t k = checked(tk >> 5, (size_t)P.P * P.R, P.vol.fail);
-            atomicAdd(&P.ray_ssteps[k], (uint32_t)steps);
-            if (is_miss(ev)) atomicOr(&P.ray_lit[k], 1u << (tk & 31u));  // hit or exhausted: occluded
+            const uint32_t f = checked(tk >> 5, (size_t)P.P * P.R, P.vol.fail);  // the hit's finalize entry
+            if (P.records) atomicAdd(&P.ray_ssteps[f], (uint32_t)steps);
+            if (is_miss(ev)) atomicOr(&P.ray_lit[f], 1u << (tk & 31u));  // hit or exhausted: occluded
         });
 }
 
@@ -766,7 +770,7 @@ __device__ __forceinline__ void finalize_body(const UpdateParams& P) {
         const uint32_t k = checked(P.fin_list[j], n, P.vol.fail);
         const float4 a = P.ray_alb[j], b = P.ray_base[j];  // in list order: albedo + gate mask, base + first task
         uint32_t gate = __float_as_uint(a.w), pos = __float_as_uint(b.w);
-        const uint32_t lit = P.ray_lit[k];
+        const uint32_t lit = P.ray_lit[j];
         float3 direct = f3(0.f, 0.f, 0.f);
         while (gate) {
             const int l = __ffs(gate) - 1;
@@ -781,7 +785,7 @@ __device__ __forceinline__ void finalize_body(const UpdateParams& P) {
         const float4 v = make_float4(fmaf(a.x * inv_pi, direct.x, b.x), fmaf(a.y * inv_pi, direct.y, b.y),
                                      fmaf(a.z * inv_pi, direct.z, b.z), fminf(P.ray_t[k], P.tmax_w));
         P.ray_val[k] = v;
-        if (P.records) write_record(P, k, P.ray_es[k], v, lit, owner);
+        if (P.records) write_record(P, k, P.ray_es[k], v, lit, owner, P.ray_ssteps[j]);
     }
 }
 
