@@ -311,6 +311,17 @@ __device__ __forceinline__ int2 border_source(int y, int x, int n) {
     return make_int2(y, x);
 }
 
+// Texel (y, x) of border texel b (0 <= b < 4n + 4) of an (n+2)^2 map: the top row, the bottom
+// row, then the left and right columns between them. Every border texel's source
+// (border_source) is an interior texel, so the border copies are independent of one another.
+__device__ __forceinline__ int2 border_texel(int b, int n) {
+    const int w = n + 2;
+    if (b < w) return make_int2(0, b);
+    if (b < 2 * w) return make_int2(n + 1, b - w);
+    b -= 2 * w;
+    return b < n ? make_int2(b + 1, 0) : make_int2(b - n + 1, n + 1);
+}
+
 // ------------------------------------------------------------------ probe interpolation
 // Normalised irradiance at world point x for unit normal nrm from an irradiance atlas:
 // trilinear over the 8 probes of the grid cell (clamped), weighted by trilinear weight

@@ -390,19 +390,18 @@ __device__ __forceinline__ void gather_tc_body(const UpdateParams& P, int block)
 
     // ---- borders of active probes (an inactive probe's staged map is its old map), then
     // contiguous stores
-    for (int e = tid; e < ng * kIrrT * kIrrT; e += kThreads) {
-        const int g = e / (kIrrT * kIrrT), k = e % (kIrrT * kIrrT);
-        const int y = k / kIrrT, x = k % kIrrT;
-        const int2 sc = border_source(y, x, kIrrN);
-        if ((s_flags[g] & SDFDDGI_PROBE_ACTIVE) && (sc.x != y || sc.y != x))
-            s_irr[e] = s_irr[g * kIrrT * kIrrT + sc.x * kIrrT + sc.y];
+    constexpr int kIrrB = 4 * kIrrN + 4, kDepB = 4 * kDepN + 4;  // border texels per map
+    for (int e = tid; e < ng * kIrrB; e += kThreads) {
+        const int g = e / kIrrB;
+        const int2 t = border_texel(e % kIrrB, kIrrN), sc = border_source(t.x, t.y, kIrrN);
+        if (s_flags[g] & SDFDDGI_PROBE_ACTIVE)
+            s_irr[g * kIrrT * kIrrT + t.x * kIrrT + t.y] = s_irr[g * kIrrT * kIrrT + sc.x * kIrrT + sc.y];
     }
-    for (int e = tid; e < ng * kDepT * kDepT; e += kThreads) {
-        const int g = e / (kDepT * kDepT), k = e % (kDepT * kDepT);
-        const int y = k / kDepT, x = k % kDepT;
-        const int2 sc = border_source(y, x, kDepN);
-        if ((s_flags[g] & SDFDDGI_PROBE_ACTIVE) && (sc.x != y || sc.y != x))
-            s_dep[e] = s_dep[g * kDepT * kDepT + sc.x * kDepT + sc.y];
+    for (int e = tid; e < ng * kDepB; e += kThreads) {
+        const int g = e / kDepB;
+        const int2 t = border_texel(e % kDepB, kDepN), sc = border_source(t.x, t.y, kDepN);
+        if (s_flags[g] & SDFDDGI_PROBE_ACTIVE)
+            s_dep[g * kDepT * kDepT + t.x * kDepT + t.y] = s_dep[g * kDepT * kDepT + sc.x * kDepT + sc.y];
     }
     __syncthreads();
     float4* cur_i = P.cur_irr + (size_t)p0 * (kIrrT * kIrrT);
