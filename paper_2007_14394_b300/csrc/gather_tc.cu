@@ -166,12 +166,6 @@ __device__ __forceinline__ void gather_tc_body(const UpdateParams& P, int block)
         mbar_init(&bar_prev, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (tid < kG) {
-        uint32_t flags = 0;
-        if (tid < ng) flags = P.states ? P.states[p0 + tid].flags : (uint32_t)SDFDDGI_PROBE_ACTIVE;
-        s_flags[tid] = flags;
-        s_hyst[tid] = (tid < ng && P.prev_valid[p0 + tid] && !(flags & SDFDDGI_PROBE_REJECT_HISTORY)) ? P.hyst : 0.f;
-    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -279,6 +273,13 @@ __device__ __forceinline__ void gather_tc_body(const UpdateParams& P, int block)
         const uint32_t no_abort = 0;
         for (int s = 0; s < kStages; ++s)
             if (last[s] >= 0) mbar_wait(&bar_full_a[s], (last[s] / kStages) & 1, &no_abort);
+    } else if (warp == 6 && lane < kG) {
+        // the probes' flags and history weights, which only the epilogue reads: fetched here,
+        // beside the K loop, rather than ahead of it
+        uint32_t flags = 0;
+        if (lane < ng) flags = P.states ? P.states[p0 + lane].flags : (uint32_t)SDFDDGI_PROBE_ACTIVE;
+        s_flags[lane] = flags;
+        s_hyst[lane] = (lane < ng && P.prev_valid[p0 + lane] && !(flags & SDFDDGI_PROBE_REJECT_HISTORY)) ? P.hyst : 0.f;
     } else if (warp == 5 && lane == 0) {
         int committed = 0;  // chunks whose MMAs were committed
         for (int c = 0; c < n_chunks && !s_fail; ++c) {
