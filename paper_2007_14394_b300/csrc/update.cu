@@ -56,7 +56,22 @@ struct TraceState {
     float omega;   //   and the relaxation factor (1: plain sphere tracing)
     int s;
     uint32_t aux;  // task payload kept for the completion handler
+    float tstop;   // plain voxel-volume traces: min(tlimit, the distance at which the ray leaves the box)
 };
+
+// Voxel coordinate o lies in the volume box [-1/2, n - 1/2] (the negated test puts NaN outside).
+__device__ __forceinline__ bool in_box(const VolumeView& v, float3 o) {
+    return o.x >= -0.5f && o.x <= v.gmax[0] && o.y >= -0.5f && o.y <= v.gmax[1] && o.z >= -0.5f && o.z <= v.gmax[2];
+}
+
+// The distance along unit direction d (voxel units) at which a ray from o, inside the volume
+// box, reaches the face it moves toward; a zero component never reaches its faces.
+__device__ __forceinline__ float box_exit(const VolumeView& v, float3 o, float3 d) {
+    const float tx = d.x != 0.f ? ((d.x > 0.f ? v.gmax[0] : -0.5f) - o.x) / d.x : INFINITY;
+    const float ty = d.y != 0.f ? ((d.y > 0.f ? v.gmax[1] : -0.5f) - o.y) / d.y : INFINITY;
+    const float tz = d.z != 0.f ? ((d.z > 0.f ? v.gmax[2] : -0.5f) - o.z) / d.z : INFINITY;
+    return fminf(tx, fminf(ty, tz));
+}
 
 // The SDF at p on a sphere trace. For a scene of primitives the query starts from the last
 // distance plus the distance moved since (the field is 1-Lipschitz; a plain step moved by the
@@ -89,6 +104,36 @@ template <typename T, bool Relax, bool Idx64>
 __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, float eps, int max_steps,
                                           int* steps, float* t_end) {
     constexpr bool kVox = !std::is_same<T, Analytic>::value;
+    if constexpr (kVox && !Relax) {
+        // A plain voxel-volume trace tests the box once per ray: it started inside, and it
+        // leaves where t passes the exit distance, folded with the limit into tstop. The events
+        // keep their order (past the limit, then the budget, then leaving the box), and the
+        // negated test ends a trace whose t is not a number.
+        const float sd = sample_sdf_vox<T, Idx64>(v, fma3(st.t, st.d, st.o));
+        if (sd < eps) {
+            *steps = st.s + 1;
+            *t_end = st.t;
+            return kHit;
+        }
+        st.t = fmaf(sd, v.inv_h, st.t);
+        const int s1 = ++st.s;
+        if (!(st.t <= st.tstop)) {
+            if (st.t > st.tlimit) {
+                *steps = s1;
+                *t_end = st.tlimit;
+                return kPastLimit;
+            }
+            *steps = s1;
+            *t_end = s1 == max_steps ? st.t : st.tlimit;
+            return s1 == max_steps ? kExhausted : kLeftVolume;
+        }
+        if (s1 == max_steps) {
+            *steps = max_steps;
+            *t_end = st.t;
+            return kExhausted;
+        }
+        return -1;
+    }
     const float3 p = fma3(st.t, st.d, st.o);  // voxel coordinate (volumes) or world point (primitives)
     // outside the box, or not a number (the negated test sends NaN out of the volume too)
     const bool outside =
@@ -207,6 +252,15 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
                     st.step = 0.f;
                     st.omega = omega;
                     busy = true;
+                    if constexpr (!std::is_same<T, Analytic>::value && !Relax) {
+                        if (in_box(v, st.o)) {
+                            st.tstop = fminf(st.tlimit, box_exit(v, st.o, st.d));
+                        } else {  // outside the volume from the start: it leaves before any sample
+                            done(st, kLeftVolume, 0, st.tlimit * v.h);
+                            busy = false;
+                            need = true;
+                        }
+                    }
                 } else {
                     need = true;  // nothing to trace for this task: take another
                 }
