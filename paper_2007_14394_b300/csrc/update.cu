@@ -65,11 +65,14 @@ __device__ __forceinline__ bool in_box(const VolumeView& v, float3 o) {
 }
 
 // The distance along unit direction d (voxel units) at which a ray from o, inside the volume
-// box, reaches the face it moves toward; a zero component never reaches its faces.
+// box, reaches the face it moves toward; a zero component never reaches its faces. The fast
+// quotient (within 2 ulp) moves the distance by rounding only: it decides only when the ray
+// leaves the box, and a sample taken up to that distance stays well inside the store's
+// half-voxel apron.
 __device__ __forceinline__ float box_exit(const VolumeView& v, float3 o, float3 d) {
-    const float tx = d.x != 0.f ? ((d.x > 0.f ? v.gmax[0] : -0.5f) - o.x) / d.x : INFINITY;
-    const float ty = d.y != 0.f ? ((d.y > 0.f ? v.gmax[1] : -0.5f) - o.y) / d.y : INFINITY;
-    const float tz = d.z != 0.f ? ((d.z > 0.f ? v.gmax[2] : -0.5f) - o.z) / d.z : INFINITY;
+    const float tx = d.x != 0.f ? __fdividef((d.x > 0.f ? v.gmax[0] : -0.5f) - o.x, d.x) : INFINITY;
+    const float ty = d.y != 0.f ? __fdividef((d.y > 0.f ? v.gmax[1] : -0.5f) - o.y, d.y) : INFINITY;
+    const float tz = d.z != 0.f ? __fdividef((d.z > 0.f ? v.gmax[2] : -0.5f) - o.z, d.z) : INFINITY;
     return fminf(tx, fminf(ty, tz));
 }
 
