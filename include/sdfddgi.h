@@ -449,7 +449,7 @@ SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* 
 /* Volume i's schedule: out[0] pool batch (tasks per warp claim; 0 = the default), out[1] CTAs
  * per SM (0 = occupancy limit),
  * out[2] gather (0 automatic, 1 tensor cores, 2 SIMT), out[3] the traces' SDF-index
- * arithmetic (0 automatic: 64-bit above a 512 MiB SDF copy; 1 a 32-bit row, 2 64-bit; the
+ * arithmetic (0 automatic: the 32-bit row; 1 a 32-bit row, 2 64-bit; the
  * same addresses, a speed choice); tuned_ms (nullable) receives the autotuner's mean update
  * time of that schedule (0 before tuning). */
 SDFDDGI_API int sdfddgi_batch_schedule(const sdfddgi_batch* b, int32_t i, int32_t out[4], float* tuned_ms);

@@ -68,7 +68,7 @@ struct Schedule {
     int blocks_per_sm;   // resident CTAs per SM of the persistent trace kernels (default: occupancy limit)
     int gather;          // 0 automatic (tensor cores when R % 16 == 0), 1 tensor cores, 2 SIMT
     int slabs;           // z-slabs of probes run as concurrent branches: 0 automatic, 1 (serial) .. kMaxSlabs
-    int index;           // the traces' quad-index arithmetic: 0 automatic (64-bit above a 512 MiB store),
+    int index;           // the traces' quad-index arithmetic: 0 automatic (the 32-bit row form),
                          // 1 a 32-bit z-pair row, 2 all in 64 bits (the same addresses either way)
     int refill;          // idle lanes of a trace warp before it hands out new tasks: 0 default, 1..32
 };

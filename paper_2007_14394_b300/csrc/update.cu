@@ -1081,9 +1081,9 @@ static cudaError_t launch_stage(const UpdateParams& p, const DeviceSetup& setup,
     const int rp = p.omega_primary > 1.f ? 1 : 0, rs = p.omega_shadow > 1.f ? 1 : 0;
     const uint32_t n = (uint32_t)p.P * (uint32_t)p.R;
     cudaError_t e = cudaSuccess;
-    // the quad-index arithmetic of the traces (same addresses): the 64-bit form above a 512 MiB store
-    const size_t store = p.vol.n_quads * (p.vol.dtype == SDFDDGI_F16 ? 8 : 16);
-    const bool i64 = p.sched.index == 2 || (p.sched.index == 0 && store > ((size_t)512 << 20));
+    // the quad-index arithmetic of the traces (same addresses): the 32-bit row form unless the
+    // schedule asks for the 64-bit one (the batch autotuner tries both)
+    const bool i64 = p.sched.index == 2;
     if (s == 0) {
         const int g = persistent_blocks(setup, setup.occ_primary[rp][type_slot<T>()], p.sched.blocks_per_sm);
         if (rp)
@@ -1225,11 +1225,10 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
 template <typename T>
 static cudaError_t launch_merged_stages(const MergedParams& m, const DeviceSetup& setup, cudaStream_t stream) {
     // the merged pools span every volume, so they take the default shapes rather than one
-    // volume's tuned schedule: the occupancy limit of CTAs and the index form by the store's size
+    // volume's tuned schedule: the occupancy limit of CTAs and the 32-bit index form
     const UpdateParams& p0 = m.p[0];
     const int rp = p0.omega_primary > 1.f ? 1 : 0, rs = p0.omega_shadow > 1.f ? 1 : 0;
-    const size_t store = p0.vol.n_quads * (p0.vol.dtype == SDFDDGI_F16 ? 8 : 16);
-    const bool i64 = store > ((size_t)512 << 20);
+    constexpr bool i64 = false;
     cudaError_t e = cudaSuccess;
     if (p0.depth_exp == 50)
         weights_merged_kernel<50><<<m.dir_begin[m.n], kThreads, 0, stream>>>(m);
