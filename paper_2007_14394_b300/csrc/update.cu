@@ -498,7 +498,9 @@ __device__ __forceinline__ void prep_body(const UpdateParams& P, uint32_t block,
             const float gy = sample_sdf<T>(V, f3(x.x, x.y + hh, x.z)) - sample_sdf<T>(V, f3(x.x, x.y - hh, x.z));
             const float gz = sample_sdf<T>(V, f3(x.x, x.y, x.z + hh)) - sample_sdf<T>(V, f3(x.x, x.y, x.z - hh));
             const float glen = sqrtf(gx * gx + gy * gy + gz * gz);
-            nr = glen > 0.f ? f3(gx / glen, gy / glen, gz / glen) : f3(-d.x, -d.y, -d.z);
+            // a gradient that is zero or not finite (an SDF holding infinities or NaN near the
+            // hit) gives no normal: the reversed ray direction stands in
+            nr = glen > 0.f && glen < INFINITY ? f3(gx / glen, gy / glen, gz / glen) : f3(-d.x, -d.y, -d.z);
             float3 albedo, emission;
             uint32_t owner = 0;  // scenes of primitives: the caller's index + 1 of the material's primitive
             if constexpr (std::is_same<T, Analytic>::value) {
