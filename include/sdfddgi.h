@@ -187,6 +187,10 @@ SDFDDGI_API void sdfddgi_destroy_scene(sdfddgi_scene* s);
  * material: NULL (albedo 0, emission 0) or [z][y][x][8] binary16 values
  * (albedo r,g,b, unused, emission r,g,b, unused), sampled trilinearly.
  * is_device_ptr: 1 if sdf/material are device pointers, 0 for host memory.
+ * Distances are not checked for being finite. An update stays inside its buffers
+ * regardless: a trace meeting NaN ends as leaving the volume, +inf passes the limit,
+ * -inf is a hit, and a hit whose gradient is not finite takes the reversed ray direction
+ * as its normal.
  * Synchronous with respect to the host for host inputs. */
 SDFDDGI_API int sdfddgi_upload_sdf(sdfddgi_scene* s, const void* sdf, const int32_t dims[3], float voxel_size,
                                    const float origin[3], int32_t dtype, const void* material,
