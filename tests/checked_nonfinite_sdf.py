@@ -5,7 +5,8 @@ buffers when they occur. In the sphere traces a NaN distance makes t NaN, and th
 stop test (not t <= the stop distance) ends the trace as leaving the volume instead of
 sampling at a NaN point. A +inf distance passes the limit. A -inf distance is a hit. A hit
 whose gradient is not finite takes the reversed ray direction as its normal. The test runs
-in the bounds-checked build (tests/test_checked_build.py starts it with SDFDDGI_CHECKED=1),
+in the bounds-checked build (tests/test_checked_build.py names this file, which pytest does not
+collect by itself, and starts it with SDFDDGI_CHECKED=1),
 where an index outside its buffer is recorded and skipped rather than used, so a mistake
 here shows as SDFDDGI_ERR_BOUNDS, never as a memory fault.
 """

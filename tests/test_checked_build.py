@@ -36,7 +36,7 @@ def test_checked_build_is_clean_on_parity_workloads(cuda_device):
            "test_update_with_relocated_probes or test_batch_equals_plain_updates or "
            "test_nonfinite_sdf_values_stay_in_bounds")
     cmd = [sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "-m", "gpu", "-k", sel,
-           "tests/test_gpu_parity.py", "tests/test_relocation.py", "tests/test_batch.py", "tests/test_nonfinite_sdf.py"]
+           "tests/test_gpu_parity.py", "tests/test_relocation.py", "tests/test_batch.py", "tests/checked_nonfinite_sdf.py"]
     run = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=1200)
     tail = run.stdout[-3000:] + run.stderr[-2000:]
     assert run.returncode == 0, tail
