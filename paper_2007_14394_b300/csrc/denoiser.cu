@@ -394,7 +394,7 @@ int run_denoise(sdfddgi_denoiser* d, const MapsView& m, float4* out, int mode, c
     cudaError_t e = prepare(d, mode, st);
     if (e == cudaSuccess) {
         if (mode == SDFDDGI_DENOISE_TENSOR)
-            e = tc_forward(d->tc, m, d->depth_scale, d->use, out, st);
+            e = tc_forward(d->tc, m, d->depth_scale, d->use, d->X0, out, st);  // X0 holds P * 64 * 140 bytes
         else
             e = forward_simt(d, m, mode == SDFDDGI_DENOISE_SIMT_BF16, nullptr, out, nullptr, st);
     }
@@ -513,6 +513,9 @@ SDFDDGI_API int sdfddgi_denoise_volume(sdfddgi_denoiser* d, sdfddgi_volume* v, c
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((rc = ensure_ws(d, m.P))) return rc;
+    // the tensor-core path reads its neighbours from the feature texels it makes first, so it
+    // writes the volume's map in place; the CUDA-core path writes a copy
+    if (mode == SDFDDGI_DENOISE_TENSOR) return run_denoise(d, m, reinterpret_cast<float4*>(v->irr[v->cur]), mode, st);
     if ((rc = run_denoise(d, m, d->out, mode, st))) return rc;
     cudaError_t e = cudaMemcpyAsync(v->irr[v->cur], d->out, (size_t)m.P * kTex * sizeof(float4),
                                     cudaMemcpyDeviceToDevice, st);

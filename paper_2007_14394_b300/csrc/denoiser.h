@@ -83,7 +83,8 @@ cudaError_t tc_create(TcState& s);
 void tc_destroy(TcState& s);
 // builds the weight images from the kernels' weight copy `use` (bf16-rounded weights, biases)
 cudaError_t tc_prepare(TcState& s, const float* use, cudaStream_t st);
-cudaError_t tc_forward(TcState& s, const MapsView& m, float depth_scale, const float* use, float4* out,
+// feat: work space of P * 64 * 16 bytes for the feature texels; out may be m.irr (in place)
+cudaError_t tc_forward(TcState& s, const MapsView& m, float depth_scale, const float* use, void* feat, float4* out,
                        cudaStream_t st);
 
 }  // namespace dn
