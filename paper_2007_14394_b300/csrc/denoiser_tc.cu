@@ -12,10 +12,12 @@
 // into the border rows that mirror it (the octahedral fixup), the next layer's padding.
 // Every MMA reads its whole 4 KiB A tile from shared memory, which bounds these narrow
 // products; layer 3 (3 outputs) therefore keeps the three horizontal taps apart in N and
-// sums them across neighbouring rows in its epilogue (9 MMAs instead of 27).
-//   weights   all three layers as bf16 B-operand images (112.5 KiB), loaded once per CTA by
+// sums them across neighbouring rows in its epilogue (9 MMAs instead of 27), and layer 1
+// puts its last 3 input channels of all three horizontal taps into one K step (21 MMAs
+// instead of 27).
+//   weights   all three layers as bf16 B-operand images (100.5 KiB), loaded once per CTA by
 //             the bulk-copy engine and kept in shared memory;
-//   layer 1   K = 35 channels padded to 48, N = 64, 9 taps;  layer 2 K = 64, N = 48, 9 taps;
+//   layer 1   K = 35 channels padded to 48, N = 64;  layer 2 K = 64, N = 48, 9 taps;
 //   layer 3   K = 48, N = 16 (3 dx x 3 outputs), 3 taps (dy);
 //   accumulators in tensor-memory columns 0, 64, 112 of the group's 128.
 // The inputs are first reduced, per probe and texel, to one 16-byte feature texel (bf16
@@ -59,8 +61,11 @@ constexpr int kThreads = kGroups * kGroupThreads;
 // B images: per layer, per tap, [K / 8][N][8 channels] bf16 (K-major, no swizzle)
 // layer 3 keeps the horizontal taps apart in N: column (dx + 1) * 3 + co of the image of
 // vertical tap dy holds W3[dy][dx][.][co], so its B images are 3 (dy) of N = 16 (9 used)
-constexpr int kImg1 = 9 * kK1 * kN1 * 2, kImg2 = 9 * kK2 * kN2 * 2, kImg3 = 3 * kK3 * kN3 * 2;
-constexpr int kImgBytes = kImg1 + kImg2 + kImg3;  // 115,200
+// layer 1: its first 32 input channels per tap (9 x [32][64]), then its channels 32-34 with
+// the three dx side by side in K per vertical tap (3 x [16][64]; see store_features)
+constexpr int kImg1a = 9 * 32 * kN1 * 2, kImg1 = kImg1a + 3 * 16 * kN1 * 2;
+constexpr int kImg2 = 9 * kK2 * kN2 * 2, kImg3 = 3 * kK3 * kN3 * 2;
+constexpr int kImgBytes = kImg1 + kImg2 + kImg3;  // 102,912
 // A images: [K / 8][kBufRows][8 channels] bf16
 // A image of a group, 64 channels: the features (48), layer 1's output (64), layer 2's (48)
 constexpr int kAct = kBufRows * kK2 * 2;
@@ -94,11 +99,26 @@ __global__ void build_images_kernel(const float* __restrict__ use, __nv_bfloat16
     } else {
         return;
     }
+    if (base == 0) {  // layer 1 (K = 48 of which 35 used, N = 64)
+        float w = 0.f;
+        int off;
+        if (e < kImg1a / 2) {  // tap, channel k < 32
+            const int tap = e / (32 * N), n = e % (32 * N) / 32, k = e % 32;
+            w = use[woff + (tap * cin + k) * cout + n];
+            off = tap * 32 * N + b_off(n, k, N) / 2;
+        } else {               // vertical tap dy + 1 = slot, K row j: channel 32 + j % 3 of dx = j / 3 - 1
+            const int f = e - kImg1a / 2, slot = f / (16 * N), n = f % (16 * N) / 16, j = f % 16;
+            if (j < 9) w = use[woff + ((slot * 3 + j / 3) * cin + 32 + j % 3) * cout + n];
+            off = kImg1a / 2 + slot * 16 * N + b_off(n, j, N) / 2;
+        }
+        img[off] = __float2bfloat16_rn(w);
+        return;
+    }
     const int slot = e / (K * N), r = e % (K * N), n = r / K, k = r % K;
     float w = 0.f;
     if (base == (kImg1 + kImg2) / 2) {  // layer 3: slot = dy + 1, n = (dx + 1) * 3 + co
         if (k < cin && n < 3 * kCout) w = use[woff + ((slot * 3 + n / kCout) * cin + k) * cout + n % kCout];
-    } else if (k < cin && n < cout) {   // layers 1, 2: slot = tap
+    } else if (k < cin && n < cout) {   // layer 2: slot = tap
         w = use[woff + (slot * cin + k) * cout + n];
     }
     img[base + slot * K * N + b_off(n, k, N) / 2] = __float2bfloat16_rn(w);
@@ -171,9 +191,13 @@ __device__ __forceinline__ void load_pending(const TcArgs& a, int tile, int gtid
     q.act = probe_active(a.m, p) ? 1u : 0u;
 }
 
-// The row's 48 input channels in the CUDA-core path's order -- irradiance rgb of the probe
-// and its 6 neighbours (channels 0-20), then their depth moment pairs (21-34), zeros (35-47)
-// -- as 24 bf16 pairs, into the group's A image.
+// The row's input channels into the group's A image as bf16 pairs: channels 0-31 in the
+// CUDA-core path's order -- irradiance rgb of the probe and its 6 neighbours (0-20), then
+// their depth moment pairs (21-34) -- and in the padding after channels 32-34, copies of
+// channels 32-34 of the next two rows (35-37, 38-40; from the neighbouring lanes, the same
+// 8-texel row wherever a kept output reads them), zeros in 41-47. One K step of layer 1 on
+// the image shifted for dx = -1 then covers channels 32-34 of all three horizontal taps.
+// Called by all threads of the group (the shuffles).
 __device__ __forceinline__ void store_features(const Pending& q, unsigned char* act, int row) {
     uint3 f[7];
     f[0] = make_uint3(q.f[0].x, q.f[0].y, q.h[0]);
@@ -195,9 +219,15 @@ __device__ __forceinline__ void store_features(const Pending& q, unsigned char* 
     w[10] = lo_hi(f[6].y, f[0].y);       // 20 (b of neighbour 6), 21 (mu of the probe)
 #pragma unroll
     for (int k = 0; k < 6; ++k) w[11 + k] = lo_hi(f[k].z, f[k + 1].y);  // mu2 of k, mu of k + 1
-    w[17] = f[6].z;                      // 34 (mu2 of neighbour 6), 35 = 0
+    // channels 32, 33 = w[16] and 34 = the low half of f[6].z, of this row and the next two
+    const uint32_t u1 = __shfl_down_sync(0xffffffffu, w[16], 1), u2 = __shfl_down_sync(0xffffffffu, w[16], 2);
+    const uint32_t c0 = f[6].z, c1 = __shfl_down_sync(0xffffffffu, c0, 1), c2 = __shfl_down_sync(0xffffffffu, c0, 2);
+    w[17] = __byte_perm(c0, u1, 0x5410);  // 34, 35 (= 32 of the next row)
+    w[18] = __byte_perm(u1, c1, 0x5432);  // 36, 37
+    w[19] = u2;                           // 38, 39
+    w[20] = c2 & 0xffffu;                 // 40, 41 = 0
 #pragma unroll
-    for (int k = 18; k < 24; ++k) w[k] = 0u;
+    for (int k = 21; k < 24; ++k) w[k] = 0u;
 #pragma unroll
     for (int g = 0; g < kK1 / 8; ++g)
         *reinterpret_cast<uint4*>(act + a_off(kGuard + row, 8 * g)) =
@@ -221,6 +251,30 @@ __device__ __forceinline__ void issue_layer(uint32_t a_img, uint32_t b_img, int 
             const uint32_t b = b_img + (uint32_t)(k * K * N * 2) + (uint32_t)(2 * s) * N * 16;
             mma_bf16(d_tmem, make_desc(a, kBufRows * 16, 128), make_desc(b, N * 16, 128), id, (k | s) ? 1u : 0u);
         }
+    }
+    mma_commit(bar);
+}
+
+// Issues layer 1's MMAs (N = 64) and arms `bar` with their completion: per tap, channels
+// 0-31 of the A image shifted by dy * 8 + dx (2 K steps); then per vertical tap, channels
+// 32-47 of the image shifted by dy * 8 - 1, which hold channels 32-34 of the rows for
+// dx = -1, 0, +1 side by side (1 K step). 21 MMAs instead of 27.
+__device__ __forceinline__ void issue_first(uint32_t a_img, uint32_t b_img, uint32_t d_tmem, uint64_t* bar) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t id = idesc(kN1);
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const uint32_t a = a_img + (uint32_t)(2 * s) * kBufRows * 16 + (uint32_t)(kGuard + tap_offset(k)) * 16;
+            const uint32_t b = b_img + (uint32_t)(k * 32 * kN1 * 2) + (uint32_t)(2 * s) * kN1 * 16;
+            mma_bf16(d_tmem, make_desc(a, kBufRows * 16, 128), make_desc(b, kN1 * 16, 128), id, (k | s) ? 1u : 0u);
+        }
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) {
+        const uint32_t a = a_img + 4u * kBufRows * 16 + (uint32_t)(kGuard + (dy - 1) * 8 - 1) * 16;
+        const uint32_t b = b_img + (uint32_t)kImg1a + (uint32_t)(dy * 16 * kN1 * 2);
+        mma_bf16(d_tmem, make_desc(a, kBufRows * 16, 128), make_desc(b, kN1 * 16, 128), id, 1u);
     }
     mma_commit(bar);
 }
@@ -380,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, 1) denoise_tc_kernel(const __grid_co
         const bool active = pend.act != 0u;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
         group_sync(grp);
-        if (leader) issue_layer<9>(img, img0, kK1, kN1, tmem + kCol1, bar);
+        if (leader) issue_first(img, img0, tmem + kCol1, bar);
         if (tile + stride < a.n_tiles) load_pending(a, tile + stride, gtid, pend);  // in flight meanwhile
 
         // ---- layer 1 epilogue into the A image (64 channels; MMA 1 is done reading it)
