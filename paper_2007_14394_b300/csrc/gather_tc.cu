@@ -2,13 +2,15 @@
 //
 // For one frame the texel weights W[texel][ray] = max(0, u.d)^e are shared by every probe,
 // so the gather of G probes is one dense contraction
-//     D[texel][probe*6 + c] = sum_ray W[texel][ray] * V[ray][probe*6 + c],
-// c = (radiance r, g, b, distance t, t^2, 1); the last channel makes D hold each texel's
-// weight sum, so that numerator and denominator see the same rounding of W.
+//     D[texel][probe*5 + c] = sum_ray W[texel][ray] * V[ray][probe*5 + c],
+// c = (radiance r, g, b, distance t, t^2), plus one column of ones shared by the G probes:
+// every ray of a probe counts in its texels' weight sums, so that sum is the same for all
+// probes, and numerator and denominator see the same rounding of W.
 //   A = W, 256 texel rows (irradiance 0..35, depth 36..231, zero padding) as two M = 128
 //       tiles, K-major, prepared once per frame by pack_weights_kernel as a shared-memory
 //       image and brought in per 16-ray chunk with one bulk copy;
-//   B = V for the CTA's 16 probes (N = 96), split by the CTA from the rays' values;
+//   B = V for the CTA's 19 probes and the ones (N = 19 * 5 + 1 = 96), split by the CTA
+//       from the rays' values;
 //   D = two 128 x 96 fp32 accumulators in tensor memory.
 // Precision (template parameter): fp32 operands split as hi + lo tf32 and multiplied as
 // hi*hi + hi*lo + lo*hi (kind::tf32, fp32 accumulation; products carry about 21 significant
@@ -29,9 +31,11 @@ namespace sdfddgi {
 
 namespace tc {
 
-constexpr int kG = 16;                        // probes per CTA
-constexpr int kCh = 6;                        // channels per probe
-constexpr int kN = kG * kCh;                  // 96 accumulator columns per tile
+constexpr int kG = kGatherTcProbes;           // probes per CTA
+constexpr int kCh = 5;                        // value channels per probe
+constexpr int kN = kG * kCh + 1;              // 96 accumulator columns per tile: the probes', then the ones
+constexpr int kOnes = kN - 1;                 // the weight-sum column
+static_assert(kN % 16 == 0 && kN <= 256, "an MMA of M = 128 takes N a multiple of 16 up to 256");
 constexpr int kChunk = 16;                    // rays per K chunk
 constexpr int kThreads = 256;
 constexpr int kTmemCols = 256;                // 2 x 96 used
@@ -65,7 +69,7 @@ struct Stages {
     static constexpr int value = BF16 ? 4 : kStagesTf32;
 };
 // Threads that build the B operand: one 16-byte core-matrix row of every channel of one
-// probe and part per chunk.
+// probe and part per chunk (the ones rows are written once per CTA).
 template <bool BF16>
 struct Producers {
     static constexpr int value = kG * (kChunk / (16 / Fmt<BF16>::kElem)) * Fmt<BF16>::kParts;
@@ -166,6 +170,12 @@ __device__ __forceinline__ void gather_tc_body(const UpdateParams& P, int block)
         mbar_init(&bar_prev, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // the ones rows of every stage's B operand (tf32: hi 1, lo 0), which no chunk rewrites
+    if (tid < kStages * F::kParts * kChunk) {
+        const int st = tid / (F::kParts * kChunk), part = tid / kChunk % F::kParts, k = tid % kChunk;
+        tc::put<BF16>(sB(st) + part * kBPart, F::offset(kOnes, k), part ? 0.f : 1.f);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -173,28 +183,30 @@ __device__ __forceinline__ void gather_tc_body(const UpdateParams& P, int block)
 
     // ---- K loop over 16-ray chunks through a ring of kStages operand stages, in three roles
     // and without a CTA-wide barrier:
-    //  the copier (warp 4, lane 0) brings chunk c's weight image into stage c % kStages with one
+    //  the copier (warp 5, lane 0) brings chunk c's weight image into stage c % kStages with one
     //    bulk copy as soon as the MMAs of chunk c - kStages are done (full_a counts the bytes);
-    //  producers (the first kProducers threads) build chunk c's B operand from the rays'
-    //    values at the same time (they too wait only for chunk c - kStages's MMAs), split as
-    //    the format asks, and arrive on full_b; each loads its values of the next chunk into
-    //    registers one chunk ahead;
-    //  the issuer (warp 5, lane 0) issues chunk c's MMAs once both operands are in and commits
+    //  producers (the first kProducers threads, in warps 0..4) build chunk c's B operand from
+    //    the rays' values at the same time (they too wait only for chunk c - kStages's MMAs),
+    //    split as the format asks, and arrive on full_b; each loads its values of the next
+    //    chunk into registers one chunk ahead;
+    //  the issuer (warp 6, lane 0) issues chunk c's MMAs once both operands are in and commits
     //    them to empty[c % kStages], which frees the stage for both.
     // Copies thus run up to kStages - 1 chunks ahead of the MMAs.
     constexpr int kVec = 16 / F::kElem;                   // K values per 16-byte core-matrix row
     constexpr int kQuads = kChunk / kVec;                 // such rows per operand row and chunk
     constexpr int kProducers = kG * kQuads * F::kParts;   // one (probe, rows, part) each
-    static_assert(kProducers <= 128, "producers fit in warps 0..3");
+    constexpr int kProducerWarps = (kProducers + 31) / 32;
+    static_assert(kProducerWarps <= 5, "producers fit in warps 0..4");
+    static_assert(kStages * F::kParts * kChunk <= kThreads, "one thread per ones element");
     const uint32_t* fail_word = &P.counters[kFailWord];
     auto give_up = [&]() {
         atomicOr(&P.counters[kFailWord], 2u);  // the other roles and CTAs stop waiting too
         s_fail = 1;
     };
-    if (tid < kProducers) {
+    if (warp < kProducerWarps) {  // whole warps: the stage wait is one lane's, shared by shuffle
+        const bool worker = tid < kProducers;
         const int g = tid % kG, kq = (tid / kG) % kQuads, part = tid / (kG * kQuads);
-        const bool live = g < ng;
-        const float one = live ? 1.f : 0.f;
+        const bool live = worker && g < ng;
         const float4* src =
             P.ray_val + checked((size_t)(p0 + (live ? g : 0)) * P.R + kq * kVec,
                                 (size_t)P.P * P.R - P.R + kChunk - kVec + 1,  // the reads below stay inside
@@ -222,6 +234,7 @@ __device__ __forceinline__ void gather_tc_body(const UpdateParams& P, int block)
                     break;
                 }
             }
+            if (!worker) continue;
             unsigned char* dst = sB(s) + part * kBPart;
 #pragma unroll
             for (int q = 0; q < kCh; ++q) {  // the channel is a compile-time index: no divergence
@@ -229,7 +242,7 @@ __device__ __forceinline__ void gather_tc_body(const UpdateParams& P, int block)
 #pragma unroll
                 for (int j = 0; j < kVec; ++j) {
                     const float4 v = cur[j];
-                    x[j] = q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : q == 3 ? v.w : q == 4 ? v.w * v.w : one;
+                    x[j] = q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : q == 3 ? v.w : v.w * v.w;
                 }
                 uint4 w;
                 if constexpr (BF16) {
@@ -254,7 +267,7 @@ __device__ __forceinline__ void gather_tc_body(const UpdateParams& P, int block)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_full_b[s])) : "memory");
         }
-    } else if (warp == 4 && lane == 0) {
+    } else if (warp == 5 && lane == 0) {
         int last[kStages];  // per stage, the last chunk whose weight copy was issued into it
         for (int s = 0; s < kStages; ++s) last[s] = -1;
         for (int c = 0; c < n_chunks && !s_fail; ++c) {
@@ -273,14 +286,14 @@ __device__ __forceinline__ void gather_tc_body(const UpdateParams& P, int block)
         const uint32_t no_abort = 0;
         for (int s = 0; s < kStages; ++s)
             if (last[s] >= 0) mbar_wait(&bar_full_a[s], (last[s] / kStages) & 1, &no_abort);
-    } else if (warp == 6 && lane < kG) {
+    } else if (warp == 7 && lane < kG) {
         // the probes' flags and history weights, which only the epilogue reads: fetched here,
         // beside the K loop, rather than ahead of it
         uint32_t flags = 0;
         if (lane < ng) flags = P.states ? P.states[p0 + lane].flags : (uint32_t)SDFDDGI_PROBE_ACTIVE;
         s_flags[lane] = flags;
         s_hyst[lane] = (lane < ng && P.prev_valid[p0 + lane] && !(flags & SDFDDGI_PROBE_REJECT_HISTORY)) ? P.hyst : 0.f;
-    } else if (warp == 5 && lane == 0) {
+    } else if (warp == 6 && lane == 0) {
         int committed = 0;  // chunks whose MMAs were committed
         for (int c = 0; c < n_chunks && !s_fail; ++c) {
             const int s = c % kStages;
@@ -338,40 +351,65 @@ __device__ __forceinline__ void gather_tc_body(const UpdateParams& P, int block)
     if (!s_fail) {
         const int t = warp >> 2, row = (warp & 3) * 32 + lane, j = t * 128 + row;
         const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + t * kN;
-        float acc[48];
-        for (int half = 0; half < 2; ++half) {  // probes 0..7, then 8..15
-            __syncwarp();                        // tcgen05.ld is warp-collective
-            tmem_ld16(lane_addr + half * 48, acc);
-            tmem_ld16(lane_addr + half * 48 + 16, acc + 16);
-            tmem_ld16(lane_addr + half * 48 + 32, acc + 32);
-            if (half == 0 && !mbar_wait(&bar_prev, 0, &P.counters[kFailWord])) s_fail = 1;
-            if (j >= kTexels || s_fail) continue;
-#pragma unroll
-            for (int gg = 0; gg < 8; ++gg) {
-                const int g = half * 8 + gg;
-                if (g >= ng) break;
-                const float* a = acc + gg * kCh;
-                const bool live = (s_flags[g] & SDFDDGI_PROBE_ACTIVE) && a[5] > 0.f;
-                const float hyst = s_hyst[g], keep = 1.f - hyst, inv = live ? 1.f / a[5] : 0.f;
-                if (j < kIrrTexels) {
-                    const int k = (j / kIrrN + 1) * kIrrT + (j % kIrrN + 1);
-                    float4 out = s_irr[g * kIrrT * kIrrT + k];  // last frame's texel
-                    if (live) {
-                        out.x = fmaf(hyst, out.x, keep * (a[0] * inv));
-                        out.y = fmaf(hyst, out.y, keep * (a[1] * inv));
-                        out.z = fmaf(hyst, out.z, keep * (a[2] * inv));
-                        out.w = 1.f;
-                    }
-                    s_irr[g * kIrrT * kIrrT + k] = out;
-                } else {
-                    const int jj = j - kIrrTexels, k = (jj / kDepN + 1) * kDepT + (jj % kDepN + 1);
-                    float2 out = s_dep[g * kDepT * kDepT + k];  // last frame's texel
-                    if (live) {
-                        out.x = fmaf(hyst, out.x, keep * (a[3] * inv));
-                        out.y = fmaf(hyst, out.y, keep * (a[4] * inv));
-                    }
-                    s_dep[g * kDepT * kDepT + k] = out;
+        // Blends probe g's texel j from its five sums and the shared weight sum.
+        auto blend = [&](int g, float wsum, float a0, float a1, float a2, float a3, float a4) {
+            if (g >= ng) return;
+            const bool live = (s_flags[g] & SDFDDGI_PROBE_ACTIVE) && wsum > 0.f;
+            const float hyst = s_hyst[g], keep = 1.f - hyst, inv = live ? 1.f / wsum : 0.f;
+            if (j < kIrrTexels) {
+                const int k = (j / kIrrN + 1) * kIrrT + (j % kIrrN + 1);
+                float4 out = s_irr[g * kIrrT * kIrrT + k];  // last frame's texel
+                if (live) {
+                    out.x = fmaf(hyst, out.x, keep * (a0 * inv));
+                    out.y = fmaf(hyst, out.y, keep * (a1 * inv));
+                    out.z = fmaf(hyst, out.z, keep * (a2 * inv));
+                    out.w = 1.f;
                 }
+                s_irr[g * kIrrT * kIrrT + k] = out;
+            } else {
+                const int jj = j - kIrrTexels, k = (jj / kDepN + 1) * kDepT + (jj % kDepN + 1);
+                float2 out = s_dep[g * kDepT * kDepT + k];  // last frame's texel
+                if (live) {
+                    out.x = fmaf(hyst, out.x, keep * (a3 * inv));
+                    out.y = fmaf(hyst, out.y, keep * (a4 * inv));
+                }
+                s_dep[g * kDepT * kDepT + k] = out;
+            }
+        };
+        static_assert(kG == 19 && kCh == 5, "the column ranges below");
+        // columns 80..95 (probes 16..18 and the weight sum), then 0..47 (probes 0..8 and the
+        // first three sums of probe 9), then 48..79 (the rest of probe 9, probes 10..15);
+        // tcgen05.ld is warp-collective, so every lane loads
+        float hi[16], lo[48], mid[32];
+        __syncwarp();
+        tmem_ld16(lane_addr + 80, hi);
+        tmem_ld16(lane_addr, lo);
+        tmem_ld16(lane_addr + 16, lo + 16);
+        tmem_ld16(lane_addr + 32, lo + 32);
+        if (!mbar_wait(&bar_prev, 0, &P.counters[kFailWord])) s_fail = 1;
+        const float wsum = hi[kOnes - 80];
+        const bool mine = j < kTexels && !s_fail;
+        if (mine) {
+#pragma unroll
+            for (int g = 0; g < 9; ++g) {
+                const float* a = lo + g * kCh;
+                blend(g, wsum, a[0], a[1], a[2], a[3], a[4]);
+            }
+        }
+        __syncwarp();
+        tmem_ld16(lane_addr + 48, mid);
+        tmem_ld16(lane_addr + 64, mid + 16);
+        if (mine) {
+            blend(9, wsum, lo[45], lo[46], lo[47], mid[0], mid[1]);
+#pragma unroll
+            for (int g = 10; g < 16; ++g) {
+                const float* a = mid + (g * kCh - 48);
+                blend(g, wsum, a[0], a[1], a[2], a[3], a[4]);
+            }
+#pragma unroll
+            for (int g = 16; g < 19; ++g) {
+                const float* a = hi + (g * kCh - 80);
+                blend(g, wsum, a[0], a[1], a[2], a[3], a[4]);
             }
         }
     }

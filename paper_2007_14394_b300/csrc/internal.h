@@ -258,6 +258,7 @@ int report_error(int code, const char* msg);  // sets the text of sdfddgi_last_e
 // the gather of Eq. 3 on the tensor cores (R a multiple of 16 and a weight image present)
 bool gather_tc_supported(const UpdateParams& p);
 size_t wimage_bytes(int R);
+constexpr int kGatherTcProbes = 19;  // probes per CTA of the tensor-core gather
 // The tensor-core gather; with pack, first the frame's weight image (otherwise already packed
 // by launch_pack_weights on a stream this one waits for).
 cudaError_t launch_gather_tc(const UpdateParams& p, cudaStream_t stream, bool pack = true);

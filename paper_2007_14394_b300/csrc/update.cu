@@ -1286,7 +1286,7 @@ cudaError_t launch_merged(const UpdateParams* p, int n, MergedParams* m, cudaStr
         rb += (rays + m->primary_batch - 1) / m->primary_batch * m->primary_batch;
         m->prep_rays[v] = prep_rays(rays, setup->sms, 2);
         pb += (rays + m->prep_rays[v] - 1) / m->prep_rays[v];
-        gb += ((uint64_t)p[v].P + 15) / 16;
+        gb += ((uint64_t)p[v].P + kGatherTcProbes - 1) / kGatherTcProbes;
         db += (uint64_t)(p[v].P > 0 ? p[v].R : 0);
     }
     if (rb >= 0xffffffffull - 2 * kShadowBatch) return cudaErrorInvalidValue;  // merged task indices are 32-bit
