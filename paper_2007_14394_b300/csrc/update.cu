@@ -1178,7 +1178,7 @@ static cudaError_t launch_stages(const UpdateParams& p, cudaStream_t stream, cud
     if (e != cudaSuccess) return e;
     const bool tc = gather_tc_supported(p) && p.sched.gather != 2;
     // the texel weights (with the frame's directions when dirs is set); the column sums serve
-    // the SIMT gather, the tensor-core gather sums a ones channel
+    // the SIMT gather, the tensor-core gather sums a column of ones
     auto weights = [&](cudaStream_t s, bool dirs) {
         if (p.depth_exp == 50) {
             if (dirs)

@@ -61,7 +61,7 @@ class Pair:
 @pytest.mark.parametrize("rays,dims,slabs", [
     (64, (8, 8, 8), 2),     # tensor-core gather, even split
     (64, (8, 8, 8), 3),     # uneven: 2, 3, 3 z-layers
-    (48, (6, 5, 7), 4),     # 1, 2, 2, 2 z-layers; slab sizes not multiples of the gather's 16 probes
+    (48, (6, 5, 7), 4),     # 1, 2, 2, 2 z-layers; slab sizes not multiples of the gather's 19 probes
     (33, (5, 3, 6), 4),     # SIMT gather (R not a multiple of 16)
 ])
 def test_slabs_equal_the_serial_update_bit_for_bit(cuda_device, rays, dims, slabs):
