@@ -550,7 +550,7 @@ def run_batch(args, rank, world, local_rank):
     t_tune = time.perf_counter()
     S.batch_autotune(batch, repeats=3, stream=stream)
     t_tune = time.perf_counter() - t_tune
-    schedules = [dict(zip(("pool_batch", "blocks_per_sm", "gather", "index", "tuned_ms"), S.batch_schedule(batch, i)))
+    schedules = [dict(zip(("pool_batch", "blocks_per_sm", "gather", "index", "steps", "tuned_ms"), S.batch_schedule(batch, i)))
                  for i in range(len(vols))]
     form, tuned_branches, tuned_merged = S.batch_form(batch)
 

@@ -442,8 +442,9 @@ SDFDDGI_API int sdfddgi_update_batch(sdfddgi_batch* b, uint32_t frame, const flo
  * each candidate on `stream`: trace-pool batch (16, 32, 64 tasks per warp claim, or, for
  * more than 64 rays per probe, a warp per probe: all of a probe's rays per claim), resident
  * CTAs per SM of the trace kernels (4 or the occupancy limit), gather (tensor cores when
- * rays_per_probe is a multiple of 16, or SIMT), and the traces' SDF-index arithmetic (a
- * 32-bit row or 64-bit; the same addresses). The trials write only each volume's
+ * rays_per_probe is a multiple of 16, or SIMT), the traces' SDF-index arithmetic (a
+ * 32-bit row or 64-bit; the same addresses), and for plain voxel primary traces one or two
+ * trace steps between a warp's votes (the same results). The trials write only each volume's
  * spare ping-pong buffer, so the maps and history are unchanged. Then, when the volumes
  * allow the merged form, it times `repeats` whole frames in each form and keeps the faster
  * one for SDFDDGI_BATCH_FORM_AUTO (sdfddgi_batch_form reports both times). Synchronises
@@ -454,9 +455,10 @@ SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* 
  * per SM (0 = occupancy limit),
  * out[2] gather (0 automatic, 1 tensor cores, 2 SIMT), out[3] the traces' SDF-index
  * arithmetic (0 automatic: the 32-bit row; 1 a 32-bit row, 2 64-bit; the
- * same addresses, a speed choice); tuned_ms (nullable) receives the autotuner's mean update
- * time of that schedule (0 before tuning). */
-SDFDDGI_API int sdfddgi_batch_schedule(const sdfddgi_batch* b, int32_t i, int32_t out[4], float* tuned_ms);
+ * same addresses, a speed choice), out[4] trace steps between a warp's votes in the primary
+ * pool of a plain voxel trace (0 automatic: 2; 1 or 2; the same results); tuned_ms
+ * (nullable) receives the autotuner's mean update time of that schedule (0 before tuning). */
+SDFDDGI_API int sdfddgi_batch_schedule(const sdfddgi_batch* b, int32_t i, int32_t out[5], float* tuned_ms);
 
 /* The form of a batch's frames. AUTO (the default): the autotuner's choice (it times whole
  * frames in both forms after choosing the volumes' schedules), branches before tuning.

@@ -437,11 +437,11 @@ def batch_autotune(batch, repeats: int = 3, stream=None) -> None:
 
 
 def batch_schedule(batch, i: int):
-    """(pool_batch, blocks_per_sm, gather, index, tuned_ms) of volume i."""
-    out = (C.c_int32 * 4)()
+    """(pool_batch, blocks_per_sm, gather, index, steps, tuned_ms) of volume i."""
+    out = (C.c_int32 * 5)()
     ms = C.c_float()
     _check(lib.sdfddgi_batch_schedule(batch, int(i), out, C.byref(ms)))
-    return out[0], out[1], out[2], out[3], ms.value
+    return out[0], out[1], out[2], out[3], out[4], ms.value
 
 
 def batch_set_form(batch, form: int) -> None:

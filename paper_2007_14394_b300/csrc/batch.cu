@@ -267,18 +267,23 @@ SDFDDGI_API int sdfddgi_batch_autotune(sdfddgi_batch* b, int32_t repeats, void* 
         const int R = probe.R;
         std::vector<int> batches = {16, 32, 64};
         if (R > 64) batches.push_back(R);
+        // one or two trace steps between a warp's votes in the primary pool (plain voxel traces)
+        const bool steps_choice = probe.vol.dtype != kAnalytic && !(probe.omega_primary > 1.f);
         for (int pb : batches)
             for (int bps : {0, 4})
                 for (int g : {1, 2})
-                    for (int ix : {1, 2}) {  // the traces' quad-index arithmetic (same addresses)
-                        if (g == 1 && !tc_ok) continue;
-                        Schedule c = {};
-                        c.pool_batch = pb;
-                        c.blocks_per_sm = bps;
-                        c.gather = g;
-                        c.index = ix;
-                        cand.push_back(c);
-                    }
+                    for (int ix : {1, 2})  // the traces' quad-index arithmetic (same addresses)
+                        for (int stp : {2, 1}) {
+                            if (g == 1 && !tc_ok) continue;
+                            if (stp == 1 && !steps_choice) continue;
+                            Schedule c = {};
+                            c.pool_batch = pb;
+                            c.blocks_per_sm = bps;
+                            c.gather = g;
+                            c.index = ix;
+                            c.steps = stp;
+                            cand.push_back(c);
+                        }
         float best = 1e30f;
         Schedule best_s = {};
         for (const Schedule& sc : cand) {
@@ -376,12 +381,13 @@ SDFDDGI_API int sdfddgi_batch_form(const sdfddgi_batch* b, int32_t* form, float 
     return SDFDDGI_OK;
 }
 
-SDFDDGI_API int sdfddgi_batch_schedule(const sdfddgi_batch* b, int32_t i, int32_t out[4], float* tuned_ms) {
+SDFDDGI_API int sdfddgi_batch_schedule(const sdfddgi_batch* b, int32_t i, int32_t out[5], float* tuned_ms) {
     if (!b || !out || i < 0 || i >= b->n) return bfail(SDFDDGI_ERR_INVALID_ARG, "batch_schedule: invalid arguments");
     out[0] = b->sched[i].pool_batch;
     out[1] = b->sched[i].blocks_per_sm;
     out[2] = b->sched[i].gather;
     out[3] = b->sched[i].index;
+    out[4] = b->sched[i].steps;
     if (tuned_ms) *tuned_ms = b->tuned_ms[i];
     return SDFDDGI_OK;
 }

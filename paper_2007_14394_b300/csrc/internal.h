@@ -71,6 +71,8 @@ struct Schedule {
     int index;           // the traces' quad-index arithmetic: 0 automatic (the 32-bit row form),
                          // 1 a 32-bit z-pair row, 2 all in 64 bits (the same addresses either way)
     int refill;          // idle lanes of a trace warp before it hands out new tasks: 0 default, 1..32
+    int steps;           // trace steps between a warp's votes in the primary pool of a plain voxel
+                         // trace: 0 automatic (2), 1 or 2 (the same results either way)
 };
 
 constexpr int kMaxSlabs = SDFDDGI_MAX_SLABS;

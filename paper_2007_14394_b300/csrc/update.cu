@@ -217,8 +217,11 @@ __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, f
 // take part (full-warp votes).
 // A warp hands out new tasks only once at least `refill` of its lanes wait for one (or no
 // lane is tracing): a ray lasts a few steps, so refilling lanes one by one would run the
-// hand-out on nearly every step for one or two lanes at a time.
-template <typename T, bool Relax, bool Idx64, typename Claim, typename Init, typename Done>
+// hand-out on nearly every step for one or two lanes at a time. STEPS: trace steps a lane
+// takes between two of the warp's votes (one or two; two halve the votes and hand-out checks,
+// which made open256's primary traces 5 % faster but leave a lane idle for a step when its
+// ray ends after the first, which cost cascade512's volumes; the shadow traces spill with two).
+template <typename T, bool Relax, bool Idx64, int STEPS = 1, typename Claim, typename Init, typename Done>
 __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint32_t* counter, float eps,
                                            int max_steps, float omega, uint32_t batch, int refill, Claim claim,
                                            Init init, Done done) {
@@ -283,7 +286,11 @@ __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint
         if (busy) {
             int steps;
             float t_end;
-            const int ev = trace_step<T, Relax, Idx64>(v, st, eps, max_steps, &steps, &t_end);
+            int ev = trace_step<T, Relax, Idx64>(v, st, eps, max_steps, &steps, &t_end);
+            if constexpr (STEPS > 1) {
+                if (ev < 0) ev = trace_step<T, Relax, Idx64>(v, st, eps, max_steps, &steps, &t_end);
+            }
+            static_assert(STEPS == 1 || STEPS == 2, "one or two steps between votes");
             if (ev >= 0) {
                 if constexpr (!std::is_same<T, Analytic>::value) t_end *= v.h;  // back to world units
                 done(st, ev, steps, t_end);
@@ -363,13 +370,13 @@ __device__ __forceinline__ bool light_may_reach(const LightDev& li, float3 x, fl
 // A claimed batch of tasks lies within one probe whenever R is a multiple of the batch
 // size, so the probe's origin and flags are decoded once per batch, by lane 0 into its
 // warp's slot; a task outside the slot's probe decodes its own.
-template <typename T, bool Relax, bool Idx64>
+template <typename T, bool Relax, bool Idx64, int STEPS>
 __global__ void __launch_bounds__(kTraceThreads, 32) primary_kernel(const __grid_constant__ UpdateParams P) {
     __shared__ float4 s_origin[kTraceThreads / 32];  // probe origin, its first task index (bits)
     __shared__ uint32_t s_flags[kTraceThreads / 32];
     const uint32_t n = (uint32_t)P.P * (uint32_t)P.R;
     const int warp = threadIdx.x >> 5;
-    trace_pool<T, Relax, Idx64>(
+    trace_pool<T, Relax, Idx64, STEPS>(
         P.vol, n, &P.counters[kPrimaryPool], P.eps_w, P.max_steps, P.omega_primary,
         pool_batch(P, n < kSmallPool ? kBatch / 2 : kBatch), pool_refill(P),
         [&](uint32_t b) {
@@ -1036,15 +1043,15 @@ cudaError_t prepare_update_kernels(const DeviceSetup** out) {
     DeviceSetup& s = g_setup[dev];
     if (!s.done) {
         s.err = cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev);
-        s.occ_primary[0][0] = occupancy((const void*)primary_kernel<float, false, false>, kTraceThreads);
-        s.occ_primary[0][1] = occupancy((const void*)primary_kernel<__half, false, false>, kTraceThreads);
-        s.occ_primary[0][2] = occupancy((const void*)primary_kernel<Analytic, false, false>, kTraceThreads);
+        s.occ_primary[0][0] = occupancy((const void*)primary_kernel<float, false, false, 2>, kTraceThreads);
+        s.occ_primary[0][1] = occupancy((const void*)primary_kernel<__half, false, false, 2>, kTraceThreads);
+        s.occ_primary[0][2] = occupancy((const void*)primary_kernel<Analytic, false, false, 1>, kTraceThreads);
         s.occ_shadow[0][0] = occupancy((const void*)shadow_kernel<float, false, false>, kTraceThreads);
         s.occ_shadow[0][1] = occupancy((const void*)shadow_kernel<__half, false, false>, kTraceThreads);
         s.occ_shadow[0][2] = occupancy((const void*)shadow_kernel<Analytic, false, false>, kTraceThreads);
-        s.occ_primary[1][0] = occupancy((const void*)primary_kernel<float, true, false>, kTraceThreads);
-        s.occ_primary[1][1] = occupancy((const void*)primary_kernel<__half, true, false>, kTraceThreads);
-        s.occ_primary[1][2] = occupancy((const void*)primary_kernel<Analytic, true, false>, kTraceThreads);
+        s.occ_primary[1][0] = occupancy((const void*)primary_kernel<float, true, false, 1>, kTraceThreads);
+        s.occ_primary[1][1] = occupancy((const void*)primary_kernel<__half, true, false, 1>, kTraceThreads);
+        s.occ_primary[1][2] = occupancy((const void*)primary_kernel<Analytic, true, false, 1>, kTraceThreads);
         s.occ_shadow[1][0] = occupancy((const void*)shadow_kernel<float, true, false>, kTraceThreads);
         s.occ_shadow[1][1] = occupancy((const void*)shadow_kernel<__half, true, false>, kTraceThreads);
         s.occ_shadow[1][2] = occupancy((const void*)shadow_kernel<Analytic, true, false>, kTraceThreads);
@@ -1095,12 +1102,17 @@ static cudaError_t launch_stage(const UpdateParams& p, const DeviceSetup& setup,
     const bool i64 = p.sched.index == 2;
     if (s == 0) {
         const int g = persistent_blocks(setup, setup.occ_primary[rp][type_slot<T>()], p.sched.blocks_per_sm);
+        // plain voxel traces take two steps between votes unless the schedule asks for one
+        constexpr int kTwo = std::is_same<T, Analytic>::value ? 1 : 2;
         if (rp)
-            i64 ? primary_kernel<T, true, true><<<g, kTraceThreads, 0, stream>>>(p)
-                : primary_kernel<T, true, false><<<g, kTraceThreads, 0, stream>>>(p);
+            i64 ? primary_kernel<T, true, true, 1><<<g, kTraceThreads, 0, stream>>>(p)
+                : primary_kernel<T, true, false, 1><<<g, kTraceThreads, 0, stream>>>(p);
+        else if (p.sched.steps != 1)
+            i64 ? primary_kernel<T, false, true, kTwo><<<g, kTraceThreads, 0, stream>>>(p)
+                : primary_kernel<T, false, false, kTwo><<<g, kTraceThreads, 0, stream>>>(p);
         else
-            i64 ? primary_kernel<T, false, true><<<g, kTraceThreads, 0, stream>>>(p)
-                : primary_kernel<T, false, false><<<g, kTraceThreads, 0, stream>>>(p);
+            i64 ? primary_kernel<T, false, true, 1><<<g, kTraceThreads, 0, stream>>>(p)
+                : primary_kernel<T, false, false, 1><<<g, kTraceThreads, 0, stream>>>(p);
     } else if (s == 1) {
         const uint32_t rays = prep_rays(n, setup.sms, 2);
         prep_kernel<T><<<(n + rays - 1) / rays, kThreads, 0, stream>>>(p, rays);

@@ -92,7 +92,7 @@ def test_batch_argument_errors_before_device_work(S):
     assert "NULL" in S.last_error()
     assert S.lib.sdfddgi_update_batch(None, 0, None, None) == S.ERR_INVALID_ARG
     assert S.lib.sdfddgi_batch_autotune(None, 3, None) == S.ERR_INVALID_ARG
-    assert S.lib.sdfddgi_batch_schedule(None, 0, (C.c_int32 * 4)(), None) == S.ERR_INVALID_ARG
+    assert S.lib.sdfddgi_batch_schedule(None, 0, (C.c_int32 * 5)(), None) == S.ERR_INVALID_ARG
     S.lib.sdfddgi_destroy_batch(None)
 
 

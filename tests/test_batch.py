@@ -80,8 +80,8 @@ def test_batch_equals_plain_updates_bit_for_bit(cuda_device):
             t.assert_equal(f"frame {frame}")
         assert np.abs(t.batched[0].state()[0][..., :3]).max() > 0
         for i, w in enumerate(t.ws):
-            pb, bps, g, ix, ms = S.batch_schedule(t.batch, i)
-            assert (pb, bps, g, ix, ms) == (0, 0, 0, 0, 0.0)
+            pb, bps, g, ix, stp, ms = S.batch_schedule(t.batch, i)
+            assert (pb, bps, g, ix, stp, ms) == (0, 0, 0, 0, 0, 0.0)
     finally:
         t.close()
 
@@ -133,10 +133,11 @@ def test_autotune_keeps_state_and_results(cuda_device):
         for b, a in zip(before, after):
             assert all(np.array_equal(x, y) for x, y in zip(b, a))
         for i, w in enumerate(t.ws):
-            pb, bps, g, ix, ms = S.batch_schedule(t.batch, i)
+            pb, bps, g, ix, stp, ms = S.batch_schedule(t.batch, i)
             R = w.params["rays"]
             assert pb in (16, 32, 64) + ((R,) if R > 64 else ()), (i, pb, R)  # or a warp per probe
             assert bps in (0, 4) and g in (1, 2) and ix in (1, 2) and ms > 0, (i, pb, bps, g, ms)
+            assert stp in (1, 2), (i, stp)  # voxel volumes, plain traces: both step counts tried
             assert g == 2 or w.params["rays"] % 16 == 0
         # the tuned schedule differs from the default one at most in the gather's rounding
         for frame in (1, 2):
