@@ -46,6 +46,7 @@ constexpr uint32_t kSmallPool = 1u << 19;
 // (the other slab's traces, the next stage) takes over freed slots sooner than from CTAs of
 // eight warps that wait for their slowest ray.
 constexpr int kTraceThreads = 64;
+constexpr size_t kSmallShadowRays = (size_t)1 << 19;  // launches below this take the small-pool shadow kernel
 
 
 // A voxel-volume trace runs in voxel coordinates: o is the origin's voxel coordinate
@@ -602,10 +603,14 @@ __global__ void __launch_bounds__(kThreads, SDFDDGI_PREP_CTAS) prep_kernel(const
 }
 
 // ------------------------------------------------------------------ 3. shadow traces
-template <typename T, bool Relax, bool Idx64>
-__global__ void __launch_bounds__(kTraceThreads, 32) shadow_kernel(const __grid_constant__ UpdateParams P) {
+// SMALL: a launch of fewer than kSmallShadowRays rays, whose small pool runs 24 CTAs per SM
+// of up to 40 registers and takes two trace steps between the warps' votes (with 32 CTAs
+// of 32 registers two steps spill): 32-ray updates' shadow stage 0.0775 -> 0.0716 ms, while
+// 256-ray updates were slower that way (0.2014 -> 0.209 ms).
+template <typename T, bool Relax, bool Idx64, bool SMALL>
+__global__ void __launch_bounds__(kTraceThreads, SMALL ? 24 : 32) shadow_kernel(const __grid_constant__ UpdateParams P) {
     const uint32_t n = min(P.counters[kTaskCount], P.task_capacity);
-    trace_pool<T, Relax, Idx64>(
+    trace_pool<T, Relax, Idx64, SMALL ? 2 : 1>(
         P.vol, n, &P.counters[kShadowPool], P.eps_w, P.max_steps, P.omega_shadow,
         pool_batch(P, n < kSmallPool ? kShadowBatch / 2 : kShadowBatch),  // n: the tasks the preparation made
         pool_refill(P),
@@ -1013,6 +1018,7 @@ struct DeviceSetup {
     int sms = 0;
     int occ_primary[2][3] = {};  // [plain, relaxed][float, __half, Analytic]
     int occ_shadow[2][3] = {};
+    int occ_shadow_small[2] = {};  // [float, __half], plain traces
     int occ_primary_merged[2][2] = {};  // [plain, relaxed][float, __half]
     int occ_shadow_merged[2][2] = {};
 };
@@ -1046,15 +1052,17 @@ cudaError_t prepare_update_kernels(const DeviceSetup** out) {
         s.occ_primary[0][0] = occupancy((const void*)primary_kernel<float, false, false, 2>, kTraceThreads);
         s.occ_primary[0][1] = occupancy((const void*)primary_kernel<__half, false, false, 2>, kTraceThreads);
         s.occ_primary[0][2] = occupancy((const void*)primary_kernel<Analytic, false, false, 1>, kTraceThreads);
-        s.occ_shadow[0][0] = occupancy((const void*)shadow_kernel<float, false, false>, kTraceThreads);
-        s.occ_shadow[0][1] = occupancy((const void*)shadow_kernel<__half, false, false>, kTraceThreads);
-        s.occ_shadow[0][2] = occupancy((const void*)shadow_kernel<Analytic, false, false>, kTraceThreads);
+        s.occ_shadow[0][0] = occupancy((const void*)shadow_kernel<float, false, false, false>, kTraceThreads);
+        s.occ_shadow[0][1] = occupancy((const void*)shadow_kernel<__half, false, false, false>, kTraceThreads);
+        s.occ_shadow[0][2] = occupancy((const void*)shadow_kernel<Analytic, false, false, false>, kTraceThreads);
+        s.occ_shadow_small[0] = occupancy((const void*)shadow_kernel<float, false, false, true>, kTraceThreads);
+        s.occ_shadow_small[1] = occupancy((const void*)shadow_kernel<__half, false, false, true>, kTraceThreads);
         s.occ_primary[1][0] = occupancy((const void*)primary_kernel<float, true, false, 1>, kTraceThreads);
         s.occ_primary[1][1] = occupancy((const void*)primary_kernel<__half, true, false, 1>, kTraceThreads);
         s.occ_primary[1][2] = occupancy((const void*)primary_kernel<Analytic, true, false, 1>, kTraceThreads);
-        s.occ_shadow[1][0] = occupancy((const void*)shadow_kernel<float, true, false>, kTraceThreads);
-        s.occ_shadow[1][1] = occupancy((const void*)shadow_kernel<__half, true, false>, kTraceThreads);
-        s.occ_shadow[1][2] = occupancy((const void*)shadow_kernel<Analytic, true, false>, kTraceThreads);
+        s.occ_shadow[1][0] = occupancy((const void*)shadow_kernel<float, true, false, false>, kTraceThreads);
+        s.occ_shadow[1][1] = occupancy((const void*)shadow_kernel<__half, true, false, false>, kTraceThreads);
+        s.occ_shadow[1][2] = occupancy((const void*)shadow_kernel<Analytic, true, false, false>, kTraceThreads);
         s.occ_primary_merged[0][0] = occupancy((const void*)primary_merged_kernel<float, false, false>, kTraceThreads);
         s.occ_primary_merged[0][1] = occupancy((const void*)primary_merged_kernel<__half, false, false>, kTraceThreads);
         s.occ_primary_merged[1][0] = occupancy((const void*)primary_merged_kernel<float, true, false>, kTraceThreads);
@@ -1117,13 +1125,24 @@ static cudaError_t launch_stage(const UpdateParams& p, const DeviceSetup& setup,
         const uint32_t rays = prep_rays(n, setup.sms, 2);
         prep_kernel<T><<<(n + rays - 1) / rays, kThreads, 0, stream>>>(p, rays);
     } else if (s == 2) {
-        const int g = persistent_blocks(setup, setup.occ_shadow[rs][type_slot<T>()], p.sched.blocks_per_sm);
-        if (rs)
-            i64 ? shadow_kernel<T, true, true><<<g, kTraceThreads, 0, stream>>>(p)
-                : shadow_kernel<T, true, false><<<g, kTraceThreads, 0, stream>>>(p);
-        else
-            i64 ? shadow_kernel<T, false, true><<<g, kTraceThreads, 0, stream>>>(p)
-                : shadow_kernel<T, false, false><<<g, kTraceThreads, 0, stream>>>(p);
+        // a launch of fewer than kSmallShadowRays rays with plain voxel traces takes the shadow
+        // kernel of 24 CTAs per SM and two steps between votes
+        constexpr bool kVoxel = !std::is_same<T, Analytic>::value;
+        if (kVoxel && !rs && (size_t)p.P * (size_t)p.R < kSmallShadowRays) {
+            if constexpr (kVoxel) {
+                const int g = persistent_blocks(setup, setup.occ_shadow_small[type_slot<T>()], p.sched.blocks_per_sm);
+                i64 ? shadow_kernel<T, false, true, true><<<g, kTraceThreads, 0, stream>>>(p)
+                    : shadow_kernel<T, false, false, true><<<g, kTraceThreads, 0, stream>>>(p);
+            }
+        } else {
+            const int g = persistent_blocks(setup, setup.occ_shadow[rs][type_slot<T>()], p.sched.blocks_per_sm);
+            if (rs)
+                i64 ? shadow_kernel<T, true, true, false><<<g, kTraceThreads, 0, stream>>>(p)
+                    : shadow_kernel<T, true, false, false><<<g, kTraceThreads, 0, stream>>>(p);
+            else
+                i64 ? shadow_kernel<T, false, true, false><<<g, kTraceThreads, 0, stream>>>(p)
+                    : shadow_kernel<T, false, false, false><<<g, kTraceThreads, 0, stream>>>(p);
+        }
     } else {
         finalize_kernel<<<max(1, min((int)((n + kThreads - 1) / kThreads), 8 * setup.sms)), kThreads, 0, stream>>>(p);
         if (gather_tc_supported(p) && p.sched.gather != 2)
