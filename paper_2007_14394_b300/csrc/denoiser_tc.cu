@@ -51,12 +51,12 @@ constexpr int kProbesPerTile = kRows / kTex;
 constexpr int kGuard = 10;                      // guard rows at each end (shifts reach +-9)
 constexpr int kBufRows = kRows + 2 * kGuard;    // 148
 constexpr int kK1 = 48, kK2 = 64, kK3 = 48;     // input channels, padded to multiples of 16
-constexpr int kN1 = 64, kN2 = 48, kN3 = 16;     // accumulator columns (layer 3: 3 used)
+constexpr int kN1 = 64, kN2 = 48, kN3 = 16;     // accumulator columns (layer 3: 3 dx x 3 outputs)
 constexpr int kCol1 = 0, kCol2 = 64, kCol3 = 112;   // within a warp group's 128 columns
 constexpr int kGroups = 4;                          // warp groups, each with its own tile stream
 constexpr int kGroupThreads = 128;
 constexpr int kGroupCols = 128;
-constexpr int kTmemCols = 512;                      // 3 x 128 used; allocations are powers of 2
+constexpr int kTmemCols = 512;                      // 4 x 128; allocations are powers of 2
 constexpr int kThreads = kGroups * kGroupThreads;
 // B images: per layer, per tap, [K / 8][N][8 channels] bf16 (K-major, no swizzle)
 // layer 3 keeps the horizontal taps apart in N: column (dx + 1) * 3 + co of the image of
@@ -72,7 +72,7 @@ constexpr int kAct = kBufRows * kK2 * 2;
 constexpr int kSmemBytes = kImgBytes + kGroups * kAct;
 static_assert(kImgBytes % 16 == 0 && kAct % 16 == 0, "16-byte alignment of the images");
 static_assert(kK2 >= kK1 && kK2 >= kK3 && kK2 >= kN1 && kK2 >= kN2, "one image holds every layer's input");
-static_assert(kK1 >= kCin && kK3 == kC2 && kK2 == kC1 && kN1 == kC1 && kN2 == kC2 && kN3 >= kCout, "layer shapes");
+static_assert(kK1 >= kCin && kK3 == kC2 && kK2 == kC1 && kN1 == kC1 && kN2 == kC2 && kN3 >= 3 * kCout, "layer shapes");
 
 // instruction descriptor: D fp32, A and B bf16, both K-major, M = 128, N = n
 __host__ __device__ constexpr uint32_t idesc(int n) { return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24); }
