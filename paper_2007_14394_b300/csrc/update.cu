@@ -219,9 +219,10 @@ __device__ __forceinline__ int trace_step(const VolumeView& v, TraceState& st, f
 // A warp hands out new tasks only once at least `refill` of its lanes wait for one (or no
 // lane is tracing): a ray lasts a few steps, so refilling lanes one by one would run the
 // hand-out on nearly every step for one or two lanes at a time. STEPS: trace steps a lane
-// takes between two of the warp's votes (one or two; two halve the votes and hand-out checks,
-// which made open256's primary traces 5 % faster but leave a lane idle for a step when its
-// ray ends after the first, which cost cascade512's volumes; the shadow traces spill with two).
+// takes per iteration, between two of the warp's votes (one or two). Two made open256's
+// primary traces 5 % faster, though a lane whose ray ends after the first step idles for the
+// second; they cost cascade512's volumes, and the large shadow pools spill with them at 32
+// registers.
 template <typename T, bool Relax, bool Idx64, int STEPS = 1, typename Claim, typename Init, typename Done>
 __device__ __forceinline__ void trace_pool(const VolumeView& v, uint32_t n, uint32_t* counter, float eps,
                                            int max_steps, float omega, uint32_t batch, int refill, Claim claim,
