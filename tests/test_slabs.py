@@ -79,6 +79,23 @@ def test_slabs_equal_the_serial_update_bit_for_bit(cuda_device, rays, dims, slab
         pr.close()
 
 
+def test_small_and_large_shadow_pools_agree_bit_for_bit(cuda_device):
+    """A launch of fewer than 2^19 rays runs its shadow pool as the small-pool kernel (24 CTAs
+    per SM, two trace steps between votes), a larger one as the large-pool kernel: the serial
+    update here has 2^19 rays (large pool), each of its two slabs 2^18 (small pool)."""
+    w = make_workload(W.PRESETS["room64"], rays=128, probe_dims=(16, 16, 16), probe_origin=(0.6, 0.55, 0.6),
+                      probe_spacing=(0.45, 0.45, 0.45), k_bounce=0.9, hysteresis=0.5)
+    assert 16 ** 3 * 128 == 1 << 19
+    pr = Pair(w, 2)
+    try:
+        for frame in range(2):
+            pr.step(frame)
+            pr.assert_equal(f"frame {frame}")
+        assert np.abs(pr.split.state()[0][..., :3]).max() > 0
+    finally:
+        pr.close()
+
+
 @pytest.mark.parametrize("form", ["binary16 SDF, bf16 gather", "relaxed traces", "analytic primitives"])
 def test_slabs_equal_serial_in_every_form(cuda_device, form):
     """The other forms of the update run through the same slab branches."""
