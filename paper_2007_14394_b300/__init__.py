@@ -468,9 +468,12 @@ def _dev_ptr(t, what):
 
 
 def probe_maps(dims, n_grids, irr, depth, valid, states=None) -> ProbeMaps:
-    """Device tensors irr [P,8,8,4] f32, depth [P,16,16,2] f32, valid [P] u8, states None or P*16 bytes."""
-    return ProbeMaps((C.c_int32 * 3)(*[int(x) for x in dims]), int(n_grids), _dev_ptr(irr, "irr"),
-                     _dev_ptr(depth, "depth"), _dev_ptr(valid, "valid"), _dev_ptr(states, "states"))
+    """Device tensors irr [P,8,8,4] f32, depth [P,16,16,2] f32, valid [P] u8, states None or P*16 bytes.
+    The view holds the tensors' device addresses and keeps the tensors alive while it lives."""
+    m = ProbeMaps((C.c_int32 * 3)(*[int(x) for x in dims]), int(n_grids), _dev_ptr(irr, "irr"),
+                  _dev_ptr(depth, "depth"), _dev_ptr(valid, "valid"), _dev_ptr(states, "states"))
+    m._tensors = (irr, depth, valid, states)  # the addresses stay valid as long as the view
+    return m
 
 
 def create_denoiser(params, depth_scale: float) -> C.c_void_p:

@@ -127,6 +127,49 @@ def test_forward_bf16_matches_oracle_with_rounding(case, mode):
     assert err.max() <= 2e-3 * scale
 
 
+def test_tensor_core_odd_probe_count(cuda_device):
+    """9 probes (one grid of 3 x 3 x 1): the tensor-core kernel's last two-probe tile holds one
+    probe. Against the oracle with bf16 rounding, as above, and the inactive pass-through."""
+    import torch
+    dims, ng, n = (3, 3, 1), 1, 9
+    rng = np.random.default_rng(7)
+    irr = np.zeros((n, 8, 8, 4))
+    irr[..., :3] = rng.uniform(0.05, 1.0, (n, 8, 8, 3))
+    irr[..., 3] = 1.0
+    for p in range(n):
+        irr[p] = oracle.border(irr[p])
+    depth = rng.uniform(0.5, 4.0, (n, 16, 16, 2))
+    depth[..., 1] = depth[..., 0] ** 2 + rng.uniform(0.0, 0.3, (n, 16, 16))
+    valid = (rng.random(n) > 0.2).astype(np.uint8)
+    st = np.zeros(n, dtype=W.PROBE_DTYPE)
+    st["flags"] = 1
+    st["flags"][4] = 0
+    theta = W.denoiser_init(3, last_scale=1.0).astype(np.float32)
+    irr, depth = irr.astype(np.float32), depth.astype(np.float32)
+    X = D.features(irr, depth, valid, dims, ng, SCALE)
+    act = (st["flags"] & 1).astype(bool)
+    Y, _ = D.forward(theta.astype(np.float64), X, irr, True)
+    ref = D.output_maps(Y, irr, act)
+    d = S.create_denoiser(theta, SCALE)
+    try:
+        # the maps view holds raw device pointers: the tensors must outlive the calls
+        irr_d, depth_d = torch.from_numpy(irr).cuda(), torch.from_numpy(depth).cuda()
+        valid_d, st_d = torch.from_numpy(valid).cuda(), torch.from_numpy(st.view(np.uint8).copy()).cuda()
+        maps = S.probe_maps(dims, ng, irr_d, depth_d, valid_d, st_d)
+        out_d = torch.full_like(irr_d, float("nan"))
+        S.denoise(d, maps, out_d, S.DENOISE_TENSOR)
+        assert S.denoiser_status(d) == 0
+        out = out_d.cpu().numpy().astype(np.float64)
+    finally:
+        S.destroy_denoiser(d)
+    _check_common(out, irr, act)
+    scale = np.abs(ref).max()
+    err = np.abs(out - ref)[act][..., :3]
+    print("odd count: max err / scale", err.max() / scale, "moved", float((err > 1e-5 * scale).mean()))
+    assert float((err > 1e-5 * scale).mean()) <= 0.05
+    assert err.max() <= 2e-3 * scale
+
+
 def test_tensor_core_matches_cuda_core_bf16(case):
     inp, dev = case
     a = dev.denoise(S.DENOISE_TENSOR)
