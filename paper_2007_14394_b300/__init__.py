@@ -416,6 +416,7 @@ def create_batch(volumes, states=None) -> C.c_void_p:
         sts = (C.c_void_p * n)(*ptrs)
     h = C.c_void_p()
     _check(lib.sdfddgi_create_batch(vols, sts, n, C.byref(h)))
+    h._states = tuple(states) if states is not None else ()  # read at every update_batch: kept alive
     return h
 
 
