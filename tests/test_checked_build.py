@@ -4,9 +4,9 @@ libsdfddgi_checked.so is compiled with SDFDDGI_CHECKED: the update's data-depend
 accesses (SDF and material samples, the multi-bounce map lookup, per-ray arrays reached
 through task payloads, the gather's ray values) check their index, and an index outside
 its buffer sets a bit of the volume's failure word, reported by sdfddgi_volume_status as
-SDFDDGI_ERR_BOUNDS, instead of being used. compute-sanitizer is not available on the GPU
-pool, so this build is the memory-safety evidence of the update path beside small cases
-and oracle parity. The parity tests below run against it in a separate process (the
+SDFDDGI_ERR_BOUNDS, instead of being used. With no memory sanitizer run, the checked
+library is the memory-safety evidence of the update path beside small cases and oracle
+parity. The parity tests below run against it in a separate process (the
 environment variable SDFDDGI_CHECKED=1 selects the library); each asserts a clean failure
 word after its updates, and their maps must still meet the float32 parity bar.
 """
