@@ -610,6 +610,17 @@ SDFDDGI_API int sdfddgi_update_probes_noalloc(
     const float* prev_irr, const float* prev_depth, const uint8_t* prev_valid, float* cur_irr, float* cur_depth,
     uint8_t* cur_valid, sdfddgi_ray_record* records, void* stream);
 
+/* ---- Measurement: the L2 read bandwidth, the second ceiling (beside the HBM copy rate) of
+ * the gathers in the traces and the hit preparation (the measurement row of the scope,
+ * "GB/s as a fraction of HBM and of the measured L2 peak").
+ *  buf   -- device buffer of `bytes` bytes (16-byte aligned, a multiple of 16), small enough
+ *           to stay in L2 (e.g. 32 MiB of the 126 MB); its contents are only read.
+ *  reps  -- sweeps over the buffer in the timed launch, 1..1000 (one untimed sweep first).
+ *  gbs   -- receives bytes * reps / time in GB/s: every SM's threads read the buffer with
+ *           16-byte loads that bypass L1, timed with CUDA events on `stream`.
+ * Synchronises `stream`. */
+SDFDDGI_API int sdfddgi_l2_read_bandwidth(const void* buf, size_t bytes, int32_t reps, float* gbs, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -123,6 +123,7 @@ def _load() -> C.CDLL:
         "sdfddgi_batch_schedule": ([vp, i32, C.POINTER(i32), C.POINTER(C.c_float)], C.c_int),
         "sdfddgi_batch_set_form": ([vp, i32], C.c_int),
         "sdfddgi_batch_form": ([vp, C.POINTER(i32), C.POINTER(C.c_float)], C.c_int),
+        "sdfddgi_l2_read_bandwidth": ([vp, C.c_size_t, i32, C.POINTER(C.c_float), vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -532,6 +533,15 @@ def volume_status(volume) -> int:
     f = C.c_uint32()
     _check(lib.sdfddgi_volume_status(volume, C.byref(f)))
     return f.value
+
+
+def l2_read_bandwidth(buf, reps: int = 20, stream=None) -> float:
+    """GB/s read from the device tensor `buf` (kept in L2: e.g. 32 MiB) by 16-byte loads that
+    bypass L1, over `reps` sweeps after one untimed sweep. Synchronises the stream."""
+    g = C.c_float()
+    nbytes = int(buf.numel() * buf.element_size())
+    _check(lib.sdfddgi_l2_read_bandwidth(_dev_ptr(buf, "buf"), nbytes, int(reps), C.byref(g), _stream(stream)))
+    return float(g.value)
 
 
 def denoiser_status(d) -> int:

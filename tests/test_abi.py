@@ -96,6 +96,20 @@ def test_batch_argument_errors_before_device_work(S):
     S.lib.sdfddgi_destroy_batch(None)
 
 
+def test_l2_bandwidth_argument_errors_before_device_work(S):
+    """The L2 read microbenchmark rejects a missing buffer or output, a size that is not a
+    multiple of 16 bytes and a repeat count outside 1..1000 before any device call."""
+    import ctypes as C
+    g = C.c_float(1.0)
+    assert S.lib.sdfddgi_l2_read_bandwidth(None, 1 << 20, 10, C.byref(g), None) == S.ERR_INVALID_ARG
+    assert g.value == 0.0
+    fake = C.c_void_p(1 << 20)  # never dereferenced: the checks come first
+    assert S.lib.sdfddgi_l2_read_bandwidth(fake, 1000, 10, C.byref(g), None) == S.ERR_INVALID_ARG
+    assert S.lib.sdfddgi_l2_read_bandwidth(fake, 1 << 20, 0, C.byref(g), None) == S.ERR_INVALID_ARG
+    assert S.lib.sdfddgi_l2_read_bandwidth(fake, 1 << 20, 10, None, None) == S.ERR_INVALID_ARG
+    assert "l2_read_bandwidth" in S.last_error()
+
+
 def test_noalloc_argument_errors_before_device_work(S):
     """The allocation-free update checks everything it can see before touching the device:
     flags it does not run, probe counts past int32, non-finite rotations, output maps that
