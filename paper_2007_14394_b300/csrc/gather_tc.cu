@@ -427,27 +427,37 @@ __device__ __forceinline__ void gather_tc_body(const UpdateParams& P, int block)
         return;
     }
 
-    // ---- borders of active probes (an inactive probe's staged map is its old map), then
-    // contiguous stores
-    constexpr int kIrrB = 4 * kIrrN + 4, kDepB = 4 * kDepN + 4;  // border texels per map
-    for (int e = tid; e < ng * kIrrB; e += kThreads) {
-        const int g = e / kIrrB;
-        const int2 t = border_texel(e % kIrrB, kIrrN), sc = border_source(t.x, t.y, kIrrN);
-        if (s_flags[g] & SDFDDGI_PROBE_ACTIVE)
-            s_irr[g * kIrrT * kIrrT + t.x * kIrrT + t.y] = s_irr[g * kIrrT * kIrrT + sc.x * kIrrT + sc.y];
-    }
-    for (int e = tid; e < ng * kDepB; e += kThreads) {
-        const int g = e / kDepB;
-        const int2 t = border_texel(e % kDepB, kDepN), sc = border_source(t.x, t.y, kDepN);
-        if (s_flags[g] & SDFDDGI_PROBE_ACTIVE)
-            s_dep[g * kDepT * kDepT + t.x * kDepT + t.y] = s_dep[g * kDepT * kDepT + sc.x * kDepT + sc.y];
-    }
-    __syncthreads();
+    // ---- contiguous stores of the staged maps. An active probe's border texel takes the
+    // interior texel it mirrors (every border texel's source is an interior one, so no border
+    // pass over shared memory is needed); an inactive probe's staged map is its old map.
+    static_assert(kIrrT == 8 && kDepT == 16, "the index arithmetic below");
     float4* cur_i = P.cur_irr + (size_t)p0 * (kIrrT * kIrrT);
-    for (int e = tid; e < ng * kIrrT * kIrrT; e += kThreads) cur_i[e] = s_irr[e];
+    for (int e = tid; e < ng * kIrrT * kIrrT; e += kThreads) {
+        const int g = e >> 6;
+        int y = (e >> 3) & 7, x = e & 7;
+        if ((y == 0 || y == kIrrT - 1 || x == 0 || x == kIrrT - 1) && (s_flags[g] & SDFDDGI_PROBE_ACTIVE)) {
+            const int2 sc = border_source(y, x, kIrrN);
+            y = sc.x;
+            x = sc.y;
+        }
+        cur_i[e] = s_irr[(g << 6) + y * kIrrT + x];
+    }
+    // depth: two texels of one row per 16-byte store
     float4* cur_d4 = reinterpret_cast<float4*>(P.cur_depth + (size_t)p0 * (kDepT * kDepT));
-    const float4* sd4 = reinterpret_cast<const float4*>(s_dep);
-    for (int e = tid; e < ng * kDepT * kDepT / 2; e += kThreads) cur_d4[e] = sd4[e];
+    for (int e = tid; e < ng * kDepT * kDepT / 2; e += kThreads) {
+        const int g = e >> 7, y = (e >> 3) & 15, x = (e & 7) * 2;
+        const float2* m = s_dep + (g << 8);
+        float2 a, b;
+        if ((y == 0 || y == kDepT - 1 || x == 0 || x + 1 == kDepT - 1) && (s_flags[g] & SDFDDGI_PROBE_ACTIVE)) {
+            const int2 sa = border_source(y, x, kDepN), sb = border_source(y, x + 1, kDepN);
+            a = m[sa.x * kDepT + sa.y];
+            b = m[sb.x * kDepT + sb.y];
+        } else {
+            a = m[y * kDepT + x];
+            b = m[y * kDepT + x + 1];
+        }
+        cur_d4[e] = make_float4(a.x, a.y, b.x, b.y);
+    }
     if (tid < ng) P.cur_valid[p0 + tid] = (s_flags[tid] & SDFDDGI_PROBE_ACTIVE) ? 1 : P.prev_valid[p0 + tid];
 }
 
