@@ -404,6 +404,29 @@ SDFDDGI_API int sdfddgi_volume_status(sdfddgi_volume* v, uint32_t* flags);
 /* Clears every map and the history (as at creation). */
 SDFDDGI_API int sdfddgi_reset(sdfddgi_volume* v, void* stream);
 
+/* Validation: how far the current irradiance maps are from a known value, reduced on the
+ * device in FP64 (the library's only FP64 device arithmetic; no update step uses it). Eq. 3
+ * (Sec. 3.3) is self-normalised, so a scene in which every ray brings radiance L (the white
+ * furnace: a sky of L and no geometry, or surfaces of emission L and albedo 0) gives L on
+ * every interior texel, and a closed room of emission Le and albedo rho lit only through the
+ * multi-bounce term (k = 1, hysteresis h) gives s_n = S + (Le - S) r^n after update n (frame
+ * 0 first), with S = Le / (1 - rho) and r = h + (1 - h) rho, for any ray set and rotation.
+ *  states  -- NULL (every probe) or DEVICE memory, P entries as for update_probes: only the
+ *             interior texels (6 x 6) of probes with SDFDDGI_PROBE_ACTIVE are counted. A host
+ *             pointer is rejected (INVALID_ARG).
+ *  ref_rgb -- host, the expected value per channel, finite and > 0.
+ *  out     -- host, 11 doubles: [0] texels counted; [1..3] their mean per channel;
+ *             [4..6] max |E - ref| / ref per channel; [7..9] root mean square of
+ *             (E - ref) / ref per channel; [10] texels with a non-finite channel (left out of
+ *             [0..9]). Zeroed first; the sums are formed in a fixed order, so equal maps give
+ *             equal results.
+ * Enqueued on `stream` after the work already there (the update that wrote the maps);
+ * allocates its partial sums with cudaMallocAsync on that stream and synchronises it.
+ * Errors: INVALID_ARG for a NULL volume/ref_rgb/out, a reference <= 0 or not finite, host
+ * states; CUDA when a device call fails. */
+SDFDDGI_API int sdfddgi_irradiance_deviation(const sdfddgi_volume* v, const sdfddgi_probe_state* states,
+                                             const float ref_rgb[3], double out[11], void* stream);
+
 /* ---- several volumes in one launch ------------------------------------- */
 
 /* Sec. 3.5 (cascade volume) covers a large scene with several probe volumes of

@@ -124,6 +124,7 @@ def _load() -> C.CDLL:
         "sdfddgi_batch_set_form": ([vp, i32], C.c_int),
         "sdfddgi_batch_form": ([vp, C.POINTER(i32), C.POINTER(C.c_float)], C.c_int),
         "sdfddgi_l2_read_bandwidth": ([vp, C.c_size_t, i32, C.POINTER(C.c_float), vp], C.c_int),
+        "sdfddgi_irradiance_deviation": ([vp, vp, C.POINTER(C.c_float), C.POINTER(C.c_double), vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -141,7 +142,7 @@ EXPORTED = ("last_error", "create_scene", "destroy_scene", "upload_sdf", "set_li
             "create_denoiser", "destroy_denoiser", "denoiser_params", "denoise", "denoise_volume",
             "denoiser_gradients", "denoiser_adam", "denoiser_train_step", "volume_status", "denoiser_status",
             "relocate_probes", "sample_irradiance_visible", "upload_primitives", "sample_irradiance_cascade",
-            "set_slabs", "volume_slabs", "read_state_async")
+            "set_slabs", "volume_slabs", "read_state_async", "irradiance_deviation")
 MAX_SLABS = 4
 DENOISER_PARAMS = 49219
 DENOISE_TENSOR, DENOISE_SIMT_BF16, DENOISE_SIMT_FP32 = 0, 1, 2
@@ -533,6 +534,17 @@ def volume_status(volume) -> int:
     f = C.c_uint32()
     _check(lib.sdfddgi_volume_status(volume, C.byref(f)))
     return f.value
+
+
+def irradiance_deviation(volume, ref_rgb, states=None, stream=None) -> dict:
+    """FP64 deviation of the current irradiance maps' interior texels from `ref_rgb` (the
+    furnace or closed-room value): states None (every probe) or a device tensor of P*16 bytes
+    (active probes only). Returns count, mean[3], max_rel[3], rms_rel[3], nonfinite."""
+    ref = (C.c_float * 3)(*[float(x) for x in ref_rgb])
+    out = (C.c_double * 11)()
+    _check(lib.sdfddgi_irradiance_deviation(volume, _dev_ptr(states, "states"), ref, out, _stream(stream)))
+    o = list(out)
+    return {"count": int(o[0]), "mean": o[1:4], "max_rel": o[4:7], "rms_rel": o[7:10], "nonfinite": int(o[10])}
 
 
 def l2_read_bandwidth(buf, reps: int = 20, stream=None) -> float:

@@ -177,3 +177,20 @@ def test_checked_build_exports_the_same_symbols(S):
     out = subprocess.check_output(["nm", "-D", "--defined-only", lib], text=True)
     exported = {line.split()[-1] for line in out.splitlines() if " T " in line and "sdfddgi_" in line}
     assert exported == set(declared_symbols())
+
+
+def test_irradiance_deviation_argument_errors_before_device_work(S):
+    """The FP64 validation reduction rejects a missing volume, reference or output and a
+    reference that is not finite and positive before any device call, and zeroes `out`."""
+    import ctypes as C
+    ref = (C.c_float * 3)(1.0, 1.0, 1.0)
+    out = (C.c_double * 11)(*([7.0] * 11))
+    assert S.lib.sdfddgi_irradiance_deviation(None, None, ref, out, None) == S.ERR_INVALID_ARG
+    assert "irradiance_deviation" in S.last_error()
+    fake = C.c_void_p(1 << 20)  # never dereferenced: the checks come first
+    assert S.lib.sdfddgi_irradiance_deviation(fake, None, None, out, None) == S.ERR_INVALID_ARG
+    assert S.lib.sdfddgi_irradiance_deviation(fake, None, ref, None, None) == S.ERR_INVALID_ARG
+    for bad in ((0.0, 1.0, 1.0), (1.0, -2.0, 1.0), (1.0, 1.0, float("nan")), (float("inf"), 1.0, 1.0)):
+        r = (C.c_float * 3)(*bad)
+        assert S.lib.sdfddgi_irradiance_deviation(fake, None, r, out, None) == S.ERR_INVALID_ARG
+        assert "ref_rgb" in S.last_error()
