@@ -162,10 +162,10 @@ class Clocks:
         import subprocess
         try:
             self._proc = subprocess.Popen(["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.Q}",
-                                           "--format=csv,noheader,nounits", "-lms", "100"],
+                                           "--format=csv,noheader,nounits", "-lms", "10"],
                                           stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._first = self._proc.stdout.readline()  # the sampler is running before the timed region
-            self.source = "nvidia-smi, 100 ms period"
+            self.source = "nvidia-smi, 10 ms period"
         except OSError:
             self._proc = None
 
